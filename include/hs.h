@@ -1,0 +1,190 @@
+/*
+ * hs.h -- C ABI of the GB300 hierarchical sparse solver.
+ *
+ * The method is the hierarchical solver of arXiv 1611.03189 (Yang, Pouransari,
+ * Darve, "Sparse Hierarchical Solvers with Guaranteed Convergence"): the
+ * LoRaSp factorization (Sec. 3) and its GC enrichment (Sec. 6), applied as a
+ * preconditioner (Appendix A, Algorithm 2) inside conjugate gradients.
+ *
+ * Conventions for every entry point:
+ *   - Return value is an hs_status code; HS_OK is 0.  On failure a message is
+ *     available from hs_last_error() (thread-local, valid until the next call
+ *     on the same thread).  No C++ exception ever crosses this boundary.
+ *   - "device" pointers are CUDA global-memory pointers on the current device;
+ *     "host" pointers are ordinary CPU memory.  Arguments are borrowed for the
+ *     duration of the call only; the library keeps no reference to them.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued on it; calls that must read results back synchronise it.
+ *   - There is no CPU fallback: without a CUDA device every compute call
+ *     returns HS_ERR_CUDA.
+ *   - Dense vectors with several right-hand sides are column-major: column j
+ *     (right-hand side j) starts at ptr + j*ld, ld >= n.
+ */
+#ifndef HS_H
+#define HS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HS_OK = 0,
+  HS_ERR_INVALID = 1,         /* bad argument, CSR, clustering or option          */
+  HS_ERR_NOT_SPD = 2,         /* a pivot block (A_ss, S or the root) lost
+                                 positive definiteness; see hs_last_error()      */
+  HS_ERR_CAPACITY = 3,        /* a size exceeded a fixed library limit             */
+  HS_ERR_OOM = 4,             /* device or host allocation failed                  */
+  HS_ERR_NO_CONVERGENCE = 5,  /* hs_pcg hit maxit; x, iters, relres still filled   */
+  HS_ERR_TIMEOUT = 6,         /* a bounded device wait ran out                     */
+  HS_ERR_CUDA = 7             /* CUDA runtime error or no device                   */
+} hs_status;
+
+/* Compression variants (Sec. 3.2 and Sec. 6). */
+enum {
+  HS_LORASP = 0,       /* truncated SVD of A_sw only (Sec. 3.2)                  */
+  HS_GC_CONSTANT = 1,  /* GC: also preserve the constant vector (Sec. 6, Sec. 7) */
+  HS_GC_USER = 2       /* GC: preserve a caller-supplied vector phi (Sec. 6)     */
+};
+
+/* Arithmetic of the factorization (north of the factor: the PCG is always FP64). */
+enum {
+  HS_PREC_F64 = 0,     /* every factor step in FP64                              */
+  HS_PREC_F32 = 1      /* blocks, Gram, eigen-solves and factor records in FP32;
+                          rank decision taken on the FP32 singular values      */
+};
+
+/* Sparse SPD matrix A in CSR form (Sec. 2: A symmetric positive definite).
+ * rowptr[n+1], col[nnz], val[nnz]: DEVICE pointers, int32 / int32 / float64.
+ * The pattern must be structurally symmetric with a full diagonal; columns
+ * within a row may come in any order. */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int32_t *rowptr;
+  const int32_t *col;
+  const double *val;
+} hs_csr;
+
+/* Leaf clustering (Sec. 3: 2N = 2^L red nodes; "recursively bisecting").
+ * HOST pointers.  perm[p] = original index of the p-th unknown in cluster
+ * order (a permutation of 0..n-1).  Leaf i holds cluster-order unknowns
+ * leaf_ptr[i] .. leaf_ptr[i+1]-1; nleaf must be a power of two, leaves must be
+ * non-empty and in sibling order (leaves 2j and 2j+1 are merged first). */
+typedef struct {
+  const int32_t *perm;
+  const int32_t *leaf_ptr;
+  int32_t nleaf;
+} hs_clustering;
+
+/* Factorization options.
+ * eps: truncation tolerance (Sec. 3.2, "compression threshold"); a singular
+ *   value is kept when sigma_i > eps * ||A_sw||_2.  eps == 0 disables
+ *   truncation (every red node keeps a complete basis; the factorization is
+ *   then exact).  0 < eps < 1e-6 is rejected (HS_ERR_INVALID): the Gram-matrix
+ *   eigen-solve cannot resolve singular values that small.
+ * variant: HS_LORASP, HS_GC_CONSTANT or HS_GC_USER.
+ * phi: HOST pointer, n doubles in the ORIGINAL ordering, used by HS_GC_USER.
+ * factor_prec: HS_PREC_F64 or HS_PREC_F32. */
+typedef struct {
+  double eps;
+  int32_t variant;
+  int32_t factor_prec;
+  const double *phi;
+} hs_opts;
+
+/* Sizes and counters of a factorization (all host values). */
+typedef struct {
+  int64_t n;
+  int32_t levels;            /* L = log2(nleaf)                                   */
+  int32_t waves;             /* total number of elimination waves                 */
+  int32_t super_nodes;       /* super nodes eliminated (root excluded)            */
+  int32_t root_size;         /* size of the dense root block (0 if none)          */
+  int32_t max_rank;          /* largest red-node size k                           */
+  int32_t max_super;         /* largest super-node size m                         */
+  int64_t device_bytes;      /* device memory held by the handle                  */
+  int64_t factor_bytes;      /* bytes one hs_apply reads from the factor records  */
+  double factor_flops;       /* algorithmic flops of the factorization            */
+  double eig_flops;          /* flops spent in eigen-solves (reported apart)      */
+  double factor_ms;          /* device time of the last factorization             */
+} hs_info;
+
+typedef struct hs_factor_s *hs_factor;
+
+/* hs_factor_create: hierarchical factorization of A (Algorithm 1; Sec. 3.2 and
+ * Sec. 6 for the compression).  A is borrowed; the handle keeps its own copy of
+ * what the solves need.  On success *out owns device memory until
+ * hs_factor_destroy.  Errors: HS_ERR_INVALID, HS_ERR_NOT_SPD (message names the
+ * level and super node), HS_ERR_OOM, HS_ERR_CUDA. */
+int hs_factor_create(const hs_csr *A, const hs_clustering *cl, const hs_opts *opts,
+                     void *stream, hs_factor *out);
+
+/* hs_apply: z = A_H^{-1} r (Appendix A, Algorithm 2: forward substitution,
+ * restriction, parent solve, prolongation, backward substitution).
+ * r, z: DEVICE, n x nrhs column-major with leading dimension ld >= n;
+ * r and z may alias.  1 <= nrhs <= 64. */
+int hs_apply(hs_factor f, const double *r, double *z, int32_t nrhs, int64_t ld, void *stream);
+
+/* hs_pcg: solve A x = b by conjugate gradients preconditioned with A_H^{-1},
+ * x_0 = 0, stopping when ||r_k||_2 <= rtol ||b||_2 for each right-hand side
+ * (Sec. 7: relative residual 1e-10).  A is the matrix given to
+ * hs_factor_create.  b, x: DEVICE, n x nrhs column-major, leading dimension
+ * ld.  iters, relres: HOST arrays of nrhs; iters[j] = completed CG updates of
+ * column j, relres[j] = ||b_j - A x_j|| / ||b_j|| recomputed at the end.
+ * Returns HS_ERR_NO_CONVERGENCE (with x, iters, relres filled) if some column
+ * needs more than maxit iterations. */
+int hs_pcg(hs_factor f, const double *b, double *x, int32_t nrhs, int64_t ld, double rtol,
+           int32_t maxit, int32_t *iters, double *relres, void *stream);
+
+/* hs_factor_info: sizes and counters of a factorization. */
+int hs_factor_info(hs_factor f, hs_info *info);
+
+/* hs_factor_ranks: red-node sizes k of one level (level = L .. 2, the level at
+ * which the super node was eliminated).  ranks[i] = k of super node i, or -1 if
+ * super node i had no well-separated block (no red node) or did not exist.
+ * `cap` is the capacity of ranks; the number of super nodes of the level
+ * (2^(level-1)) is returned in *count.  HOST arrays. */
+int hs_factor_ranks(hs_factor f, int32_t level, int32_t *ranks, int32_t cap, int32_t *count);
+
+/* hs_factor_destroy: release the handle and its device memory (NULL is OK). */
+int hs_factor_destroy(hs_factor f);
+
+/* hs_last_error: message of the last failing call on this thread. */
+const char *hs_last_error(void);
+
+/* ---------------------------------------------------------------------------
+ * Symbolic planner (host only; no device needed).  The elimination order is
+ * "a given ordering" of super nodes (Sec. 3.2); this library uses canonical
+ * waves: within a level, repeatedly take, in ascending super-node index, a
+ * maximal set of super nodes no two of which share a block, and eliminate it.
+ * Blocks and well-separatedness follow Sec. 3.1 (adjacency in the original
+ * graph; fill-in creates blocks, never adjacency).
+ * ------------------------------------------------------------------------- */
+typedef struct hs_plan_s *hs_plan;
+
+/* hs_plan_create: plan from the HOST CSR pattern (rowptr[n+1], col[nnz]) and
+ * the clustering.  Errors: HS_ERR_INVALID, HS_ERR_OOM. */
+int hs_plan_create(int64_t n, const int32_t *rowptr, const int32_t *col,
+                   const hs_clustering *cl, hs_plan *out);
+
+/* hs_plan_level_waves: for level `level` (L .. 2), writes wave_of[i] = wave
+ * index of super node i (or -1 if the super node does not exist) for
+ * i < 2^(level-1) <= cap, and *nwaves.  HOST arrays. */
+int hs_plan_level_waves(hs_plan p, int32_t level, int32_t *wave_of, int32_t cap,
+                        int32_t *nwaves);
+
+/* hs_plan_super_lists: neighbour set N(s) and well-separated set W(s) of super
+ * node s at `level`, as node keys (super j -> j, red node made from super j ->
+ * 2^(level-1) + j), ascending.  Writes at most cap entries into each array;
+ * *nn and *nw receive the full counts. */
+int hs_plan_super_lists(hs_plan p, int32_t level, int32_t s, int32_t *nbrs, int32_t *wsep,
+                        int32_t cap, int32_t *nn, int32_t *nw);
+
+int hs_plan_destroy(hs_plan p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HS_H */
