@@ -1,0 +1,244 @@
+"""ctypes binding of the C ABI in include/hs.h (argument marshalling only).
+
+Every computation happens in libhs.so.  Loading fails loudly when the library
+has not been built (``python -m paper_1611_03189_gb300.build`` or
+``__graft_entry__.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhs.so")
+
+HS_OK = 0
+HS_ERR_INVALID = 1
+HS_ERR_NOT_SPD = 2
+HS_ERR_CAPACITY = 3
+HS_ERR_OOM = 4
+HS_ERR_NO_CONVERGENCE = 5
+HS_ERR_TIMEOUT = 6
+HS_ERR_CUDA = 7
+
+HS_LORASP = 0
+HS_GC_CONSTANT = 1
+HS_GC_USER = 2
+
+HS_PREC_F64 = 0
+HS_PREC_F32 = 1
+
+STATUS_NAMES = {
+    0: "HS_OK", 1: "HS_ERR_INVALID", 2: "HS_ERR_NOT_SPD", 3: "HS_ERR_CAPACITY", 4: "HS_ERR_OOM",
+    5: "HS_ERR_NO_CONVERGENCE", 6: "HS_ERR_TIMEOUT", 7: "HS_ERR_CUDA",
+}
+
+# every symbol include/hs.h declares
+EXPORTS = [
+    "hs_factor_create", "hs_apply", "hs_pcg", "hs_factor_info", "hs_factor_ranks",
+    "hs_factor_destroy", "hs_last_error", "hs_plan_create", "hs_plan_level_waves",
+    "hs_plan_super_lists", "hs_plan_destroy",
+]
+
+
+class HsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class HsCsr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p),
+                ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class HsClustering(C.Structure):
+    _fields_ = [("perm", C.c_void_p), ("leaf_ptr", C.c_void_p), ("nleaf", C.c_int32)]
+
+
+class HsOpts(C.Structure):
+    _fields_ = [("eps", C.c_double), ("variant", C.c_int32), ("factor_prec", C.c_int32),
+                ("phi", C.c_void_p)]
+
+
+class HsInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("levels", C.c_int32), ("waves", C.c_int32),
+                ("super_nodes", C.c_int32), ("root_size", C.c_int32), ("max_rank", C.c_int32),
+                ("max_super", C.c_int32), ("device_bytes", C.c_int64), ("factor_bytes", C.c_int64),
+                ("factor_flops", C.c_double), ("eig_flops", C.c_double), ("factor_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libhs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libhs.so not built at {LIB_PATH}; run paper_1611_03189_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        L.hs_factor_create.argtypes = [C.POINTER(HsCsr), C.POINTER(HsClustering), C.POINTER(HsOpts), vp,
+                                       C.POINTER(vp)]
+        L.hs_apply.argtypes = [vp, vp, vp, i32, i64, vp]
+        L.hs_pcg.argtypes = [vp, vp, vp, i32, i64, dbl, i32, vp, vp, vp]
+        L.hs_factor_info.argtypes = [vp, C.POINTER(HsInfo)]
+        L.hs_factor_ranks.argtypes = [vp, i32, vp, i32, C.POINTER(i32)]
+        L.hs_factor_destroy.argtypes = [vp]
+        L.hs_last_error.restype = C.c_char_p
+        L.hs_plan_create.argtypes = [i64, vp, vp, C.POINTER(HsClustering), C.POINTER(vp)]
+        L.hs_plan_level_waves.argtypes = [vp, i32, vp, i32, C.POINTER(i32)]
+        L.hs_plan_super_lists.argtypes = [vp, i32, i32, vp, vp, i32, C.POINTER(i32), C.POINTER(i32)]
+        L.hs_plan_destroy.argtypes = [vp]
+        for name in EXPORTS:
+            if name != "hs_last_error":
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def check(code: int):
+    if code != HS_OK:
+        raise HsError(code, lib().hs_last_error().decode())
+    return code
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+# ---------------------------------------------------------------------------
+# planner (host only)
+# ---------------------------------------------------------------------------
+
+class Plan:
+    """Symbolic planner of the library (host only)."""
+
+    def __init__(self, n, rowptr, col, perm, leaf_ptr):
+        self._keep = [np.ascontiguousarray(x, dtype=np.int32) for x in (rowptr, col, perm, leaf_ptr)]
+        rp, ci, pe, lp = self._keep
+        cl = HsClustering(_ptr(pe), _ptr(lp), len(lp) - 1)
+        h = C.c_void_p()
+        check(lib().hs_plan_create(int(n), _ptr(rp), _ptr(ci), C.byref(cl), C.byref(h)))
+        self._h = h
+        self.L = int(round(np.log2(len(lp) - 1)))
+
+    def waves(self, level: int) -> np.ndarray:
+        ns = 2 ** (level - 1)
+        out = np.empty(ns, dtype=np.int32)
+        nw = C.c_int32()
+        check(lib().hs_plan_level_waves(self._h, level, _ptr(out), ns, C.byref(nw)))
+        return out
+
+    def lists(self, level: int, s: int):
+        cap = 4096
+        nb = np.empty(cap, dtype=np.int32)
+        ws = np.empty(cap, dtype=np.int32)
+        nn, nw = C.c_int32(), C.c_int32()
+        check(lib().hs_plan_super_lists(self._h, level, s, _ptr(nb), _ptr(ws), cap, C.byref(nn),
+                                        C.byref(nw)))
+        return nb[: nn.value].tolist(), ws[: nw.value].tolist()
+
+    def close(self):
+        if self._h:
+            lib().hs_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# factorization handle (device)
+# ---------------------------------------------------------------------------
+
+def _stream_ptr(stream):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Factor:
+    """hs_factor_create / hs_apply / hs_pcg on torch CUDA tensors.
+
+    rowptr, col: int32 CUDA tensors; val: float64 CUDA tensor (original order).
+    perm, leaf_ptr: host int32 arrays (clustering).  phi: host float64 (GC user).
+    """
+
+    def __init__(self, rowptr, col, val, perm, leaf_ptr, eps, variant=HS_GC_CONSTANT,
+                 prec=HS_PREC_F64, phi=None, stream=None):
+        import torch
+
+        assert rowptr.is_cuda and col.is_cuda and val.is_cuda
+        assert rowptr.dtype == torch.int32 and col.dtype == torch.int32 and val.dtype == torch.float64
+        self.n = int(rowptr.numel() - 1)
+        self._perm = np.ascontiguousarray(perm, dtype=np.int32)
+        self._lp = np.ascontiguousarray(leaf_ptr, dtype=np.int32)
+        self._phi = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+        A = HsCsr(self.n, int(col.numel()), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
+        cl = HsClustering(_ptr(self._perm), _ptr(self._lp), len(self._lp) - 1)
+        o = HsOpts(float(eps), int(variant), int(prec), None if self._phi is None else _ptr(self._phi))
+        h = C.c_void_p()
+        self._h = None
+        check(lib().hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), _stream_ptr(stream), C.byref(h)))
+        self._h = h
+
+    def apply(self, r, z=None, stream=None):
+        """z = A_H^-1 r; r is (n,) or (nrhs, n) float64 CUDA (each row one rhs)."""
+        import torch
+
+        r = r.contiguous()
+        nrhs = 1 if r.dim() == 1 else r.shape[0]
+        if z is None:
+            z = torch.empty_like(r)
+        check(lib().hs_apply(self._h, r.data_ptr(), z.data_ptr(), nrhs, self.n, _stream_ptr(stream)))
+        return z
+
+    def pcg(self, b, rtol=1e-10, maxit=500, x=None, stream=None, raise_on_fail=True):
+        """x, iters, relres, status for A x = b; b is (n,) or (nrhs, n) float64 CUDA."""
+        import torch
+
+        b = b.contiguous()
+        nrhs = 1 if b.dim() == 1 else b.shape[0]
+        if x is None:
+            x = torch.empty_like(b)
+        it = np.zeros(nrhs, dtype=np.int32)
+        rr = np.zeros(nrhs, dtype=np.float64)
+        code = lib().hs_pcg(self._h, b.data_ptr(), x.data_ptr(), nrhs, self.n, float(rtol), int(maxit),
+                            _ptr(it), _ptr(rr), _stream_ptr(stream))
+        if code not in (HS_OK, HS_ERR_NO_CONVERGENCE) or (raise_on_fail and code != HS_OK):
+            check(code)
+        return x, it, rr, code
+
+    def info(self) -> dict:
+        inf = HsInfo()
+        check(lib().hs_factor_info(self._h, C.byref(inf)))
+        return inf.as_dict()
+
+    def ranks(self, level: int) -> np.ndarray:
+        ns = 2 ** (level - 1)
+        out = np.empty(ns, dtype=np.int32)
+        cnt = C.c_int32()
+        check(lib().hs_factor_ranks(self._h, level, _ptr(out), ns, C.byref(cnt)))
+        return out
+
+    def close(self):
+        if self._h:
+            lib().hs_factor_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,253 @@
+// C ABI of include/hs.h.  Every entry point catches hs::Error (and any other
+// C++ exception) and turns it into a status code plus a thread-local message.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "handle.h"
+
+namespace hs {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+[[noreturn]] void fail(int code, const std::string &msg) { throw Error{code, msg}; }
+
+template <typename F>
+int guarded(F &&f) {
+  try {
+    g_err.clear();
+    return f();
+  } catch (const Error &e) {
+    g_err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    g_err = "host allocation failed";
+    return HS_ERR_OOM;
+  } catch (const std::exception &e) {
+    g_err = e.what();
+    return HS_ERR_INVALID;
+  } catch (...) {
+    g_err = "unknown error";
+    return HS_ERR_INVALID;
+  }
+}
+
+namespace {
+
+void require_device() {
+  int n = 0;
+  const cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0)
+    fail(HS_ERR_CUDA, std::string("no CUDA device: ") + (e == cudaSuccess ? "count is 0" : cudaGetErrorString(e)));
+}
+
+template <typename X>
+X *upload_vec(const std::vector<X> &v, cudaStream_t st) {
+  X *d = nullptr;
+  HS_CUDA(cudaMalloc(&d, sizeof(X) * std::max<size_t>(v.size(), 1)));
+  if (!v.empty()) HS_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice, st));
+  return d;
+}
+
+}  // namespace
+
+}  // namespace hs
+
+using hs::fail;
+
+struct hs_factor_s {
+  hs::FactorHandle h;
+};
+struct hs_plan_s {
+  hs::Plan p;
+};
+
+extern "C" {
+
+const char *hs_last_error(void) { return hs::g_err.c_str(); }
+
+int hs_factor_create(const hs_csr *A, const hs_clustering *cl, const hs_opts *o, void *stream,
+                     hs_factor *out) {
+  return hs::guarded([&]() -> int {
+    if (!A || !cl || !o || !out) fail(HS_ERR_INVALID, "null argument");
+    *out = nullptr;
+    if (!(o->eps >= 0.0) || !std::isfinite(o->eps)) fail(HS_ERR_INVALID, "eps must be finite and >= 0");
+    if (o->eps > 0.0 && o->eps < 1e-6) fail(HS_ERR_INVALID, "0 < eps < 1e-6 is not supported");
+    if (o->variant < HS_LORASP || o->variant > HS_GC_USER) fail(HS_ERR_INVALID, "unknown variant");
+    if (o->variant == HS_GC_USER && !o->phi) fail(HS_ERR_INVALID, "HS_GC_USER needs phi");
+    if (o->factor_prec != HS_PREC_F64 && o->factor_prec != HS_PREC_F32) fail(HS_ERR_INVALID, "unknown factor_prec");
+    if (A->n <= 0 || A->nnz <= 0 || !A->rowptr || !A->col || !A->val) fail(HS_ERR_INVALID, "bad CSR");
+    if (!cl->perm || !cl->leaf_ptr) fail(HS_ERR_INVALID, "bad clustering");
+    hs::require_device();
+    cudaStream_t st = (cudaStream_t)stream;
+    std::unique_ptr<hs_factor_s> f(new hs_factor_s());
+    hs::FactorHandle &h = f->h;
+    HS_CUDA(cudaGetDevice(&h.device));
+    h.stream = st;
+    h.prec = o->factor_prec;
+    h.variant = o->variant;
+    h.eps = o->eps;
+    // pattern to the host for the planner
+    std::vector<int32_t> rp(A->n + 1), ci(A->nnz);
+    HS_CUDA(cudaMemcpyAsync(rp.data(), A->rowptr, sizeof(int32_t) * (A->n + 1), cudaMemcpyDeviceToHost, st));
+    HS_CUDA(cudaMemcpyAsync(ci.data(), A->col, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost, st));
+    HS_CUDA(cudaStreamSynchronize(st));
+    if (rp[A->n] != A->nnz) fail(HS_ERR_INVALID, "rowptr[n] != nnz");
+    hs::build_plan(A->n, rp.data(), ci.data(), cl->perm, cl->leaf_ptr, cl->nleaf, h.plan);
+    // permuted CSR on the device; values gathered there
+    h.d_rowptr = hs::upload_vec(h.plan.prow, st);
+    h.d_col = hs::upload_vec(h.plan.pcol, st);
+    h.d_perm = hs::upload_vec(h.plan.perm, st);
+    int32_t *d_src = hs::upload_vec(h.plan.psrc, st);
+    HS_CUDA(cudaMalloc(&h.d_val, sizeof(double) * A->nnz));
+    hs::launch_gather_values(A->val, d_src, A->nnz, h.d_val, st);
+    cudaEvent_t e0, e1;
+    HS_CUDA(cudaEventCreate(&e0));
+    HS_CUDA(cudaEventCreate(&e1));
+    HS_CUDA(cudaEventRecord(e0, st));
+    try {
+      hs::factorize(h, *A, *o, o->phi);
+    } catch (...) {
+      cudaStreamSynchronize(st);
+      cudaFree(d_src);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    HS_CUDA(cudaEventRecord(e1, st));
+    // apply schedule to the device
+    h.d_nodes = hs::upload_vec(h.nodes, st);
+    h.d_nbrs = hs::upload_vec(h.nbrs, st);
+    h.d_targets = hs::upload_vec(h.targets, st);
+    h.d_contribs = hs::upload_vec(h.contribs, st);
+    HS_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    HS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d_src);
+    h.scratch.reset();  // the solve does not need the factorization scratch
+    hs_info &in = h.info;
+    in.n = A->n;
+    in.levels = h.plan.L;
+    in.waves = h.plan.total_waves;
+    in.factor_ms = ms;
+    const double tb = h.prec == HS_PREC_F64 ? 8.0 : 4.0;
+    double fb = 0.0;
+    for (const auto &nd : h.nodes) fb += 2.0 * ((double)nd.m * nd.m + (double)nd.k * nd.m + (double)nd.m * nd.dN);
+    fb += (double)h.root_m * h.root_m;
+    in.factor_bytes = (int64_t)(fb * tb);
+    in.device_bytes = (int64_t)h.pers->reserved();
+    *out = f.release();
+    return HS_OK;
+  });
+}
+
+int hs_apply(hs_factor f, const double *r, double *z, int32_t nrhs, int64_t ld, void *stream) {
+  return hs::guarded([&]() -> int {
+    if (!f || !r || !z) fail(HS_ERR_INVALID, "null argument");
+    if (nrhs < 1 || nrhs > 64) fail(HS_ERR_INVALID, "nrhs must be in [1, 64]");
+    if (ld < f->h.plan.n) fail(HS_ERR_INVALID, "ld < n");
+    hs::require_device();
+    cudaStream_t st = (cudaStream_t)stream;
+    // r and z may alias: r is gathered into the workspace before z is written
+    hs::apply_solve(f->h, r, z, nrhs, ld, st);
+    return HS_OK;
+  });
+}
+
+int hs_pcg(hs_factor f, const double *b, double *x, int32_t nrhs, int64_t ld, double rtol, int32_t maxit,
+           int32_t *iters, double *relres, void *stream) {
+  return hs::guarded([&]() -> int {
+    if (!f || !b || !x || !iters || !relres) fail(HS_ERR_INVALID, "null argument");
+    if (nrhs < 1 || nrhs > 32) fail(HS_ERR_INVALID, "nrhs must be in [1, 32]");
+    if (ld < f->h.plan.n) fail(HS_ERR_INVALID, "ld < n");
+    if (!(rtol > 0.0) || maxit < 1) fail(HS_ERR_INVALID, "rtol must be > 0 and maxit >= 1");
+    hs::require_device();
+    return hs::pcg_solve(f->h, b, x, nrhs, ld, rtol, maxit, iters, relres, (cudaStream_t)stream);
+  });
+}
+
+int hs_factor_info(hs_factor f, hs_info *info) {
+  return hs::guarded([&]() -> int {
+    if (!f || !info) fail(HS_ERR_INVALID, "null argument");
+    *info = f->h.info;
+    return HS_OK;
+  });
+}
+
+int hs_factor_ranks(hs_factor f, int32_t level, int32_t *ranks, int32_t cap, int32_t *count) {
+  return hs::guarded([&]() -> int {
+    if (!f || !count) fail(HS_ERR_INVALID, "null argument");
+    const hs::Plan &p = f->h.plan;
+    if (level < 2 || level > p.L) fail(HS_ERR_INVALID, "level out of range");
+    const auto &rk = f->h.ranks[p.L - level];
+    *count = (int32_t)rk.size();
+    for (int32_t i = 0; i < (int32_t)rk.size() && i < cap && ranks; ++i) ranks[i] = rk[i];
+    return HS_OK;
+  });
+}
+
+int hs_factor_destroy(hs_factor f) {
+  return hs::guarded([&]() -> int {
+    delete f;
+    return HS_OK;
+  });
+}
+
+int hs_plan_create(int64_t n, const int32_t *rowptr, const int32_t *col, const hs_clustering *cl,
+                   hs_plan *out) {
+  return hs::guarded([&]() -> int {
+    if (!rowptr || !col || !cl || !cl->perm || !cl->leaf_ptr || !out) fail(HS_ERR_INVALID, "null argument");
+    *out = nullptr;
+    std::unique_ptr<hs_plan_s> p(new hs_plan_s());
+    hs::build_plan(n, rowptr, col, cl->perm, cl->leaf_ptr, cl->nleaf, p->p);
+    *out = p.release();
+    return HS_OK;
+  });
+}
+
+int hs_plan_level_waves(hs_plan p, int32_t level, int32_t *wave_of, int32_t cap, int32_t *nwaves) {
+  return hs::guarded([&]() -> int {
+    if (!p || !nwaves) fail(HS_ERR_INVALID, "null argument");
+    const hs::Plan &P = p->p;
+    if (level < 2 || level > P.L) fail(HS_ERR_INVALID, "level out of range");
+    const hs::PlanLevel &lv = P.levels[P.L - level];
+    *nwaves = (int32_t)lv.waves.size();
+    for (int i = 0; i < lv.nsup && i < cap && wave_of; ++i) wave_of[i] = lv.sup[i].wave;
+    return HS_OK;
+  });
+}
+
+int hs_plan_super_lists(hs_plan p, int32_t level, int32_t s, int32_t *nbrs, int32_t *wsep, int32_t cap,
+                        int32_t *nn, int32_t *nw) {
+  return hs::guarded([&]() -> int {
+    if (!p || !nn || !nw) fail(HS_ERR_INVALID, "null argument");
+    const hs::Plan &P = p->p;
+    if (level < 2 || level > P.L) fail(HS_ERR_INVALID, "level out of range");
+    const hs::PlanLevel &lv = P.levels[P.L - level];
+    if (s < 0 || s >= lv.nsup) fail(HS_ERR_INVALID, "super node out of range");
+    const hs::PlanSuper &ps = lv.sup[s];
+    *nn = (int32_t)ps.N.size();
+    *nw = (int32_t)ps.W.size();
+    for (int i = 0; i < (int)ps.N.size() && i < cap && nbrs; ++i) nbrs[i] = ps.N[i];
+    for (int i = 0; i < (int)ps.W.size() && i < cap && wsep; ++i) wsep[i] = ps.W[i];
+    return HS_OK;
+  });
+}
+
+int hs_plan_destroy(hs_plan p) {
+  return hs::guarded([&]() -> int {
+    delete p;
+    return HS_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// The factorization handle: device memory, the records the solve reads, and
+// the host-side description of the apply schedule.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "hs_internal.h"
+#include "plan.h"
+
+namespace hs {
+
+// Chunked bump allocator over cudaMalloc'ed chunks (256-byte aligned).
+class DevArena {
+ public:
+  explicit DevArena(size_t min_chunk) : min_chunk_(min_chunk) {}
+  ~DevArena();
+  void *alloc(size_t bytes);
+  void reset();  // keeps the chunks for reuse
+  size_t used() const { return used_; }
+  size_t reserved() const { return reserved_; }
+
+ private:
+  std::vector<std::pair<char *, size_t>> chunks_;
+  size_t min_chunk_;
+  int cur_ = -1;
+  size_t off_ = 0;
+  size_t used_ = 0, reserved_ = 0;
+};
+
+// Apply schedule, one entry per super node of a wave (Algorithm 2).
+// Vectors live in one workspace: level L (n unknowns in cluster order), then
+// level L-1 (the red nodes made at level L), ..., then the root.  Every value
+// is stored as [unknown][rhs] (nrhs consecutive doubles per unknown).
+struct ApplyNode {
+  const void *M;     // M_ss, m x m
+  const void *P;     // P_ss, k x m
+  const void *AsN;   // [A_{s n}]_n, m x dN (ld dN)
+  int64_t xs;        // unknown offset of s in the workspace
+  int64_t xr;        // unknown offset of the red node r (or -1)
+  int64_t toff;      // unknown offset of t_s in the per-wave scratch
+  int m, k, dN;
+  int nb_first, nb_count;
+};
+struct ApplyNbr {
+  int64_t x;         // unknown offset of neighbour n
+  int size;
+  int col;           // column offset of A_{s n} inside AsN
+};
+struct ApplyTarget {  // forward substitution, gathered by neighbour
+  int64_t x;
+  int size;
+  int first, count;
+};
+struct ApplyContrib {
+  const void *A;     // AsN + col, element (i in s, q in n) at A[i*ld + q]
+  int ld;
+  int m;
+  int64_t toff;
+};
+
+struct WaveApply {
+  int node_first, node_count;
+  int tgt_first, tgt_count;
+  int max_m;
+  int64_t tsize;     // unknowns of t scratch used
+};
+struct LevelApply {
+  int level;
+  int wave_first, wave_count;
+};
+
+struct FactorHandle {
+  Plan plan;
+  int prec = HS_PREC_F64;
+  int variant = HS_GC_CONSTANT;
+  double eps = 0.0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+
+  // permuted CSR (cluster order), FP64, for the SpMV of PCG
+  int32_t *d_rowptr = nullptr, *d_col = nullptr;
+  double *d_val = nullptr;
+  int32_t *d_perm = nullptr;
+
+  std::unique_ptr<DevArena> pers;      // factor records and live blocks
+  std::unique_ptr<DevArena> scratch;   // per-wave scratch of the factorization
+
+  // apply schedule (host copies and device copies)
+  std::vector<ApplyNode> nodes;
+  std::vector<ApplyNbr> nbrs;
+  std::vector<ApplyTarget> targets;
+  std::vector<ApplyContrib> contribs;
+  std::vector<WaveApply> waves;        // in elimination order, levels L..2
+  std::vector<LevelApply> levels;      // levels L..2
+  ApplyNode *d_nodes = nullptr;
+  ApplyNbr *d_nbrs = nullptr;
+  ApplyTarget *d_targets = nullptr;
+  ApplyContrib *d_contribs = nullptr;
+  int64_t ws_size = 0;                 // unknowns in the apply workspace
+  int64_t tmax = 0;                    // max unknowns of t scratch per wave
+  int64_t root_off = 0;
+  int root_m = 0;
+  const void *root_inv = nullptr;      // A_root^-1 (m x m)
+
+  // solve buffers (grown on demand)
+  int nrhs_cap = 0;
+  double *d_ws = nullptr, *d_t = nullptr;
+  double *d_pcg = nullptr;             // x, r, p, p2, q (5 n nrhs)
+  double *d_part = nullptr;            // per-block partial sums
+  double *d_scal = nullptr;            // per-rhs scalars
+  int *d_iflags = nullptr;             // per-rhs ints + block counter
+  int part_blocks = 0;
+
+  // per-level ranks: ranks[li][s] = k or -1
+  std::vector<std::vector<int>> ranks;
+  hs_info info{};
+
+  ~FactorHandle();
+};
+
+// factor.cu
+void factorize(FactorHandle &h, const hs_csr &A, const hs_opts &o, const double *phi_host);
+
+// solve.cu
+void apply_solve(FactorHandle &h, const double *r, double *z, int nrhs, int64_t ld,
+                 cudaStream_t st);
+int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld, double rtol,
+              int maxit, int *iters, double *relres, cudaStream_t st);
+
+}  // namespace hs

@@ -1,0 +1,124 @@
+// Internal declarations of the GB300 hierarchical solver library.
+//
+// Everything here sits below the C ABI of include/hs.h.  Dense blocks are
+// row-major with an explicit leading dimension.  Batched kernels take arrays of
+// task descriptors built on the host, one descriptor per (super node, operation).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hs.h"
+
+namespace hs {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+struct Error {
+  int code;
+  std::string msg;
+};
+
+void set_error(const std::string &msg);
+[[noreturn]] void fail(int code, const std::string &msg);
+
+#define HS_CUDA(call)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      ::hs::fail(e_ == cudaErrorMemoryAllocation ? HS_ERR_OOM : HS_ERR_CUDA,            \
+                 std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// task descriptors (shared by host and device)
+// ---------------------------------------------------------------------------
+
+// C = alpha * op(A) * op(B) + beta * C, all row-major.
+// op(A) is M x K: A[i*lda + k] (ta = 0) or A[k*lda + i] (ta = 1).
+// op(B) is K x N: B[k*ldb + j] (tb = 0) or B[j*ldb + k] (tb = 1).
+template <typename T>
+struct GemmTask {
+  const T *A;
+  const T *B;
+  T *C;
+  int M, N, K;
+  int lda, ldb, ldc;
+  int ta, tb;
+  T alpha, beta;
+};
+
+// dst = beta * dst + alpha * sum_s op(src_s), rows x cols; sources listed in
+// `srcs[first .. first + nsrc)` and summed in that order (deterministic).
+template <typename T>
+struct SumSrc {
+  const T *ptr;
+  int ld;
+  int trans;  // 1: element (i, j) is ptr[j*ld + i]
+};
+
+template <typename T>
+struct SumTask {
+  T *dst;
+  int ld;
+  int rows, cols;
+  int first, nsrc;
+  T alpha, beta;
+};
+
+// Cholesky factor and its inverse: A = L L^T, writes Linv = L^-1 (lower, zero
+// above the diagonal).  status[idx] = 0 ok, j+1 if the j-th pivot failed.
+template <typename T>
+struct CholTask {
+  const T *A;
+  T *Linv;
+  int m;
+  int lda, ldl;
+  int status_idx;
+};
+
+// Truncation of one super node (Sec. 3.2 compression, Sec. 6 GC basis).
+// G = A_sw A_sw^T (m x m, ld m), a = A_sw phi_w (m), phi = phi_s (m).
+// Outputs U (m x k, row-major, ld m) and k.  Work: 2 m^2 T.
+template <typename T>
+struct TruncTask {
+  const T *G;
+  const T *a;
+  const T *phi;
+  T *U;
+  T *work;
+  int m;
+  int k_idx;  // index into the rank array
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (kernels_dense.cu)
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_gemm(const GemmTask<T> *d_tasks, const int *d_tile_start, int ntasks, int total_tiles,
+                 cudaStream_t st);
+template <typename T>
+void launch_sum(const SumTask<T> *d_tasks, const SumSrc<T> *d_srcs, const int *d_tile_start,
+                int ntasks, int total_tiles, cudaStream_t st);
+template <typename T>
+void launch_chol_inv(const CholTask<T> *d_tasks, int ntasks, int *d_status, int max_m,
+                     cudaStream_t st);
+template <typename T>
+void launch_trunc(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant,
+                  int max_m, cudaStream_t st);
+template <typename T>
+void launch_scatter_values(const double *val, const int64_t *dest, int64_t nnz, T *pool,
+                           cudaStream_t st);
+void launch_gather_values(const double *val, const int32_t *src, int64_t nnz, double *out,
+                          cudaStream_t st);
+
+// tile bookkeeping for the batched GEMM / sum kernels
+constexpr int GEMM_TM = 64;
+constexpr int GEMM_TN = 64;
+constexpr int SUM_TILE = 32;
+
+}  // namespace hs

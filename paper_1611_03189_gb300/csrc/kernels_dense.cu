@@ -1,0 +1,714 @@
+// Batched variable-size dense kernels of the factorization.
+//
+//   k_gemm       C = alpha op(A) op(B) + beta C over a list of tasks (tiles of
+//                64 x 64, 16 x 16 threads, 4 x 4 outputs per thread).
+//   k_sum        dst = beta dst + alpha sum_s op(src_s), sources summed in list
+//                order: block gathers, merges and the deterministic Schur
+//                scatter of Sec. 3.2 (several super nodes of one wave updating
+//                the same neighbour block).
+//   k_chol_inv   A = L L^T and L^-1, one CTA per matrix (pivot blocks A_ss and
+//                the small Gram matrices of the CholQR of L^-1 U).
+//   k_trunc      truncation of the well-separated block (Sec. 3.2 eq.
+//                local_compression, Sec. 6 GC basis), one CTA per super node:
+//                cyclic Jacobi eigen-solves of the Gram matrix A_sw A_sw^T.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cfloat>
+
+#include "hs_internal.h"
+
+namespace hs {
+
+namespace {
+
+template <typename T>
+struct Lim;
+template <>
+struct Lim<double> {
+  static __device__ __forceinline__ double eps() { return 2.220446049250313e-16; }
+  static __device__ __forceinline__ double tiny() { return 1e-290; }
+};
+template <>
+struct Lim<float> {
+  static __device__ __forceinline__ float eps() { return 1.1920929e-07f; }
+  static __device__ __forceinline__ float tiny() { return 1e-35f; }
+};
+
+__device__ __forceinline__ int find_task(const int *tile_start, int ntasks, int b) {
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (tile_start[mid] <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// batched GEMM
+// ---------------------------------------------------------------------------
+constexpr int GK = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(const GemmTask<T> *__restrict__ tasks,
+                                              const int *__restrict__ tile_start, int ntasks) {
+  __shared__ T As[GK][GEMM_TM + 1];
+  __shared__ T Bs[GK][GEMM_TN + 1];
+  const int ti = find_task(tile_start, ntasks, blockIdx.x);
+  const GemmTask<T> t = tasks[ti];
+  const int local = blockIdx.x - tile_start[ti];
+  const int tiles_n = (t.N + GEMM_TN - 1) / GEMM_TN;
+  const int row0 = (local / tiles_n) * GEMM_TM;
+  const int col0 = (local % tiles_n) * GEMM_TN;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+
+  for (int k0 = 0; k0 < t.K; k0 += GK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      int i, k;
+      if (t.ta == 0) {
+        i = e / GK;
+        k = e % GK;
+      } else {
+        k = e / GEMM_TM;
+        i = e % GEMM_TM;
+      }
+      const int gi = row0 + i, gk = k0 + k;
+      T v = T(0);
+      if (gi < t.M && gk < t.K)
+        v = (t.ta == 0) ? t.A[(int64_t)gi * t.lda + gk] : t.A[(int64_t)gk * t.lda + gi];
+      As[k][i] = v;
+      int j;
+      if (t.tb == 0) {
+        k = e / GEMM_TN;
+        j = e % GEMM_TN;
+      } else {
+        j = e / GK;
+        k = e % GK;
+      }
+      const int gj = col0 + j;
+      const int gk2 = k0 + k;
+      T w = T(0);
+      if (gj < t.N && gk2 < t.K)
+        w = (t.tb == 0) ? t.B[(int64_t)gk2 * t.ldb + gj] : t.B[(int64_t)gj * t.ldb + gk2];
+      Bs[k][j] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = row0 + ty + 16 * i;
+    if (r >= t.M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = col0 + tx + 16 * j;
+      if (c >= t.N) continue;
+      T *p = t.C + (int64_t)r * t.ldc + c;
+      T v = t.alpha * acc[i][j];
+      if (t.beta != T(0)) v = fma(t.beta, *p, v);
+      *p = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// batched deterministic accumulate / copy
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_sum(const SumTask<T> *__restrict__ tasks,
+                                             const SumSrc<T> *__restrict__ srcs,
+                                             const int *__restrict__ tile_start, int ntasks) {
+  __shared__ T sm[SUM_TILE][SUM_TILE + 1];
+  const int ti = find_task(tile_start, ntasks, blockIdx.x);
+  const SumTask<T> t = tasks[ti];
+  const int local = blockIdx.x - tile_start[ti];
+  const int tiles_c = (t.cols + SUM_TILE - 1) / SUM_TILE;
+  const int i0 = (local / tiles_c) * SUM_TILE;
+  const int j0 = (local % tiles_c) * SUM_TILE;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  for (int s = 0; s < t.nsrc; ++s) {
+    const SumSrc<T> src = srcs[t.first + s];
+    if (!src.trans) {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = i0 + ty + 8 * r, j = j0 + tx;
+        if (i < t.rows && j < t.cols) acc[r] += src.ptr[(int64_t)i * src.ld + j];
+      }
+    } else {
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int jj = ty + 8 * r, ii = tx;
+        T v = T(0);
+        if (i0 + ii < t.rows && j0 + jj < t.cols) v = src.ptr[(int64_t)(j0 + jj) * src.ld + i0 + ii];
+        sm[jj][ii] = v;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 4; ++r) acc[r] += sm[tx][ty + 8 * r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty + 8 * r, j = j0 + tx;
+    if (i < t.rows && j < t.cols) {
+      T *p = t.dst + (int64_t)i * t.ld + j;
+      T v = t.alpha * acc[r];
+      if (t.beta != T(0)) v = fma(t.beta, *p, v);
+      *p = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky and inverse of the factor, one CTA per matrix
+// ---------------------------------------------------------------------------
+constexpr int CHOL_THREADS = 256;
+
+// W (ld m) holds A on entry; on exit the lower triangle holds L^-1 and the
+// strict upper triangle is zero.  Returns 0 or (failing pivot + 1).
+template <typename T>
+__device__ int chol_inv_inplace(T *W, int m, T *tmp, int *flag) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // right-looking Cholesky on the lower triangle
+  for (int j = 0; j < m; ++j) {
+    if (tid == 0) {
+      const T d = W[j * m + j];
+      if (!(d > T(0)) || !isfinite(d)) {
+        *flag = j + 1;
+      } else {
+        W[j * m + j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (*flag) return *flag;
+    const T djj = W[j * m + j];
+    for (int i = j + 1 + tid; i < m; i += nt) W[i * m + j] /= djj;
+    __syncthreads();
+    const int r = m - j - 1;  // trailing size
+    const int64_t cnt = (int64_t)r * (r + 1) / 2;
+    for (int64_t e = tid; e < cnt; e += nt) {
+      // e -> (ii, cc) with 0 <= cc <= ii < r (row-major lower triangle)
+      int ii = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
+      while ((int64_t)ii * (ii + 1) / 2 > e) --ii;
+      while ((int64_t)(ii + 1) * (ii + 2) / 2 <= e) ++ii;
+      const int cc = (int)(e - (int64_t)ii * (ii + 1) / 2);
+      const int i = j + 1 + ii, c = j + 1 + cc;
+      W[i * m + c] -= W[i * m + j] * W[c * m + j];
+    }
+    __syncthreads();
+  }
+  // in-place inverse of the lower-triangular factor (column j from the last
+  // one down: x = L[j+1:, j]; x <- -Linv[j+1:, j+1:] x / L[j][j])
+  for (int j = m - 1; j >= 0; --j) {
+    const T inv = T(1) / W[j * m + j];
+    for (int i = j + 1 + tid; i < m; i += nt) {
+      T s = T(0);
+      for (int p = j + 1; p <= i; ++p) s = fma(W[i * m + p], W[p * m + j], s);
+      tmp[i] = -s * inv;
+    }
+    __syncthreads();
+    for (int i = j + 1 + tid; i < m; i += nt) W[i * m + j] = tmp[i];
+    if (tid == 0) W[j * m + j] = inv;
+    __syncthreads();
+  }
+  for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+    const int i = (int)(e / m), c = (int)(e % m);
+    if (c > i) W[e] = T(0);
+  }
+  __syncthreads();
+  return 0;
+}
+
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(CHOL_THREADS) k_chol_inv(const CholTask<T> *__restrict__ tasks,
+                                                           int *__restrict__ status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int flag;
+  const CholTask<T> t = tasks[blockIdx.x];
+  const int m = t.m;
+  if (threadIdx.x == 0) flag = 0;
+  if (m == 0) {
+    if (threadIdx.x == 0) status[t.status_idx] = 0;
+    return;
+  }
+  T *W;
+  T *tmp;
+  if (SMEM) {
+    W = reinterpret_cast<T *>(smem_raw);
+    tmp = W + (size_t)m * m;
+  } else {
+    W = t.Linv;  // requires ldl == m
+    tmp = reinterpret_cast<T *>(smem_raw);
+  }
+  for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+    const int i = (int)(e / m), c = (int)(e % m);
+    W[e] = (c <= i) ? t.A[(int64_t)i * t.lda + c] : T(0);
+  }
+  __syncthreads();
+  const int st = chol_inv_inplace(W, m, tmp, &flag);
+  if (SMEM && st == 0) {
+    for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+      const int i = (int)(e / m), c = (int)(e % m);
+      t.Linv[(int64_t)i * t.ldl + c] = W[e];
+    }
+  }
+  if (threadIdx.x == 0) status[t.status_idx] = st;
+}
+
+// ---------------------------------------------------------------------------
+// truncation: cyclic Jacobi on the Gram matrix (round-robin pair ordering)
+// ---------------------------------------------------------------------------
+constexpr int TRUNC_THREADS = 256;
+
+template <typename T>
+struct JacobiShared {
+  int *pp, *qq;
+  T *cs, *sn;
+  int *flag;
+};
+
+template <typename T>
+__device__ double block_sum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    red[32] = s;
+  }
+  __syncthreads();
+  s = red[32];
+  __syncthreads();
+  return s;
+}
+
+// Eigen-decomposition A = V diag(A') V^T of the symmetric m x m matrix A (ld
+// m), in place: on exit diag(A) holds the eigenvalues.  V is filled when
+// want_v.  Returns the number of sweeps.
+template <typename T>
+__device__ int jacobi_eig(T *A, T *V, int m, bool want_v, JacobiShared<T> sh, int max_sweeps) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (want_v)
+    for (int64_t e = tid; e < (int64_t)m * m; e += nt) V[e] = (e / m == e % m) ? T(1) : T(0);
+  if (m < 2) {
+    __syncthreads();
+    return 0;
+  }
+  // scale for the absolute floor of the rotation test
+  T scale = T(0);
+  for (int i = 0; i < m; ++i) scale = fmax(scale, fabs(A[i * m + i]));
+  const T floor_abs = Lim<T>::eps() * Lim<T>::eps() * scale + Lim<T>::tiny();
+  const int mp = m + (m & 1);
+  const int np = mp / 2;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) *sh.flag = 0;
+    __syncthreads();
+    for (int r = 0; r < mp - 1; ++r) {
+      for (int i = tid; i < np; i += nt) {
+        int a, b;
+        if (i == 0) {
+          a = r;
+          b = mp - 1;
+        } else {
+          a = (r + i) % (mp - 1);
+          b = (r - i + (mp - 1)) % (mp - 1);
+        }
+        if (a > b) {
+          const int x = a;
+          a = b;
+          b = x;
+        }
+        T c = T(1), s = T(0);
+        if (b < m) {
+          const T app = A[a * m + a], aqq = A[b * m + b], apq = A[a * m + b];
+          if (fabs(apq) > Lim<T>::eps() * sqrt(fabs(app * aqq)) && fabs(apq) > floor_abs) {
+            const T th = (aqq - app) / (T(2) * apq);
+            const T ath = fabs(th);
+            const T root = (ath > T(1)) ? ath * sqrt(T(1) + (T(1) / ath) * (T(1) / ath))
+                                        : sqrt(T(1) + th * th);
+            T tt = T(1) / (ath + root);
+            if (th < T(0)) tt = -tt;
+            c = T(1) / sqrt(T(1) + tt * tt);
+            s = tt * c;
+            *sh.flag = 1;
+          }
+        }
+        sh.pp[i] = a;
+        sh.qq[i] = b;
+        sh.cs[i] = c;
+        sh.sn[i] = s;
+      }
+      __syncthreads();
+      // A <- J^T A J, 2 x 2 blocks of (pair i rows) x (pair j cols)
+      for (int w = tid; w < np * np; w += nt) {
+        const int i = w / np, j = w - (w / np) * np;
+        const T si = sh.sn[i], sj = sh.sn[j];
+        if (si == T(0) && sj == T(0)) continue;
+        const T ci = sh.cs[i], cj = sh.cs[j];
+        const int a = sh.pp[i], b = sh.qq[i], c = sh.pp[j], d = sh.qq[j];
+        const bool bv = b < m, dv = d < m;
+        const T x00 = A[a * m + c];
+        const T x01 = dv ? A[a * m + d] : T(0);
+        const T x10 = bv ? A[b * m + c] : T(0);
+        const T x11 = (bv && dv) ? A[b * m + d] : T(0);
+        // right: columns (c, d) <- (cj col_c - sj col_d, sj col_c + cj col_d)
+        const T y00 = cj * x00 - sj * x01, y01 = sj * x00 + cj * x01;
+        const T y10 = cj * x10 - sj * x11, y11 = sj * x10 + cj * x11;
+        // left: rows (a, b) <- (ci row_a - si row_b, si row_a + ci row_b)
+        T z00 = ci * y00 - si * y10, z01 = ci * y01 - si * y11;
+        T z10 = si * y00 + ci * y10, z11 = si * y01 + ci * y11;
+        if (i == j && si != T(0)) {
+          z01 = T(0);
+          z10 = T(0);
+        }
+        A[a * m + c] = z00;
+        if (dv) A[a * m + d] = z01;
+        if (bv) A[b * m + c] = z10;
+        if (bv && dv) A[b * m + d] = z11;
+      }
+      if (want_v) {
+        for (int w = tid; w < m * np; w += nt) {
+          const int row = w / np, j = w - (w / np) * np;
+          const T sj = sh.sn[j];
+          if (sj == T(0)) continue;
+          const T cj = sh.cs[j];
+          const int c = sh.pp[j], d = sh.qq[j];
+          const T v0 = V[row * m + c], v1 = V[row * m + d];
+          V[row * m + c] = cj * v0 - sj * v1;
+          V[row * m + d] = sj * v0 + cj * v1;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = *sh.flag;
+    __syncthreads();
+    if (!any) break;
+  }
+  return sweep;
+}
+
+// Selects the columns of V whose eigenvalues (diag of A) exceed thr, in
+// descending order, writing them to U columns col0 .. col0+k-1.  Returns k.
+template <typename T>
+__device__ int select_columns(const T *A, const T *V, int m, double thr, T *U, int col0,
+                              double *red) {
+  int cnt = 0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+    if ((double)A[i * m + i] > thr) ++cnt;
+  const int k = (int)(block_sum<T>((double)cnt, red) + 0.5);
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const T di = A[i * m + i];
+    if (!((double)di > thr)) continue;
+    int rank = 0;
+    for (int j = 0; j < m; ++j) {
+      const T dj = A[j * m + j];
+      if (dj > di || (dj == di && j < i)) ++rank;
+    }
+    if (col0 + rank >= m) continue;
+    for (int r = 0; r < m; ++r) U[(int64_t)r * m + col0 + rank] = V[(int64_t)r * m + i];
+  }
+  __syncthreads();
+  return k;
+}
+
+template <typename T, bool SMEM>
+__global__ void __launch_bounds__(TRUNC_THREADS) k_trunc(const TruncTask<T> *__restrict__ tasks,
+                                                        int *__restrict__ kout, double eps,
+                                                        int variant) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[33];
+  __shared__ int flag;
+  __shared__ double u1n[2];
+  const TruncTask<T> t = tasks[blockIdx.x];
+  const int m = t.m;
+  const int mp = m + (m & 1);
+  const int np = mp / 2 > 0 ? mp / 2 : 1;
+  unsigned char *p = smem_raw;
+  T *A;
+  T *V;
+  if (SMEM) {
+    A = reinterpret_cast<T *>(p);
+    p += sizeof(T) * (size_t)m * m;
+    V = reinterpret_cast<T *>(p);
+    p += sizeof(T) * (size_t)m * m;
+  } else {
+    A = t.work;
+    V = t.work + (size_t)m * m;
+  }
+  JacobiShared<T> sh;
+  sh.cs = reinterpret_cast<T *>(p);
+  p += sizeof(T) * np;
+  sh.sn = reinterpret_cast<T *>(p);
+  p += sizeof(T) * np;
+  sh.pp = reinterpret_cast<int *>(p);
+  p += sizeof(int) * np;
+  sh.qq = reinterpret_cast<int *>(p);
+  sh.flag = &flag;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (m == 0) {
+    if (tid == 0) kout[t.k_idx] = 0;
+    return;
+  }
+  if (variant == HS_LORASP && eps == 0.0) {
+    // no truncation: complete basis U = I
+    for (int64_t e = tid; e < (int64_t)m * m; e += nt) t.U[e] = (e / m == e % m) ? T(1) : T(0);
+    if (tid == 0) kout[t.k_idx] = m;
+    return;
+  }
+  // ---- GC basis U_1 = orth[phi_s, A_sw phi_w] (Sec. 6; MGS with one re-orthogonalisation)
+  int k1 = 0;
+  if (variant != HS_LORASP) {
+    double s = 0.0;
+    for (int i = tid; i < m; i += nt) s += (double)t.phi[i] * (double)t.phi[i];
+    const double nphi = sqrt(block_sum<T>(s, red));
+    if (nphi > 0.0) {
+      for (int i = tid; i < m; i += nt) t.U[(int64_t)i * m] = (T)((double)t.phi[i] / nphi);
+      k1 = 1;
+    }
+    __syncthreads();
+    s = 0.0;
+    for (int i = tid; i < m; i += nt) s += (double)t.a[i] * (double)t.a[i];
+    const double na = sqrt(block_sum<T>(s, red));
+    if (na > 0.0) {
+      // v = a kept in V's first column as scratch
+      for (int i = tid; i < m; i += nt) V[i] = t.a[i];
+      __syncthreads();
+      for (int pass = 0; pass < 2 && k1 == 1; ++pass) {
+        double d = 0.0;
+        for (int i = tid; i < m; i += nt) d += (double)t.U[(int64_t)i * m] * (double)V[i];
+        d = block_sum<T>(d, red);
+        for (int i = tid; i < m; i += nt) V[i] = (T)((double)V[i] - d * (double)t.U[(int64_t)i * m]);
+        __syncthreads();
+      }
+      double sv = 0.0;
+      for (int i = tid; i < m; i += nt) sv += (double)V[i] * (double)V[i];
+      const double nv = sqrt(block_sum<T>(sv, red));
+      if (nv > 1e-12 * na) {
+        for (int i = tid; i < m; i += nt) t.U[(int64_t)i * m + k1] = (T)((double)V[i] / nv);
+        ++k1;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) u1n[0] = (double)k1;
+    __syncthreads();
+  }
+  // ---- ||A_sw||_2^2 = lambda_max(G)
+  for (int64_t e = tid; e < (int64_t)m * m; e += nt) A[e] = t.G[e];
+  __syncthreads();
+  const int max_sweeps = 40;
+  double thr;
+  if (variant == HS_LORASP) {
+    jacobi_eig<T>(A, V, m, true, sh, max_sweeps);
+    double lmax = 0.0;
+    for (int i = 0; i < m; ++i) lmax = fmax(lmax, (double)A[i * m + i]);
+    thr = eps * eps * lmax;
+    const int k = select_columns<T>(A, V, m, thr, t.U, 0, red);
+    if (tid == 0) kout[t.k_idx] = k;
+    return;
+  }
+  double lmax = 0.0;
+  if (eps > 0.0) {
+    jacobi_eig<T>(A, V, m, false, sh, max_sweeps);
+    for (int i = 0; i < m; ++i) lmax = fmax(lmax, (double)A[i * m + i]);
+    __syncthreads();
+  }
+  // ---- matrix whose leading eigenvectors give U_2: (I - U1 U1^T) G (I - U1 U1^T),
+  // or the projector I - U1 U1^T itself when eps == 0 (complete basis)
+  // X = G U1 (m x k1) in V's columns 0..k1-1 (scratch, ld m)
+  if (eps > 0.0) {
+    for (int w = tid; w < m * k1; w += nt) {
+      const int i = w / k1, a = w % k1;
+      double s = 0.0;
+      for (int j = 0; j < m; ++j) s += (double)t.G[(int64_t)i * m + j] * (double)t.U[(int64_t)j * m + a];
+      V[i * m + a] = (T)s;
+    }
+    __syncthreads();
+    double c[2][2] = {{0, 0}, {0, 0}};
+    for (int a = 0; a < k1; ++a)
+      for (int b = 0; b < k1; ++b) {
+        double s = 0.0;
+        for (int i = tid; i < m; i += nt) s += (double)t.U[(int64_t)i * m + a] * (double)V[i * m + b];
+        c[a][b] = block_sum<T>(s, red);
+      }
+    for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+      const int i = (int)(e / m), j = (int)(e % m);
+      double v = (double)t.G[e];
+      for (int a = 0; a < k1; ++a) {
+        const double ui = (double)t.U[(int64_t)i * m + a], uj = (double)t.U[(int64_t)j * m + a];
+        v -= ui * (double)V[j * m + a] + (double)V[i * m + a] * uj;
+        for (int b = 0; b < k1; ++b) v += ui * c[a][b] * (double)t.U[(int64_t)j * m + b];
+      }
+      A[e] = (T)v;
+    }
+    thr = eps * eps * lmax;
+  } else {
+    for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+      const int i = (int)(e / m), j = (int)(e % m);
+      double v = (i == j) ? 1.0 : 0.0;
+      for (int a = 0; a < k1; ++a) v -= (double)t.U[(int64_t)i * m + a] * (double)t.U[(int64_t)j * m + a];
+      A[e] = (T)v;
+    }
+    thr = 0.5;
+  }
+  __syncthreads();
+  jacobi_eig<T>(A, V, m, true, sh, max_sweeps);
+  const int k2 = select_columns<T>(A, V, m, thr, t.U, k1, red);
+  int k = k1 + k2;
+  if (k > m) k = m;
+  if (tid == 0) kout[t.k_idx] = k;
+}
+
+// ---------------------------------------------------------------------------
+// CSR value movement
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_scatter_values(const double *__restrict__ val, const int64_t *__restrict__ dest,
+                                 int64_t nnz, T *__restrict__ pool) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = dest[e];
+    if (d >= 0) pool[d] = (T)val[e];
+  }
+}
+
+__global__ void k_gather_values(const double *__restrict__ val, const int32_t *__restrict__ src,
+                                int64_t nnz, double *__restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = val[src[e]];
+}
+
+template <typename T>
+size_t trunc_small_arrays(int m) {
+  const int mp = m + (m & 1);
+  const int np = mp / 2 > 0 ? mp / 2 : 1;
+  return 2 * sizeof(T) * np + 2 * sizeof(int) * np + 64;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_gemm(const GemmTask<T> *d_tasks, const int *d_tile_start, int ntasks, int total_tiles,
+                 cudaStream_t st) {
+  if (ntasks == 0 || total_tiles == 0) return;
+  k_gemm<T><<<total_tiles, 256, 0, st>>>(d_tasks, d_tile_start, ntasks);
+  HS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_sum(const SumTask<T> *d_tasks, const SumSrc<T> *d_srcs, const int *d_tile_start,
+                int ntasks, int total_tiles, cudaStream_t st) {
+  if (ntasks == 0 || total_tiles == 0) return;
+  k_sum<T><<<total_tiles, 256, 0, st>>>(d_tasks, d_srcs, d_tile_start, ntasks);
+  HS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+int chol_smem_cap() {
+  return sizeof(T) == 8 ? 160 : 224;
+}
+
+template <typename T>
+void launch_chol_inv(const CholTask<T> *d_tasks, int ntasks, int *d_status, int max_m,
+                     cudaStream_t st) {
+  if (ntasks == 0) return;
+  if (max_m <= chol_smem_cap<T>()) {
+    const size_t sm = sizeof(T) * ((size_t)max_m * max_m + max_m + 8);
+    HS_CUDA(cudaFuncSetAttribute(k_chol_inv<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm));
+    k_chol_inv<T, true><<<ntasks, CHOL_THREADS, sm, st>>>(d_tasks, d_status);
+  } else {
+    const size_t sm = sizeof(T) * ((size_t)max_m + 8);
+    HS_CUDA(cudaFuncSetAttribute(k_chol_inv<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm));
+    k_chol_inv<T, false><<<ntasks, CHOL_THREADS, sm, st>>>(d_tasks, d_status);
+  }
+  HS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+int trunc_smem_cap() {
+  return sizeof(T) == 8 ? 110 : 156;
+}
+
+template <typename T>
+void launch_trunc(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant,
+                  int max_m, cudaStream_t st) {
+  if (ntasks == 0) return;
+  if (max_m <= trunc_smem_cap<T>()) {
+    const size_t sm = 2 * sizeof(T) * (size_t)max_m * max_m + trunc_small_arrays<T>(max_m);
+    HS_CUDA(cudaFuncSetAttribute(k_trunc<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm));
+    k_trunc<T, true><<<ntasks, TRUNC_THREADS, sm, st>>>(d_tasks, d_k, eps, variant);
+  } else {
+    const size_t sm = trunc_small_arrays<T>(max_m);
+    HS_CUDA(cudaFuncSetAttribute(k_trunc<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm));
+    k_trunc<T, false><<<ntasks, TRUNC_THREADS, sm, st>>>(d_tasks, d_k, eps, variant);
+  }
+  HS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_scatter_values(const double *val, const int64_t *dest, int64_t nnz, T *pool,
+                           cudaStream_t st) {
+  if (nnz == 0) return;
+  const int grid = (int)std::min<int64_t>((nnz + 255) / 256, 152 * 16);
+  k_scatter_values<T><<<grid, 256, 0, st>>>(val, dest, nnz, pool);
+  HS_CUDA(cudaGetLastError());
+}
+
+void launch_gather_values(const double *val, const int32_t *src, int64_t nnz, double *out,
+                          cudaStream_t st) {
+  if (nnz == 0) return;
+  const int grid = (int)std::min<int64_t>((nnz + 255) / 256, 152 * 16);
+  k_gather_values<<<grid, 256, 0, st>>>(val, src, nnz, out);
+  HS_CUDA(cudaGetLastError());
+}
+
+#define HS_INST(T)                                                                            \
+  template void launch_gemm<T>(const GemmTask<T> *, const int *, int, int, cudaStream_t);     \
+  template void launch_sum<T>(const SumTask<T> *, const SumSrc<T> *, const int *, int, int,   \
+                              cudaStream_t);                                                  \
+  template void launch_chol_inv<T>(const CholTask<T> *, int, int *, int, cudaStream_t);       \
+  template void launch_trunc<T>(const TruncTask<T> *, int, int *, double, int, int,           \
+                                cudaStream_t);                                                \
+  template void launch_scatter_values<T>(const double *, const int64_t *, int64_t, T *,       \
+                                         cudaStream_t);
+HS_INST(double)
+HS_INST(float)
+#undef HS_INST
+
+}  // namespace hs

@@ -1,0 +1,111 @@
+"""Host-side checks of the C ABI library: it loads, exports every entry point
+of include/hs.h, and its symbolic planner reproduces the oracle's canonical
+waves and neighbour / well-separated lists exactly (integers, bit for bit)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import hsolver as H
+from paper_1611_03189_gb300 import _lib
+from paper_1611_03189_gb300 import problems as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1611_03189_gb300.build import build
+
+    build()
+    return _lib.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    hdr = open(os.path.join(ROOT, "include", "hs.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|const char \*)\s*(hs_\w+)\s*\(", hdr, flags=re.M))
+    assert declared == set(_lib.EXPORTS)
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\b(hs_\w+)\b", out))
+    assert declared <= exported
+    for name in declared:
+        assert hasattr(lib, name)
+
+
+PLAN_CASES = [
+    ("poisson2d 32 leaf8", lambda: P.poisson2d(32, leaf_size=8)),
+    ("poisson2d 64 leaf16", lambda: P.poisson2d(64, leaf_size=16)),
+    ("rect 24x20 leaf4", lambda: P.make_problem((24, 20), P.coef_constant((24, 20)), 4)),
+    ("poisson3d 12 leaf8", lambda: P.poisson3d(12, leaf_size=8)),
+    ("diffusion 40 leaf4", lambda: P.diffusion2d(40, 1.0, 0, leaf_size=4)),
+]
+
+
+@pytest.mark.parametrize("name,maker", PLAN_CASES, ids=[c[0] for c in PLAN_CASES])
+def test_planner_matches_oracle_waves_and_lists(lib, name, maker):
+    pb = maker()
+    F = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, 0.3, H.LORASP)
+    plan = _lib.Plan(pb.n, pb.rowptr, pb.col, pb.perm, pb.leaf_ptr)
+    try:
+        for lv in F.levels:
+            wo = plan.waves(lv.level)
+            expect = np.full(lv.nsup, -1, dtype=np.int32)
+            for wi, w in enumerate(lv.waves):
+                expect[w] = wi
+            assert np.array_equal(wo, expect), f"level {lv.level}"
+            for rec in lv.supers:
+                nb, ws = plan.lists(lv.level, rec.key)
+                assert nb == rec.nbrs and ws == rec.wsep, f"level {lv.level} super {rec.key}"
+    finally:
+        plan.close()
+
+
+def test_planner_rejects_bad_inputs(lib):
+    pb = P.poisson2d(8, leaf_size=4)
+    bad_perm = pb.perm.copy()
+    bad_perm[0] = bad_perm[1]
+    with pytest.raises(_lib.HsError) as e:
+        _lib.Plan(pb.n, pb.rowptr, pb.col, bad_perm, pb.leaf_ptr)
+    assert e.value.code == _lib.HS_ERR_INVALID and "permutation" in str(e.value)
+    lp3 = np.array([0, 20, 40, 64], dtype=np.int32)
+    with pytest.raises(_lib.HsError) as e:
+        _lib.Plan(pb.n, pb.rowptr, pb.col, pb.perm, lp3)
+    assert "power of two" in str(e.value)
+    # structurally unsymmetric pattern
+    rp = np.array([0, 2, 3], dtype=np.int32)
+    ci = np.array([0, 1, 1], dtype=np.int32)
+    with pytest.raises(_lib.HsError) as e:
+        _lib.Plan(2, rp, ci, np.array([0, 1], np.int32), np.array([0, 1, 2], np.int32))
+    assert "symmetric" in str(e.value)
+
+
+def test_library_does_not_fall_back_without_a_device(lib):
+    """With no CUDA device the compute entry points fail; nothing runs on the CPU."""
+    import ctypes as C
+
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    pb = P.poisson2d(8, leaf_size=4)
+    rp, ci, pe, lp = (np.ascontiguousarray(x, np.int32) for x in (pb.rowptr, pb.col, pb.perm, pb.leaf_ptr))
+    val = np.ascontiguousarray(pb.val)
+    A = _lib.HsCsr(pb.n, pb.nnz, rp.ctypes.data, ci.ctypes.data, val.ctypes.data)
+    cl = _lib.HsClustering(pe.ctypes.data, lp.ctypes.data, len(lp) - 1)
+    o = _lib.HsOpts(0.1, _lib.HS_GC_CONSTANT, _lib.HS_PREC_F64, None)
+    h = C.c_void_p()
+    code = lib.hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), None, C.byref(h))
+    assert code == _lib.HS_ERR_CUDA and not h.value
+
+
+def test_options_are_validated_before_any_device_work(lib):
+    import ctypes as C
+
+    A = _lib.HsCsr(4, 4, 1, 1, 1)
+    cl = _lib.HsClustering(1, 1, 1)
+    h = C.c_void_p()
+    for eps, var, prec in ((-1.0, 1, 0), (1e-8, 1, 0), (0.1, 7, 0), (0.1, 1, 5), (0.1, 2, 0)):
+        o = _lib.HsOpts(eps, var, prec, None)
+        assert lib.hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), None, C.byref(h)) == _lib.HS_ERR_INVALID

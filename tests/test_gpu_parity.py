@@ -1,0 +1,175 @@
+"""Parity of the CUDA path with the FP64 oracle on the same seeded inputs.
+
+Bars (derived in the design notes): FP64 apply within 1e-10 relative of the
+oracle's A_H^-1 r; ranks equal except singular values within 1e-10 relative of
+the threshold; PCG iteration counts within +-1 and relative residual <= 1e-10;
+eps = 0 reproduces a direct solve.  The FP32 factor is checked against the
+oracle within its own rounding level and must still reach 1e-10 under FP64 PCG.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import hsolver as H
+from paper_1611_03189_gb300 import _lib
+from paper_1611_03189_gb300 import problems as P
+
+from gpu_util import gpu_factor, need_gpu, oracle_factor, rel
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    ("poisson2d 32 leaf8", lambda: P.poisson2d(32, leaf_size=8)),
+    ("poisson2d 64 leaf16", lambda: P.poisson2d(64, leaf_size=16)),
+    ("rect 40x28 leaf4", lambda: P.make_problem((40, 28), P.coef_constant((40, 28)), 4)),
+    ("diffusion2d 64 s1", lambda: P.diffusion2d(64, 1.0, 0, leaf_size=16)),
+    ("poisson3d 16 leaf64", lambda: P.poisson3d(16, leaf_size=64)),
+]
+
+
+def _ranks_match(F, G, tol_rel=1e-10):
+    """Oracle vs GPU ranks per super node; a mismatch is allowed only when a
+    singular value lies within tol_rel of the threshold (checked by the test
+    that needs it) -- here none is expected, so ranks must be equal."""
+    bad = []
+    for lv in F.levels:
+        g = G.ranks(lv.level)
+        for rec in lv.supers:
+            want = rec.k if rec.wsep else -1
+            if g[rec.key] != want:
+                bad.append((lv.level, rec.key, want, int(g[rec.key])))
+    return bad
+
+
+@pytest.mark.parametrize("name,maker", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("variant", [H.LORASP, H.GC_CONSTANT])
+@pytest.mark.parametrize("eps", [1e-1, 1e-2])
+def test_apply_and_ranks_match_oracle_fp64(name, maker, variant, eps):
+    torch = need_gpu()
+    pb = maker()
+    F = oracle_factor(pb, eps, variant)
+    G = gpu_factor(pb, eps, variant)
+    assert _ranks_match(F, G) == []
+    B = P.rhs(pb.n, 7, nrhs=3)
+    Z = H.apply(F, B)
+    zg = G.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
+    assert rel(zg, Z) <= 1e-10
+
+
+@pytest.mark.parametrize("name,maker", CASES[:3], ids=[c[0] for c in CASES[:3]])
+@pytest.mark.parametrize("variant", [H.LORASP, H.GC_CONSTANT])
+def test_eps0_is_exact_on_gpu(name, maker, variant):
+    torch = need_gpu()
+    pb = maker()
+    G = gpu_factor(pb, 0.0, variant)
+    b = P.rhs(pb.n, 3)
+    x = spla.spsolve(pb.to_scipy().tocsc(), b)
+    z = G.apply(torch.as_tensor(b, device="cuda")).cpu().numpy()
+    assert rel(z, x) <= 1e-11
+
+
+@pytest.mark.parametrize("name,maker", CASES, ids=[c[0] for c in CASES])
+def test_pcg_matches_oracle(name, maker):
+    torch = need_gpu()
+    pb = maker()
+    F = oracle_factor(pb, 1e-2, H.GC_CONSTANT)
+    G = gpu_factor(pb, 1e-2, H.GC_CONSTANT)
+    b = P.rhs(pb.n, 0)
+    xo, ito, rro = H.pcg(F, pb.rowptr, pb.col, pb.val, b)
+    x, it, rr, code = G.pcg(torch.as_tensor(b, device="cuda"), rtol=1e-10, maxit=500)
+    x = x.cpu().numpy()
+    assert code == _lib.HS_OK
+    assert abs(int(it[0]) - ito) <= 1
+    assert rr[0] <= 1e-10
+    true_rr = np.linalg.norm(b - pb.to_scipy() @ x) / np.linalg.norm(b)
+    assert true_rr <= 1e-10 and abs(true_rr - rr[0]) <= 1e-12
+    if int(it[0]) == ito:
+        assert rel(x, xo) <= 1e-9
+
+
+def test_gc_preserves_constant_vector_on_gpu():
+    torch = need_gpu()
+    pb = P.diffusion2d(64, 1.0, 3, leaf_size=16)
+    G = gpu_factor(pb, 1e-1, H.GC_CONSTANT)
+    one = np.ones(pb.n)
+    z = G.apply(torch.as_tensor(pb.to_scipy() @ one, device="cuda")).cpu().numpy()
+    assert rel(z, one) <= 1e-11
+    G0 = gpu_factor(pb, 1e-1, H.LORASP)
+    z0 = G0.apply(torch.as_tensor(pb.to_scipy() @ one, device="cuda")).cpu().numpy()
+    assert rel(z0, one) > 1e-6
+
+
+def test_gc_user_vector_on_gpu():
+    torch = need_gpu()
+    nx = 32
+    pb = P.poisson2d(nx, leaf_size=8)
+    phi = P.laplacian_eigvec_2d(nx, nx)
+    lam = P.laplacian_eigval_2d(nx, nx)
+    G = gpu_factor(pb, 0.2, H.GC_USER, phi=phi)
+    F = oracle_factor(pb, 0.2, H.GC_USER, phi=phi)
+    z = G.apply(torch.as_tensor(phi, device="cuda")).cpu().numpy()
+    assert rel(z, phi / lam) <= 1e-11
+    b = P.rhs(pb.n, 9)
+    assert rel(G.apply(torch.as_tensor(b, device="cuda")).cpu().numpy(), H.apply(F, b)) <= 1e-10
+
+
+def test_multi_rhs_apply_equals_single():
+    torch = need_gpu()
+    pb = P.poisson2d(48, leaf_size=8)
+    G = gpu_factor(pb, 1e-2, H.GC_CONSTANT)
+    B = torch.as_tensor(P.rhs(pb.n, 5, nrhs=20).T.copy(), device="cuda")
+    Z = G.apply(B)
+    for j in (0, 7, 19):
+        zj = G.apply(B[j].contiguous())
+        assert torch.equal(zj, Z[j])
+
+
+def test_multi_rhs_pcg():
+    torch = need_gpu()
+    pb = P.poisson2d(48, leaf_size=8)
+    G = gpu_factor(pb, 1e-2, H.GC_CONSTANT)
+    B = torch.as_tensor(P.rhs(pb.n, 5, nrhs=5).T.copy(), device="cuda")
+    X, it, rr, code = G.pcg(B)
+    assert code == _lib.HS_OK and np.all(rr <= 1e-10)
+    for j in range(5):
+        xj, itj, rrj, _ = G.pcg(B[j].contiguous())
+        assert int(itj[0]) == int(it[j])
+        assert torch.allclose(xj, X[j], rtol=0, atol=1e-12 * float(X[j].abs().max()))
+
+
+@pytest.mark.parametrize("name,maker", [CASES[1], CASES[3]], ids=[CASES[1][0], CASES[3][0]])
+def test_fp32_factor_reaches_fp64_accuracy_under_pcg(name, maker):
+    torch = need_gpu()
+    pb = maker()
+    F = oracle_factor(pb, 1e-2, H.GC_CONSTANT)
+    G = gpu_factor(pb, 1e-2, H.GC_CONSTANT, prec=_lib.HS_PREC_F32)
+    b = P.rhs(pb.n, 1)
+    z = G.apply(torch.as_tensor(b, device="cuda")).cpu().numpy()
+    assert rel(z, H.apply(F, b)) <= 1e-3
+    x, it, rr, code = G.pcg(torch.as_tensor(b, device="cuda"))
+    _, ito, _ = H.pcg(F, pb.rowptr, pb.col, pb.val, b)
+    assert code == _lib.HS_OK and rr[0] <= 1e-10
+    assert int(it[0]) <= ito + 5
+
+
+def test_not_spd_is_reported_by_gpu():
+    need_gpu()
+    pb = P.diffusion2d(16, 3.0, 2, leaf_size=8)
+    with pytest.raises(_lib.HsError) as e:
+        gpu_factor(pb, 0.1, H.GC_CONSTANT)
+    assert e.value.code == _lib.HS_ERR_NOT_SPD
+
+
+def test_edge_cases_single_leaf_and_tiny_levels():
+    torch = need_gpu()
+    for L in (0, 1, 2):
+        pb = P.make_problem((6, 5), P.coef_constant((6, 5)), levels=L)
+        b = P.rhs(pb.n, 2)
+        x = spla.spsolve(pb.to_scipy().tocsc(), b)
+        for eps in (0.0, 0.3):
+            G = gpu_factor(pb, eps, H.GC_CONSTANT)
+            F = oracle_factor(pb, eps, H.GC_CONSTANT)
+            z = G.apply(torch.as_tensor(b, device="cuda")).cpu().numpy()
+            assert rel(z, H.apply(F, b)) <= 1e-11
+            if eps == 0.0:
+                assert rel(z, x) <= 1e-11
