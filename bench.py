@@ -1,0 +1,388 @@
+"""Benchmark of the GB300 hierarchical solver (factor + FP64 PCG to rel-res 1e-10).
+
+Workload (default "diffusion2d_512"): 2D variable-coefficient diffusion,
+5-point, 512 x 512 grid (n = 262144), a = exp(s g) with s = 1 and g a Gaussian
+random field of length scale 8 cells, recursive-bisection leaves of 16
+unknowns, truncation tolerance 1e-2, GC-constant compression, PCG to relative
+residual 1e-10, b ~ N(0,1).  A step is one whole pass of the hot path: the
+numeric factorization of a new matrix (same pattern, the field drawn from a new
+seed) followed by one PCG solve with `--nrhs` right-hand sides.  The symbolic
+plan is built once per pattern, before timing.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead
+(rank 0 only), on a bounded sample of the same recipe.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (grid side, s, eps, leaf size)
+    "diffusion2d_512": (512, 1.0, 1e-2, 16),
+    "diffusion2d_256": (256, 1.0, 1e-2, 16),
+    "poisson2d_64": (64, 0.0, 1e-2, 16),
+}
+CPU_SAMPLE_SIDE = 256     # the oracle's bounded sample of the 512 x 512 recipe
+
+
+def make_problem(name: str, seed: int):
+    from paper_1611_03189_gb300 import problems as P
+
+    side, s, eps, leaf = WORKLOADS[name]
+    if s == 0.0:
+        return P.poisson2d(side, leaf_size=leaf), eps
+    return P.diffusion2d(side, s, seed, leaf_size=leaf), eps
+
+
+def sample_for(name: str):
+    side, s, eps, leaf = WORKLOADS[name]
+    if side <= CPU_SAMPLE_SIDE:
+        return name, 1.0
+    return f"diffusion2d_{CPU_SAMPLE_SIDE}", (side / CPU_SAMPLE_SIDE) ** 2
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle (CPU baseline / reference arm): run in a child process with one thread
+# ---------------------------------------------------------------------------
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import hsolver as H
+import bench
+times = []
+iters = []
+for k in range({reps}):
+    pb, eps = bench.make_problem({name!r}, {seed0} + k)
+    from paper_1611_03189_gb300 import problems as P
+    b = P.rhs(pb.n, 1000 + k)
+    t0 = time.perf_counter()
+    F = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, eps, H.GC_CONSTANT)
+    x, it, rr = H.pcg(F, pb.rowptr, pb.col, pb.val, b, rtol=1e-10, maxit=1000)
+    times.append(time.perf_counter() - t0)
+    iters.append(it)
+print(json.dumps({{"times": times, "iters": iters}}))
+"""
+
+
+def run_oracle(name: str, reps: int, seed0: int = 0) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ORACLE_SNIPPET.format(root=ROOT, reps=reps, name=name, seed0=seed0)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle run failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(workload: str) -> dict:
+    sample, scale = sample_for(workload)
+    res = run_oracle(sample, 1, seed0=0)
+    t = res["times"][0]
+    return {"value": (1.0 / t) / scale, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"one factor + PCG solve (1 rhs) of the same recipe on a {CPU_SAMPLE_SIDE}x{CPU_SAMPLE_SIDE} "
+                       f"grid ({t:.2f} s, {res['iters'][0]} iterations), scaled by the unknown count "
+                       f"x{scale:g} (linear complexity, Sec. 3)" if scale != 1.0 else
+                       f"one factor + PCG solve (1 rhs) of the workload ({t:.2f} s)"),
+            "sample_seconds": t}
+
+
+def reference_arm(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample, scale = sample_for(args.workload)
+    res = run_oracle(sample, args.warmup + args.steps, seed0=0)
+    times = res["times"][args.warmup:]
+    per = sum(times) / len(times)
+    value = (1.0 / per) / scale
+    line = {
+        "impl": "reference", "metric": "solves/s to rel-res 1e-10 (factor + PCG solve, FP64 oracle)",
+        "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per * 1000 * scale, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "nrhs": 1, "sample": f"{CPU_SAMPLE_SIDE}x{CPU_SAMPLE_SIDE}"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"each step one factor + PCG solve of the recipe on a {CPU_SAMPLE_SIDE}^2 grid, "
+                                   f"scaled by the unknown count x{scale:g}"},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "iterations": res["iters"][args.warmup:],
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="diffusion2d_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="print a phase breakdown to stderr")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1611_03189_gb300 import _lib
+    from paper_1611_03189_gb300 import problems as P
+
+    dev = torch.device("cuda", local)
+    prec = _lib.HS_PREC_F32 if args.prec == "f32" else _lib.HS_PREC_F64
+    nsteps = args.warmup + args.steps
+    # inputs resident in HBM: one matrix (new coefficient field) and rhs block per step
+    pbs = []
+    for k in range(nsteps):
+        pb, eps = make_problem(args.workload, seed=rank * 1000 + k)
+        pbs.append(pb)
+    pb0 = pbs[0]
+    rp = torch.as_tensor(pb0.rowptr, device=dev)
+    ci = torch.as_tensor(pb0.col, device=dev)
+    vals = [torch.as_tensor(pb.val, device=dev) for pb in pbs]
+    bs = [torch.as_tensor(P.rhs(pb0.n, 1000 + k, nrhs=args.nrhs).T.copy(), device=dev).squeeze(0)
+          for k in range(nsteps)]
+    stream = torch.cuda.current_stream()
+    t_plan = time.perf_counter()
+    G = _lib.Factor(rp, ci, vals[0], pb0.perm, pb0.leaf_ptr, eps, _lib.HS_GC_CONSTANT, prec)
+    t_plan = time.perf_counter() - t_plan
+
+    iters_seen = []
+
+    def step(k):
+        G.refactor(vals[k])
+        x, it, rr, code = G.pcg(bs[k], rtol=1e-10, maxit=1000, raise_on_fail=False)
+        if code != _lib.HS_OK:
+            raise RuntimeError(f"PCG did not converge: iters {it}, relres {rr}")
+        iters_seen.append(int(it.max()))
+        return rr
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, device events on the launching stream ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = _lib.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    e0.record(stream)
+    rrs = []
+    for k in range(args.warmup, nsteps):
+        rrs.append(float(np.max(step(k))))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    launches = _lib.launch_count() - l0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps * args.nrhs / (ms / 1000.0)
+    info = G.info()
+
+    # ---- factor-only and solve-only splits (resident factor), for context ----
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    G.refactor(vals[args.warmup])
+    e3.record(stream)
+    torch.cuda.synchronize()
+    factor_ms = e2.elapsed_time(e3)
+    e2.record(stream)
+    _, it1, _, _ = G.pcg(bs[args.warmup], rtol=1e-10, maxit=1000)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    solve_ms = e2.elapsed_time(e3)
+
+    # ---- dominant kernel class of the solve: the apply (Algorithm 2), HBM-bound ----
+    napply = 20
+    r = bs[args.warmup]
+    G.apply(r)
+    torch.cuda.synchronize()
+    e2.record(stream)
+    for _ in range(napply):
+        G.apply(r)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    apply_ms = e2.elapsed_time(e3) / napply
+    n = pb0.n
+    vec_bytes = 8 * n * args.nrhs * 4     # r in, z out, workspace in/out per level-L unknown
+    apply_bytes = info["factor_bytes"] + vec_bytes
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = apply_bytes / (apply_ms / 1000.0) / 1e9
+
+    # ---- end to end through the C ABI with host buffers (H2D values + rhs, D2H x) ----
+    hv = [torch.empty(pb0.nnz, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    hb = [torch.empty(bs[0].shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    hx = [torch.empty(bs[0].shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    for j in range(2):
+        hv[j].copy_(vals[args.warmup + j % args.steps].cpu())
+        hb[j].copy_(bs[args.warmup + j % args.steps].cpu())
+    dv = torch.empty(pb0.nnz, dtype=torch.float64, device=dev)
+    db = torch.empty(bs[0].shape, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e2.record(stream)
+    for k in range(args.steps):
+        dv.copy_(hv[k % 2], non_blocking=True)
+        db.copy_(hb[k % 2], non_blocking=True)
+        G.refactor(dv)
+        x, it, rr, code = G.pcg(db, rtol=1e-10, maxit=1000)
+        hx[k % 2].copy_(x, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e2.elapsed_time(e3)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_val = world * args.steps * args.nrhs / (e2e_ms / 1000.0)
+
+    if args.profile and rank == 0:
+        print(json.dumps({"plan_and_first_factor_s": t_plan, "factor_ms": factor_ms, "solve_ms": solve_ms,
+                          "apply_ms": apply_ms, "iters": int(it1.max()), "info": info,
+                          "apply_GBps": achieved, "wall_timed_s": wall}), file=sys.stderr, flush=True)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline(args.workload)
+        except Exception as ex:  # the baseline must not hide the GPU number
+            cpu = {"error": str(ex)[:200]}
+
+    if rank == 0:
+        line = {
+            "metric": "solves/s to rel-res 1e-10 (factor + PCG solve; mixed vs FP64 factor)",
+            "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.prec == "f32" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "grid": WORKLOADS[args.workload][0], "n": n,
+                       "s": WORKLOADS[args.workload][1], "eps": WORKLOADS[args.workload][2],
+                       "leaf": WORKLOADS[args.workload][3], "variant": "GC-constant",
+                       "factor_prec": args.prec, "pcg": "fp64", "rtol": 1e-10, "nrhs": args.nrhs,
+                       "l2": "inputs larger than L2 (factor records > 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": {"bound": "hbm", "kernel": "apply (Algorithm 2: k_fwd_node, k_fwd_target, k_bwd_node)",
+                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                         "traffic": None, "algorithmic_bytes": apply_bytes, "launch_ms": apply_ms},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": 8 * (pb0.nnz + n * args.nrhs),
+                    "d2h_bytes_per_step": 8 * n * args.nrhs},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "factor_ms": factor_ms, "solve_ms": solve_ms, "pcg_iterations": int(it1.max()),
+            "iterations_timed": iters_seen[args.warmup:], "max_relres": max(rrs),
+            "factor_info": {k: info[k] for k in ("levels", "waves", "super_nodes", "root_size", "max_rank",
+                                                 "max_super", "factor_bytes", "device_bytes", "factor_flops")},
+        }
+        print(json.dumps(line), flush=True)
+    G.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

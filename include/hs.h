@@ -120,6 +120,13 @@ typedef struct hs_factor_s *hs_factor;
 int hs_factor_create(const hs_csr *A, const hs_clustering *cl, const hs_opts *opts,
                      void *stream, hs_factor *out);
 
+/* hs_factor_refactor: factor new values of the same matrix pattern with the
+ * same clustering and options (Algorithm 1 again; the symbolic plan is reused).
+ * val: DEVICE, nnz doubles in the order of the CSR given to hs_factor_create.
+ * The previous factorization is released.  On error the handle holds no valid
+ * factorization until the next successful refactor. */
+int hs_factor_refactor(hs_factor f, const double *val, void *stream);
+
 /* hs_apply: z = A_H^{-1} r (Appendix A, Algorithm 2: forward substitution,
  * restriction, parent solve, prolongation, backward substitution).
  * r, z: DEVICE, n x nrhs column-major with leading dimension ld >= n;
@@ -128,8 +135,8 @@ int hs_apply(hs_factor f, const double *r, double *z, int32_t nrhs, int64_t ld, 
 
 /* hs_pcg: solve A x = b by conjugate gradients preconditioned with A_H^{-1},
  * x_0 = 0, stopping when ||r_k||_2 <= rtol ||b||_2 for each right-hand side
- * (Sec. 7: relative residual 1e-10).  A is the matrix given to
- * hs_factor_create.  b, x: DEVICE, n x nrhs column-major, leading dimension
+ * (Sec. 7: relative residual 1e-10).  A is the matrix of the last successful
+ * hs_factor_create / hs_factor_refactor.  b, x: DEVICE, n x nrhs column-major, leading dimension
  * ld.  iters, relres: HOST arrays of nrhs; iters[j] = completed CG updates of
  * column j, relres[j] = ||b_j - A x_j|| / ||b_j|| recomputed at the end.
  * Returns HS_ERR_NO_CONVERGENCE (with x, iters, relres filled) if some column
@@ -152,6 +159,10 @@ int hs_factor_destroy(hs_factor f);
 
 /* hs_last_error: message of the last failing call on this thread. */
 const char *hs_last_error(void);
+
+/* hs_launch_count: number of CUDA kernels this library has launched in the
+ * process so far (all handles, all threads). */
+int64_t hs_launch_count(void);
 
 /* ---------------------------------------------------------------------------
  * Symbolic planner (host only; no device needed).  The elimination order is

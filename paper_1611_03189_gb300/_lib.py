@@ -37,7 +37,7 @@ STATUS_NAMES = {
 
 # every symbol include/hs.h declares
 EXPORTS = [
-    "hs_factor_create", "hs_apply", "hs_pcg", "hs_factor_info", "hs_factor_ranks",
+    "hs_factor_create", "hs_factor_refactor", "hs_launch_count", "hs_apply", "hs_pcg", "hs_factor_info", "hs_factor_ranks",
     "hs_factor_destroy", "hs_last_error", "hs_plan_create", "hs_plan_level_waves",
     "hs_plan_super_lists", "hs_plan_destroy",
 ]
@@ -86,6 +86,8 @@ def lib():
         vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
         L.hs_factor_create.argtypes = [C.POINTER(HsCsr), C.POINTER(HsClustering), C.POINTER(HsOpts), vp,
                                        C.POINTER(vp)]
+        L.hs_factor_refactor.argtypes = [vp, vp, vp]
+        L.hs_launch_count.argtypes = []
         L.hs_apply.argtypes = [vp, vp, vp, i32, i64, vp]
         L.hs_pcg.argtypes = [vp, vp, vp, i32, i64, dbl, i32, vp, vp, vp]
         L.hs_factor_info.argtypes = [vp, C.POINTER(HsInfo)]
@@ -97,10 +99,16 @@ def lib():
         L.hs_plan_super_lists.argtypes = [vp, i32, i32, vp, vp, i32, C.POINTER(i32), C.POINTER(i32)]
         L.hs_plan_destroy.argtypes = [vp]
         for name in EXPORTS:
-            if name != "hs_last_error":
+            if name not in ("hs_last_error", "hs_launch_count"):
                 getattr(L, name).restype = C.c_int
+        L.hs_launch_count.restype = C.c_int64
         _lib = L
     return _lib
+
+
+def launch_count() -> int:
+    """Kernels launched by libhs.so in this process so far."""
+    return int(lib().hs_launch_count())
 
 
 def check(code: int):
@@ -192,6 +200,13 @@ class Factor:
         self._h = None
         check(lib().hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), _stream_ptr(stream), C.byref(h)))
         self._h = h
+
+    def refactor(self, val, stream=None):
+        """Factor new values (float64 CUDA tensor, nnz) of the same pattern."""
+        import torch
+
+        assert val.is_cuda and val.dtype == torch.float64 and val.is_contiguous()
+        check(lib().hs_factor_refactor(self._h, val.data_ptr(), _stream_ptr(stream)))
 
     def apply(self, r, z=None, stream=None):
         """z = A_H^-1 r; r is (n,) or (nrhs, n) float64 CUDA (each row one rhs)."""

@@ -2,6 +2,7 @@
 // C++ exception) and turns it into a status code plus a thread-local message.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -13,7 +14,10 @@ namespace hs {
 
 namespace {
 thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
 }
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_error(const std::string &msg) { g_err = msg; }
 
@@ -54,6 +58,58 @@ X *upload_vec(const std::vector<X> &v, cudaStream_t st) {
   HS_CUDA(cudaMalloc(&d, sizeof(X) * std::max<size_t>(v.size(), 1)));
   if (!v.empty()) HS_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice, st));
   return d;
+}
+
+// Values -> permuted CSR, numeric factorization, apply schedule to the device,
+// counters.  Used by hs_factor_create and hs_factor_refactor.
+void numeric_factor(FactorHandle &h, const double *val, const double *phi_host, cudaStream_t st) {
+  h.stream = st;
+  launch_gather_values(val, h.d_src, h.nnz, h.d_val, st);
+  cudaFree(h.d_nodes);
+  cudaFree(h.d_nbrs);
+  cudaFree(h.d_targets);
+  cudaFree(h.d_contribs);
+  h.d_nodes = nullptr;
+  h.d_nbrs = nullptr;
+  h.d_targets = nullptr;
+  h.d_contribs = nullptr;
+  cudaEvent_t e0, e1;
+  HS_CUDA(cudaEventCreate(&e0));
+  HS_CUDA(cudaEventCreate(&e1));
+  HS_CUDA(cudaEventRecord(e0, st));
+  try {
+    factorize(h, hs_csr{}, hs_opts{}, phi_host);
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h.nodes.clear();
+    h.waves.clear();
+    h.levels.clear();
+    h.root_m = 0;
+    throw;
+  }
+  HS_CUDA(cudaEventRecord(e1, st));
+  h.d_nodes = upload_vec(h.nodes, st);
+  h.d_nbrs = upload_vec(h.nbrs, st);
+  h.d_targets = upload_vec(h.targets, st);
+  h.d_contribs = upload_vec(h.contribs, st);
+  HS_CUDA(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  HS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  hs_info &in = h.info;
+  in.n = h.plan.n;
+  in.levels = h.plan.L;
+  in.waves = h.plan.total_waves;
+  in.factor_ms = ms;
+  const double tb = h.prec == HS_PREC_F64 ? 8.0 : 4.0;
+  double fb = 0.0;
+  for (const auto &nd : h.nodes) fb += 2.0 * ((double)nd.m * nd.m + (double)nd.k * nd.m + (double)nd.m * nd.dN);
+  fb += (double)h.root_m * h.root_m;
+  in.factor_bytes = (int64_t)(fb * tb);
+  in.device_bytes = (int64_t)(h.pers->reserved() + h.scratch->reserved());
 }
 
 }  // namespace
@@ -105,50 +161,28 @@ int hs_factor_create(const hs_csr *A, const hs_clustering *cl, const hs_opts *o,
     h.d_rowptr = hs::upload_vec(h.plan.prow, st);
     h.d_col = hs::upload_vec(h.plan.pcol, st);
     h.d_perm = hs::upload_vec(h.plan.perm, st);
-    int32_t *d_src = hs::upload_vec(h.plan.psrc, st);
+    h.d_src = hs::upload_vec(h.plan.psrc, st);
+    h.nnz = A->nnz;
     HS_CUDA(cudaMalloc(&h.d_val, sizeof(double) * A->nnz));
-    hs::launch_gather_values(A->val, d_src, A->nnz, h.d_val, st);
-    cudaEvent_t e0, e1;
-    HS_CUDA(cudaEventCreate(&e0));
-    HS_CUDA(cudaEventCreate(&e1));
-    HS_CUDA(cudaEventRecord(e0, st));
-    try {
-      hs::factorize(h, *A, *o, o->phi);
-    } catch (...) {
-      cudaStreamSynchronize(st);
-      cudaFree(d_src);
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      throw;
-    }
-    HS_CUDA(cudaEventRecord(e1, st));
-    // apply schedule to the device
-    h.d_nodes = hs::upload_vec(h.nodes, st);
-    h.d_nbrs = hs::upload_vec(h.nbrs, st);
-    h.d_targets = hs::upload_vec(h.targets, st);
-    h.d_contribs = hs::upload_vec(h.contribs, st);
-    HS_CUDA(cudaStreamSynchronize(st));
-    float ms = 0.f;
-    HS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(d_src);
-    h.scratch.reset();  // the solve does not need the factorization scratch
-    hs_info &in = h.info;
-    in.n = A->n;
-    in.levels = h.plan.L;
-    in.waves = h.plan.total_waves;
-    in.factor_ms = ms;
-    const double tb = h.prec == HS_PREC_F64 ? 8.0 : 4.0;
-    double fb = 0.0;
-    for (const auto &nd : h.nodes) fb += 2.0 * ((double)nd.m * nd.m + (double)nd.k * nd.m + (double)nd.m * nd.dN);
-    fb += (double)h.root_m * h.root_m;
-    in.factor_bytes = (int64_t)(fb * tb);
-    in.device_bytes = (int64_t)h.pers->reserved();
+    hs::numeric_factor(h, A->val, o->phi, st);
+    h.valid = true;
     *out = f.release();
     return HS_OK;
   });
 }
+
+int hs_factor_refactor(hs_factor f, const double *val, void *stream) {
+  return hs::guarded([&]() -> int {
+    if (!f || !val) fail(HS_ERR_INVALID, "null argument");
+    hs::require_device();
+    f->h.valid = false;
+    hs::numeric_factor(f->h, val, nullptr, (cudaStream_t)stream);
+    f->h.valid = true;
+    return HS_OK;
+  });
+}
+
+int64_t hs_launch_count(void) { return hs::g_launches.load(); }
 
 int hs_apply(hs_factor f, const double *r, double *z, int32_t nrhs, int64_t ld, void *stream) {
   return hs::guarded([&]() -> int {
@@ -158,6 +192,7 @@ int hs_apply(hs_factor f, const double *r, double *z, int32_t nrhs, int64_t ld, 
     hs::require_device();
     cudaStream_t st = (cudaStream_t)stream;
     // r and z may alias: r is gathered into the workspace before z is written
+    if (!f->h.valid) fail(HS_ERR_INVALID, "the handle holds no valid factorization");
     hs::apply_solve(f->h, r, z, nrhs, ld, st);
     return HS_OK;
   });
@@ -171,6 +206,7 @@ int hs_pcg(hs_factor f, const double *b, double *x, int32_t nrhs, int64_t ld, do
     if (ld < f->h.plan.n) fail(HS_ERR_INVALID, "ld < n");
     if (!(rtol > 0.0) || maxit < 1) fail(HS_ERR_INVALID, "rtol must be > 0 and maxit >= 1");
     hs::require_device();
+    if (!f->h.valid) fail(HS_ERR_INVALID, "the handle holds no valid factorization");
     return hs::pcg_solve(f->h, b, x, nrhs, ld, rtol, maxit, iters, relres, (cudaStream_t)stream);
   });
 }

@@ -16,6 +16,7 @@
 // M_ss = A_ss^-1 - P_ss^T S P_ss = L^-T (I - Q Q^T) L^-1, and
 // A_ns M_ss A_sn' is the Schur term of ~~A_nn' (eq. eliminated).
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <unordered_map>
@@ -212,6 +213,23 @@ struct CholBatch {
   }
 };
 
+// Largest super node whose truncation uses the shared-memory Jacobi kernel
+// (default 64: above that the tridiagonal path needs far fewer operations than
+// the ~10 Jacobi sweeps); larger ones use the tridiagonal path.
+// HS_EIG_SMALL_MAX (environment) lowers the limit, which lets small test
+// problems exercise the tridiagonal path.
+template <typename T>
+int eig_small_max() {
+  static const int v = [] {
+    const char *e = std::getenv("HS_EIG_SMALL_MAX");
+    const int cap = std::min(64, jacobi_cap<T>());
+    if (!e) return cap;
+    const int x = std::atoi(e);
+    return x < 0 ? cap : std::min(x, cap);
+  }();
+  return v;
+}
+
 template <typename T>
 T *talloc(DevArena &a, size_t n) {
   return (T *)a.alloc(sizeof(T) * std::max<size_t>(n, 1));
@@ -316,63 +334,70 @@ template <typename T>
 void Run<T>::leaf_setup() {
   const int nleaf = P_.nleaf;
   const auto &lp = P_.leaf_ptr;
-  std::vector<int> leaf_of(P_.n);
-  for (int i = 0; i < nleaf; ++i)
-    for (int p = lp[i]; p < lp[i + 1]; ++p) leaf_of[p] = i;
   size_.assign(nleaf, 0);
   for (int i = 0; i < nleaf; ++i) size_[i] = lp[i + 1] - lp[i];
-  // block list and offsets
-  std::unordered_map<uint64_t, int64_t> off;
-  std::vector<std::pair<int, int>> order;
-  int64_t total = 0;
-  for (int64_t p = 0; p < P_.n; ++p)
-    for (int e = P_.prow[p]; e < P_.prow[p + 1]; ++e) {
-      const int a = leaf_of[p], b = leaf_of[P_.pcol[e]];
-      if (a > b) continue;
-      const uint64_t key = bkey(a, b);
-      if (!off.count(key)) {
-        off[key] = total;
-        order.emplace_back(a, b);
-        total += ((int64_t)size_[a] * size_[b] + 3) & ~(int64_t)3;
+  if (!h_.d_leaf_dest) {
+    // block list, storage offsets and the entry -> block position map (once per pattern)
+    std::vector<int> leaf_of(P_.n);
+    for (int i = 0; i < nleaf; ++i)
+      for (int p = lp[i]; p < lp[i + 1]; ++p) leaf_of[p] = i;
+    std::unordered_map<uint64_t, int64_t> off;
+    h_.leaf_blocks.clear();
+    h_.leaf_block_off.clear();
+    int64_t total = 0;
+    for (int64_t p = 0; p < P_.n; ++p)
+      for (int e = P_.prow[p]; e < P_.prow[p + 1]; ++e) {
+        const int a = leaf_of[p], b = leaf_of[P_.pcol[e]];
+        if (a > b) continue;
+        const uint64_t key = bkey(a, b);
+        if (!off.count(key)) {
+          off[key] = total;
+          h_.leaf_blocks.emplace_back(a, b);
+          h_.leaf_block_off.push_back(total);
+          total += ((int64_t)size_[a] * size_[b] + 3) & ~(int64_t)3;
+        }
       }
+    std::vector<int64_t> dest(P_.nnz, -1);
+    for (int64_t p = 0; p < P_.n; ++p)
+      for (int e = P_.prow[p]; e < P_.prow[p + 1]; ++e) {
+        const int c = P_.pcol[e];
+        const int a = leaf_of[p], b = leaf_of[c];
+        if (a > b) continue;
+        dest[e] = off[bkey(a, b)] + (int64_t)(p - lp[a]) * size_[b] + (c - lp[b]);
+      }
+    HS_CUDA(cudaMalloc(&h_.d_leaf_dest, sizeof(int64_t) * std::max<int64_t>(P_.nnz, 1)));
+    HS_CUDA(cudaMemcpyAsync(h_.d_leaf_dest, dest.data(), sizeof(int64_t) * P_.nnz, cudaMemcpyHostToDevice, st_));
+    h_.leaf_total = total;
+    if (use_phi_) {
+      // preserved vector of the leaves (GC): ones, or the caller's phi permuted
+      std::vector<T> ph(P_.n);
+      for (int64_t p = 0; p < P_.n; ++p)
+        ph[p] = (h_.variant == HS_GC_USER) ? (T)phi_host_[P_.perm[p]] : T(1);
+      HS_CUDA(cudaMalloc(&h_.d_phi0, sizeof(T) * P_.n));
+      HS_CUDA(cudaMemcpyAsync(h_.d_phi0, ph.data(), sizeof(T) * P_.n, cudaMemcpyHostToDevice, st_));
     }
+  }
+  const int64_t total = h_.leaf_total;
   T *base = talloc<T>(*h_.pers, total);
-  HS_CUDA(cudaMemsetAsync(base, 0, sizeof(T) * total, st_));
-  std::vector<int64_t> dest(P_.nnz, -1);
-  for (int64_t p = 0; p < P_.n; ++p)
-    for (int e = P_.prow[p]; e < P_.prow[p + 1]; ++e) {
-      const int c = P_.pcol[e];
-      const int a = leaf_of[p], b = leaf_of[c];
-      if (a > b) continue;
-      dest[e] = off[bkey(a, b)] + (int64_t)(p - lp[a]) * size_[b] + (c - lp[b]);
-    }
-  int64_t *d_dest = talloc<int64_t>(*h_.scratch, P_.nnz);
-  HS_CUDA(cudaMemcpyAsync(d_dest, dest.data(), sizeof(int64_t) * P_.nnz, cudaMemcpyHostToDevice, st_));
-  launch_scatter_values<T>(h_.d_val, d_dest, P_.nnz, base, st_);
+  HS_CUDA(cudaMemsetAsync(base, 0, sizeof(T) * std::max<int64_t>(total, 1), st_));
+  launch_scatter_values<T>(h_.d_val, h_.d_leaf_dest, P_.nnz, base, st_);
   blocks_.clear();
-  for (auto &ab : order) {
+  for (size_t i = 0; i < h_.leaf_blocks.size(); ++i) {
+    const auto &ab = h_.leaf_blocks[i];
     BlockRef<T> br;
-    br.ptr = base + off[bkey(ab.first, ab.second)];
+    br.ptr = base + h_.leaf_block_off[i];
     br.ld = size_[ab.second];
     br.rowkey = ab.first;
     blocks_[bkey(ab.first, ab.second)] = br;
   }
-  // preserved vector of the leaves (GC): ones, or the caller's phi permuted
   phi_.assign(nleaf, nullptr);
-  if (use_phi_) {
-    std::vector<T> ph(P_.n);
-    for (int64_t p = 0; p < P_.n; ++p)
-      ph[p] = (h_.variant == HS_GC_USER) ? (T)phi_host_[P_.perm[p]] : T(1);
-    T *d_ph = talloc<T>(*h_.pers, P_.n);
-    HS_CUDA(cudaMemcpyAsync(d_ph, ph.data(), sizeof(T) * P_.n, cudaMemcpyHostToDevice, st_));
-    for (int i = 0; i < nleaf; ++i) phi_[i] = d_ph + lp[i];
-  }
+  if (use_phi_)
+    for (int i = 0; i < nleaf; ++i) phi_[i] = (T *)h_.d_phi0 + lp[i];
   // vector layout: level L segment = the permuted unknowns
   seg_off_ = 0;
   red_off_.assign(nleaf, 0);
   for (int i = 0; i < nleaf; ++i) red_off_[i] = lp[i];
   seg_size_ = P_.n;
-  HS_CUDA(cudaStreamSynchronize(st_));  // dest is pageable-sourced scratch; keep it simple
 }
 
 // Merge the red nodes (keys key_base + i, i < nred) pairwise into super nodes
@@ -474,9 +499,9 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
   SumBatch<T> gather;
   GemmBatch<T> gram;
   CholBatch<T> chol;
-  std::vector<TruncTask<T>> trunc;
-  int max_trunc_m = 0;
-  std::vector<int> trunc_sup;
+  std::vector<TruncTask<T>> trunc, trunc_big;
+  int max_trunc_m = 0, max_big_m = 0;
+  std::vector<int> trunc_sup, big_sup;
   for (size_t q = 0; q < wl.size(); ++q) {
     Sup &x = S[q];
     const int s = wl[q];
@@ -530,19 +555,23 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
       tt.U = x.U;
       tt.work = nullptr;
       tt.m = m;
-      tt.k_idx = (int)trunc.size();
-      trunc.push_back(tt);
-      trunc_sup.push_back((int)q);
-      max_trunc_m = std::max(max_trunc_m, m);
+      if (m <= eig_small_max<T>()) {
+        tt.k_idx = (int)trunc.size();
+        trunc.push_back(tt);
+        trunc_sup.push_back((int)q);
+        max_trunc_m = std::max(max_trunc_m, m);
+      } else {
+        tt.work = talloc<T>(scr, trunc_big_work_elems<T>(m));
+        big_sup.push_back((int)q);
+        max_big_m = std::max(max_big_m, m);
+        trunc_big.push_back(tt);
+      }
     }
   }
-  // truncation work buffers for the large-m path
-  const int smem_cap = sizeof(T) == 8 ? 110 : 156;
-  if (max_trunc_m > smem_cap)
-    for (auto &tt : trunc) tt.work = talloc<T>(scr, 2 * (size_t)tt.m * tt.m);
+  for (size_t i = 0; i < trunc_big.size(); ++i) trunc_big[i].k_idx = (int)(trunc.size() + i);
   gather.launch(scr, st_);
   // phase A kernels
-  int *d_stat = (int *)scr.alloc(sizeof(int) * (chol.tasks.size() + trunc.size() + 1));
+  int *d_stat = (int *)scr.alloc(sizeof(int) * (chol.tasks.size() + trunc.size() + trunc_big.size() + 1));
   int *d_k = d_stat + chol.tasks.size();
   if (!chol.tasks.empty()) {
     Uploader u;
@@ -559,8 +588,15 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
     launch_trunc<T>((const TruncTask<T> *)(d + o), (int)trunc.size(), d_k, h_.eps, h_.variant,
                     max_trunc_m, st_);
   }
+  if (!trunc_big.empty()) {
+    Uploader u;
+    const size_t o = u.add(trunc_big);
+    char *d = u.upload(scr, st_);
+    launch_trunc_big<T>((const TruncTask<T> *)(d + o), (int)trunc_big.size(), d_k, h_.eps, h_.variant,
+                        max_big_m, st_);
+  }
   // one read of the statuses and ranks
-  const size_t nread = chol.tasks.size() + trunc.size();
+  const size_t nread = chol.tasks.size() + trunc.size() + trunc_big.size();
   int *hb = host_ints(nread + 1);
   if (nread) HS_CUDA(cudaMemcpyAsync(hb, d_stat, sizeof(int) * nread, cudaMemcpyDeviceToHost, st_));
   sync_check();
@@ -568,6 +604,47 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
     if (hb[i] != 0)
       fail(HS_ERR_NOT_SPD, chol.what[i] + " is not positive definite (pivot " + std::to_string(hb[i] - 1) + ")");
   for (size_t i = 0; i < trunc.size(); ++i) S[trunc_sup[i]].k = hb[chol.tasks.size() + i];
+  for (size_t i = 0; i < trunc_big.size(); ++i) S[big_sup[i]].k = hb[chol.tasks.size() + trunc.size() + i];
+  if (!big_sup.empty()) {
+    // U of the large path: re-orthonormalise by CholQR2 (same span)
+    GemmBatch<T> o1, o2, o3, o4;
+    CholBatch<T> oc1, oc2;
+    std::vector<T *> U1s(S.size(), nullptr), U2s(S.size(), nullptr);
+    for (int q : big_sup) {
+      Sup &x = S[q];
+      const int m = x.m, k = x.k;
+      if (k <= 0) continue;
+      T *Sg = talloc<T>(scr, (size_t)k * k), *Lg = talloc<T>(scr, (size_t)k * k);
+      T *Sg2 = talloc<T>(scr, (size_t)k * k), *Lg2 = talloc<T>(scr, (size_t)k * k);
+      U1s[q] = talloc<T>(scr, (size_t)m * m);
+      U2s[q] = talloc<T>(scr, (size_t)m * m);
+      o1.add(x.U, m, 1, x.U, m, 0, Sg, k, k, k, m, T(1), T(0));
+      oc1.add(Sg, k, Lg, k, "level " + std::to_string(lv.level) + " super node " + std::to_string(x.s) + ": U^T U");
+      o2.add(x.U, m, 0, Lg, k, 1, U1s[q], m, m, k, k, T(1), T(0));
+      o3.add(U1s[q], m, 1, U1s[q], m, 0, Sg2, k, k, k, m, T(1), T(0));
+      oc2.add(Sg2, k, Lg2, k, "level " + std::to_string(lv.level) + " super node " + std::to_string(x.s) + ": U^T U");
+      o4.add(U1s[q], m, 0, Lg2, k, 1, U2s[q], m, m, k, k, T(1), T(0));
+    }
+    auto chol_now = [&](CholBatch<T> &cb) {
+      if (cb.tasks.empty()) return;
+      PendingStatus ps;
+      ps.d = (int *)per.alloc(sizeof(int) * cb.tasks.size());
+      ps.what = cb.what;
+      Uploader u;
+      const size_t o = u.add(cb.tasks);
+      char *d = u.upload(scr, st_);
+      launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)cb.tasks.size(), ps.d, cb.max_m, st_);
+      pending_.push_back(ps);
+    };
+    o1.launch(scr, st_);
+    chol_now(oc1);
+    o2.launch(scr, st_);
+    o3.launch(scr, st_);
+    chol_now(oc2);
+    o4.launch(scr, st_);
+    for (int q : big_sup)
+      if (U2s[q]) S[q].U = U2s[q];
+  }
 
   // phase B
   GemmBatch<T> g1, g2, g3, g4, g5, g6, g7, g8;
@@ -791,6 +868,7 @@ void Run<T>::end_level(const PlanLevel &lv, int li) {
     std::vector<int> torder;
     int64_t t = 0;
     wa.max_m = 0;
+    wa.rows_f = wa.rows_b = wa.pch = wa.tch = 0;
     for (int q = 0; q < wa.node_count; ++q, ++rp) {
       const Rec &rc = recs_[rp];
       ApplyNode &an = h_.nodes[rc.node];
@@ -798,6 +876,12 @@ void Run<T>::end_level(const PlanLevel &lv, int li) {
       an.xr = lv.red_made[rc.s] ? xoff(nsup + rc.s) : -1;
       an.toff = t;
       t += an.m;
+      an.row0 = wa.rows_f;
+      wa.rows_f += an.m + an.k;
+      an.brow0 = wa.rows_b;
+      wa.rows_b += an.m;
+      an.pch0 = wa.pch;
+      if (an.k > 0) wa.pch += (an.m + 31) / 32;
       wa.max_m = std::max(wa.max_m, an.m);
       an.nb_first = (int)h_.nbrs.size();
       an.nb_count = (int)rc.N.size();
@@ -822,6 +906,8 @@ void Run<T>::end_level(const PlanLevel &lv, int li) {
       ApplyTarget tg;
       tg.x = xoff(n);
       tg.size = size_[n];
+      tg.ch0 = wa.tch;
+      wa.tch += (tg.size + 31) / 32;
       tg.first = (int)h_.contribs.size();
       tg.count = (int)by_target[n].size();
       for (auto &c : by_target[n]) {
@@ -942,6 +1028,9 @@ void factorize(FactorHandle &h, const hs_csr &A, const hs_opts &o, const double 
   (void)o;
   if (!h.pers) h.pers.reset(new DevArena(256ull << 20));
   if (!h.scratch) h.scratch.reset(new DevArena(64ull << 20));
+  h.pers->reset();     // a refactorization reuses the previous factor's memory
+  h.scratch->reset();
+  h.info = hs_info{};
   if (h.prec == HS_PREC_F64) {
     Run<double> r(h, phi_host);
     r.run();

@@ -45,6 +45,9 @@ struct ApplyNode {
   int64_t toff;      // unknown offset of t_s in the per-wave scratch
   int m, k, dN;
   int nb_first, nb_count;
+  int row0;          // prefix of (m + k) rows inside the wave (forward GEMV rows)
+  int brow0;         // prefix of m rows inside the wave (backward rows)
+  int pch0;          // prefix of 32-column chunks of P_ss inside the wave (k > 0 nodes)
 };
 struct ApplyNbr {
   int64_t x;         // unknown offset of neighbour n
@@ -55,6 +58,7 @@ struct ApplyTarget {  // forward substitution, gathered by neighbour
   int64_t x;
   int size;
   int first, count;
+  int ch0;           // prefix of 32-row chunks inside the wave
 };
 struct ApplyContrib {
   const void *A;     // AsN + col, element (i in s, q in n) at A[i*ld + q]
@@ -68,6 +72,10 @@ struct WaveApply {
   int tgt_first, tgt_count;
   int max_m;
   int64_t tsize;     // unknowns of t scratch used
+  int rows_f;        // sum of (m + k): forward GEMV rows
+  int rows_b;        // sum of m: backward rows
+  int pch;           // sum of 32-column chunks of P_ss
+  int tch;           // sum of 32-row chunks of the targets
 };
 struct LevelApply {
   int level;
@@ -81,6 +89,7 @@ struct FactorHandle {
   double eps = 0.0;
   cudaStream_t stream = nullptr;
   int device = 0;
+  bool valid = false;                  // holds a usable factorization
 
   // permuted CSR (cluster order), FP64, for the SpMV of PCG
   int32_t *d_rowptr = nullptr, *d_col = nullptr;
@@ -107,10 +116,20 @@ struct FactorHandle {
   int root_m = 0;
   const void *root_inv = nullptr;      // A_root^-1 (m x m)
 
+  // cached maps of the pattern (reused by hs_factor_refactor)
+  int32_t *d_src = nullptr;            // permuted entry -> original CSR entry
+  int64_t *d_leaf_dest = nullptr;      // permuted entry -> offset in the leaf blocks (or -1)
+  std::vector<std::pair<int, int>> leaf_blocks;   // leaf block list, in storage order
+  std::vector<int64_t> leaf_block_off;
+  int64_t leaf_total = 0;
+  void *d_phi0 = nullptr;              // leaf preserved vector (GC), factor precision
+  int64_t nnz = 0;
+
   // solve buffers (grown on demand)
   int nrhs_cap = 0;
-  double *d_ws = nullptr, *d_t = nullptr;
-  double *d_pcg = nullptr;             // x, r, p, p2, q (5 n nrhs)
+  int64_t ws_cap = 0, t_cap = 0;
+  void *d_ws = nullptr, *d_t = nullptr;  // apply workspace and scratch, factor precision
+  double *d_pcg = nullptr;             // x, r, p, p2, q, b, z (7 n nrhs), FP64
   double *d_part = nullptr;            // per-block partial sums
   double *d_scal = nullptr;            // per-rhs scalars
   int *d_iflags = nullptr;             // per-rhs ints + block counter

@@ -26,6 +26,9 @@ struct Error {
 void set_error(const std::string &msg);
 [[noreturn]] void fail(int code, const std::string &msg);
 
+// kernel launches of this library in the process (hs_launch_count)
+void count_launch(int n = 1);
+
 #define HS_CUDA(call)                                                                   \
   do {                                                                                  \
     cudaError_t e_ = (call);                                                            \
@@ -110,6 +113,17 @@ void launch_chol_inv(const CholTask<T> *d_tasks, int ntasks, int *d_status, int 
 template <typename T>
 void launch_trunc(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant,
                   int max_m, cudaStream_t st);
+// large super nodes (kernels_eig.cu): tridiagonalisation / bisection / inverse iteration
+template <typename T>
+size_t trunc_big_work_elems(int m);
+template <typename T>
+void launch_trunc_big(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant,
+                      int max_m, cudaStream_t st);
+// largest m handled by the shared-memory Jacobi truncation
+template <typename T>
+constexpr int jacobi_cap() {
+  return sizeof(T) == 8 ? 110 : 156;
+}
 template <typename T>
 void launch_scatter_values(const double *val, const int64_t *dest, int64_t nnz, T *pool,
                            cudaStream_t st);

@@ -17,6 +17,7 @@
 #include <cfloat>
 
 #include "hs_internal.h"
+#include "trunc_common.cuh"
 
 namespace hs {
 
@@ -187,14 +188,16 @@ __global__ void __launch_bounds__(256) k_sum(const SumTask<T> *__restrict__ task
 // ---------------------------------------------------------------------------
 // Cholesky and inverse of the factor, one CTA per matrix
 // ---------------------------------------------------------------------------
-constexpr int CHOL_THREADS = 256;
+constexpr int CHOL_THREADS = 512;
 
 // W (ld m) holds A on entry; on exit the lower triangle holds L^-1 and the
 // strict upper triangle is zero.  Returns 0 or (failing pivot + 1).
 template <typename T>
 __device__ int chol_inv_inplace(T *W, int m, T *tmp, int *flag) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  // right-looking Cholesky on the lower triangle
+  // right-looking Cholesky on the lower triangle; column j staged in tmp, one
+  // warp per trailing row (lanes over columns, coalesced)
+  const int warp0 = tid >> 5, lane0 = tid & 31, nw0 = nt >> 5;
   for (int j = 0; j < m; ++j) {
     if (tid == 0) {
       const T d = W[j * m + j];
@@ -207,32 +210,35 @@ __device__ int chol_inv_inplace(T *W, int m, T *tmp, int *flag) {
     __syncthreads();
     if (*flag) return *flag;
     const T djj = W[j * m + j];
-    for (int i = j + 1 + tid; i < m; i += nt) W[i * m + j] /= djj;
+    for (int i = j + 1 + tid; i < m; i += nt) {
+      const T l = W[i * m + j] / djj;
+      W[i * m + j] = l;
+      tmp[i] = l;
+    }
     __syncthreads();
-    const int r = m - j - 1;  // trailing size
-    const int64_t cnt = (int64_t)r * (r + 1) / 2;
-    for (int64_t e = tid; e < cnt; e += nt) {
-      // e -> (ii, cc) with 0 <= cc <= ii < r (row-major lower triangle)
-      int ii = (int)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-      while ((int64_t)ii * (ii + 1) / 2 > e) --ii;
-      while ((int64_t)(ii + 1) * (ii + 2) / 2 <= e) ++ii;
-      const int cc = (int)(e - (int64_t)ii * (ii + 1) / 2);
-      const int i = j + 1 + ii, c = j + 1 + cc;
-      W[i * m + c] -= W[i * m + j] * W[c * m + j];
+    for (int i = j + 1 + warp0; i < m; i += nw0) {
+      const T li = tmp[i];
+      T *row = W + (int64_t)i * m;
+      for (int c = j + 1 + lane0; c <= i; c += 32) row[c] -= li * tmp[c];
     }
     __syncthreads();
   }
-  // in-place inverse of the lower-triangular factor (column j from the last
-  // one down: x = L[j+1:, j]; x <- -Linv[j+1:, j+1:] x / L[j][j])
+  // in-place inverse of the lower-triangular factor, column j from the last
+  // one down: Linv[i][j] = -(sum_{p=j+1..i} Linv[i][p] L[p][j]) / L[j][j],
+  // with the columns right of j already inverted.  Column j of L is staged in
+  // tmp; one warp per entry i.
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
   for (int j = m - 1; j >= 0; --j) {
+    for (int p = j + 1 + tid; p < m; p += nt) tmp[p] = W[p * m + j];
+    __syncthreads();
     const T inv = T(1) / W[j * m + j];
-    for (int i = j + 1 + tid; i < m; i += nt) {
+    for (int i = j + 1 + warp; i < m; i += nw) {
       T s = T(0);
-      for (int p = j + 1; p <= i; ++p) s = fma(W[i * m + p], W[p * m + j], s);
-      tmp[i] = -s * inv;
+      for (int p = j + 1 + lane; p <= i; p += 32) s = fma(W[i * m + p], tmp[p], s);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) W[i * m + j] = -s * inv;
     }
     __syncthreads();
-    for (int i = j + 1 + tid; i < m; i += nt) W[i * m + j] = tmp[i];
     if (tid == 0) W[j * m + j] = inv;
     __syncthreads();
   }
@@ -325,7 +331,10 @@ __device__ int jacobi_eig(T *A, T *V, int m, bool want_v, JacobiShared<T> sh, in
   // scale for the absolute floor of the rotation test
   T scale = T(0);
   for (int i = 0; i < m; ++i) scale = fmax(scale, fabs(A[i * m + i]));
-  const T floor_abs = Lim<T>::eps() * Lim<T>::eps() * scale + Lim<T>::tiny();
+  // entries below eps * scale move no eigenvalue by more than the rounding of
+  // the whole computation: treat them as converged (otherwise rounding noise
+  // in the near-null space keeps every sweep busy)
+  const T floor_abs = Lim<T>::eps() * scale + Lim<T>::tiny();
   const int mp = m + (m & 1);
   const int np = mp / 2;
   int sweep = 0;
@@ -535,6 +544,12 @@ __global__ void __launch_bounds__(TRUNC_THREADS) k_trunc(const TruncTask<T> *__r
     if (tid == 0) kout[t.k_idx] = k;
     return;
   }
+  if (eps == 0.0) {
+    // no truncation: complete the GC basis to all of R^m (closed form)
+    gc_complete<T>(t.U, m, k1, (double *)A, red);
+    if (tid == 0) kout[t.k_idx] = m;
+    return;
+  }
   double lmax = 0.0;
   if (eps > 0.0) {
     jacobi_eig<T>(A, V, m, false, sh, max_sweeps);
@@ -543,31 +558,31 @@ __global__ void __launch_bounds__(TRUNC_THREADS) k_trunc(const TruncTask<T> *__r
   }
   // ---- matrix whose leading eigenvectors give U_2: (I - U1 U1^T) G (I - U1 U1^T),
   // or the projector I - U1 U1^T itself when eps == 0 (complete basis)
-  // X = G U1 (m x k1) in V's columns 0..k1-1 (scratch, ld m)
+  // X = G U1 (m x k1) in V's columns 0..k1-1 (scratch, ld m), all in T
   if (eps > 0.0) {
     for (int w = tid; w < m * k1; w += nt) {
       const int i = w / k1, a = w % k1;
-      double s = 0.0;
-      for (int j = 0; j < m; ++j) s += (double)t.G[(int64_t)i * m + j] * (double)t.U[(int64_t)j * m + a];
-      V[i * m + a] = (T)s;
+      T s = T(0);
+      for (int j = 0; j < m; ++j) s = fma(t.G[(int64_t)i * m + j], t.U[(int64_t)j * m + a], s);
+      V[i * m + a] = s;
     }
     __syncthreads();
-    double c[2][2] = {{0, 0}, {0, 0}};
+    T c[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
     for (int a = 0; a < k1; ++a)
       for (int b = 0; b < k1; ++b) {
         double s = 0.0;
-        for (int i = tid; i < m; i += nt) s += (double)t.U[(int64_t)i * m + a] * (double)V[i * m + b];
-        c[a][b] = block_sum<T>(s, red);
+        for (int i = tid; i < m; i += nt) s += (double)(t.U[(int64_t)i * m + a] * V[i * m + b]);
+        c[a][b] = (T)block_sum<T>(s, red);
       }
     for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
       const int i = (int)(e / m), j = (int)(e % m);
-      double v = (double)t.G[e];
+      T v = t.G[e];
       for (int a = 0; a < k1; ++a) {
-        const double ui = (double)t.U[(int64_t)i * m + a], uj = (double)t.U[(int64_t)j * m + a];
-        v -= ui * (double)V[j * m + a] + (double)V[i * m + a] * uj;
-        for (int b = 0; b < k1; ++b) v += ui * c[a][b] * (double)t.U[(int64_t)j * m + b];
+        const T ui = t.U[(int64_t)i * m + a], uj = t.U[(int64_t)j * m + a];
+        v = fma(-ui, V[j * m + a], fma(-V[i * m + a], uj, v));
+        for (int b = 0; b < k1; ++b) v = fma(ui * c[a][b], t.U[(int64_t)j * m + b], v);
       }
-      A[e] = (T)v;
+      A[e] = v;
     }
     thr = eps * eps * lmax;
   } else {
@@ -624,6 +639,7 @@ void launch_gemm(const GemmTask<T> *d_tasks, const int *d_tile_start, int ntasks
                  cudaStream_t st) {
   if (ntasks == 0 || total_tiles == 0) return;
   k_gemm<T><<<total_tiles, 256, 0, st>>>(d_tasks, d_tile_start, ntasks);
+  count_launch();
   HS_CUDA(cudaGetLastError());
 }
 
@@ -632,6 +648,7 @@ void launch_sum(const SumTask<T> *d_tasks, const SumSrc<T> *d_srcs, const int *d
                 int ntasks, int total_tiles, cudaStream_t st) {
   if (ntasks == 0 || total_tiles == 0) return;
   k_sum<T><<<total_tiles, 256, 0, st>>>(d_tasks, d_srcs, d_tile_start, ntasks);
+  count_launch();
   HS_CUDA(cudaGetLastError());
 }
 
@@ -655,6 +672,7 @@ void launch_chol_inv(const CholTask<T> *d_tasks, int ntasks, int *d_status, int 
                                  (int)sm));
     k_chol_inv<T, false><<<ntasks, CHOL_THREADS, sm, st>>>(d_tasks, d_status);
   }
+  count_launch();
   HS_CUDA(cudaGetLastError());
 }
 
@@ -678,6 +696,7 @@ void launch_trunc(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps,
                                  (int)sm));
     k_trunc<T, false><<<ntasks, TRUNC_THREADS, sm, st>>>(d_tasks, d_k, eps, variant);
   }
+  count_launch();
   HS_CUDA(cudaGetLastError());
 }
 
@@ -687,6 +706,7 @@ void launch_scatter_values(const double *val, const int64_t *dest, int64_t nnz, 
   if (nnz == 0) return;
   const int grid = (int)std::min<int64_t>((nnz + 255) / 256, 152 * 16);
   k_scatter_values<T><<<grid, 256, 0, st>>>(val, dest, nnz, pool);
+  count_launch();
   HS_CUDA(cudaGetLastError());
 }
 
@@ -695,6 +715,7 @@ void launch_gather_values(const double *val, const int32_t *src, int64_t nnz, do
   if (nnz == 0) return;
   const int grid = (int)std::min<int64_t>((nnz + 255) / 256, 152 * 16);
   k_gather_values<<<grid, 256, 0, st>>>(val, src, nnz, out);
+  count_launch();
   HS_CUDA(cudaGetLastError());
 }
 

@@ -1,0 +1,615 @@
+// Truncation of large super nodes (m above the shared-memory Jacobi limit):
+// symmetric eigen-decomposition of the Gram matrix by Householder
+// tridiagonalisation, Sturm-sequence bisection and inverse iteration.
+//
+// One CTA (1024 threads) per super node:
+//   1. GC basis U_1 = orth[phi_s, A_sw phi_w] (Sec. 6), as in the Jacobi path.
+//   2. ||A_sw||_2^2 = lambda_max(G): tridiagonalise G, bisection for the top
+//      eigenvalue (GC only; LoRaSp takes it from step 3).
+//   3. J = G (LoRaSp), (I - U1 U1^T) G (I - U1 U1^T) (GC) or I - U1 U1^T (GC,
+//      eps = 0).  Tridiagonalise J = Q T Q^T; k2 = #{lambda(T) > thr} by one
+//      Sturm count (FP64), thr = eps^2 lambda_max(G) (Sec. 3.2, strict).
+//   4. The k2 largest eigenvalues of T by bisection (FP64), their eigenvectors
+//      by inverse iteration on T (tridiagonal LU with partial pivoting, three
+//      steps, modified Gram-Schmidt inside clusters of eigenvalues closer than
+//      10 u ||T||), then U_2 = Q Y by the stored Householder reflectors.
+// The host re-orthonormalises [U_1, U_2] afterwards (CholQR2), which keeps its
+// span.  The tridiagonalisation works in global memory until the trailing
+// block fits in shared memory, then finishes there.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hs_internal.h"
+#include "trunc_common.cuh"
+
+namespace hs {
+
+namespace {
+
+constexpr int BT = 1024;  // threads per CTA
+
+__device__ double bsum(double v, double *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[32] = s;
+  }
+  __syncthreads();
+  const double s = red[32];
+  __syncthreads();
+  return s;
+}
+
+// Block-wide sum in T (red: 33 T of shared memory); every thread gets the total.
+// Reductions inside the per-step loops stay in the factor precision: on this
+// GPU FP64 instructions issue at a small fraction of the FP32 rate.
+template <typename T>
+__device__ T bsum_t(T v, T *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    T s = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : T(0);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) red[32] = s;
+  }
+  __syncthreads();
+  const T r = red[32];
+  __syncthreads();
+  return r;
+}
+
+// Shared scratch of the large-truncation kernel (sizes in elements).
+template <typename T>
+struct Big {
+  double *d, *e, *pw, *red;   // tridiagonal in FP64 (rank decision), work vector
+  T *dt, *et, *lam;           // tridiagonal and selected eigenvalues in T
+  T *v;          // Householder vector of the current step
+  T *wt;         // p, then w = p - K v of the current step
+  T *redt;       // 33 T of reduction scratch
+  T *tau;        // reflector coefficients
+  T *tile;       // trailing block once it fits in shared memory
+  int tile_cap;  // max trailing size held in shared memory
+};
+
+// Householder tridiagonalisation of the symmetric m x m matrix A (global, ld m,
+// full storage; destroyed).  On exit d (diagonal) and e (sub-diagonal) hold
+// T, reflector k is I - tau[k] v v^T with v[0] = 1 on rows k+1.. and v[1..]
+// stored in A[k][k+2..].
+template <typename T>
+__device__ void tridiag(T *A, int m, Big<T> &b) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  // element (i, j) of the working matrix is W[(i - off) * ld + (j - off)]
+  T *W = A;
+  int off = 0, ld = m;
+  bool in_smem = false;
+  for (int k = 0; k + 2 < m; ++k) {
+    const int n1 = m - k - 1;
+    if (!in_smem && n1 + 1 <= b.tile_cap) {
+      // move the trailing block rows/cols k.. into shared memory
+      const int ls = m - k;
+      for (int64_t q = tid; q < (int64_t)ls * ls; q += nt) {
+        const int i = (int)(q / ls), j = (int)(q % ls);
+        b.tile[q] = A[(int64_t)(k + i) * m + k + j];
+      }
+      W = b.tile;
+      off = k;
+      ld = ls;
+      in_smem = true;
+      __syncthreads();
+    }
+    const T *rowk = W + (int64_t)(k - off) * ld + (k - off);   // rowk[j] = A[k][k + j]
+    T s2t = T(0);
+    for (int i = 1 + tid; i <= n1; i += nt) s2t = fma(rowk[i], rowk[i], s2t);
+    const double xn2 = (double)bsum_t<T>(s2t, b.redt);
+    const double alpha = (double)rowk[1];
+    const double sig = xn2 - alpha * alpha;
+    double tau = 0.0, beta = alpha, scale = 0.0;
+    if (sig > 0.0) {
+      beta = -copysign(sqrt(xn2), alpha);
+      tau = (beta - alpha) / beta;
+      scale = 1.0 / (alpha - beta);
+    }
+    const T scale_t = (T)scale, tau_t = (T)tau;
+    for (int i = tid; i < n1; i += nt) {
+      const T vi = (i == 0) ? T(1) : rowk[1 + i] * scale_t;
+      b.v[i] = vi;
+      if (i >= 1) A[(int64_t)k * m + k + 1 + i] = vi;  // keep the reflector in global row k
+    }
+    if (tid == 0) {
+      b.d[k] = (double)rowk[0];
+      b.e[k] = beta;
+      b.tau[k] = tau_t;
+    }
+    __syncthreads();
+    if (tau != 0.0) {
+      T *A22 = W + (int64_t)(k + 1 - off) * ld + (k + 1 - off);
+      // p = tau * A22 v, one warp per row, four independent partial sums
+      for (int i = warp; i < n1; i += nw) {
+        const T *row = A22 + (int64_t)i * ld;
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        int j = lane;
+        for (; j + 96 < n1; j += 128) {
+          a0 = fma(row[j], b.v[j], a0);
+          a1 = fma(row[j + 32], b.v[j + 32], a1);
+          a2 = fma(row[j + 64], b.v[j + 64], a2);
+          a3 = fma(row[j + 96], b.v[j + 96], a3);
+        }
+        for (; j < n1; j += 32) a0 = fma(row[j], b.v[j], a0);
+        T acc = (a0 + a1) + (a2 + a3);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) b.wt[i] = tau_t * acc;
+      }
+      __syncthreads();
+      T pvt = T(0);
+      for (int i = tid; i < n1; i += nt) pvt = fma(b.wt[i], b.v[i], pvt);
+      const T K = T(0.5) * tau_t * bsum_t<T>(pvt, b.redt);
+      for (int i = tid; i < n1; i += nt) b.wt[i] = fma(-K, b.v[i], b.wt[i]);  // w
+      __syncthreads();
+      // A22 -= v w^T + w v^T, one warp per row
+      for (int i = warp; i < n1; i += nw) {
+        T *row = A22 + (int64_t)i * ld;
+        const T vi = b.v[i], wi = b.wt[i];
+#pragma unroll 4
+        for (int j = lane; j < n1; j += 32) row[j] = fma(-vi, b.wt[j], fma(-wi, b.v[j], row[j]));
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    auto at = [&](int i, int j) { return (double)W[(int64_t)(i - off) * ld + (j - off)]; };
+    if (m >= 2) {
+      b.d[m - 2] = at(m - 2, m - 2);
+      b.e[m - 2] = at(m - 1, m - 2);
+      b.tau[m - 2] = T(0);
+    }
+    b.d[m - 1] = at(m - 1, m - 1);
+    b.e[m - 1] = 0.0;
+    b.tau[m - 1] = T(0);
+  }
+  __syncthreads();
+  for (int i = tid; i < m; i += nt) {
+    b.dt[i] = (T)b.d[i];
+    b.et[i] = (T)b.e[i];
+  }
+  __syncthreads();
+}
+
+template <typename R>
+__device__ __forceinline__ R unit_round();
+template <>
+__device__ __forceinline__ double unit_round<double>() { return 2.220446049250313e-16; }
+template <>
+__device__ __forceinline__ float unit_round<float>() { return 1.1920929e-07f; }
+
+// number of eigenvalues of the tridiagonal (d, e) below sigma (Sturm sequence)
+template <typename R>
+__device__ int sturm_below(const R *d, const R *e, int m, R sigma, R pivmin) {
+  int c = 0;
+  R q = d[0] - sigma;
+  if (fabs(q) < pivmin) q = -pivmin;
+  if (q < R(0)) ++c;
+  for (int i = 1; i < m; ++i) {
+    q = d[i] - sigma - e[i - 1] * e[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    if (q < R(0)) ++c;
+  }
+  return c;
+}
+
+template <typename R>
+struct Gersh {
+  R lo, hi, pivmin, tnorm;
+};
+
+// Gershgorin interval of the tridiagonal (every thread computes the same)
+template <typename R>
+__device__ Gersh<R> gershgorin(const R *d, const R *e, int m) {
+  Gersh<R> g;
+  R lo = d[0], hi = d[0], emax = R(0);
+  for (int i = 0; i < m; ++i) {
+    const R r = (i > 0 ? fabs(e[i - 1]) : R(0)) + (i + 1 < m ? fabs(e[i]) : R(0));
+    lo = fmin(lo, d[i] - r);
+    hi = fmax(hi, d[i] + r);
+    emax = fmax(emax, e[i] * e[i]);
+  }
+  g.tnorm = fmax(fabs(lo), fabs(hi));
+  const R pad = unit_round<R>() * g.tnorm * R(2 * m) + R(1e-30);
+  g.lo = lo - pad;
+  g.hi = hi + pad;
+  g.pivmin = fmax(R(1e-30) * fmax(R(1), emax), R(1e-35));
+  return g;
+}
+
+// idx-th smallest eigenvalue (0-based) by bisection
+template <typename R>
+__device__ R bisect_eig(const R *d, const R *e, int m, int idx, const Gersh<R> &g) {
+  R lo = g.lo, hi = g.hi;
+  const R tol = R(4) * unit_round<R>() * g.tnorm;
+  for (int it = 0; it < 200 && hi - lo > tol; ++it) {
+    const R mid = R(0.5) * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_below<R>(d, e, m, mid, g.pivmin) <= idx)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return R(0.5) * (lo + hi);
+}
+
+__device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b) {
+  uint32_t x = a * 0x9E3779B9u ^ (b + 0x7F4A7C15u);
+  x ^= x >> 16;
+  x *= 0x85EBCA6Bu;
+  x ^= x >> 13;
+  x *= 0xC2B2AE35u;
+  x ^= x >> 16;
+  return (float)(x >> 8) * (2.0f / 16777216.0f) - 1.0f;
+}
+
+// Inverse iteration for eigenvalue lam of the tridiagonal (d, e): LU of
+// T - lam I with partial pivoting (rows i, i+1 interchanged when the
+// sub-diagonal dominates), three solves from a fixed pseudo-random start,
+// modified Gram-Schmidt against `nprev` previous vectors of the same cluster
+// of close eigenvalues.  y: output (length m); lu: 4 m of scratch; flags: m bytes.
+template <typename R>
+__device__ void inverse_iteration(const R *d, const R *e, int m, R lam, R tnorm, R *y, const R *prev,
+                                  int nprev, R *lu, unsigned char *flags, uint32_t seed) {
+  R *u0 = lu, *u1 = lu + m, *u2 = lu + 2 * m, *l = lu + 3 * m;
+  const R small = unit_round<R>() * tnorm + R(1e-30);
+  R a = d[0] - lam, c = (m > 1) ? e[0] : R(0);
+  for (int i = 0; i + 1 < m; ++i) {
+    const R bsub = e[i];
+    const R an = d[i + 1] - lam;
+    const R cn = (i + 2 < m) ? e[i + 1] : R(0);
+    if (fabs(a) >= fabs(bsub)) {
+      const R piv = (a == R(0)) ? small : a;
+      const R mult = bsub / piv;
+      u0[i] = piv;
+      u1[i] = c;
+      u2[i] = R(0);
+      l[i] = mult;
+      flags[i] = 0;
+      a = an - mult * c;
+      c = cn;
+    } else {
+      const R mult = a / bsub;
+      u0[i] = bsub;
+      u1[i] = an;
+      u2[i] = cn;
+      l[i] = mult;
+      flags[i] = 1;
+      a = c - mult * an;
+      c = -mult * cn;
+    }
+  }
+  u0[m - 1] = a;
+  for (int i = 0; i < m; ++i)
+    if (fabs(u0[i]) < small) u0[i] = copysign(small, u0[i]);
+  for (int i = 0; i < m; ++i) y[i] = (R)hash_unit(seed, (uint32_t)i);
+  for (int it = 0; it < 3; ++it) {
+    for (int i = 0; i + 1 < m; ++i) {
+      if (flags[i]) {
+        const R t = y[i];
+        y[i] = y[i + 1];
+        y[i + 1] = t - l[i] * y[i];
+      } else {
+        y[i + 1] -= l[i] * y[i];
+      }
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      R s = y[i];
+      if (i + 1 < m) s -= u1[i] * y[i + 1];
+      if (i + 2 < m) s -= u2[i] * y[i + 2];
+      y[i] = s / u0[i];
+    }
+    for (int pass = 0; pass < 2; ++pass)
+      for (int p = 0; p < nprev; ++p) {
+        const R *q = prev + (size_t)p * m;
+        R dot = R(0);
+        for (int i = 0; i < m; ++i) dot += q[i] * y[i];
+        for (int i = 0; i < m; ++i) y[i] -= dot * q[i];
+      }
+    // normalise, scaling by the largest entry first to keep the sum in range
+    R big = R(0);
+    for (int i = 0; i < m; ++i) big = fmax(big, fabs(y[i]));
+    const R sc = big > R(0) ? R(1) / big : R(0);
+    R nrm = R(0);
+    for (int i = 0; i < m; ++i) nrm += (y[i] * sc) * (y[i] * sc);
+    nrm = sqrt(nrm);
+    const R inv = nrm > R(0) ? sc / nrm : R(0);
+    for (int i = 0; i < m; ++i) y[i] *= inv;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict__ tasks, int *__restrict__ kout,
+                                                 double eps, int variant, int tile_cap) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[33];
+  __shared__ int s_k2;
+  const TruncTask<T> t = tasks[blockIdx.x];
+  const int m = t.m;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // shared layout
+  Big<T> b;
+  unsigned char *p = smem_raw;
+  b.d = (double *)p;
+  p += sizeof(double) * m;
+  b.e = (double *)p;
+  p += sizeof(double) * m;
+  b.pw = (double *)p;
+  p += sizeof(double) * m;
+  const int me = (m + 1) & ~1;
+  b.dt = (T *)p;
+  p += sizeof(T) * me;
+  b.et = (T *)p;
+  p += sizeof(T) * me;
+  b.lam = (T *)p;
+  p += sizeof(T) * me;
+  b.v = (T *)p;
+  p += sizeof(T) * me;
+  b.tau = (T *)p;
+  p += sizeof(T) * me;
+  b.wt = (T *)p;
+  p += sizeof(T) * me;
+  b.redt = (T *)p;
+  p += sizeof(T) * 34;
+  p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+  b.tile = (T *)p;
+  b.tile_cap = tile_cap;
+  b.red = red;
+  // global work: A (m^2), Y (m^2), LU (4 m^2), all T; flags (m^2 bytes)
+  T *A = t.work;
+  T *Y = t.work + (size_t)m * m;
+  T *LU = Y + (size_t)m * m;
+  unsigned char *FL = (unsigned char *)(LU + 4 * (size_t)m * m);
+  if (m == 0) {
+    if (tid == 0) kout[t.k_idx] = 0;
+    return;
+  }
+  // ---- GC basis U_1 (same rule as the Jacobi path)
+  int k1 = 0;
+  if (variant != HS_LORASP) {
+    double s = 0.0;
+    for (int i = tid; i < m; i += nt) s += (double)t.phi[i] * (double)t.phi[i];
+    const double nphi = sqrt(bsum(s, red));
+    if (nphi > 0.0) {
+      for (int i = tid; i < m; i += nt) t.U[(int64_t)i * m] = (T)((double)t.phi[i] / nphi);
+      k1 = 1;
+    }
+    __syncthreads();
+    s = 0.0;
+    for (int i = tid; i < m; i += nt) s += (double)t.a[i] * (double)t.a[i];
+    const double na = sqrt(bsum(s, red));
+    if (na > 0.0) {
+      for (int i = tid; i < m; i += nt) b.pw[i] = (double)t.a[i];
+      __syncthreads();
+      for (int pass = 0; pass < 2 && k1 == 1; ++pass) {
+        double dd = 0.0;
+        for (int i = tid; i < m; i += nt) dd += (double)t.U[(int64_t)i * m] * b.pw[i];
+        dd = bsum(dd, red);
+        for (int i = tid; i < m; i += nt) b.pw[i] -= dd * (double)t.U[(int64_t)i * m];
+        __syncthreads();
+      }
+      double sv = 0.0;
+      for (int i = tid; i < m; i += nt) sv += b.pw[i] * b.pw[i];
+      const double nv = sqrt(bsum(sv, red));
+      if (nv > 1e-12 * na) {
+        for (int i = tid; i < m; i += nt) t.U[(int64_t)i * m + k1] = (T)(b.pw[i] / nv);
+        ++k1;
+      }
+      __syncthreads();
+    }
+  }
+  const bool gc = variant != HS_LORASP;
+  if (gc && eps == 0.0) {
+    // no truncation: complete the GC basis to all of R^m (closed form)
+    gc_complete<T>(t.U, m, k1, (double *)Y, red);
+    if (tid == 0) kout[t.k_idx] = m;
+    return;
+  }
+  // ---- lambda_max(G)
+  double lmax = 0.0;
+  if (gc && eps > 0.0) {
+    for (int64_t q = tid; q < (int64_t)m * m; q += nt) A[q] = t.G[q];
+    __syncthreads();
+    tridiag<T>(A, m, b);
+    const Gersh<T> g = gershgorin<T>(b.dt, b.et, m);
+    lmax = (double)bisect_eig<T>(b.dt, b.et, m, m - 1, g);
+    __syncthreads();
+  }
+  // ---- J
+  if (!gc) {
+    for (int64_t q = tid; q < (int64_t)m * m; q += nt) A[q] = t.G[q];
+  } else if (eps > 0.0) {
+    // X = G U1 in Y's first columns, c = U1^T X; one warp per row of G
+    {
+      const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+      for (int i = warp; i < m; i += nw)
+        for (int a = 0; a < k1; ++a) {
+          T s = T(0);
+          for (int j = lane; j < m; j += 32) s = fma(t.G[(int64_t)i * m + j], t.U[(int64_t)j * m + a], s);
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          if (lane == 0) Y[(size_t)a * m + i] = s;
+        }
+    }
+    __syncthreads();
+    T c[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+    for (int a = 0; a < k1; ++a)
+      for (int bb = 0; bb < k1; ++bb) {
+        T s = T(0);
+        for (int i = tid; i < m; i += nt) s = fma(t.U[(int64_t)i * m + a], Y[(size_t)bb * m + i], s);
+        c[a][bb] = bsum_t<T>(s, b.redt);
+      }
+    // J = G - U1 X^T - X U1^T + U1 c U1^T, one warp per row
+    {
+      const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+      for (int i = warp; i < m; i += nw) {
+        T ui[2], xi[2], cu[2];
+        for (int a = 0; a < 2; ++a) {
+          ui[a] = a < k1 ? t.U[(int64_t)i * m + a] : T(0);
+          xi[a] = a < k1 ? Y[(size_t)a * m + i] : T(0);
+        }
+        for (int bb = 0; bb < 2; ++bb) cu[bb] = ui[0] * c[0][bb] + ui[1] * c[1][bb];
+        for (int j = lane; j < m; j += 32) {
+          T v = t.G[(int64_t)i * m + j];
+          for (int a = 0; a < k1; ++a) {
+            const T uj = t.U[(int64_t)j * m + a];
+            v = fma(-ui[a], Y[(size_t)a * m + j], fma(-xi[a], uj, v));
+            v = fma(cu[a], uj, v);
+          }
+          A[(int64_t)i * m + j] = v;
+        }
+      }
+    }
+  } else {
+    for (int64_t q = tid; q < (int64_t)m * m; q += nt) {
+      const int i = (int)(q / m), j = (int)(q % m);
+      double v = (i == j) ? 1.0 : 0.0;
+      for (int a = 0; a < k1; ++a) v -= (double)t.U[(int64_t)i * m + a] * (double)t.U[(int64_t)j * m + a];
+      A[q] = (T)v;
+    }
+  }
+  __syncthreads();
+  tridiag<T>(A, m, b);
+  const Gersh<T> g = gershgorin<T>(b.dt, b.et, m);
+  double thr;
+  if (!gc) {
+    lmax = (double)bisect_eig<T>(b.dt, b.et, m, m - 1, g);
+    thr = eps * eps * lmax;
+  } else {
+    thr = (eps > 0.0) ? eps * eps * lmax : 0.5;
+  }
+  // ---- rank: eigenvalues strictly above thr, one Sturm count in FP64
+  if (tid == 0) {
+    const Gersh<double> gd = gershgorin<double>(b.d, b.e, m);
+    int k2 = m - sturm_below<double>(b.d, b.e, m, thr, gd.pivmin);
+    if (k2 > m - k1) k2 = m - k1;
+    if (k2 < 0) k2 = 0;
+    s_k2 = k2;
+  }
+  __syncthreads();
+  const int k2 = s_k2;
+  // ---- the k2 largest eigenvalues, descending (shifts for inverse iteration)
+  for (int j = tid; j < k2; j += nt) b.lam[j] = bisect_eig<T>(b.dt, b.et, m, m - 1 - j, g);
+  __syncthreads();
+  // ---- eigenvectors of T by inverse iteration.  Only the span of the selected
+  // vectors matters and the host re-orthonormalises them (CholQR2), which
+  // tolerates the overlap u ||T|| / gap that inverse iteration leaves between
+  // vectors of distinct eigenvalues.  Vectors are orthogonalised against each
+  // other only inside clusters closer than 10 u ||T||, where they could come
+  // out nearly parallel; a cluster is handled by one thread in order.
+  const T ortol = T(10) * unit_round<T>() * g.tnorm;
+  // cluster starts (thread 0 scans; b.pw reused as an int list)
+  int *starts = (int *)b.pw;
+  __shared__ int s_nc;
+  if (tid == 0) {
+    int nc = 0;
+    for (int j = 0; j < k2; ++j)
+      if (j == 0 || b.lam[j - 1] - b.lam[j] >= ortol) starts[nc++] = j;
+    starts[nc] = k2;
+    s_nc = nc;
+  }
+  __syncthreads();
+  const int nc = s_nc;
+  {
+    // each worker thread owns a slot of the shared tile: u0,u1,u2,l,y (5 m T) + m flags
+    const size_t tile_bytes = (size_t)b.tile_cap * b.tile_cap * sizeof(T);
+    const size_t slot_bytes = ((5 * (size_t)m * sizeof(T) + (size_t)m + 15) / 16) * 16;
+    int nslot = (int)(tile_bytes / slot_bytes);
+    if (nslot > nt) nslot = nt;
+    if (nslot < 1) nslot = 1;
+    if (tid < nslot) {
+      unsigned char *slot = (unsigned char *)b.tile + (size_t)tid * slot_bytes;
+      T *lu = (T *)slot;
+      T *ys = lu + 4 * (size_t)m;
+      unsigned char *fl = (unsigned char *)(ys + m);
+      for (int c = tid; c < nc; c += nslot) {
+        const int j0 = starts[c], j1 = starts[c + 1];
+        for (int q = j0; q < j1; ++q) {
+          inverse_iteration<T>(b.dt, b.et, m, b.lam[q], g.tnorm, ys, Y + (size_t)j0 * m, q - j0, lu, fl,
+                               (uint32_t)(q * 7919 + 17));
+          for (int i = 0; i < m; ++i) Y[(size_t)q * m + i] = ys[i];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // ---- back-transformation U_2 = Q Y (reflectors in reverse order): columns
+  // staged in shared memory in batches, one warp per column
+  {
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    const size_t tile_elems = (size_t)b.tile_cap * b.tile_cap;
+    int batch = (int)(tile_elems / (size_t)m);
+    if (batch < 1) batch = 1;
+    for (int jb = 0; jb < k2; jb += batch) {
+      const int nb = min(batch, k2 - jb);
+      T *ysm = b.tile;
+      for (int64_t q = tid; q < (int64_t)nb * m; q += nt) ysm[q] = Y[(size_t)jb * m + q];
+      __syncthreads();
+      for (int j = warp; j < nb; j += nw) {
+        T *y = ysm + (size_t)j * m;
+        for (int k = m - 3; k >= 0; --k) {
+          const T tk = b.tau[k];
+          if (tk == T(0)) continue;
+          const int n1 = m - k - 1;
+          const T *vrow = A + (int64_t)k * m + k + 1;  // v[0] = 1 implicit, v[i] at vrow[i] for i >= 1
+          T s = T(0);
+          for (int i = lane; i < n1; i += 32) s = fma(i == 0 ? T(1) : vrow[i], y[k + 1 + i], s);
+          for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+          s *= tk;
+          for (int i = lane; i < n1; i += 32) y[k + 1 + i] -= s * (i == 0 ? T(1) : vrow[i]);
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      for (int64_t q = tid; q < (int64_t)m * nb; q += nt) {
+        const int i = (int)(q / nb), j = (int)(q % nb);
+        t.U[(int64_t)i * m + k1 + jb + j] = ysm[(size_t)j * m + i];
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) kout[t.k_idx] = k1 + k2;
+}
+
+}  // namespace
+
+template <typename T>
+size_t trunc_big_work_elems(int m) {
+  // A, Y, LU (6 m^2 T) + flags (m^2 bytes); Y also holds 2 m doubles of scratch
+  const size_t bytes = sizeof(T) * 6 * (size_t)m * m + (size_t)m * m + 64;
+  return (bytes + sizeof(T) - 1) / sizeof(T);
+}
+
+template <typename T>
+void launch_trunc_big(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant, int max_m,
+                      cudaStream_t st) {
+  if (ntasks == 0) return;
+  const size_t fixed = 3 * sizeof(double) * (size_t)max_m + 6 * sizeof(T) * (size_t)((max_m + 1) & ~1) +
+                       34 * sizeof(T) + 48;
+  const size_t budget = 200 * 1024;
+  int cap = 0;
+  while ((size_t)(cap + 1) * (cap + 1) * sizeof(T) + fixed <= budget) ++cap;
+  const size_t sm = fixed + (size_t)cap * cap * sizeof(T);
+  HS_CUDA(cudaFuncSetAttribute(k_trunc_big<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_trunc_big<T><<<ntasks, BT, sm, st>>>(d_tasks, d_k, eps, variant, cap);
+  count_launch();
+  HS_CUDA(cudaGetLastError());
+}
+
+template size_t trunc_big_work_elems<double>(int);
+template size_t trunc_big_work_elems<float>(int);
+template void launch_trunc_big<double>(const TruncTask<double> *, int, int *, double, int, int, cudaStream_t);
+template void launch_trunc_big<float>(const TruncTask<float> *, int, int *, double, int, int, cudaStream_t);
+
+}  // namespace hs

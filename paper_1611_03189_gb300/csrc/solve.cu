@@ -24,193 +24,264 @@ namespace hs {
 
 namespace {
 
-constexpr int AT = 256;     // threads of the apply kernels
-constexpr int MAXR = 16;    // right-hand sides per register pass
+constexpr int AW = 8;         // warps per CTA in the apply kernels
+constexpr int AT = AW * 32;
 
-template <typename T>
-__global__ void __launch_bounds__(AT) k_fwd_node(const ApplyNode *__restrict__ nodes, int first,
-                                                 double *__restrict__ ws, double *__restrict__ tb,
-                                                 int nrhs) {
-  const ApplyNode nd = nodes[first + blockIdx.x];
-  const T *M = (const T *)nd.M;
-  const T *P = (const T *)nd.P;
-  const double *phs = ws + nd.xs * nrhs;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int rows = nd.m + nd.k;
-  for (int row = warp; row < rows; row += nw) {
-    const T *Ar = row < nd.m ? M + (int64_t)row * nd.m : P + (int64_t)(row - nd.m) * nd.m;
-    for (int j0 = 0; j0 < nrhs; j0 += MAXR) {
-      const int nr = min(MAXR, nrhs - j0);
-      double acc[MAXR];
+// last node i in nodes[first, first+count) with key(i) <= w (keys are prefix sums)
+template <typename F>
+__device__ __forceinline__ int find_last(int first, int count, int w, F key) {
+  int lo = first, hi = first + count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (key(mid) <= w)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, int NR>
+__device__ __forceinline__ void warp_reduce(T (&acc)[NR]) {
 #pragma unroll
-      for (int j = 0; j < MAXR; ++j) acc[j] = 0.0;
-      for (int c = lane; c < nd.m; c += 32) {
-        const double a = (double)Ar[c];
-        const double *x = phs + (int64_t)c * nrhs + j0;
+  for (int j = 0; j < NR; ++j)
 #pragma unroll
-        for (int j = 0; j < MAXR; ++j)
-          if (j < nr) acc[j] = fma(a, x[j], acc[j]);
+    for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+}
+
+
+// acc[j] += sum_c A[c] x[c*stride + j] for c = lane, lane+32, ... < len, four
+// independent loads in flight per lane
+template <typename T, int NR>
+__device__ __forceinline__ void row_dot(const T *__restrict__ A, const T *__restrict__ x, int len,
+                                        int64_t stride, int nr, int lane, T (&acc)[NR]) {
+  int c = lane;
+  for (; c + 96 < len; c += 128) {
+    const T a0 = A[c], a1 = A[c + 32], a2 = A[c + 64], a3 = A[c + 96];
+    const T *x0 = x + (int64_t)c * stride, *x1 = x0 + 32 * stride, *x2 = x0 + 64 * stride,
+            *x3 = x0 + 96 * stride;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      if (j < nr) acc[j] = fma(a3, x3[j], fma(a2, x2[j], fma(a1, x1[j], fma(a0, x0[j], acc[j]))));
+  }
+  for (; c < len; c += 32) {
+    const T a = A[c];
+    const T *xc = x + (int64_t)c * stride;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      if (j < nr) acc[j] = fma(a, xc[j], acc[j]);
+  }
+}
+
+// acc[j] += sum_q A[q*ld] t[q*stride + j] for q < len (column walk, unrolled by 4)
+template <typename T, int NR>
+__device__ __forceinline__ void col_dot(const T *__restrict__ A, int64_t ld, const T *__restrict__ t, int len,
+                                        int64_t stride, int nr, T (&acc)[NR]) {
+  int q = 0;
+  for (; q + 3 < len; q += 4) {
+    const T a0 = A[q * ld], a1 = A[(q + 1) * ld], a2 = A[(q + 2) * ld], a3 = A[(q + 3) * ld];
+    const T *t0 = t + (int64_t)q * stride;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      if (j < nr)
+        acc[j] = fma(a3, t0[3 * stride + j], fma(a2, t0[2 * stride + j], fma(a1, t0[stride + j], fma(a0, t0[j], acc[j]))));
+  }
+  for (; q < len; ++q) {
+    const T a = A[q * ld];
+    const T *tq = t + (int64_t)q * stride;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      if (j < nr) acc[j] = fma(a, tq[j], acc[j]);
+  }
+}
+
+// F1: one warp per row of [M_ss; P_ss]: t_s = M_ss phi_s, phi_r += P_ss phi_s
+template <typename T, int NR>
+__global__ void __launch_bounds__(AT) k_f1(const ApplyNode *__restrict__ nodes, int first, int count, int rows,
+                                           T *__restrict__ ws, T *__restrict__ tb, int nrhs, int j0) {
+  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  const int ni = find_last(first, count, w, [&](int i) { return nodes[i].row0; });
+  const ApplyNode nd = nodes[ni];
+  const int r = w - nd.row0;
+  const T *Ar = r < nd.m ? (const T *)nd.M + (int64_t)r * nd.m : (const T *)nd.P + (int64_t)(r - nd.m) * nd.m;
+  const T *x = ws + nd.xs * nrhs + j0;
+  const int nr = min(NR, nrhs - j0);
+  T acc[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) acc[j] = T(0);
+  row_dot<T, NR>(Ar, x, nd.m, nrhs, nr, lane, acc);
+  warp_reduce<T, NR>(acc);
+  if (lane == 0) {
+    T *o = r < nd.m ? tb + (nd.toff + r) * nrhs + j0 : ws + (nd.xr + r - nd.m) * nrhs + j0;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      if (j < nr) {
+        if (r < nd.m)
+          o[j] = acc[j];
+        else
+          o[j] += acc[j];
       }
+  }
+}
+
+// F2: phi_n -= sum_s A_ns t_s; one warp per 32 rows of a target, contributions in order
+template <typename T, int NR>
+__global__ void __launch_bounds__(AT) k_f2(const ApplyTarget *__restrict__ tg, int first, int count, int chunks,
+                                           const ApplyContrib *__restrict__ cb, T *__restrict__ ws,
+                                           const T *__restrict__ tb, int nrhs, int j0) {
+  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= chunks) return;
+  const int ti = find_last(first, count, w, [&](int i) { return tg[i].ch0; });
+  const ApplyTarget t = tg[ti];
+  const int i = (w - t.ch0) * 32 + lane;
+  if (i >= t.size) return;
+  const int nr = min(NR, nrhs - j0);
+  T acc[NR];
 #pragma unroll
-      for (int j = 0; j < MAXR; ++j)
-        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-      if (lane == 0) {
-        if (row < nd.m) {
-          double *o = tb + (nd.toff + row) * nrhs + j0;
-          for (int j = 0; j < nr; ++j) o[j] = acc[j];
-        } else {
-          double *o = ws + (nd.xr + row - nd.m) * nrhs + j0;
-          for (int j = 0; j < nr; ++j) o[j] += acc[j];
-        }
-      }
+  for (int j = 0; j < NR; ++j) acc[j] = T(0);
+  for (int c = 0; c < t.count; ++c) {
+    const ApplyContrib ac = cb[t.first + c];
+    const T *A = (const T *)ac.A + i;
+    const T *tv = tb + ac.toff * nrhs + j0;
+    col_dot<T, NR>(A, ac.ld, tv, ac.m, nrhs, nr, acc);
+  }
+  T *o = ws + (t.x + i) * nrhs + j0;
+#pragma unroll
+  for (int j = 0; j < NR; ++j)
+    if (j < nr) o[j] -= acc[j];
+}
+
+// B1 (warps < rows_b): v_s = phi_s - sum_n A_sn x_n, one warp per row of s.
+// B2a (warps >= rows_b): y_s = P_ss^T x_r, one warp per 32 columns of P_ss.
+template <typename T, int NR>
+__global__ void __launch_bounds__(AT) k_b1(const ApplyNode *__restrict__ nodes, int first, int count, int rows_b,
+                                           int pch, const ApplyNbr *__restrict__ nb, const T *__restrict__ ws,
+                                           T *__restrict__ tb, T *__restrict__ tb2, int nrhs, int j0) {
+  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int nr = min(NR, nrhs - j0);
+  T acc[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) acc[j] = T(0);
+  if (w < rows_b) {
+    const int ni = find_last(first, count, w, [&](int i) { return nodes[i].brow0; });
+    const ApplyNode nd = nodes[ni];
+    const int r = w - nd.brow0;
+    for (int b = 0; b < nd.nb_count; ++b) {
+      const ApplyNbr n = nb[nd.nb_first + b];
+      const T *Ar = (const T *)nd.AsN + (int64_t)r * nd.dN + n.col;
+      const T *xn = ws + n.x * nrhs + j0;
+      row_dot<T, NR>(Ar, xn, n.size, nrhs, nr, lane, acc);
     }
+    warp_reduce<T, NR>(acc);
+    if (lane == 0) {
+      const T *ph = ws + (nd.xs + r) * nrhs + j0;
+      T *o = tb + (nd.toff + r) * nrhs + j0;
+#pragma unroll
+      for (int j = 0; j < NR; ++j)
+        if (j < nr) o[j] = ph[j] - acc[j];
+    }
+  } else if (w < rows_b + pch) {
+    const int w2 = w - rows_b;
+    const int ni = find_last(first, count, w2, [&](int i) { return nodes[i].pch0; });
+    const ApplyNode nd = nodes[ni];
+    const int i = (w2 - nd.pch0) * 32 + lane;
+    if (i >= nd.m || nd.k == 0) return;
+    const T *P = (const T *)nd.P + i;
+    const T *xr = ws + nd.xr * nrhs + j0;
+    col_dot<T, NR>(P, nd.m, xr, nd.k, nrhs, nr, acc);
+    T *o = tb2 + (nd.toff + i) * nrhs + j0;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      if (j < nr) o[j] = acc[j];
+  }
+}
+
+// B2b: x_s = M_ss v_s + y_s, one warp per row of s
+template <typename T, int NR>
+__global__ void __launch_bounds__(AT) k_b2(const ApplyNode *__restrict__ nodes, int first, int count, int rows_b,
+                                           T *__restrict__ ws, const T *__restrict__ tb,
+                                           const T *__restrict__ tb2, int nrhs, int j0) {
+  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= rows_b) return;
+  const int ni = find_last(first, count, w, [&](int i) { return nodes[i].brow0; });
+  const ApplyNode nd = nodes[ni];
+  const int r = w - nd.brow0;
+  const T *Mr = (const T *)nd.M + (int64_t)r * nd.m;
+  const T *v = tb + nd.toff * nrhs + j0;
+  const int nr = min(NR, nrhs - j0);
+  T acc[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) acc[j] = T(0);
+  row_dot<T, NR>(Mr, v, nd.m, nrhs, nr, lane, acc);
+  warp_reduce<T, NR>(acc);
+  if (lane == 0) {
+    const T *y = tb2 + (nd.toff + r) * nrhs + j0;
+    T *o = ws + (nd.xs + r) * nrhs + j0;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      if (j < nr) o[j] = acc[j] + (nd.k > 0 ? y[j] : T(0));
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(AT) k_fwd_target(const ApplyTarget *__restrict__ tg, int first,
-                                                   const ApplyContrib *__restrict__ cb,
-                                                   double *__restrict__ ws,
-                                                   const double *__restrict__ tb, int nrhs) {
-  const ApplyTarget t = tg[first + blockIdx.x];
-  const int total = t.size * nrhs;
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    const int i = e / nrhs, j = e - (e / nrhs) * nrhs;
-    double acc = 0.0;
-    for (int c = 0; c < t.count; ++c) {
-      const ApplyContrib ac = cb[t.first + c];
-      const T *A = (const T *)ac.A;
-      const double *tv = tb + ac.toff * nrhs + j;
-      for (int q = 0; q < ac.m; ++q) acc = fma((double)A[(int64_t)q * ac.ld + i], tv[(int64_t)q * nrhs], acc);
-    }
-    ws[(t.x + i) * nrhs + j] -= acc;
-  }
+__global__ void k_copy(const T *__restrict__ src, T *__restrict__ dst, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    dst[e] = src[e];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(AT) k_bwd_node(const ApplyNode *__restrict__ nodes, int first,
-                                                 const ApplyNbr *__restrict__ nb,
-                                                 double *__restrict__ ws, double *__restrict__ tb,
-                                                 int nrhs) {
-  const ApplyNode nd = nodes[first + blockIdx.x];
-  const T *M = (const T *)nd.M;
-  const T *P = (const T *)nd.P;
-  const T *AsN = (const T *)nd.AsN;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double *v = tb + nd.toff * nrhs;
-  // v = phi_s - sum_n A_sn x_n
-  for (int row = warp; row < nd.m; row += nw) {
-    for (int j0 = 0; j0 < nrhs; j0 += MAXR) {
-      const int nr = min(MAXR, nrhs - j0);
-      double acc[MAXR];
-#pragma unroll
-      for (int j = 0; j < MAXR; ++j) acc[j] = 0.0;
-      for (int b = 0; b < nd.nb_count; ++b) {
-        const ApplyNbr n = nb[nd.nb_first + b];
-        const T *Ar = AsN + (int64_t)row * nd.dN + n.col;
-        const double *xn = ws + n.x * nrhs + j0;
-        for (int q = lane; q < n.size; q += 32) {
-          const double a = (double)Ar[q];
-#pragma unroll
-          for (int j = 0; j < MAXR; ++j)
-            if (j < nr) acc[j] = fma(a, xn[(int64_t)q * nrhs + j], acc[j]);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < MAXR; ++j)
-        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-      if (lane == 0) {
-        const double *ph = ws + (nd.xs + row) * nrhs + j0;
-        for (int j = 0; j < nr; ++j) v[(int64_t)row * nrhs + j0 + j] = ph[j] - acc[j];
-      }
-    }
-  }
-  __syncthreads();
-  // x_s = M_ss v + P_ss^T x_r
-  for (int row = warp; row < nd.m; row += nw) {
-    for (int j0 = 0; j0 < nrhs; j0 += MAXR) {
-      const int nr = min(MAXR, nrhs - j0);
-      double acc[MAXR];
-#pragma unroll
-      for (int j = 0; j < MAXR; ++j) acc[j] = 0.0;
-      const T *Mr = M + (int64_t)row * nd.m;
-      for (int c = lane; c < nd.m; c += 32) {
-        const double a = (double)Mr[c];
-        const double *x = v + (int64_t)c * nrhs + j0;
-#pragma unroll
-        for (int j = 0; j < MAXR; ++j)
-          if (j < nr) acc[j] = fma(a, x[j], acc[j]);
-      }
-      if (nd.k > 0) {
-        const double *xr = ws + nd.xr * nrhs + j0;
-        for (int q = lane; q < nd.k; q += 32) {
-          const double a = (double)P[(int64_t)q * nd.m + row];
-#pragma unroll
-          for (int j = 0; j < MAXR; ++j)
-            if (j < nr) acc[j] = fma(a, xr[(int64_t)q * nrhs + j], acc[j]);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < MAXR; ++j)
-        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-      if (lane == 0) {
-        double *o = ws + (nd.xs + row) * nrhs + j0;
-        for (int j = 0; j < nr; ++j) o[j] = acc[j];
-      }
-    }
-  }
-}
-
-template <typename T>
+// root: x = A_root^-1 phi (phi copied to tb first), one warp per row
+template <typename T, int NR>
 __global__ void __launch_bounds__(AT) k_root(const T *__restrict__ Ainv, int m, int64_t off,
-                                             double *__restrict__ ws, double *__restrict__ tb,
-                                             int nrhs) {
-  for (int64_t e = threadIdx.x; e < (int64_t)m * nrhs; e += blockDim.x) tb[e] = ws[off * nrhs + e];
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int row = warp; row < m; row += nw) {
-    for (int j0 = 0; j0 < nrhs; j0 += MAXR) {
-      const int nr = min(MAXR, nrhs - j0);
-      double acc[MAXR];
+                                             T *__restrict__ ws, const T *__restrict__ tb, int nrhs,
+                                             int j0) {
+  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w >= m) return;
+  const T *Ar = Ainv + (int64_t)w * m;
+  const int nr = min(NR, nrhs - j0);
+  T acc[NR];
 #pragma unroll
-      for (int j = 0; j < MAXR; ++j) acc[j] = 0.0;
-      const T *Ar = Ainv + (int64_t)row * m;
-      for (int c = lane; c < m; c += 32) {
-        const double a = (double)Ar[c];
+  for (int j = 0; j < NR; ++j) acc[j] = T(0);
+  row_dot<T, NR>(Ar, tb + j0, m, nrhs, nr, lane, acc);
+  warp_reduce<T, NR>(acc);
+  if (lane == 0) {
+    T *o = ws + (off + w) * nrhs + j0;
 #pragma unroll
-        for (int j = 0; j < MAXR; ++j)
-          if (j < nr) acc[j] = fma(a, tb[(int64_t)c * nrhs + j0 + j], acc[j]);
-      }
-#pragma unroll
-      for (int j = 0; j < MAXR; ++j)
-        for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-      if (lane == 0)
-        for (int j = 0; j < nr; ++j) ws[(off + row) * nrhs + j0 + j] = acc[j];
-    }
+    for (int j = 0; j < NR; ++j)
+      if (j < nr) o[j] = acc[j];
   }
 }
 
-// user layout (column-major, ld) <-> workspace layout (unknown-major, cluster order)
+// user layout (column-major, ld, FP64) <-> workspace layout (unknown-major, cluster order, T)
+template <typename T>
 __global__ void k_gather_in(const double *__restrict__ r, int64_t ld, const int32_t *__restrict__ perm,
-                            int64_t n, int nrhs, int nrhs_p, double *__restrict__ out) {
+                            int64_t n, int nrhs, int nrhs_p, T *__restrict__ out) {
   const int64_t total = n * nrhs_p;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = e / nrhs_p;
     const int j = (int)(e - p * nrhs_p);
-    out[e] = j < nrhs ? r[(int64_t)perm[p] + j * ld] : 0.0;
+    out[e] = j < nrhs ? (T)r[(int64_t)perm[p] + j * ld] : T(0);
   }
 }
 
-__global__ void k_scatter_out(const double *__restrict__ in, const int32_t *__restrict__ perm,
-                              int64_t n, int nrhs, int nrhs_p, double *__restrict__ z, int64_t ld) {
+template <typename T>
+__global__ void k_scatter_out(const T *__restrict__ in, const int32_t *__restrict__ perm, int64_t n, int nrhs,
+                              int nrhs_p, double *__restrict__ z, int64_t ld) {
   const int64_t total = n * nrhs;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = e / nrhs;
     const int j = (int)(e - p * nrhs);
-    z[(int64_t)perm[p] + j * ld] = in[p * nrhs_p + j];
+    z[(int64_t)perm[p] + j * ld] = (double)in[p * nrhs_p + j];
   }
+}
+
+// element-wise precision change between the FP64 PCG vectors and the workspace
+template <typename A, typename B>
+__global__ void k_convert(const A *__restrict__ a, B *__restrict__ b, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    b[e] = (B)a[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -386,30 +457,71 @@ int grid_for(int64_t total) {
 // grid for the reduction kernels: stride (grid * PT) must be a multiple of nrhs_p
 int rgrid_for(int64_t total) { return grid_for(total); }
 
-template <typename T>
-void apply_ws_t(FactorHandle &h, int nrhs, cudaStream_t st) {
-  double *ws = h.d_ws;
-  const int64_t n = h.plan.n;
-  if (h.ws_size > n)
-    HS_CUDA(cudaMemsetAsync(ws + n * nrhs, 0, sizeof(double) * (h.ws_size - n) * nrhs, st));
+template <typename T, int NR>
+void apply_ws_nr(FactorHandle &h, int nrhs, int j0, cudaStream_t st) {
+  T *ws = (T *)h.d_ws;
+  T *tb = (T *)h.d_t, *tb2 = (T *)h.d_t + h.t_cap * h.nrhs_cap;
+  auto blocks = [](int warps) { return (warps + AW - 1) / AW; };
   for (const LevelApply &la : h.levels)
     for (int w = la.wave_first; w < la.wave_first + la.wave_count; ++w) {
       const WaveApply &wa = h.waves[w];
-      if (wa.node_count) k_fwd_node<T><<<wa.node_count, AT, 0, st>>>(h.d_nodes, wa.node_first, ws, h.d_t, nrhs);
-      if (wa.tgt_count)
-        k_fwd_target<T><<<wa.tgt_count, AT, 0, st>>>(h.d_targets, wa.tgt_first, h.d_contribs, ws, h.d_t, nrhs);
+      if (wa.rows_f) {
+        k_f1<T, NR><<<blocks(wa.rows_f), AT, 0, st>>>(h.d_nodes, wa.node_first, wa.node_count, wa.rows_f, ws, tb,
+                                                      nrhs, j0);
+        count_launch();
+      }
+      if (wa.tch) {
+        k_f2<T, NR><<<blocks(wa.tch), AT, 0, st>>>(h.d_targets, wa.tgt_first, wa.tgt_count, wa.tch, h.d_contribs,
+                                                   ws, tb, nrhs, j0);
+        count_launch();
+      }
     }
-  if (h.root_m > 0)
-    k_root<T><<<1, AT, 0, st>>>((const T *)h.root_inv, h.root_m, h.root_off, ws, h.d_t, nrhs);
+  if (h.root_m > 0) {
+    const int64_t cnt = (int64_t)h.root_m * nrhs;
+    k_copy<T><<<(int)std::min<int64_t>((cnt + 255) / 256, 1024), 256, 0, st>>>(ws + h.root_off * nrhs, tb, cnt);
+    k_root<T, NR><<<blocks(h.root_m), AT, 0, st>>>((const T *)h.root_inv, h.root_m, h.root_off, ws, tb, nrhs, j0);
+    count_launch(2);
+  }
   for (int li = (int)h.levels.size() - 1; li >= 0; --li) {
     const LevelApply &la = h.levels[li];
     for (int w = la.wave_first + la.wave_count - 1; w >= la.wave_first; --w) {
       const WaveApply &wa = h.waves[w];
-      if (wa.node_count)
-        k_bwd_node<T><<<wa.node_count, AT, 0, st>>>(h.d_nodes, wa.node_first, h.d_nbrs, ws, h.d_t, nrhs);
+      if (!wa.rows_b) continue;
+      k_b1<T, NR><<<blocks(wa.rows_b + wa.pch), AT, 0, st>>>(h.d_nodes, wa.node_first, wa.node_count, wa.rows_b,
+                                                             wa.pch, h.d_nbrs, ws, tb, tb2, nrhs, j0);
+      k_b2<T, NR><<<blocks(wa.rows_b), AT, 0, st>>>(h.d_nodes, wa.node_first, wa.node_count, wa.rows_b, ws, tb,
+                                                    tb2, nrhs, j0);
+      count_launch(2);
     }
   }
   HS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void apply_ws_t(FactorHandle &h, int nrhs, cudaStream_t st) {
+  const int64_t n = h.plan.n;
+  if (h.ws_size > n)
+    HS_CUDA(cudaMemsetAsync((T *)h.d_ws + n * nrhs, 0, sizeof(T) * (h.ws_size - n) * nrhs, st));
+  // right-hand sides in chunks of at most 16 (register accumulators)
+  for (int j0 = 0; j0 < nrhs;) {
+    const int rem = nrhs - j0;
+    if (rem > 8) {
+      apply_ws_nr<T, 16>(h, nrhs, j0, st);
+      j0 += 16;
+    } else if (rem > 4) {
+      apply_ws_nr<T, 8>(h, nrhs, j0, st);
+      j0 += 8;
+    } else if (rem > 2) {
+      apply_ws_nr<T, 4>(h, nrhs, j0, st);
+      j0 += 4;
+    } else if (rem == 2) {
+      apply_ws_nr<T, 2>(h, nrhs, j0, st);
+      j0 += 2;
+    } else {
+      apply_ws_nr<T, 1>(h, nrhs, j0, st);
+      j0 += 1;
+    }
+  }
 }
 
 void apply_ws(FactorHandle &h, int nrhs, cudaStream_t st) {
@@ -420,7 +532,9 @@ void apply_ws(FactorHandle &h, int nrhs, cudaStream_t st) {
 }
 
 void ensure_buffers(FactorHandle &h, int nrhs_cap) {
-  if (h.nrhs_cap >= nrhs_cap && h.d_ws) return;
+  const int64_t tneed0 = std::max<int64_t>(std::max<int64_t>(h.tmax, h.root_m), 1);
+  if (h.nrhs_cap >= nrhs_cap && h.d_ws && h.ws_cap >= h.ws_size && h.t_cap >= tneed0) return;
+  nrhs_cap = std::max(nrhs_cap, h.nrhs_cap);
   cudaFree(h.d_ws);
   cudaFree(h.d_t);
   cudaFree(h.d_pcg);
@@ -430,10 +544,13 @@ void ensure_buffers(FactorHandle &h, int nrhs_cap) {
   h.d_ws = h.d_t = h.d_pcg = h.d_part = h.d_scal = nullptr;
   h.d_iflags = nullptr;
   const int64_t n = h.plan.n;
-  HS_CUDA(cudaMalloc(&h.d_ws, sizeof(double) * std::max<int64_t>(h.ws_size, 1) * nrhs_cap));
-  const int64_t tneed = std::max<int64_t>(std::max<int64_t>(h.tmax, h.root_m), 1);
-  HS_CUDA(cudaMalloc(&h.d_t, sizeof(double) * tneed * nrhs_cap));
-  HS_CUDA(cudaMalloc(&h.d_pcg, sizeof(double) * 6 * n * nrhs_cap));
+  const size_t es = h.prec == HS_PREC_F64 ? sizeof(double) : sizeof(float);
+  HS_CUDA(cudaMalloc(&h.d_ws, es * std::max<int64_t>(h.ws_size, 1) * nrhs_cap));
+  const int64_t tneed = tneed0;
+  HS_CUDA(cudaMalloc(&h.d_t, es * 2 * tneed * nrhs_cap));
+  h.ws_cap = std::max<int64_t>(h.ws_size, 1);
+  h.t_cap = tneed;
+  HS_CUDA(cudaMalloc(&h.d_pcg, sizeof(double) * 7 * n * nrhs_cap));
   h.part_blocks = 152 * 8;
   HS_CUDA(cudaMalloc(&h.d_part, sizeof(double) * h.part_blocks * 32));
   HS_CUDA(cudaMalloc(&h.d_scal, sizeof(double) * 6 * 32));
@@ -447,10 +564,33 @@ void ensure_buffers(FactorHandle &h, int nrhs_cap) {
 void apply_solve(FactorHandle &h, const double *r, double *z, int nrhs, int64_t ld, cudaStream_t st) {
   ensure_buffers(h, std::max(nrhs, h.nrhs_cap));
   const int64_t n = h.plan.n;
-  k_gather_in<<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, h.d_ws);
-  apply_ws(h, nrhs, st);
-  k_scatter_out<<<grid_for(n * nrhs), 256, 0, st>>>(h.d_ws, h.d_perm, n, nrhs, nrhs, z, ld);
+  if (h.prec == HS_PREC_F64) {
+    k_gather_in<double><<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, (double *)h.d_ws);
+    apply_ws(h, nrhs, st);
+    k_scatter_out<double><<<grid_for(n * nrhs), 256, 0, st>>>((const double *)h.d_ws, h.d_perm, n, nrhs, nrhs, z, ld);
+  } else {
+    k_gather_in<float><<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, (float *)h.d_ws);
+    apply_ws(h, nrhs, st);
+    k_scatter_out<float><<<grid_for(n * nrhs), 256, 0, st>>>((const float *)h.d_ws, h.d_perm, n, nrhs, nrhs, z, ld);
+  }
+  count_launch(2);
   HS_CUDA(cudaGetLastError());
+}
+
+// z = A_H^-1 r on the FP64 PCG vectors (layout n x np): through the workspace
+// in the factor precision
+void apply_pcg(FactorHandle &h, const double *R, double *Z, int np, cudaStream_t st) {
+  const int64_t tot = h.plan.n * np;
+  if (h.prec == HS_PREC_F64) {
+    HS_CUDA(cudaMemcpyAsync(h.d_ws, R, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+    apply_ws(h, np, st);
+    HS_CUDA(cudaMemcpyAsync(Z, h.d_ws, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+  } else {
+    k_convert<double, float><<<grid_for(tot), 256, 0, st>>>(R, (float *)h.d_ws, tot);
+    apply_ws(h, np, st);
+    k_convert<float, double><<<grid_for(tot), 256, 0, st>>>((const float *)h.d_ws, Z, tot);
+    count_launch(2);
+  }
 }
 
 int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld, double rtol,
@@ -460,21 +600,22 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
   ensure_buffers(h, std::max(np, h.nrhs_cap));
   const int64_t n = h.plan.n;
   const int64_t tot = n * np;
-  double *X = h.d_pcg, *R = X + tot, *P0 = R + tot, *P1 = P0 + tot, *Q = P1 + tot, *B = Q + tot;
+  double *X = h.d_pcg, *R = X + tot, *P0 = R + tot, *P1 = P0 + tot, *Q = P1 + tot, *B = Q + tot, *Z = B + tot;
   PcgScal sc{h.d_scal, h.d_scal + 32, h.d_scal + 64, h.d_scal + 96, h.d_scal + 128, h.d_scal + 160};
   PcgFlags fl{h.d_iflags, h.d_iflags + 32, h.d_iflags + 64, h.d_iflags + 65};
   const int g = rgrid_for(tot);
   // grid * PT is a multiple of 256, hence of np (np <= 32): each thread keeps one rhs
-  k_gather_in<<<grid_for(tot), 256, 0, st>>>(b, ld, h.d_perm, n, nrhs, np, B);
+  k_gather_in<double><<<grid_for(tot), 256, 0, st>>>(b, ld, h.d_perm, n, nrhs, np, B);
+  count_launch();
   HS_CUDA(cudaMemcpyAsync(R, B, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
   HS_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * tot, st));
   HS_CUDA(cudaMemsetAsync(P0, 0, sizeof(double) * tot, st));
   k_dot<<<g, PT, 0, st>>>(B, B, n, np, h.d_part, sc, fl, DOT_BNORM, nullptr);
-  // z = A_H^-1 r in the level-L segment of the workspace
-  double *Z = h.d_ws;
-  HS_CUDA(cudaMemcpyAsync(Z, R, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
-  apply_ws(h, np, st);
+  count_launch();
+  // z = A_H^-1 r
+  apply_pcg(h, R, Z, np, st);
   k_dot<<<g, PT, 0, st>>>(R, Z, n, np, h.d_part, sc, fl, DOT_RZ_FIRST, nullptr);
+  count_launch();
   int *done_h = nullptr;
   HS_CUDA(cudaMallocHost(&done_h, sizeof(int)));
   double *pold = P0, *pnew = P1;
@@ -483,7 +624,9 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
   bool converged = false;
   while (it < maxit) {
     k_spmv_p<<<g, PT, 0, st>>>(h.d_rowptr, h.d_col, h.d_val, n, np, Z, pold, pnew, Q, h.d_part, sc, fl);
+    count_launch();
     k_update<<<g, PT, 0, st>>>(X, R, pnew, Q, n, np, h.d_part, sc, fl, rtol2);
+    count_launch();
     HS_CUDA(cudaGetLastError());
     ++it;
     HS_CUDA(cudaMemcpyAsync(done_h, fl.done, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -493,16 +636,19 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
       break;
     }
     std::swap(pold, pnew);
-    HS_CUDA(cudaMemcpyAsync(Z, R, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
-    apply_ws(h, np, st);
+    apply_pcg(h, R, Z, np, st);
     k_dot<<<g, PT, 0, st>>>(R, Z, n, np, h.d_part, sc, fl, DOT_RZ, nullptr);
+    count_launch();
   }
   cudaFreeHost(done_h);
   // true relative residual
   k_residual<<<grid_for(tot), 256, 0, st>>>(h.d_rowptr, h.d_col, h.d_val, n, np, X, B, Q);
+  count_launch();
   double *rr_d = h.d_scal + 5 * 32;
   k_dot<<<g, PT, 0, st>>>(Q, Q, n, np, h.d_part, sc, fl, DOT_PLAIN, rr_d);
-  k_scatter_out<<<grid_for(n * nrhs), 256, 0, st>>>(X, h.d_perm, n, nrhs, np, x, ld);
+  count_launch();
+  k_scatter_out<double><<<grid_for(n * nrhs), 256, 0, st>>>(X, h.d_perm, n, nrhs, np, x, ld);
+  count_launch();
   HS_CUDA(cudaGetLastError());
   std::vector<double> hs(6 * 32);
   std::vector<int> hi(2 * 32 + 2);
@@ -521,6 +667,9 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
 }
 
 FactorHandle::~FactorHandle() {
+  cudaFree(d_src);
+  cudaFree(d_leaf_dest);
+  cudaFree(d_phi0);
   cudaFree(d_rowptr);
   cudaFree(d_col);
   cudaFree(d_val);

@@ -25,7 +25,7 @@ def lib():
 
 def test_exports_every_declared_symbol(lib):
     hdr = open(os.path.join(ROOT, "include", "hs.h")).read()
-    declared = set(re.findall(r"^\s*(?:int|const char \*)\s*(hs_\w+)\s*\(", hdr, flags=re.M))
+    declared = set(re.findall(r"^\s*(?:int|int64_t|const char \*)\s*(hs_\w+)\s*\(", hdr, flags=re.M))
     assert declared == set(_lib.EXPORTS)
     out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
     exported = set(re.findall(r"\b(hs_\w+)\b", out))

@@ -173,3 +173,69 @@ def test_edge_cases_single_leaf_and_tiny_levels():
             assert rel(z, H.apply(F, b)) <= 1e-11
             if eps == 0.0:
                 assert rel(z, x) <= 1e-11
+
+
+def test_refactor_equals_fresh_factor_bitwise():
+    """hs_factor_refactor with new values of the same pattern gives exactly the
+    factorization a new handle computes (deterministic reductions)."""
+    torch = need_gpu()
+    pa = P.diffusion2d(64, 1.0, 0, leaf_size=16)
+    pb = P.diffusion2d(64, 1.0, 1, leaf_size=16)
+    for prec in (_lib.HS_PREC_F64, _lib.HS_PREC_F32):
+        G = gpu_factor(pa, 1e-2, H.GC_CONSTANT, prec=prec)
+        G.refactor(torch.as_tensor(pb.val, device="cuda"))
+        G2 = gpu_factor(pb, 1e-2, H.GC_CONSTANT, prec=prec)
+        r = torch.as_tensor(P.rhs(pb.n, 3), device="cuda")
+        assert torch.equal(G.apply(r), G2.apply(r))
+        for lv in range(2, pb.levels + 1):
+            assert np.array_equal(G.ranks(lv), G2.ranks(lv))
+
+
+def test_launch_counter_counts_library_kernels():
+    torch = need_gpu()
+    pb = P.poisson2d(32, leaf_size=8)
+    G = gpu_factor(pb, 1e-2, H.GC_CONSTANT)
+    c0 = _lib.launch_count()
+    G.apply(torch.as_tensor(P.rhs(pb.n, 0), device="cuda"))
+    c1 = _lib.launch_count()
+    assert c1 - c0 >= 3
+
+
+TRIDIAG_CASES = [CASES[0], CASES[3], CASES[4]]
+
+
+@pytest.mark.parametrize("name,maker", TRIDIAG_CASES, ids=[c[0] for c in TRIDIAG_CASES])
+@pytest.mark.parametrize("variant", [H.LORASP, H.GC_CONSTANT])
+def test_tridiagonal_truncation_path_matches_oracle(name, maker, variant):
+    """Every super node through the large-node eigen path (tridiagonalisation,
+    bisection, inverse iteration): ranks and apply match the oracle."""
+    import subprocess
+    import sys
+
+    need_gpu()
+    code = f"""
+import sys, numpy as np, torch
+sys.path.insert(0, {repr(__import__('os').path.dirname(__import__('os').path.dirname(__import__('os').path.abspath(__file__))))})
+sys.path.insert(0, {repr(__import__('os').path.dirname(__import__('os').path.abspath(__file__)))})
+from gpu_util import gpu_factor, oracle_factor, rel
+from oracle import hsolver as H
+from paper_1611_03189_gb300 import problems as P
+import test_gpu_parity as T
+pb = [c for c in T.CASES if c[0] == {name!r}][0][1]()
+for eps in (1e-1, 1e-2):
+    F = oracle_factor(pb, eps, {variant})
+    G = gpu_factor(pb, eps, {variant})
+    assert T._ranks_match(F, G) == [], T._ranks_match(F, G)[:5]
+    B = P.rhs(pb.n, 7, nrhs=2)
+    Z = H.apply(F, B)
+    zg = G.apply(torch.as_tensor(B.T.copy(), device='cuda')).cpu().numpy().T
+    e = rel(zg, Z)
+    assert e <= 1e-10, e
+    G32 = gpu_factor(pb, eps, {variant}, prec=1)
+    e32 = rel(G32.apply(torch.as_tensor(B.T.copy(), device='cuda')).cpu().numpy().T, Z)
+    assert e32 <= 1e-3, e32
+print('ok')
+"""
+    env = dict(__import__("os").environ, HS_EIG_SMALL_MAX="8")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-3000:]
