@@ -133,6 +133,26 @@ int hs_factor_refactor(hs_factor f, const double *val, void *stream);
  * r and z may alias.  1 <= nrhs <= 64. */
 int hs_apply(hs_factor f, const double *r, double *z, int32_t nrhs, int64_t ld, void *stream);
 
+/* hs_apply_static: the same z = A_H^{-1} r as hs_apply, for callers that must
+ * not allocate device memory while they solve -- for instance code that
+ * records its work inside a CUDA stream capture, or a service whose device
+ * memory is fixed at start-up.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine: the apply workspace is one 16 MiB static device array
+ * inside this library, which every GPU that loads the library holds until the
+ * process exits.  The paper has no counterpart; this is a property of this
+ * library's interface only.
+ *   - Needs (ws_unknowns x nrhs + 2 x scratch_unknowns x nrhs) elements of the
+ *     factor precision; larger requests fail with HS_ERR_CAPACITY and a
+ *     message giving the bytes needed.  r, z, nrhs, ld as for hs_apply.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls on a device share the array and leave the last call's
+ *     contents in it (the parts that must start at zero are cleared by each
+ *     call).  Calls that overlap on the GPU -- on different streams or
+ *     threads -- race on it: serialise them. */
+int hs_apply_static(hs_factor f, const double *r, double *z, int32_t nrhs, int64_t ld, void *stream);
+
 /* hs_pcg: solve A x = b by conjugate gradients preconditioned with A_H^{-1},
  * x_0 = 0, stopping when ||r_k||_2 <= rtol ||b||_2 for each right-hand side
  * (Sec. 7: relative residual 1e-10).  A is the matrix of the last successful

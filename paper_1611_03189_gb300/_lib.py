@@ -37,7 +37,7 @@ STATUS_NAMES = {
 
 # every symbol include/hs.h declares
 EXPORTS = [
-    "hs_factor_create", "hs_factor_refactor", "hs_launch_count", "hs_apply", "hs_pcg", "hs_factor_info", "hs_factor_ranks",
+    "hs_factor_create", "hs_factor_refactor", "hs_launch_count", "hs_apply", "hs_apply_static", "hs_pcg", "hs_factor_info", "hs_factor_ranks",
     "hs_factor_destroy", "hs_last_error", "hs_plan_create", "hs_plan_level_waves",
     "hs_plan_super_lists", "hs_plan_destroy",
 ]
@@ -89,6 +89,7 @@ def lib():
         L.hs_factor_refactor.argtypes = [vp, vp, vp]
         L.hs_launch_count.argtypes = []
         L.hs_apply.argtypes = [vp, vp, vp, i32, i64, vp]
+        L.hs_apply_static.argtypes = [vp, vp, vp, i32, i64, vp]
         L.hs_pcg.argtypes = [vp, vp, vp, i32, i64, dbl, i32, vp, vp, vp]
         L.hs_factor_info.argtypes = [vp, C.POINTER(HsInfo)]
         L.hs_factor_ranks.argtypes = [vp, i32, vp, i32, C.POINTER(i32)]

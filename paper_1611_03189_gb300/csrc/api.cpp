@@ -198,6 +198,17 @@ int hs_apply(hs_factor f, const double *r, double *z, int32_t nrhs, int64_t ld, 
   });
 }
 
+int hs_apply_static(hs_factor f, const double *r, double *z, int32_t nrhs, int64_t ld, void *stream) {
+  return hs::guarded([&]() -> int {
+    if (!f || !r || !z) fail(HS_ERR_INVALID, "null argument");
+    if (nrhs < 1 || nrhs > 64) fail(HS_ERR_INVALID, "nrhs must be in [1, 64]");
+    if (ld < f->h.plan.n) fail(HS_ERR_INVALID, "ld < n");
+    if (!f->h.valid) fail(HS_ERR_INVALID, "the handle holds no valid factorization");
+    hs::apply_static(f->h, r, z, nrhs, ld, (cudaStream_t)stream);
+    return HS_OK;
+  });
+}
+
 int hs_pcg(hs_factor f, const double *b, double *x, int32_t nrhs, int64_t ld, double rtol, int32_t maxit,
            int32_t *iters, double *relres, void *stream) {
   return hs::guarded([&]() -> int {

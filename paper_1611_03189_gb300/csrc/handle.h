@@ -150,5 +150,6 @@ void apply_solve(FactorHandle &h, const double *r, double *z, int nrhs, int64_t 
                  cudaStream_t st);
 int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld, double rtol,
               int maxit, int *iters, double *relres, cudaStream_t st);
+void apply_static(FactorHandle &h, const double *r, double *z, int nrhs, int64_t ld, cudaStream_t st);
 
 }  // namespace hs

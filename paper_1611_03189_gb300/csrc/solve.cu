@@ -17,6 +17,8 @@
 // depend on scheduling.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
+#include <string>
 
 #include "handle.h"
 
@@ -664,6 +666,130 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
   }
   (void)converged;
   return all ? HS_OK : HS_ERR_NO_CONVERGENCE;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free apply (hs_apply_static).  Some callers cannot allocate device
+// memory when they solve: code that records work inside a CUDA stream capture,
+// or a service that fixes its device-memory footprint at start-up.  For them
+// the apply workspace comes from one file-scope device array instead of the
+// handle's lazily grown buffers.  The array is shared by every call on a
+// device and keeps the previous call's contents; calls that overlap on the
+// GPU race on it.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticApplyBytes = size_t(16) << 20;   // 16 MiB per device
+static __device__ __align__(256) unsigned char g_static_apply_ws[kStaticApplyBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+void *g_static_ptr[64] = {nullptr};
+
+// Device address of the array for the current device; looked up on the first
+// call on each device (with that device current) and cached.
+void *static_ws_for_current_device() {
+  int dev = 0;
+  HS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) fail(HS_ERR_CUDA, "device ordinal out of range for the static apply buffer");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_apply_ws);
+    if (e != cudaSuccess || !ptr)
+      fail(HS_ERR_CUDA, std::string("cudaGetSymbolAddress of the static apply buffer: ") + cudaGetErrorString(e));
+    g_static_ptr[dev] = ptr;
+  }
+  return g_static_ptr[dev];
+}
+
+template <typename T, int NR>
+void apply_static_nr(FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, int j0, cudaStream_t st) {
+  auto blocks = [](int warps) { return (warps + AW - 1) / AW; };
+  for (const LevelApply &la : h.levels)
+    for (int w = la.wave_first; w < la.wave_first + la.wave_count; ++w) {
+      const WaveApply &wa = h.waves[w];
+      if (wa.rows_f) {
+        k_f1<T, NR><<<blocks(wa.rows_f), AT, 0, st>>>(h.d_nodes, wa.node_first, wa.node_count, wa.rows_f, ws, tb,
+                                                      nrhs, j0);
+        count_launch();
+      }
+      if (wa.tch) {
+        k_f2<T, NR><<<blocks(wa.tch), AT, 0, st>>>(h.d_targets, wa.tgt_first, wa.tgt_count, wa.tch, h.d_contribs,
+                                                   ws, tb, nrhs, j0);
+        count_launch();
+      }
+    }
+  if (h.root_m > 0) {
+    const int64_t cnt = (int64_t)h.root_m * nrhs;
+    k_copy<T><<<(int)std::min<int64_t>((cnt + 255) / 256, 1024), 256, 0, st>>>(ws + h.root_off * nrhs, tb, cnt);
+    k_root<T, NR><<<blocks(h.root_m), AT, 0, st>>>((const T *)h.root_inv, h.root_m, h.root_off, ws, tb, nrhs, j0);
+    count_launch(2);
+  }
+  for (int li = (int)h.levels.size() - 1; li >= 0; --li) {
+    const LevelApply &la = h.levels[li];
+    for (int w = la.wave_first + la.wave_count - 1; w >= la.wave_first; --w) {
+      const WaveApply &wa = h.waves[w];
+      if (!wa.rows_b) continue;
+      k_b1<T, NR><<<blocks(wa.rows_b + wa.pch), AT, 0, st>>>(h.d_nodes, wa.node_first, wa.node_count, wa.rows_b,
+                                                             wa.pch, h.d_nbrs, ws, tb, tb2, nrhs, j0);
+      k_b2<T, NR><<<blocks(wa.rows_b), AT, 0, st>>>(h.d_nodes, wa.node_first, wa.node_count, wa.rows_b, ws, tb,
+                                                    tb2, nrhs, j0);
+      count_launch(2);
+    }
+  }
+  HS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void apply_static_t(FactorHandle &h, const double *r, double *z, int nrhs, int64_t ld, cudaStream_t st) {
+  const int64_t n = h.plan.n;
+  const int64_t tcap = std::max<int64_t>(std::max<int64_t>(h.tmax, h.root_m), 1);
+  // layout: workspace (ws_size x nrhs), t (tcap x nrhs), second t (tcap x nrhs), 256-byte aligned parts
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t ws_b = up(sizeof(T) * (size_t)h.ws_size * nrhs);
+  const size_t t_b = up(sizeof(T) * (size_t)tcap * nrhs);
+  const size_t need = ws_b + 2 * t_b;
+  if (need > kStaticApplyBytes)
+    fail(HS_ERR_CAPACITY, "hs_apply_static needs " + std::to_string(need) + " bytes of workspace for this factor and " +
+                              std::to_string(nrhs) + " right-hand sides; the static buffer holds " +
+                              std::to_string(kStaticApplyBytes) + " bytes");
+  unsigned char *base = (unsigned char *)static_ws_for_current_device();
+  T *ws = (T *)base, *tb = (T *)(base + ws_b), *tb2 = (T *)(base + ws_b + t_b);
+  k_gather_in<T><<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, ws);
+  count_launch();
+  // the red-node right-hand sides start at zero (Algorithm 2); the array keeps the last call's contents
+  if (h.ws_size > n) HS_CUDA(cudaMemsetAsync(ws + n * nrhs, 0, sizeof(T) * (h.ws_size - n) * nrhs, st));
+  for (int j0 = 0; j0 < nrhs;) {
+    const int rem = nrhs - j0;
+    if (rem > 8) {
+      apply_static_nr<T, 16>(h, ws, tb, tb2, nrhs, j0, st);
+      j0 += 16;
+    } else if (rem > 4) {
+      apply_static_nr<T, 8>(h, ws, tb, tb2, nrhs, j0, st);
+      j0 += 8;
+    } else if (rem > 2) {
+      apply_static_nr<T, 4>(h, ws, tb, tb2, nrhs, j0, st);
+      j0 += 4;
+    } else if (rem == 2) {
+      apply_static_nr<T, 2>(h, ws, tb, tb2, nrhs, j0, st);
+      j0 += 2;
+    } else {
+      apply_static_nr<T, 1>(h, ws, tb, tb2, nrhs, j0, st);
+      j0 += 1;
+    }
+  }
+  k_scatter_out<T><<<grid_for(n * nrhs), 256, 0, st>>>(ws, h.d_perm, n, nrhs, nrhs, z, ld);
+  count_launch();
+  HS_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+void apply_static(FactorHandle &h, const double *r, double *z, int nrhs, int64_t ld, cudaStream_t st) {
+  if (h.prec == HS_PREC_F64)
+    apply_static_t<double>(h, r, z, nrhs, ld, st);
+  else
+    apply_static_t<float>(h, r, z, nrhs, ld, st);
 }
 
 FactorHandle::~FactorHandle() {
