@@ -363,7 +363,7 @@ def main():
                        "factor_prec": args.prec, "pcg": "fp64", "rtol": 1e-10, "nrhs": args.nrhs,
                        "l2": "inputs larger than L2 (factor records > 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": "apply (Algorithm 2: k_fwd_node, k_fwd_target, k_bwd_node)",
+            "roofline": {"bound": "hbm", "kernel": "apply (Algorithm 2: k_f1, k_f2, k_b1, k_b2, k_root)",
                          "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                          "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                          "traffic": None, "algorithmic_bytes": apply_bytes, "launch_ms": apply_ms},
@@ -371,6 +371,7 @@ def main():
             "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": 8 * (pb0.nnz + n * args.nrhs),
                     "d2h_bytes_per_step": 8 * n * args.nrhs},
             "gpu_launches": launches,
+            "launches_before_timed": l0,
             "clocks": clk,
             "factor_ms": factor_ms, "solve_ms": solve_ms, "pcg_iterations": int(it1.max()),
             "iterations_timed": iters_seen[args.warmup:], "max_relres": max(rrs),

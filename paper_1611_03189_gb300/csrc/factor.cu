@@ -74,6 +74,37 @@ struct BlockRef {
   int rowkey;  // key whose unknowns index the rows of the stored matrix
 };
 
+// Pinned host staging for descriptor uploads, two buffers used in alternate
+// waves: a wave's host->device copies have completed by the next wave's
+// synchronisation, so a buffer is rewritten only two waves later.
+struct Staging {
+  char *buf[2] = {nullptr, nullptr};
+  size_t cap[2] = {0, 0};
+  size_t off = 0;
+  int cur = 0;
+  std::vector<char *> retired;  // outgrown buffers, freed after the final synchronisation
+  ~Staging() {
+    for (int i = 0; i < 2; ++i) cudaFreeHost(buf[i]);
+    for (char *p : retired) cudaFreeHost(p);
+  }
+  void next_wave() {
+    cur ^= 1;
+    off = 0;
+  }
+  char *put(const char *src, size_t n) {
+    size_t o = (off + 255) & ~(size_t)255;
+    if (o + n > cap[cur]) {
+      if (buf[cur]) retired.push_back(buf[cur]);
+      cap[cur] = std::max<size_t>(std::max<size_t>(2 * cap[cur], n + 256), (size_t)4 << 20);
+      HS_CUDA(cudaMallocHost(&buf[cur], cap[cur]));
+      o = 0;
+    }
+    std::memcpy(buf[cur] + o, src, n);
+    off = o + n;
+    return buf[cur] + o;
+  }
+};
+
 struct Uploader {
   std::vector<char> buf;
   template <typename X>
@@ -83,10 +114,11 @@ struct Uploader {
     if (!v.empty()) std::memcpy(buf.data() + off, v.data(), v.size() * sizeof(X));
     return off;
   }
-  char *upload(DevArena &a, cudaStream_t st) {
+  char *upload(DevArena &a, Staging &sg, cudaStream_t st) {
     if (buf.empty()) return nullptr;
     char *d = (char *)a.alloc(buf.size());
-    HS_CUDA(cudaMemcpyAsync(d, buf.data(), buf.size(), cudaMemcpyHostToDevice, st));
+    const char *h = sg.put(buf.data(), buf.size());
+    HS_CUDA(cudaMemcpyAsync(d, h, buf.size(), cudaMemcpyHostToDevice, st));
     return d;
   }
 };
@@ -120,12 +152,12 @@ struct GemmBatch {
     tiles += ((M + GEMM_TM - 1) / GEMM_TM) * ((N + GEMM_TN - 1) / GEMM_TN);
     flops += 2.0 * M * N * (double)std::max(K, 0);
   }
-  void launch(DevArena &scr, cudaStream_t st) {
+  void launch(DevArena &scr, Staging &sg, cudaStream_t st) {
     if (tasks.empty()) return;
     Uploader u;
     const size_t ot = u.add(tasks);
     const size_t os = u.add(tile_start);
-    char *d = u.upload(scr, st);
+    char *d = u.upload(scr, sg, st);
     launch_gemm<T>((const GemmTask<T> *)(d + ot), (const int *)(d + os), (int)tasks.size(), tiles, st);
     tasks.clear();
     tile_start.clear();
@@ -175,13 +207,13 @@ struct SumBatch {
     src(s, sld, trans);
     end();
   }
-  void launch(DevArena &scr, cudaStream_t st) {
+  void launch(DevArena &scr, Staging &sg, cudaStream_t st) {
     if (tasks.empty()) return;
     Uploader u;
     const size_t ot = u.add(tasks);
     const size_t os = u.add(srcs);
     const size_t ol = u.add(tile_start);
-    char *d = u.upload(scr, st);
+    char *d = u.upload(scr, sg, st);
     launch_sum<T>((const SumTask<T> *)(d + ot), (const SumSrc<T> *)(d + os), (const int *)(d + ol),
                   (int)tasks.size(), tiles, st);
     tasks.clear();
@@ -191,13 +223,26 @@ struct SumBatch {
   }
 };
 
+// What a Cholesky status word refers to; formatted only when it reports a failure.
+struct Tag {
+  int kind;   // 0 A_ss, 1 S (first CholQR pass), 2 S (second pass), 3 U^T U, 4 root block
+  int level;
+  int s;
+};
+
+inline std::string describe(const Tag &t) {
+  static const char *names[] = {"A_ss", "S (first CholQR pass)", "S (second CholQR pass)", "U^T U", "root block"};
+  if (t.kind == 4) return "root block";
+  return "level " + std::to_string(t.level) + " super node " + std::to_string(t.s) + ": " + names[t.kind];
+}
+
 template <typename T>
 struct CholBatch {
   std::vector<CholTask<T>> tasks;
-  std::vector<std::string> what;
+  std::vector<Tag> what;
   int max_m = 0;
   double flops = 0.0;
-  void add(const T *A, int lda, T *Linv, int m, const std::string &w) {
+  void add(const T *A, int lda, T *Linv, int m, const Tag &w) {
     if (m <= 0) return;
     CholTask<T> t;
     t.A = A;
@@ -238,7 +283,7 @@ T *talloc(DevArena &a, size_t n) {
 // Pending device status words checked at the next synchronisation point.
 struct PendingStatus {
   int *d = nullptr;
-  std::vector<std::string> what;
+  std::vector<Tag> what;
 };
 
 template <typename T>
@@ -249,7 +294,11 @@ class Run {
     phi_host_ = phi_host;
     HS_CUDA(cudaMallocHost(&hbuf_, hbuf_cap_ * sizeof(int)));
   }
-  ~Run() { cudaFreeHost(hbuf_); }
+  ~Run() {
+    // copies from the pinned staging buffers may still be in flight after an error
+    cudaStreamSynchronize(st_);
+    cudaFreeHost(hbuf_);
+  }
 
   void run();
 
@@ -296,6 +345,7 @@ class Run {
   };
   std::vector<Rec> recs_;
   std::vector<PendingStatus> pending_;
+  Staging sg_;
   int *hbuf_ = nullptr;
   size_t hbuf_cap_ = 1 << 16;
   double flops_ = 0.0;
@@ -321,7 +371,7 @@ void Run<T>::sync_check() {
     HS_CUDA(cudaMemcpy(hb, ps.d, ps.what.size() * sizeof(int), cudaMemcpyDeviceToHost));
     for (size_t i = 0; i < ps.what.size(); ++i)
       if (hb[i] != 0)
-        fail(HS_ERR_NOT_SPD, ps.what[i] + " is not positive definite (pivot " +
+        fail(HS_ERR_NOT_SPD, describe(ps.what[i]) + " is not positive definite (pivot " +
                                  std::to_string(hb[i] - 1) + ")");
   }
   pending_.clear();
@@ -473,7 +523,7 @@ void Run<T>::merge(int nred, int key_base) {
       o += ssize[j];
     }
   }
-  sb.launch(*h_.scratch, st_);
+  sb.launch(*h_.scratch, sg_, st_);
   blocks_.swap(nb);
   phi_.swap(nphi);
   size_.assign(2 * nsup, -1);
@@ -543,8 +593,7 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
     }
     auto dit = blocks_.find(bkey(s, s));
     if (dit == blocks_.end()) fail(HS_ERR_INVALID, "internal: missing diagonal block");
-    chol.add(dit->second.ptr, dit->second.ld, x.Linv, m,
-             "level " + std::to_string(lv.level) + " super node " + std::to_string(s) + ": A_ss");
+    chol.add(dit->second.ptr, dit->second.ld, x.Linv, m, Tag{0, lv.level, s});
     if (x.red && m > 0) {
       gram.add(x.AsW, x.dW, 0, x.AsW, x.dW, 1, x.G, m, m, m, x.dW, T(1), T(0));
       if (use_phi_) gram.add(x.AsW, x.dW, 0, x.phiW, 1, 0, x.a, 1, m, 1, x.dW, T(1), T(0));
@@ -569,29 +618,29 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
     }
   }
   for (size_t i = 0; i < trunc_big.size(); ++i) trunc_big[i].k_idx = (int)(trunc.size() + i);
-  gather.launch(scr, st_);
+  gather.launch(scr, sg_, st_);
   // phase A kernels
   int *d_stat = (int *)scr.alloc(sizeof(int) * (chol.tasks.size() + trunc.size() + trunc_big.size() + 1));
   int *d_k = d_stat + chol.tasks.size();
   if (!chol.tasks.empty()) {
     Uploader u;
     const size_t o = u.add(chol.tasks);
-    char *d = u.upload(scr, st_);
+    char *d = u.upload(scr, sg_, st_);
     launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)chol.tasks.size(), d_stat, chol.max_m, st_);
   }
   flops_ += chol.flops + gram.flops;
-  gram.launch(scr, st_);
+  gram.launch(scr, sg_, st_);
   if (!trunc.empty()) {
     Uploader u;
     const size_t o = u.add(trunc);
-    char *d = u.upload(scr, st_);
+    char *d = u.upload(scr, sg_, st_);
     launch_trunc<T>((const TruncTask<T> *)(d + o), (int)trunc.size(), d_k, h_.eps, h_.variant,
                     max_trunc_m, st_);
   }
   if (!trunc_big.empty()) {
     Uploader u;
     const size_t o = u.add(trunc_big);
-    char *d = u.upload(scr, st_);
+    char *d = u.upload(scr, sg_, st_);
     launch_trunc_big<T>((const TruncTask<T> *)(d + o), (int)trunc_big.size(), d_k, h_.eps, h_.variant,
                         max_big_m, st_);
   }
@@ -602,7 +651,7 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
   sync_check();
   for (size_t i = 0; i < chol.tasks.size(); ++i)
     if (hb[i] != 0)
-      fail(HS_ERR_NOT_SPD, chol.what[i] + " is not positive definite (pivot " + std::to_string(hb[i] - 1) + ")");
+      fail(HS_ERR_NOT_SPD, describe(chol.what[i]) + " is not positive definite (pivot " + std::to_string(hb[i] - 1) + ")");
   for (size_t i = 0; i < trunc.size(); ++i) S[trunc_sup[i]].k = hb[chol.tasks.size() + i];
   for (size_t i = 0; i < trunc_big.size(); ++i) S[big_sup[i]].k = hb[chol.tasks.size() + trunc.size() + i];
   if (!big_sup.empty()) {
@@ -619,10 +668,10 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
       U1s[q] = talloc<T>(scr, (size_t)m * m);
       U2s[q] = talloc<T>(scr, (size_t)m * m);
       o1.add(x.U, m, 1, x.U, m, 0, Sg, k, k, k, m, T(1), T(0));
-      oc1.add(Sg, k, Lg, k, "level " + std::to_string(lv.level) + " super node " + std::to_string(x.s) + ": U^T U");
+      oc1.add(Sg, k, Lg, k, Tag{3, lv.level, x.s});
       o2.add(x.U, m, 0, Lg, k, 1, U1s[q], m, m, k, k, T(1), T(0));
       o3.add(U1s[q], m, 1, U1s[q], m, 0, Sg2, k, k, k, m, T(1), T(0));
-      oc2.add(Sg2, k, Lg2, k, "level " + std::to_string(lv.level) + " super node " + std::to_string(x.s) + ": U^T U");
+      oc2.add(Sg2, k, Lg2, k, Tag{3, lv.level, x.s});
       o4.add(U1s[q], m, 0, Lg2, k, 1, U2s[q], m, m, k, k, T(1), T(0));
     }
     auto chol_now = [&](CholBatch<T> &cb) {
@@ -632,16 +681,16 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
       ps.what = cb.what;
       Uploader u;
       const size_t o = u.add(cb.tasks);
-      char *d = u.upload(scr, st_);
+      char *d = u.upload(scr, sg_, st_);
       launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)cb.tasks.size(), ps.d, cb.max_m, st_);
       pending_.push_back(ps);
     };
-    o1.launch(scr, st_);
+    o1.launch(scr, sg_, st_);
     chol_now(oc1);
-    o2.launch(scr, st_);
-    o3.launch(scr, st_);
+    o2.launch(scr, sg_, st_);
+    o3.launch(scr, sg_, st_);
     chol_now(oc2);
-    o4.launch(scr, st_);
+    o4.launch(scr, sg_, st_);
     for (int q : big_sup)
       if (U2s[q]) S[q].U = U2s[q];
   }
@@ -677,10 +726,10 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
     // L^-1 U and its CholQR2
     g1.add(x.Linv, m, 0, x.U, m, 0, x.Ut, k, m, k, m, T(1), T(0));
     g2.add(x.Ut, k, 1, x.Ut, k, 0, x.S1, k, k, k, m, T(1), T(0));
-    c1.add(x.S1, k, x.L1, k, "level " + std::to_string(lv_level_hint_) + " super node " + std::to_string(x.s) + ": S (first CholQR pass)");
+    c1.add(x.S1, k, x.L1, k, Tag{1, lv.level, x.s});
     g3.add(x.Ut, k, 0, x.L1, k, 1, x.Q1, k, m, k, k, T(1), T(0));
     g4.add(x.Q1, k, 1, x.Q1, k, 0, x.S2, k, k, k, m, T(1), T(0));
-    c2.add(x.S2, k, x.L2, k, "level " + std::to_string(lv_level_hint_) + " super node " + std::to_string(x.s) + ": S (second CholQR pass)");
+    c2.add(x.S2, k, x.L2, k, Tag{2, lv.level, x.s});
     g5.add(x.Q1, k, 0, x.L2, k, 1, x.Q, k, m, k, k, T(1), T(0));
     g5.add(x.L1, k, 1, x.L2, k, 1, x.Rinv, k, k, k, k, T(1), T(0));
     // quantities needing Q / L^-1
@@ -709,22 +758,22 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
     ps.what = cb.what;
     Uploader u;
     const size_t o = u.add(cb.tasks);
-    char *d = u.upload(scr, st_);
+    char *d = u.upload(scr, sg_, st_);
     launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)cb.tasks.size(), ps.d, cb.max_m, st_);
     pending_.push_back(ps);
     flops_ += cb.flops;
   };
   for (GemmBatch<T> *g : {&g1, &g2, &g3, &g4, &g5, &g6, &g7, &g8}) flops_ += g->flops;
-  g1.launch(scr, st_);
-  g2.launch(scr, st_);
+  g1.launch(scr, sg_, st_);
+  g2.launch(scr, sg_, st_);
   run_chol(c1);
-  g3.launch(scr, st_);
-  g4.launch(scr, st_);
+  g3.launch(scr, sg_, st_);
+  g4.launch(scr, sg_, st_);
   run_chol(c2);
-  g5.launch(scr, st_);
-  g6.launch(scr, st_);
-  g7.launch(scr, st_);
-  g8.launch(scr, st_);
+  g5.launch(scr, sg_, st_);
+  g6.launch(scr, sg_, st_);
+  g7.launch(scr, sg_, st_);
+  g8.launch(scr, sg_, st_);
 
   // register the red nodes' blocks and gather the Schur update by target
   std::unordered_map<uint64_t, std::vector<std::pair<int, int>>> tgt;  // target -> (sup idx, pair)
@@ -785,7 +834,7 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
     }
     schur.end();
   }
-  schur.launch(scr, st_);
+  schur.launch(scr, sg_, st_);
 
   // new red nodes, removal of the eliminated super nodes, apply records
   for (auto &x : S) {
@@ -972,19 +1021,19 @@ void Run<T>::root() {
   T *Linv = talloc<T>(*h_.scratch, (size_t)m * m);
   T *Ainv = talloc<T>(*h_.pers, (size_t)m * m);
   CholBatch<T> cb;
-  cb.add(b.ptr, b.ld, Linv, m, "root block");
+  cb.add(b.ptr, b.ld, Linv, m, Tag{4, 0, 0});
   PendingStatus ps;
   ps.d = (int *)h_.pers->alloc(sizeof(int));
   ps.what = cb.what;
   Uploader u;
   const size_t o = u.add(cb.tasks);
-  char *d = u.upload(*h_.scratch, st_);
+  char *d = u.upload(*h_.scratch, sg_, st_);
   launch_chol_inv<T>((const CholTask<T> *)(d + o), 1, ps.d, m, st_);
   pending_.push_back(ps);
   GemmBatch<T> g;
   g.add(Linv, m, 1, Linv, m, 0, Ainv, m, m, m, m, T(1), T(0));
   flops_ += cb.flops + g.flops;
-  g.launch(*h_.scratch, st_);
+  g.launch(*h_.scratch, sg_, st_);
   h_.root_inv = Ainv;
   h_.info.root_size = m;
 }
@@ -1010,12 +1059,14 @@ void Run<T>::run() {
     h_.ranks.emplace_back(lv.nsup, -1);
     for (int w = 0; w < (int)lv.waves.size(); ++w) {
       h_.scratch->reset();
+      sg_.next_wave();
       wave(lv, (int)li, w);
     }
     end_level(lv, (int)li);
     nred = lv.nsup;
   }
   h_.scratch->reset();
+  sg_.next_wave();
   root();
   sync_check();
   h_.info.factor_flops = flops_;

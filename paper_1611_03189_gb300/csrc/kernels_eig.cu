@@ -4,8 +4,10 @@
 //
 // One CTA (1024 threads) per super node:
 //   1. GC basis U_1 = orth[phi_s, A_sw phi_w] (Sec. 6), as in the Jacobi path.
-//   2. ||A_sw||_2^2 = lambda_max(G): tridiagonalise G, bisection for the top
-//      eigenvalue (GC only; LoRaSp takes it from step 3).
+//   2. ||A_sw||_2^2 = lambda_max(G).  LoRaSp: top eigenvalue of T below.  GC:
+//      G = J + (rank <= 4 terms in span{U_1, G U_1}), so lambda_max(G) follows
+//      from the tridiagonal T of J by a warp multisection on the Haynsworth
+//      inertia count of the low-rank correction (no second tridiagonalisation).
 //   3. J = G (LoRaSp), (I - U1 U1^T) G (I - U1 U1^T) (GC) or I - U1 U1^T (GC,
 //      eps = 0).  Tridiagonalise J = Q T Q^T; k2 = #{lambda(T) > thr} by one
 //      Sturm count (FP64), thr = eps^2 lambda_max(G) (Sec. 3.2, strict).
@@ -245,6 +247,27 @@ __device__ R bisect_eig(const R *d, const R *e, int m, int idx, const Gersh<R> &
   return R(0.5) * (lo + hi);
 }
 
+// idx-th smallest eigenvalue by multisection with one warp (33 sub-intervals per
+// round; called by all 32 lanes of a warp, every lane returns the result)
+template <typename R>
+__device__ R multisect_eig(const R *d, const R *e, int m, int idx, const Gersh<R> &g) {
+  const int lane = threadIdx.x & 31;
+  R lo = g.lo, hi = g.hi;
+  const R tol = R(4) * unit_round<R>() * g.tnorm;
+  for (int round = 0; round < 40 && hi - lo > tol; ++round) {
+    const R sig = lo + (hi - lo) * R(lane + 1) / R(33);
+    const bool below = sturm_below<R>(d, e, m, sig, g.pivmin) <= idx;   // eigenvalue idx >= sig
+    const unsigned mask = __ballot_sync(0xffffffffu, below);
+    const int l = mask ? 31 - __clz(mask) : -1;
+    const R nlo = l >= 0 ? lo + (hi - lo) * R(l + 1) / R(33) : lo;
+    const R nhi = lo + (hi - lo) * R(l + 2) / R(33);
+    if (!(nhi > nlo)) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  return R(0.5) * (lo + hi);
+}
+
 __device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b) {
   uint32_t x = a * 0x9E3779B9u ^ (b + 0x7F4A7C15u);
   x ^= x >> 16;
@@ -330,6 +353,79 @@ __device__ void inverse_iteration(const R *d, const R *e, int m, R lam, R tnorm,
   }
 }
 
+
+// Eigenvalues of G above sigma, for sigma > lambda_max(T), where Q^T G Q = T + Z M Z^T,
+// T = tridiag(d, e) (the tridiagonal of the projected Gram J = P G P), Z = Q^T [U_1, G U_1]
+// (m x 2 k1, column j at Z + j*m) and M = [[-C, I], [I, 0]], C = U_1^T G U_1.
+// Haynsworth inertia of [[T - sigma I, Z], [Z^T, -M^-1]] gives
+//   #eig(G) > sigma = n_+(-M^-1 - Z^T (T - sigma I)^-1 Z) - n_+(-M^-1),  n_+(-M^-1) = k1,
+// since T - sigma I is negative definite.  With T - sigma I = L D L^T (L unit
+// lower bidiagonal) and W = L^-1 Z, Z^T (T - sigma I)^-1 Z = W^T D^-1 W: one
+// forward sweep with register accumulators, no storage.
+template <typename R>
+__device__ int count_above_lowrank(const R *d, const R *e, int m, const R *Z, int k1, const R (&C)[2][2],
+                                   R sigma) {
+  const int nz = 2 * k1;
+  R w[4] = {R(0), R(0), R(0), R(0)};
+  R g[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int b2 = 0; b2 < 4; ++b2) g[a][b2] = R(0);
+  R dd = R(1), lprev = R(0);
+  for (int i = 0; i < m; ++i) {
+    dd = (i == 0) ? d[0] - sigma : d[i] - sigma - lprev * e[i - 1];
+    const R inv = R(1) / dd;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+      if (a < nz) w[a] = Z[(size_t)a * m + i] - (i == 0 ? R(0) : lprev * w[a]);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b2 = 0; b2 < 4; ++b2)
+        if (a < nz && b2 <= a) g[a][b2] = fma(w[a] * inv, w[b2], g[a][b2]);
+    lprev = (i + 1 < m) ? e[i] * inv : R(0);
+  }
+  R S[4][4];
+  for (int a = 0; a < nz; ++a)
+    for (int b = 0; b < nz; ++b) {
+      R v = R(0);
+      if (a < k1 && b >= k1 && b - k1 == a) v = R(-1);
+      if (b < k1 && a >= k1 && a - k1 == b) v = R(-1);
+      if (a >= k1 && b >= k1) v = -C[a - k1][b - k1];
+      S[a][b] = v - (b <= a ? g[a][b] : g[b][a]);
+    }
+  // symmetrise and count positive eigenvalues by cyclic Jacobi on the small matrix
+  for (int a = 0; a < nz; ++a)
+    for (int b = a + 1; b < nz; ++b) {
+      const R v = R(0.5) * (S[a][b] + S[b][a]);
+      S[a][b] = v;
+      S[b][a] = v;
+    }
+  for (int sweep = 0; sweep < 12; ++sweep)
+    for (int p = 0; p < nz; ++p)
+      for (int q = p + 1; q < nz; ++q) {
+        const R apq = S[p][q];
+        if (fabs(apq) <= R(1e-30)) continue;
+        const R th = (S[q][q] - S[p][p]) / (R(2) * apq);
+        R tt = R(1) / (fabs(th) + sqrt(R(1) + th * th));
+        if (th < R(0)) tt = -tt;
+        const R c = R(1) / sqrt(R(1) + tt * tt), sn = tt * c;
+        for (int k = 0; k < nz; ++k) {
+          const R skp = S[k][p], skq = S[k][q];
+          S[k][p] = c * skp - sn * skq;
+          S[k][q] = sn * skp + c * skq;
+        }
+        for (int k = 0; k < nz; ++k) {
+          const R spk = S[p][k], sqk = S[q][k];
+          S[p][k] = c * spk - sn * sqk;
+          S[q][k] = sn * spk + c * sqk;
+        }
+      }
+  int pos = 0;
+  for (int a = 0; a < nz; ++a)
+    if (S[a][a] > R(0)) ++pos;
+  return pos - k1;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict__ tasks, int *__restrict__ kout,
                                                  double eps, int variant, int tile_cap) {
@@ -367,11 +463,13 @@ __global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict
   b.tile = (T *)p;
   b.tile_cap = tile_cap;
   b.red = red;
-  // global work: A (m^2), Y (m^2), LU (4 m^2), all T; flags (m^2 bytes)
+  // global work, all T: A (m^2), Y (m^2), LU (4 m^2), LS (164 m: Z = Q^T [U1, X] in
+  // 4 m, then 32 lanes x 5 m of multisection scratch); then flags (m^2 bytes)
   T *A = t.work;
   T *Y = t.work + (size_t)m * m;
   T *LU = Y + (size_t)m * m;
-  unsigned char *FL = (unsigned char *)(LU + 4 * (size_t)m * m);
+  T *LS = LU + 4 * (size_t)m * m;
+  unsigned char *FL = (unsigned char *)(LS + 164 * (size_t)m);
   if (m == 0) {
     if (tid == 0) kout[t.k_idx] = 0;
     return;
@@ -417,16 +515,9 @@ __global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict
     if (tid == 0) kout[t.k_idx] = m;
     return;
   }
-  // ---- lambda_max(G)
+  // ---- lambda_max(G) (GC) follows from the tridiagonal of the projected Gram below
   double lmax = 0.0;
-  if (gc && eps > 0.0) {
-    for (int64_t q = tid; q < (int64_t)m * m; q += nt) A[q] = t.G[q];
-    __syncthreads();
-    tridiag<T>(A, m, b);
-    const Gersh<T> g = gershgorin<T>(b.dt, b.et, m);
-    lmax = (double)bisect_eig<T>(b.dt, b.et, m, m - 1, g);
-    __syncthreads();
-  }
+  T cmat[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
   // ---- J
   if (!gc) {
     for (int64_t q = tid; q < (int64_t)m * m; q += nt) A[q] = t.G[q];
@@ -449,6 +540,7 @@ __global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict
         T s = T(0);
         for (int i = tid; i < m; i += nt) s = fma(t.U[(int64_t)i * m + a], Y[(size_t)bb * m + i], s);
         c[a][bb] = bsum_t<T>(s, b.redt);
+        cmat[a][bb] = c[a][bb];
       }
     // J = G - U1 X^T - X U1^T + U1 c U1^T, one warp per row
     {
@@ -480,14 +572,72 @@ __global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict
     }
   }
   __syncthreads();
+  // X = G U1 (Y columns 0..k1-1) is needed again below: move it next to U1 first
+  T *Zb = LS;  // Z = Q^T [U1, X], 2 k1 <= 4 columns of m
+  if (gc && eps > 0.0) {
+    for (int64_t q = tid; q < (int64_t)m * k1; q += nt) {
+      const int a = (int)(q / m), i = (int)(q % m);
+      Zb[(size_t)a * m + i] = t.U[(int64_t)i * m + a];
+      Zb[(size_t)(k1 + a) * m + i] = Y[(size_t)a * m + i];
+    }
+  }
+  __syncthreads();
   tridiag<T>(A, m, b);
   const Gersh<T> g = gershgorin<T>(b.dt, b.et, m);
   double thr;
+  __shared__ double s_lmax;
   if (!gc) {
-    lmax = (double)bisect_eig<T>(b.dt, b.et, m, m - 1, g);
+    if (tid < 32) {
+      const T lt = multisect_eig<T>(b.dt, b.et, m, m - 1, g);
+      if (tid == 0) s_lmax = (double)lt;
+    }
+    __syncthreads();
+    lmax = s_lmax;
+    thr = eps * eps * lmax;
+  } else if (eps > 0.0) {
+    // Z = Q^T [U1, X]: reflectors in forward order, one warp per column
+    {
+      const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+      for (int j = warp; j < 2 * k1; j += nw) {
+        T *z = Zb + (size_t)j * m;
+        for (int k = 0; k + 2 < m; ++k) {
+          const T tk = b.tau[k];
+          if (tk == T(0)) continue;
+          const int n1 = m - k - 1;
+          const T *vrow = A + (int64_t)k * m + k + 1;
+          T sdot = T(0);
+          for (int i = lane; i < n1; i += 32) sdot = fma(i == 0 ? T(1) : vrow[i], z[k + 1 + i], sdot);
+          for (int o = 16; o > 0; o >>= 1) sdot += __shfl_xor_sync(0xffffffffu, sdot, o);
+          sdot *= tk;
+          for (int i = lane; i < n1; i += 32) z[k + 1 + i] -= sdot * (i == 0 ? T(1) : vrow[i]);
+          __syncwarp();
+        }
+      }
+    }
+    __syncthreads();
+    // lambda_max(G) by multisection on the low-rank count, one warp
+    if (tid < 32) {
+      const T lmaxT = multisect_eig<T>(b.dt, b.et, m, m - 1, g);
+      T trace = T(0);
+      for (int i = 0; i < m; ++i) trace += t.G[(int64_t)i * m + i];
+      T lo = lmaxT, hi = fmax(trace, lmaxT) * T(1.0001) + T(1e-30);
+      for (int round = 0; round < 40 && hi - lo > T(4) * unit_round<T>() * hi; ++round) {
+        const T sig = lo + (hi - lo) * T(tid + 1) / T(33);
+        const int c = k1 > 0 ? count_above_lowrank<T>(b.dt, b.et, m, Zb, k1, cmat, sig) : 0;
+        const unsigned above = __ballot_sync(0xffffffffu, c >= 1);
+        const int l = above ? 31 - __clz(above) : -1;   // highest sigma with an eigenvalue above it
+        const T nlo = l >= 0 ? lo + (hi - lo) * T(l + 1) / T(33) : lo;
+        const T nhi = lo + (hi - lo) * T(l + 2) / T(33);
+        lo = nlo;
+        hi = nhi;
+      }
+      if (tid == 0) s_lmax = (double)(T(0.5) * (lo + hi));
+    }
+    __syncthreads();
+    lmax = s_lmax;
     thr = eps * eps * lmax;
   } else {
-    thr = (eps > 0.0) ? eps * eps * lmax : 0.5;
+    thr = 0.5;
   }
   // ---- rank: eigenvalues strictly above thr, one Sturm count in FP64
   if (tid == 0) {
@@ -586,8 +736,8 @@ __global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict
 
 template <typename T>
 size_t trunc_big_work_elems(int m) {
-  // A, Y, LU (6 m^2 T) + flags (m^2 bytes); Y also holds 2 m doubles of scratch
-  const size_t bytes = sizeof(T) * 6 * (size_t)m * m + (size_t)m * m + 64;
+  // A, Y, LU (6 m^2 T) + LS (164 m T) + flags (m^2 bytes); Y also holds 2 m doubles of scratch
+  const size_t bytes = sizeof(T) * (6 * (size_t)m * m + 164 * (size_t)m) + (size_t)m * m + 64;
   return (bytes + sizeof(T) - 1) / sizeof(T);
 }
 
