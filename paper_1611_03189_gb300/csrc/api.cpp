@@ -15,9 +15,14 @@ namespace hs {
 namespace {
 thread_local std::string g_err;
 std::atomic<int64_t> g_launches{0};
+thread_local int g_count_paused = 0;
 }
 
-void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void count_launch(int n) {
+  if (!g_count_paused) g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+CountPause::CountPause() { ++g_count_paused; }
+CountPause::~CountPause() { --g_count_paused; }
 
 void set_error(const std::string &msg) { g_err = msg; }
 
@@ -64,6 +69,7 @@ X *upload_vec(const std::vector<X> &v, cudaStream_t st) {
 // counters.  Used by hs_factor_create and hs_factor_refactor.
 void numeric_factor(FactorHandle &h, const double *val, const double *phi_host, cudaStream_t st) {
   h.stream = st;
+  h.drop_graphs();   // the schedule and the record pointers change
   launch_gather_values(val, h.d_src, h.nnz, h.d_val, st);
   cudaFree(h.d_nodes);
   cudaFree(h.d_nbrs);

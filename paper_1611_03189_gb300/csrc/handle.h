@@ -82,6 +82,16 @@ struct LevelApply {
   int wave_first, wave_count;
 };
 
+// A recorded launch sequence (CUDA graph) of the solve.  key: the
+// right-hand-side count of an apply, or kPcgGraphKey + 2 * nrhs_p + parity
+// for one PCG iteration.
+struct GraphEntry {
+  int key;
+  cudaGraphExec_t exec;
+  int kernels;       // kernel nodes, counted by hs_launch_count per replay
+};
+constexpr int kPcgGraphKey = 1 << 16;
+
 struct FactorHandle {
   Plan plan;
   int prec = HS_PREC_F64;
@@ -134,6 +144,15 @@ struct FactorHandle {
   double *d_scal = nullptr;            // per-rhs scalars
   int *d_iflags = nullptr;             // per-rhs ints + block counter
   int part_blocks = 0;
+  int *h_done = nullptr;               // pinned: PCG "all converged" flag
+
+  // recorded solve graphs and the private stream they are recorded on
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;
+  void drop_graphs() {
+    for (GraphEntry &g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
 
   // per-level ranks: ranks[li][s] = k or -1
   std::vector<std::vector<int>> ranks;

@@ -28,6 +28,12 @@ void set_error(const std::string &msg);
 
 // kernel launches of this library in the process (hs_launch_count)
 void count_launch(int n = 1);
+// While one is alive, count_launch on this thread counts nothing (launches
+// recorded into a CUDA graph are counted when the graph runs).
+struct CountPause {
+  CountPause();
+  ~CountPause();
+};
 
 #define HS_CUDA(call)                                                                   \
   do {                                                                                  \

@@ -8,17 +8,19 @@
 // a level share the same memory.
 //
 // Per wave (in elimination order) the forward pass runs
-//   k_fwd_node:   t_s = M_ss phi_s, phi_r += P_ss phi_s      (restriction)
-//   k_fwd_target: phi_n -= sum_s A_ns t_s                    (forward substitution)
-// then the root solve, then per wave in reverse order
-//   k_bwd_node:   x_s = M_ss (phi_s - sum_n A_sn x_n) + P_ss^T x_r
-//                                        (backward substitution and prolongation).
+//   k_f1:  t_s = M_ss phi_s, phi_r += P_ss phi_s       (restriction)
+//   k_f2:  phi_n -= sum_s A_ns t_s                     (forward substitution)
+// then the root solve (k_copy, k_root), then per wave in reverse order
+//   k_b1:  v_s = phi_s - sum_n A_sn x_n, y_s = P_ss^T x_r
+//   k_b2:  x_s = M_ss v_s + y_s           (backward substitution and prolongation).
 // Contributions to one phi_n are summed in a fixed order, so results do not
 // depend on scheduling.
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "handle.h"
 
@@ -287,36 +289,46 @@ __global__ void k_convert(const A *__restrict__ a, B *__restrict__ b, int64_t n)
 }
 
 // ---------------------------------------------------------------------------
-// PCG kernels.  nrhs_p is a power of two <= 32; element e = (row, rhs) with the
-// rhs fastest.  Block partial sums are reduced by the last block to finish, in
-// block order, so every reduction is deterministic.
+// PCG kernels.  Vectors are n x NP (row-major, NP = right-hand sides rounded up
+// to a power of two <= 32).  Every reduction visits the rows of one right-hand
+// side in an order that depends on n alone: thread t of block b takes rows
+// b*PT + t + k*gridDim*PT in turn, blocks reduce in a fixed tree, and the last
+// block to finish adds the block partials in block order.  So a right-hand
+// side gets the same bits whether it is solved alone or batched with others
+// (the apply and the SpMV are column-wise already).
 // ---------------------------------------------------------------------------
 constexpr int PT = 256;
 
-struct PcgScal {       // per-rhs scalars, each an array of nrhs_p doubles
+struct PcgScal {       // per-rhs scalars, each an array of NP doubles
   double *bnorm2, *rz, *alpha, *beta, *pq, *rr;
 };
 struct PcgFlags {
   int *active, *iters, *counter, *done;
 };
 
-// block partial of v (one value per thread, rhs = e % nrhs_p) -> part[block*nrhs_p + j]
-__device__ void block_partial(double v, int nrhs_p, double *part) {
-  __shared__ double wsum[PT / 32][32];
-  for (int o = 16; o >= nrhs_p; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// block sums of v[j] -> part[block*NP + j], in a fixed order
+template <int NP>
+__device__ void block_partial(const double (&v)[NP], double *part) {
+  __shared__ double wsum[PT / 32][NP];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane < nrhs_p) wsum[warp][lane] = v;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    double s = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) wsum[warp][j] = s;
+  }
   __syncthreads();
-  if (threadIdx.x < nrhs_p) {
-    // warps cover consecutive element ranges, lane j of each warp holds rhs j
+  if (threadIdx.x < NP) {
     double s = 0.0;
     for (int w = 0; w < PT / 32; ++w) s += wsum[w][threadIdx.x];
-    part[blockIdx.x * nrhs_p + threadIdx.x] = s;
+    part[blockIdx.x * NP + threadIdx.x] = s;
   }
 }
 
 // returns true in the last block to finish; sums[j] = ordered total
-__device__ bool finish_sum(const double *part, int nrhs_p, int *counter, double *sums) {
+template <int NP>
+__device__ bool finish_sum(const double *part, int *counter, double *sums) {
   __shared__ bool last;
   __threadfence();
   __syncthreads();
@@ -324,9 +336,9 @@ __device__ bool finish_sum(const double *part, int nrhs_p, int *counter, double 
   __syncthreads();
   if (!last) return false;
   __threadfence();
-  if (threadIdx.x < nrhs_p) {
+  if (threadIdx.x < NP) {
     double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile const double *)part)[b * nrhs_p + threadIdx.x];
+    for (int b = 0; b < (int)gridDim.x; ++b) s += ((volatile const double *)part)[b * NP + threadIdx.x];
     sums[threadIdx.x] = s;
   }
   __syncthreads();
@@ -336,20 +348,20 @@ __device__ bool finish_sum(const double *part, int nrhs_p, int *counter, double 
 
 enum { DOT_BNORM = 0, DOT_RZ_FIRST = 1, DOT_RZ = 2, DOT_PLAIN = 3 };
 
-__global__ void __launch_bounds__(PT) k_dot(const double *__restrict__ u, const double *__restrict__ w,
-                                            int64_t n, int nrhs_p, double *part, PcgScal sc,
-                                            PcgFlags fl, int mode, double *plain_out) {
-  __shared__ double sums[32];
-  double v = 0.0;
-  const int64_t total = n * nrhs_p;
-  // each thread walks e = base + k * stride with stride a multiple of nrhs_p, so its rhs is fixed
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x)
-    v = fma(u[e], w[e], v);
-  block_partial(v, nrhs_p, part);
-  if (!finish_sum(part, nrhs_p, fl.counter, sums)) return;
+template <int NP>
+__global__ void __launch_bounds__(PT) k_dot(const double *__restrict__ u, const double *__restrict__ w, int64_t n,
+                                            double *part, PcgScal sc, PcgFlags fl, int mode, double *plain_out) {
+  __shared__ double sums[NP];
+  double v[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) v[j] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)PT + threadIdx.x; i < n; i += (int64_t)gridDim.x * PT)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) v[j] = fma(u[i * NP + j], w[i * NP + j], v[j]);
+  block_partial<NP>(v, part);
+  if (!finish_sum<NP>(part, fl.counter, sums)) return;
   const int j = threadIdx.x;
-  if (j < nrhs_p) {
+  if (j < NP) {
     const double s = sums[j];
     if (mode == DOT_BNORM) {
       sc.bnorm2[j] = s;
@@ -368,60 +380,72 @@ __global__ void __launch_bounds__(PT) k_dot(const double *__restrict__ u, const 
 }
 
 // p_new = z + beta p_old ; q = A p_new ; partial p_new . q ; alpha = rz / (p.q)
+template <int NP>
 __global__ void __launch_bounds__(PT) k_spmv_p(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
-                                               const double *__restrict__ va, int64_t n, int nrhs_p,
+                                               const double *__restrict__ va, int64_t n,
                                                const double *__restrict__ z, const double *__restrict__ pold,
                                                double *__restrict__ pnew, double *__restrict__ q,
                                                double *part, PcgScal sc, PcgFlags fl) {
-  __shared__ double sums[32];
-  double v = 0.0;
-  const int64_t total = n * nrhs_p;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / nrhs_p;
-    const int j = (int)(e - i * nrhs_p);
-    const double b = sc.beta[j];
-    double acc = 0.0;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
-      const int64_t c = (int64_t)ci[k] * nrhs_p + j;
-      acc = fma(va[k], fma(b, pold[c], z[c]), acc);
-    }
-    const double pn = fma(b, pold[e], z[e]);
-    pnew[e] = pn;
-    q[e] = acc;
-    v = fma(pn, acc, v);
+  __shared__ double sums[NP];
+  double beta[NP], v[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    beta[j] = sc.beta[j];
+    v[j] = 0.0;
   }
-  block_partial(v, nrhs_p, part);
-  if (!finish_sum(part, nrhs_p, fl.counter, sums)) return;
+  for (int64_t i = blockIdx.x * (int64_t)PT + threadIdx.x; i < n; i += (int64_t)gridDim.x * PT) {
+    double acc[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) acc[j] = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) {
+      const double a = va[k];
+      const int64_t c = (int64_t)ci[k] * NP;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) acc[j] = fma(a, fma(beta[j], pold[c + j], z[c + j]), acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const double pn = fma(beta[j], pold[i * NP + j], z[i * NP + j]);
+      pnew[i * NP + j] = pn;
+      q[i * NP + j] = acc[j];
+      v[j] = fma(pn, acc[j], v[j]);
+    }
+  }
+  block_partial<NP>(v, part);
+  if (!finish_sum<NP>(part, fl.counter, sums)) return;
   const int j = threadIdx.x;
-  if (j < nrhs_p) {
+  if (j < NP) {
     sc.pq[j] = sums[j];
     sc.alpha[j] = (fl.active[j] && sums[j] != 0.0) ? sc.rz[j] / sums[j] : 0.0;
   }
 }
 
 // x += alpha p ; r -= alpha q ; partial ||r||^2 ; convergence per rhs
+template <int NP>
 __global__ void __launch_bounds__(PT) k_update(double *__restrict__ x, double *__restrict__ r,
-                                               const double *__restrict__ p, const double *__restrict__ q,
-                                               int64_t n, int nrhs_p, double *part, PcgScal sc,
-                                               PcgFlags fl, double rtol2) {
-  __shared__ double sums[32];
-  double v = 0.0;
-  const int64_t total = n * nrhs_p;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int j = (int)(e % nrhs_p);
-    const double a = sc.alpha[j];
-    const double xv = fma(a, p[e], x[e]);
-    const double rv = fma(-a, q[e], r[e]);
-    x[e] = xv;
-    r[e] = rv;
-    v = fma(rv, rv, v);
+                                               const double *__restrict__ p, const double *__restrict__ q, int64_t n,
+                                               double *part, PcgScal sc, PcgFlags fl, double rtol2) {
+  __shared__ double sums[NP];
+  double alpha[NP], v[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    alpha[j] = sc.alpha[j];
+    v[j] = 0.0;
   }
-  block_partial(v, nrhs_p, part);
-  if (!finish_sum(part, nrhs_p, fl.counter, sums)) return;
+  for (int64_t i = blockIdx.x * (int64_t)PT + threadIdx.x; i < n; i += (int64_t)gridDim.x * PT)
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      const int64_t e = i * NP + j;
+      const double xv = fma(alpha[j], p[e], x[e]);
+      const double rv = fma(-alpha[j], q[e], r[e]);
+      x[e] = xv;
+      r[e] = rv;
+      v[j] = fma(rv, rv, v[j]);
+    }
+  block_partial<NP>(v, part);
+  if (!finish_sum<NP>(part, fl.counter, sums)) return;
   const int j = threadIdx.x;
-  if (j < nrhs_p) {
+  if (j < NP) {
     sc.rr[j] = sums[j];
     if (fl.active[j]) {
       fl.iters[j] += 1;
@@ -431,8 +455,22 @@ __global__ void __launch_bounds__(PT) k_update(double *__restrict__ x, double *_
   __syncthreads();
   if (threadIdx.x == 0) {
     int any = 0;
-    for (int i = 0; i < nrhs_p; ++i) any |= fl.active[i];
+    for (int i = 0; i < NP; ++i) any |= fl.active[i];
     *fl.done = any ? 0 : 1;
+  }
+}
+
+// calls f(std::integral_constant<int, NP>{}) for the power of two np <= 32
+template <typename F>
+void with_np(int np, F &&f) {
+  switch (np) {
+    case 1: f(std::integral_constant<int, 1>{}); break;
+    case 2: f(std::integral_constant<int, 2>{}); break;
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    case 16: f(std::integral_constant<int, 16>{}); break;
+    case 32: f(std::integral_constant<int, 32>{}); break;
+    default: fail(HS_ERR_INVALID, "right-hand-side block must be a power of two <= 32");
   }
 }
 
@@ -456,13 +494,13 @@ int grid_for(int64_t total) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 8));
 }
 
-// grid for the reduction kernels: stride (grid * PT) must be a multiple of nrhs_p
-int rgrid_for(int64_t total) { return grid_for(total); }
+// grid of the PCG reduction kernels: a function of n only (see above)
+int rgrid_for(int64_t n) { return grid_for(n); }
 
+// One pass of Algorithm 2 over right-hand sides [j0, j0 + NR) of the
+// workspace ws (layout [unknown][nrhs]); tb and tb2 are the per-wave scratch.
 template <typename T, int NR>
-void apply_ws_nr(FactorHandle &h, int nrhs, int j0, cudaStream_t st) {
-  T *ws = (T *)h.d_ws;
-  T *tb = (T *)h.d_t, *tb2 = (T *)h.d_t + h.t_cap * h.nrhs_cap;
+void apply_waves_nr(const FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, int j0, cudaStream_t st) {
   auto blocks = [](int warps) { return (warps + AW - 1) / AW; };
   for (const LevelApply &la : h.levels)
     for (int w = la.wave_first; w < la.wave_first + la.wave_count; ++w) {
@@ -499,44 +537,116 @@ void apply_ws_nr(FactorHandle &h, int nrhs, int j0, cudaStream_t st) {
   HS_CUDA(cudaGetLastError());
 }
 
+// The whole apply on a workspace whose level-L part holds the right-hand
+// sides: red-node parts cleared (Algorithm 2 starts them at zero), then the
+// right-hand sides in chunks of at most 16 (register accumulators).
 template <typename T>
-void apply_ws_t(FactorHandle &h, int nrhs, cudaStream_t st) {
+void apply_chunks(const FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, cudaStream_t st) {
   const int64_t n = h.plan.n;
-  if (h.ws_size > n)
-    HS_CUDA(cudaMemsetAsync((T *)h.d_ws + n * nrhs, 0, sizeof(T) * (h.ws_size - n) * nrhs, st));
-  // right-hand sides in chunks of at most 16 (register accumulators)
+  if (h.ws_size > n) HS_CUDA(cudaMemsetAsync(ws + n * nrhs, 0, sizeof(T) * (h.ws_size - n) * nrhs, st));
   for (int j0 = 0; j0 < nrhs;) {
     const int rem = nrhs - j0;
     if (rem > 8) {
-      apply_ws_nr<T, 16>(h, nrhs, j0, st);
+      apply_waves_nr<T, 16>(h, ws, tb, tb2, nrhs, j0, st);
       j0 += 16;
     } else if (rem > 4) {
-      apply_ws_nr<T, 8>(h, nrhs, j0, st);
+      apply_waves_nr<T, 8>(h, ws, tb, tb2, nrhs, j0, st);
       j0 += 8;
     } else if (rem > 2) {
-      apply_ws_nr<T, 4>(h, nrhs, j0, st);
+      apply_waves_nr<T, 4>(h, ws, tb, tb2, nrhs, j0, st);
       j0 += 4;
     } else if (rem == 2) {
-      apply_ws_nr<T, 2>(h, nrhs, j0, st);
+      apply_waves_nr<T, 2>(h, ws, tb, tb2, nrhs, j0, st);
       j0 += 2;
     } else {
-      apply_ws_nr<T, 1>(h, nrhs, j0, st);
+      apply_waves_nr<T, 1>(h, ws, tb, tb2, nrhs, j0, st);
       j0 += 1;
     }
   }
 }
 
+// apply on the handle's workspace d_ws, launched directly
+void apply_ws_direct(const FactorHandle &h, int nrhs, cudaStream_t st) {
+  if (h.prec == HS_PREC_F64) {
+    double *tb = (double *)h.d_t;
+    apply_chunks<double>(h, (double *)h.d_ws, tb, tb + h.t_cap * h.nrhs_cap, nrhs, st);
+  } else {
+    float *tb = (float *)h.d_t;
+    apply_chunks<float>(h, (float *)h.d_ws, tb, tb + h.t_cap * h.nrhs_cap, nrhs, st);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs.  One apply is about four dependent launches per wave (some 240
+// at the 512 x 512 workload), each too short to hide its launch latency, so
+// the launch sequence is recorded once per factorization and right-hand-side
+// count and replayed with one cudaGraphLaunch.  Recording happens on a private
+// stream of the handle in thread-local capture mode (other threads keep
+// working); the graph is then launched on the caller's stream.  Graphs hold
+// the handle's device pointers, so they are dropped whenever the schedule or
+// the solve buffers change.  HS_APPLY_GRAPH=0 in the environment selects
+// direct launches instead.
+// ---------------------------------------------------------------------------
+bool graphs_enabled() {
+  static const bool on = [] {
+    const char *e = std::getenv("HS_APPLY_GRAPH");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+template <typename F>
+const GraphEntry &graph_for(FactorHandle &h, int key, F &&record) {
+  for (const GraphEntry &g : h.graphs)
+    if (g.key == key) return g;
+  if (!h.cap_stream) HS_CUDA(cudaStreamCreateWithFlags(&h.cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  HS_CUDA(cudaStreamBeginCapture(h.cap_stream, cudaStreamCaptureModeThreadLocal));
+  try {
+    CountPause pause;   // launches are counted when the graph runs
+    record(h.cap_stream);
+  } catch (...) {
+    cudaStreamEndCapture(h.cap_stream, &graph);
+    if (graph) cudaGraphDestroy(graph);
+    throw;
+  }
+  HS_CUDA(cudaStreamEndCapture(h.cap_stream, &graph));
+  size_t nn = 0;
+  cudaError_t e = cudaGraphGetNodes(graph, nullptr, &nn);
+  std::vector<cudaGraphNode_t> nodes(nn);
+  if (e == cudaSuccess && nn) e = cudaGraphGetNodes(graph, nodes.data(), &nn);
+  int kernels = 0;
+  for (size_t i = 0; e == cudaSuccess && i < nn; ++i) {
+    cudaGraphNodeType t;
+    e = cudaGraphNodeGetType(nodes[i], &t);
+    kernels += (e == cudaSuccess && t == cudaGraphNodeTypeKernel) ? 1 : 0;
+  }
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  HS_CUDA(e);
+  h.graphs.push_back(GraphEntry{key, exec, kernels});
+  return h.graphs.back();
+}
+
+void run_graph(const GraphEntry &g, cudaStream_t st) {
+  HS_CUDA(cudaGraphLaunch(g.exec, st));
+  count_launch(g.kernels);
+}
+
 void apply_ws(FactorHandle &h, int nrhs, cudaStream_t st) {
-  if (h.prec == HS_PREC_F64)
-    apply_ws_t<double>(h, nrhs, st);
-  else
-    apply_ws_t<float>(h, nrhs, st);
+  if (!graphs_enabled()) {
+    apply_ws_direct(h, nrhs, st);
+    return;
+  }
+  run_graph(graph_for(h, nrhs, [&](cudaStream_t cs) { apply_ws_direct(h, nrhs, cs); }), st);
 }
 
 void ensure_buffers(FactorHandle &h, int nrhs_cap) {
   const int64_t tneed0 = std::max<int64_t>(std::max<int64_t>(h.tmax, h.root_m), 1);
   if (h.nrhs_cap >= nrhs_cap && h.d_ws && h.ws_cap >= h.ws_size && h.t_cap >= tneed0) return;
   nrhs_cap = std::max(nrhs_cap, h.nrhs_cap);
+  h.drop_graphs();   // they hold the old buffers
   cudaFree(h.d_ws);
   cudaFree(h.d_t);
   cudaFree(h.d_pcg);
@@ -558,6 +668,7 @@ void ensure_buffers(FactorHandle &h, int nrhs_cap) {
   HS_CUDA(cudaMalloc(&h.d_scal, sizeof(double) * 6 * 32));
   HS_CUDA(cudaMalloc(&h.d_iflags, sizeof(int) * (2 * 32 + 2)));
   HS_CUDA(cudaMemset(h.d_iflags, 0, sizeof(int) * (2 * 32 + 2)));
+  if (!h.h_done) HS_CUDA(cudaMallocHost(&h.h_done, sizeof(int)));
   h.nrhs_cap = nrhs_cap;
 }
 
@@ -579,21 +690,31 @@ void apply_solve(FactorHandle &h, const double *r, double *z, int nrhs, int64_t 
   HS_CUDA(cudaGetLastError());
 }
 
+namespace {
+
 // z = A_H^-1 r on the FP64 PCG vectors (layout n x np): through the workspace
 // in the factor precision
-void apply_pcg(FactorHandle &h, const double *R, double *Z, int np, cudaStream_t st) {
+void apply_pcg(FactorHandle &h, const double *R, double *Z, int np, cudaStream_t st, bool direct) {
   const int64_t tot = h.plan.n * np;
   if (h.prec == HS_PREC_F64) {
     HS_CUDA(cudaMemcpyAsync(h.d_ws, R, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
-    apply_ws(h, np, st);
-    HS_CUDA(cudaMemcpyAsync(Z, h.d_ws, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
   } else {
     k_convert<double, float><<<grid_for(tot), 256, 0, st>>>(R, (float *)h.d_ws, tot);
+    count_launch();
+  }
+  if (direct)
+    apply_ws_direct(h, np, st);
+  else
     apply_ws(h, np, st);
+  if (h.prec == HS_PREC_F64) {
+    HS_CUDA(cudaMemcpyAsync(Z, h.d_ws, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+  } else {
     k_convert<float, double><<<grid_for(tot), 256, 0, st>>>((const float *)h.d_ws, Z, tot);
-    count_launch(2);
+    count_launch();
   }
 }
+
+}  // namespace
 
 int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld, double rtol,
               int maxit, int *iters, double *relres, cudaStream_t st) {
@@ -605,49 +726,66 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
   double *X = h.d_pcg, *R = X + tot, *P0 = R + tot, *P1 = P0 + tot, *Q = P1 + tot, *B = Q + tot, *Z = B + tot;
   PcgScal sc{h.d_scal, h.d_scal + 32, h.d_scal + 64, h.d_scal + 96, h.d_scal + 128, h.d_scal + 160};
   PcgFlags fl{h.d_iflags, h.d_iflags + 32, h.d_iflags + 64, h.d_iflags + 65};
-  const int g = rgrid_for(tot);
-  // grid * PT is a multiple of 256, hence of np (np <= 32): each thread keeps one rhs
+  const int g = rgrid_for(n);
+  const double rtol2 = rtol * rtol;
   k_gather_in<double><<<grid_for(tot), 256, 0, st>>>(b, ld, h.d_perm, n, nrhs, np, B);
   count_launch();
   HS_CUDA(cudaMemcpyAsync(R, B, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
   HS_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * tot, st));
   HS_CUDA(cudaMemsetAsync(P0, 0, sizeof(double) * tot, st));
-  k_dot<<<g, PT, 0, st>>>(B, B, n, np, h.d_part, sc, fl, DOT_BNORM, nullptr);
+  with_np(np, [&](auto c) {
+    constexpr int NP = decltype(c)::value;
+    k_dot<NP><<<g, PT, 0, st>>>(B, B, n, h.d_part, sc, fl, DOT_BNORM, nullptr);
+  });
   count_launch();
-  // z = A_H^-1 r
-  apply_pcg(h, R, Z, np, st);
-  k_dot<<<g, PT, 0, st>>>(R, Z, n, np, h.d_part, sc, fl, DOT_RZ_FIRST, nullptr);
-  count_launch();
-  int *done_h = nullptr;
-  HS_CUDA(cudaMallocHost(&done_h, sizeof(int)));
-  double *pold = P0, *pnew = P1;
-  int it = 0;
-  const double rtol2 = rtol * rtol;
-  bool converged = false;
-  while (it < maxit) {
-    k_spmv_p<<<g, PT, 0, st>>>(h.d_rowptr, h.d_col, h.d_val, n, np, Z, pold, pnew, Q, h.d_part, sc, fl);
-    count_launch();
-    k_update<<<g, PT, 0, st>>>(X, R, pnew, Q, n, np, h.d_part, sc, fl, rtol2);
-    count_launch();
+  // z = A_H^-1 r ; first direction p = z (beta = 0)
+  apply_pcg(h, R, Z, np, st, !graphs_enabled());
+  with_np(np, [&](auto c) {
+    constexpr int NP = decltype(c)::value;
+    k_dot<NP><<<g, PT, 0, st>>>(R, Z, n, h.d_part, sc, fl, DOT_RZ_FIRST, nullptr);
+    k_spmv_p<NP><<<g, PT, 0, st>>>(h.d_rowptr, h.d_col, h.d_val, n, Z, P0, P1, Q, h.d_part, sc, fl);
+    k_update<NP><<<g, PT, 0, st>>>(X, R, P1, Q, n, h.d_part, sc, fl, rtol2);
+  });
+  count_launch(3);
+  HS_CUDA(cudaGetLastError());
+  // One iteration after the first: z = A_H^-1 r, beta, p_new = z + beta p_old,
+  // q = A p_new, alpha, x and r updates.  Right-hand sides that have converged
+  // get alpha = beta = 0 and stay as they are.  Recorded as a graph per
+  // direction buffer pair.
+  auto body = [&, np](cudaStream_t cs, double *pold, double *pnew) {
+    apply_pcg(h, R, Z, np, cs, true);
+    with_np(np, [&](auto c) {
+      constexpr int NP = decltype(c)::value;
+      k_dot<NP><<<g, PT, 0, cs>>>(R, Z, n, h.d_part, sc, fl, DOT_RZ, nullptr);
+      k_spmv_p<NP><<<g, PT, 0, cs>>>(h.d_rowptr, h.d_col, h.d_val, n, Z, pold, pnew, Q, h.d_part, sc, fl);
+      k_update<NP><<<g, PT, 0, cs>>>(X, R, pnew, Q, n, h.d_part, sc, fl, rtol2);
+    });
+    count_launch(3);
     HS_CUDA(cudaGetLastError());
-    ++it;
-    HS_CUDA(cudaMemcpyAsync(done_h, fl.done, sizeof(int), cudaMemcpyDeviceToHost, st));
+  };
+  int it = 1;
+  while (true) {
+    HS_CUDA(cudaMemcpyAsync(h.h_done, fl.done, sizeof(int), cudaMemcpyDeviceToHost, st));
     HS_CUDA(cudaStreamSynchronize(st));
-    if (*done_h) {
-      converged = true;
-      break;
+    if (*h.h_done || it >= maxit) break;
+    // after an odd number of iterations the latest direction is in P1
+    double *pold = (it & 1) ? P1 : P0, *pnew = (it & 1) ? P0 : P1;
+    if (graphs_enabled()) {
+      const int key = kPcgGraphKey + 2 * np + (it & 1);
+      run_graph(graph_for(h, key, [&](cudaStream_t cs) { body(cs, pold, pnew); }), st);
+    } else {
+      body(st, pold, pnew);
     }
-    std::swap(pold, pnew);
-    apply_pcg(h, R, Z, np, st);
-    k_dot<<<g, PT, 0, st>>>(R, Z, n, np, h.d_part, sc, fl, DOT_RZ, nullptr);
-    count_launch();
+    ++it;
   }
-  cudaFreeHost(done_h);
   // true relative residual
   k_residual<<<grid_for(tot), 256, 0, st>>>(h.d_rowptr, h.d_col, h.d_val, n, np, X, B, Q);
   count_launch();
   double *rr_d = h.d_scal + 5 * 32;
-  k_dot<<<g, PT, 0, st>>>(Q, Q, n, np, h.d_part, sc, fl, DOT_PLAIN, rr_d);
+  with_np(np, [&](auto c) {
+    constexpr int NP = decltype(c)::value;
+    k_dot<NP><<<g, PT, 0, st>>>(Q, Q, n, h.d_part, sc, fl, DOT_PLAIN, rr_d);
+  });
   count_launch();
   k_scatter_out<double><<<grid_for(n * nrhs), 256, 0, st>>>(X, h.d_perm, n, nrhs, np, x, ld);
   count_launch();
@@ -664,7 +802,6 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
     relres[j] = bn > 0 ? std::sqrt(hs[160 + j] / bn) : 0.0;
     all = all && hi[j] == 0;
   }
-  (void)converged;
   return all ? HS_OK : HS_ERR_NO_CONVERGENCE;
 }
 
@@ -702,44 +839,6 @@ void *static_ws_for_current_device() {
   return g_static_ptr[dev];
 }
 
-template <typename T, int NR>
-void apply_static_nr(FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, int j0, cudaStream_t st) {
-  auto blocks = [](int warps) { return (warps + AW - 1) / AW; };
-  for (const LevelApply &la : h.levels)
-    for (int w = la.wave_first; w < la.wave_first + la.wave_count; ++w) {
-      const WaveApply &wa = h.waves[w];
-      if (wa.rows_f) {
-        k_f1<T, NR><<<blocks(wa.rows_f), AT, 0, st>>>(h.d_nodes, wa.node_first, wa.node_count, wa.rows_f, ws, tb,
-                                                      nrhs, j0);
-        count_launch();
-      }
-      if (wa.tch) {
-        k_f2<T, NR><<<blocks(wa.tch), AT, 0, st>>>(h.d_targets, wa.tgt_first, wa.tgt_count, wa.tch, h.d_contribs,
-                                                   ws, tb, nrhs, j0);
-        count_launch();
-      }
-    }
-  if (h.root_m > 0) {
-    const int64_t cnt = (int64_t)h.root_m * nrhs;
-    k_copy<T><<<(int)std::min<int64_t>((cnt + 255) / 256, 1024), 256, 0, st>>>(ws + h.root_off * nrhs, tb, cnt);
-    k_root<T, NR><<<blocks(h.root_m), AT, 0, st>>>((const T *)h.root_inv, h.root_m, h.root_off, ws, tb, nrhs, j0);
-    count_launch(2);
-  }
-  for (int li = (int)h.levels.size() - 1; li >= 0; --li) {
-    const LevelApply &la = h.levels[li];
-    for (int w = la.wave_first + la.wave_count - 1; w >= la.wave_first; --w) {
-      const WaveApply &wa = h.waves[w];
-      if (!wa.rows_b) continue;
-      k_b1<T, NR><<<blocks(wa.rows_b + wa.pch), AT, 0, st>>>(h.d_nodes, wa.node_first, wa.node_count, wa.rows_b,
-                                                             wa.pch, h.d_nbrs, ws, tb, tb2, nrhs, j0);
-      k_b2<T, NR><<<blocks(wa.rows_b), AT, 0, st>>>(h.d_nodes, wa.node_first, wa.node_count, wa.rows_b, ws, tb,
-                                                    tb2, nrhs, j0);
-      count_launch(2);
-    }
-  }
-  HS_CUDA(cudaGetLastError());
-}
-
 template <typename T>
 void apply_static_t(FactorHandle &h, const double *r, double *z, int nrhs, int64_t ld, cudaStream_t st) {
   const int64_t n = h.plan.n;
@@ -757,27 +856,7 @@ void apply_static_t(FactorHandle &h, const double *r, double *z, int nrhs, int64
   T *ws = (T *)base, *tb = (T *)(base + ws_b), *tb2 = (T *)(base + ws_b + t_b);
   k_gather_in<T><<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, ws);
   count_launch();
-  // the red-node right-hand sides start at zero (Algorithm 2); the array keeps the last call's contents
-  if (h.ws_size > n) HS_CUDA(cudaMemsetAsync(ws + n * nrhs, 0, sizeof(T) * (h.ws_size - n) * nrhs, st));
-  for (int j0 = 0; j0 < nrhs;) {
-    const int rem = nrhs - j0;
-    if (rem > 8) {
-      apply_static_nr<T, 16>(h, ws, tb, tb2, nrhs, j0, st);
-      j0 += 16;
-    } else if (rem > 4) {
-      apply_static_nr<T, 8>(h, ws, tb, tb2, nrhs, j0, st);
-      j0 += 8;
-    } else if (rem > 2) {
-      apply_static_nr<T, 4>(h, ws, tb, tb2, nrhs, j0, st);
-      j0 += 4;
-    } else if (rem == 2) {
-      apply_static_nr<T, 2>(h, ws, tb, tb2, nrhs, j0, st);
-      j0 += 2;
-    } else {
-      apply_static_nr<T, 1>(h, ws, tb, tb2, nrhs, j0, st);
-      j0 += 1;
-    }
-  }
+  apply_chunks<T>(h, ws, tb, tb2, nrhs, st);
   k_scatter_out<T><<<grid_for(n * nrhs), 256, 0, st>>>(ws, h.d_perm, n, nrhs, nrhs, z, ld);
   count_launch();
   HS_CUDA(cudaGetLastError());
@@ -793,6 +872,9 @@ void apply_static(FactorHandle &h, const double *r, double *z, int nrhs, int64_t
 }
 
 FactorHandle::~FactorHandle() {
+  drop_graphs();
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  if (h_done) cudaFreeHost(h_done);
   cudaFree(d_src);
   cudaFree(d_leaf_dest);
   cudaFree(d_phi0);
