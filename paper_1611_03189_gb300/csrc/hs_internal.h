@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -42,6 +43,38 @@ struct CountPause {
       ::hs::fail(e_ == cudaErrorMemoryAllocation ? HS_ERR_OOM : HS_ERR_CUDA,            \
                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
   } while (0)
+
+// The largest dynamic shared memory a kernel may request is a process-wide
+// attribute of the function.  It is raised once per kernel and device to the
+// device's opt-in limit and never lowered, so launches from several host
+// threads cannot undo each other's setting between set and launch.  Returns
+// the usable dynamic bytes.
+template <auto Kernel>
+int allow_max_dynamic_smem() {
+  static std::mutex mu;
+  static int limit[64] = {0};
+  int dev = 0;
+  HS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) fail(HS_ERR_CUDA, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!limit[dev]) {
+    int optin = 0;
+    HS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    HS_CUDA(cudaFuncGetAttributes(&fa, Kernel));
+    const int dyn = optin - (int)fa.sharedSizeBytes;
+    HS_CUDA(cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    limit[dev] = dyn;
+  }
+  return limit[dev];
+}
+
+// fails with HS_ERR_CAPACITY when `bytes` exceed what the kernel may request
+inline void check_dynamic_smem(size_t bytes, int limit, const char *what) {
+  if (bytes > (size_t)limit)
+    fail(HS_ERR_CAPACITY, std::string(what) + " needs " + std::to_string(bytes) +
+                              " bytes of shared memory; the device allows " + std::to_string(limit));
+}
 
 // ---------------------------------------------------------------------------
 // task descriptors (shared by host and device)

@@ -663,13 +663,11 @@ void launch_chol_inv(const CholTask<T> *d_tasks, int ntasks, int *d_status, int 
   if (ntasks == 0) return;
   if (max_m <= chol_smem_cap<T>()) {
     const size_t sm = sizeof(T) * ((size_t)max_m * max_m + max_m + 8);
-    HS_CUDA(cudaFuncSetAttribute(k_chol_inv<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm));
+    check_dynamic_smem(sm, allow_max_dynamic_smem<&k_chol_inv<T, true>>(), "k_chol_inv");
     k_chol_inv<T, true><<<ntasks, CHOL_THREADS, sm, st>>>(d_tasks, d_status);
   } else {
     const size_t sm = sizeof(T) * ((size_t)max_m + 8);
-    HS_CUDA(cudaFuncSetAttribute(k_chol_inv<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm));
+    check_dynamic_smem(sm, allow_max_dynamic_smem<&k_chol_inv<T, false>>(), "k_chol_inv");
     k_chol_inv<T, false><<<ntasks, CHOL_THREADS, sm, st>>>(d_tasks, d_status);
   }
   count_launch();
@@ -687,13 +685,11 @@ void launch_trunc(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps,
   if (ntasks == 0) return;
   if (max_m <= trunc_smem_cap<T>()) {
     const size_t sm = 2 * sizeof(T) * (size_t)max_m * max_m + trunc_small_arrays<T>(max_m);
-    HS_CUDA(cudaFuncSetAttribute(k_trunc<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm));
+    check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc<T, true>>(), "k_trunc");
     k_trunc<T, true><<<ntasks, TRUNC_THREADS, sm, st>>>(d_tasks, d_k, eps, variant);
   } else {
     const size_t sm = trunc_small_arrays<T>(max_m);
-    HS_CUDA(cudaFuncSetAttribute(k_trunc<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sm));
+    check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc<T, false>>(), "k_trunc");
     k_trunc<T, false><<<ntasks, TRUNC_THREADS, sm, st>>>(d_tasks, d_k, eps, variant);
   }
   count_launch();

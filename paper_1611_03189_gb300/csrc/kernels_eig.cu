@@ -428,16 +428,26 @@ __device__ int count_above_lowrank(const R *d, const R *e, int m, const R *Z, in
 
 template <typename T>
 __global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict__ tasks, int *__restrict__ kout,
-                                                 double eps, int variant, int tile_cap) {
+                                                 double eps, int variant, int tile_cap, int vec_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
   __shared__ int s_k2;
   const TruncTask<T> t = tasks[blockIdx.x];
   const int m = t.m;
   const int tid = threadIdx.x, nt = blockDim.x;
-  // shared layout
+  // global work, all T: A (m^2), Y (m^2), LU (4 m^2), LS (164 m: Z = Q^T [U1, X] in
+  // 4 m, then per-thread inverse-iteration slots when the shared tile is too
+  // small); then flags (m^2 bytes); then the per-node vectors when they do not
+  // fit in shared memory (vec_smem == 0)
+  T *A = t.work;
+  T *Y = t.work + (size_t)m * m;
+  T *LU = Y + (size_t)m * m;
+  T *LS = LU + 4 * (size_t)m * m;
+  unsigned char *FL = (unsigned char *)(LS + 164 * (size_t)m);
+  unsigned char *VG = (unsigned char *)(((uintptr_t)(FL + (size_t)m * m) + 15) & ~(uintptr_t)15);
+  // vector layout (shared memory, or global at VG), then the shared tile
   Big<T> b;
-  unsigned char *p = smem_raw;
+  unsigned char *p = vec_smem ? smem_raw : VG;
   b.d = (double *)p;
   p += sizeof(double) * m;
   b.e = (double *)p;
@@ -460,16 +470,9 @@ __global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict
   b.redt = (T *)p;
   p += sizeof(T) * 34;
   p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-  b.tile = (T *)p;
+  b.tile = (T *)(vec_smem ? p : smem_raw);
   b.tile_cap = tile_cap;
   b.red = red;
-  // global work, all T: A (m^2), Y (m^2), LU (4 m^2), LS (164 m: Z = Q^T [U1, X] in
-  // 4 m, then 32 lanes x 5 m of multisection scratch); then flags (m^2 bytes)
-  T *A = t.work;
-  T *Y = t.work + (size_t)m * m;
-  T *LU = Y + (size_t)m * m;
-  T *LS = LU + 4 * (size_t)m * m;
-  unsigned char *FL = (unsigned char *)(LS + 164 * (size_t)m);
   if (m == 0) {
     if (tid == 0) kout[t.k_idx] = 0;
     return;
@@ -672,14 +675,21 @@ __global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict
   __syncthreads();
   const int nc = s_nc;
   {
-    // each worker thread owns a slot of the shared tile: u0,u1,u2,l,y (5 m T) + m flags
+    // each worker thread owns a slot: u0,u1,u2,l,y (5 m T) + m flags, in the
+    // shared tile, or in the global LS region (Z is no longer needed) when the
+    // tile holds fewer than 8 slots
     const size_t tile_bytes = (size_t)b.tile_cap * b.tile_cap * sizeof(T);
     const size_t slot_bytes = ((5 * (size_t)m * sizeof(T) + (size_t)m + 15) / 16) * 16;
+    unsigned char *slot_base = (unsigned char *)b.tile;
     int nslot = (int)(tile_bytes / slot_bytes);
+    const int nslot_g = (int)((164 * (size_t)m * sizeof(T) - 16) / slot_bytes);   // 31 or more
+    if (nslot < 8 && nslot < nslot_g) {
+      slot_base = (unsigned char *)(((uintptr_t)LS + 15) & ~(uintptr_t)15);
+      nslot = nslot_g;
+    }
     if (nslot > nt) nslot = nt;
-    if (nslot < 1) nslot = 1;
     if (tid < nslot) {
-      unsigned char *slot = (unsigned char *)b.tile + (size_t)tid * slot_bytes;
+      unsigned char *slot = slot_base + (size_t)tid * slot_bytes;
       T *lu = (T *)slot;
       T *ys = lu + 4 * (size_t)m;
       unsigned char *fl = (unsigned char *)(ys + m);
@@ -699,12 +709,15 @@ __global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict
   {
     const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
     const size_t tile_elems = (size_t)b.tile_cap * b.tile_cap;
-    int batch = (int)(tile_elems / (size_t)m);
-    if (batch < 1) batch = 1;
+    // columns staged in the shared tile, or transformed in place in Y when
+    // the tile cannot hold one column
+    const bool in_place = tile_elems < (size_t)m;
+    int batch = in_place ? max(k2, 1) : (int)(tile_elems / (size_t)m);
     for (int jb = 0; jb < k2; jb += batch) {
       const int nb = min(batch, k2 - jb);
-      T *ysm = b.tile;
-      for (int64_t q = tid; q < (int64_t)nb * m; q += nt) ysm[q] = Y[(size_t)jb * m + q];
+      T *ysm = in_place ? Y + (size_t)jb * m : b.tile;
+      if (!in_place)
+        for (int64_t q = tid; q < (int64_t)nb * m; q += nt) ysm[q] = Y[(size_t)jb * m + q];
       __syncthreads();
       for (int j = warp; j < nb; j += nw) {
         T *y = ysm + (size_t)j * m;
@@ -734,10 +747,19 @@ __global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict
 
 }  // namespace
 
+// bytes of the per-node vectors of k_trunc_big (d, e, pw in FP64; six m-vectors
+// and 34 reduction slots in T), 16-byte aligned
+template <typename T>
+size_t trunc_big_vec_bytes(int m) {
+  return 3 * sizeof(double) * (size_t)m + 6 * sizeof(T) * (size_t)((m + 1) & ~1) + 34 * sizeof(T) + 16;
+}
+
 template <typename T>
 size_t trunc_big_work_elems(int m) {
-  // A, Y, LU (6 m^2 T) + LS (164 m T) + flags (m^2 bytes); Y also holds 2 m doubles of scratch
-  const size_t bytes = sizeof(T) * (6 * (size_t)m * m + 164 * (size_t)m) + (size_t)m * m + 64;
+  // A, Y, LU (6 m^2 T) + LS (164 m T) + flags (m^2 bytes) + the vectors (when
+  // they do not fit in shared memory); Y also holds 2 m doubles of scratch
+  const size_t bytes = sizeof(T) * (6 * (size_t)m * m + 164 * (size_t)m) + (size_t)m * m + 16 +
+                       trunc_big_vec_bytes<T>(m) + 64;
   return (bytes + sizeof(T) - 1) / sizeof(T);
 }
 
@@ -745,14 +767,17 @@ template <typename T>
 void launch_trunc_big(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant, int max_m,
                       cudaStream_t st) {
   if (ntasks == 0) return;
-  const size_t fixed = 3 * sizeof(double) * (size_t)max_m + 6 * sizeof(T) * (size_t)((max_m + 1) & ~1) +
-                       34 * sizeof(T) + 48;
+  // the per-node vectors go to shared memory while they leave room for a
+  // tile of at least 64 x 64; the rest of the budget is the tile
   const size_t budget = 200 * 1024;
+  size_t fixed = trunc_big_vec_bytes<T>(max_m) + 32;
+  const int vec_smem = fixed + 64 * 64 * sizeof(T) <= budget ? 1 : 0;
+  if (!vec_smem) fixed = 32;
   int cap = 0;
   while ((size_t)(cap + 1) * (cap + 1) * sizeof(T) + fixed <= budget) ++cap;
   const size_t sm = fixed + (size_t)cap * cap * sizeof(T);
-  HS_CUDA(cudaFuncSetAttribute(k_trunc_big<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_trunc_big<T><<<ntasks, BT, sm, st>>>(d_tasks, d_k, eps, variant, cap);
+  check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc_big<T>>(), "k_trunc_big");
+  k_trunc_big<T><<<ntasks, BT, sm, st>>>(d_tasks, d_k, eps, variant, cap, vec_smem);
   count_launch();
   HS_CUDA(cudaGetLastError());
 }

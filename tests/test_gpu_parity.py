@@ -239,3 +239,35 @@ print('ok')
     env = dict(__import__("os").environ, HS_EIG_SMALL_MAX="8")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-3000:]
+
+
+LARGE_NODE_CASES = [
+    # 8 leaves of 1728: level-3 super nodes of m = 3456; the per-node vectors
+    # fit in shared memory, the inverse-iteration slots do not
+    ("poisson3d 24 leaf1728", lambda: P.poisson3d(24, leaf_size=1728)),
+    # 8 leaves of 2197: m = 4394, the per-node vectors move to global memory
+    ("poisson3d 26 leaf2197", lambda: P.poisson3d(26, leaf_size=2197)),
+]
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,maker", LARGE_NODE_CASES, ids=[c[0] for c in LARGE_NODE_CASES])
+def test_large_super_nodes_match_oracle(name, maker):
+    """Super nodes of several thousand unknowns (as at the top levels of 3D
+    problems): the large-node truncation keeps its work in global memory where
+    the shared tile is too small, with ranks and apply equal to the oracle."""
+    torch = need_gpu()
+    pb = maker()
+    F = oracle_factor(pb, 1e-2, H.GC_CONSTANT)
+    assert max(r.m for lv in F.levels for r in lv.supers) > 3000
+    G = gpu_factor(pb, 1e-2, H.GC_CONSTANT)
+    assert _ranks_match(F, G) == []
+    B = P.rhs(pb.n, 3, nrhs=2)
+    Z = H.apply(F, B)
+    zg = G.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
+    assert rel(zg, Z) <= 1e-10
+    G32 = gpu_factor(pb, 1e-2, H.GC_CONSTANT, prec=1)
+    z32 = G32.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
+    assert rel(z32, Z) <= 1e-3
+    x, it, rr, _ = G32.pcg(torch.as_tensor(B[:, 0].copy(), device="cuda"), rtol=1e-10, maxit=200)
+    assert rr[0] <= 1e-10
