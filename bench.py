@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import numpy as np
 import os
 import statistics
 import subprocess
@@ -29,28 +30,37 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    # name: (grid side, s, eps, leaf size)
-    "diffusion2d_512": (512, 1.0, 1e-2, 16),
-    "diffusion2d_256": (256, 1.0, 1e-2, 16),
-    "poisson2d_64": (64, 0.0, 1e-2, 16),
+    # name: (dimension, grid side, s, eps, leaf size); s = 0 is the constant-coefficient Poisson problem
+    "diffusion2d_512": (2, 512, 1.0, 1e-2, 16),
+    "diffusion2d_256": (2, 256, 1.0, 1e-2, 16),
+    "poisson2d_64": (2, 64, 0.0, 1e-2, 16),
+    "poisson3d_64": (3, 64, 0.0, 1e-2, 64),
+    "poisson3d_32": (3, 32, 0.0, 1e-2, 64),
+    "poisson3d_24": (3, 24, 0.0, 1e-2, 64),
 }
-CPU_SAMPLE_SIDE = 256     # the oracle's bounded sample of the 512 x 512 recipe
+# the oracle's bounded sample of each workload (10-30 s of one core)
+CPU_SAMPLE = {"diffusion2d_512": "diffusion2d_256", "poisson3d_64": "poisson3d_24", "poisson3d_32": "poisson3d_24"}
 
 
 def make_problem(name: str, seed: int):
     from paper_1611_03189_gb300 import problems as P
 
-    side, s, eps, leaf = WORKLOADS[name]
+    dim, side, s, eps, leaf = WORKLOADS[name]
+    if dim == 3:
+        if s == 0.0:
+            return P.poisson3d(side, leaf_size=leaf), eps
+        return P.diffusion3d(side, s, seed, leaf_size=leaf), eps
     if s == 0.0:
         return P.poisson2d(side, leaf_size=leaf), eps
     return P.diffusion2d(side, s, seed, leaf_size=leaf), eps
 
 
 def sample_for(name: str):
-    side, s, eps, leaf = WORKLOADS[name]
-    if side <= CPU_SAMPLE_SIDE:
-        return name, 1.0
-    return f"diffusion2d_{CPU_SAMPLE_SIDE}", (side / CPU_SAMPLE_SIDE) ** 2
+    """(sample workload, unknowns of the workload / unknowns of the sample)."""
+    sample = CPU_SAMPLE.get(name, name)
+    d, side, *_ = WORKLOADS[name]
+    _, sside, *_ = WORKLOADS[sample]
+    return sample, (side / sside) ** d
 
 
 # ---------------------------------------------------------------------------
@@ -142,8 +152,8 @@ def cpu_baseline(workload: str) -> dict:
     res = run_oracle(sample, 1, seed0=0)
     t = res["times"][0]
     return {"value": (1.0 / t) / scale, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"one factor + PCG solve (1 rhs) of the same recipe on a {CPU_SAMPLE_SIDE}x{CPU_SAMPLE_SIDE} "
-                       f"grid ({t:.2f} s, {res['iters'][0]} iterations), scaled by the unknown count "
+            "sample": (f"one factor + PCG solve (1 rhs) of the same recipe on the smaller grid {sample} "
+                       f"({t:.2f} s, {res['iters'][0]} iterations), scaled by the unknown count "
                        f"x{scale:g} (linear complexity, Sec. 3)" if scale != 1.0 else
                        f"one factor + PCG solve (1 rhs) of the workload ({t:.2f} s)"),
             "sample_seconds": t}
@@ -163,12 +173,174 @@ def reference_arm(args) -> None:
         "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": per * 1000 * scale, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "nrhs": 1, "sample": f"{CPU_SAMPLE_SIDE}x{CPU_SAMPLE_SIDE}"},
+        "config": {"workload": args.workload, "nrhs": 1, "sample": sample},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": f"each step one factor + PCG solve of the recipe on a {CPU_SAMPLE_SIDE}^2 grid, "
+                         "sample": f"each step one factor + PCG solve of the recipe on the smaller grid {sample}, "
                                    f"scaled by the unknown count x{scale:g}"},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "iterations": res["iters"][args.warmup:],
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# batched: many independent 2D diffusion problems factored in lock step
+# ---------------------------------------------------------------------------
+def batched_arm(args) -> None:
+    """Each step: the numeric factorization of all problems in lock step
+    (hs_factor_refactor_batch: one launch per kernel kind and wave step for all
+    of them), then a 4-RHS FP64 PCG solve of every problem, the solves spread
+    over CUDA streams.  Compared with the same problems factored one by one."""
+    import concurrent.futures as cf
+
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1611_03189_gb300 import _lib
+    from paper_1611_03189_gb300 import problems as P
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    count, nrhs = args.batch_count, 4
+    t_gen = time.perf_counter()
+    sides = P.batched_sides(count, seed=3, lo=32, hi=256)
+    pbs = [P.diffusion2d(side, 2.0, 7000 + i, leaf_size=16) for i, side in enumerate(sides)]
+    t_gen = time.perf_counter() - t_gen
+    devs = [(torch.as_tensor(pb.rowptr, device=dev), torch.as_tensor(pb.col, device=dev),
+             torch.as_tensor(pb.val, device=dev)) for pb in pbs]
+    rhs = [torch.as_tensor(P.rhs(pb.n, 100 + i, nrhs=nrhs).T.copy(), device=dev) for i, pb in enumerate(pbs)]
+    prec = _lib.HS_PREC_F32 if args.prec == "f32" else _lib.HS_PREC_F64
+    fs, status = _lib.factor_batch([d + (pb.perm, pb.leaf_ptr) for d, pb in zip(devs, pbs)], 1e-2,
+                                   _lib.HS_GC_CONSTANT, prec)
+    live = [i for i in range(count) if status[i] == _lib.HS_OK]
+    streams = [torch.cuda.Stream(device=dev) for _ in range(8)]
+    pool = cf.ThreadPoolExecutor(max_workers=len(streams))
+
+    def solve_one(j):
+        i = live[j]
+        s = streams[j % len(streams)]
+        with torch.cuda.stream(s):
+            x, it, rr, code = fs[i].pcg(rhs[i], rtol=1e-10, maxit=1000, stream=s, raise_on_fail=False)
+            s.synchronize()
+        return int(it.max()), float(np.max(rr)), code
+
+    def step():
+        st = _lib.refactor_batch([fs[i] for i in live], [devs[i][2] for i in live])
+        if any(int(c) != _lib.HS_OK for c in st):
+            raise RuntimeError("a refactor in the batch failed")
+        torch.cuda.synchronize()
+        return list(pool.map(solve_one, range(len(live))))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = _lib.launch_count()
+    w0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    res = []
+    for _ in range(args.steps):
+        res = step()
+    e1.record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    launches = _lib.launch_count() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    # the factor part alone: batched vs one problem at a time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _lib.refactor_batch([fs[i] for i in live], [devs[i][2] for i in live])
+    torch.cuda.synchronize()
+    batched_factor_ms = (time.perf_counter() - t0) * 1e3
+    t0 = time.perf_counter()
+    for i in live:
+        fs[i].refactor(devs[i][2])
+    torch.cuda.synchronize()
+    single_factor_ms = (time.perf_counter() - t0) * 1e3
+    solves = len(live) * nrhs * args.steps
+    line = {
+        "metric": "solves/s to rel-res 1e-10 (batched factor + PCG, 4 rhs per problem)",
+        "value": solves / (ms / 1000.0), "unit": "rhs solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.prec == "f32" else "f64", "data": "synthetic",
+        "config": {"workload": f"batched_{count}", "problems": count, "sides": "log-uniform [32, 256]",
+                   "s": 2.0, "leaf": 16, "eps": 1e-2, "variant": "GC-constant", "nrhs": nrhs,
+                   "factor_prec": args.prec, "unknowns_total": int(sum(pb.n for pb in pbs)),
+                   "generation_s": t_gen, "pcg_streams": len(streams),
+                   "l2": "inputs larger than L2 (factor records > 129 MB)"},
+        "problems_not_spd": int(count - len(live)),
+        "systems_per_s": len(live) * args.steps / (ms / 1000.0),
+        "factor_batched_ms": batched_factor_ms, "factor_one_by_one_ms": single_factor_ms,
+        "max_pcg_iterations": max(r[0] for r in res), "max_relres": max(r[1] for r in res),
+        "gpu_launches": launches, "clocks": clk, "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+    pool.shutdown()
+    for f in fs:
+        if f is not None:
+            f.close()
+
+
+# ---------------------------------------------------------------------------
+# serving: a Poisson stream of 3D diffusion factor / solve requests
+# ---------------------------------------------------------------------------
+def serve_arm(args) -> None:
+    """Served latency (p50/p99) and throughput of the continuous-batching loop,
+    mixed (FP32) factor against the plain FP64 factor on the same stream."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1611_03189_gb300 import _lib
+    from paper_1611_03189_gb300 import serving as S
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    lo, hi = (int(v) for v in args.serve_sides.split(","))
+    t_gen = time.perf_counter()
+    reqs = S.poisson_stream(args.serve_requests, args.serve_rate, seed=11, sides=(lo, hi), s=2.0, leaf=64)
+    t_gen = time.perf_counter() - t_gen
+    budget = int(args.serve_budget_gb * (1 << 30))
+    # warm-up: kernels loaded, graphs and allocator primed on a few small requests
+    warm = S.poisson_stream(8, 1000.0, seed=12, sides=(lo, lo), s=2.0, leaf=64)
+    out = {}
+    for name, prec in (("mixed_f32", _lib.HS_PREC_F32), ("f64", _lib.HS_PREC_F64)):
+        if name == "f64" and args.no_f64_arm:
+            continue
+        srv = S.Server(budget, slots=args.serve_slots, max_rhs=16, prec=prec)
+        srv.run(warm, realtime=False)
+        clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+        clocks.start()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        res = srv.run(reqs, realtime=True)
+        wall = time.perf_counter() - w0
+        clk = clocks.stop()
+        summ = S.summarize(res, wall)
+        summ["clocks"] = clk
+        summ["peak_charged_gb"] = srv.peak_used / 2**30
+        rr = [float(np.max(r.relres)) for r in res if r.kind == "solve" and r.relres is not None]
+        summ["max_relres"] = max(rr) if rr else None
+        out[name] = summ
+    m = out["mixed_f32"]
+    line = {
+        "metric": "served p50/p99 latency and solves/s (continuous batching; mixed vs FP64 factor)",
+        "value": m["solves_per_s"], "unit": "solve requests/s", "n_gpus": 1, "steps": args.serve_requests,
+        "warmup": len(warm), "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "serving_diffusion3d", "sides": [lo, hi], "s": 2.0, "leaf": 64, "eps": 1e-2,
+                   "p_factor": 0.2, "nrhs": [1, 16], "rate_per_s": args.serve_rate,
+                   "budget_gb": args.serve_budget_gb, "slots": args.serve_slots, "max_batch_rhs": 16,
+                   "requests": args.serve_requests, "generation_s": t_gen},
+        "p50_ms": m["p50_ms"], "p99_ms": m["p99_ms"],
+        "serving": out,
     }
     print(json.dumps(line), flush=True)
 
@@ -186,10 +358,25 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-f64-arm", action="store_true", help="skip the FP64-factor comparison")
     ap.add_argument("--profile", action="store_true", help="print a phase breakdown to stderr")
+    ap.add_argument("--batched", action="store_true", help="run the batched many-problem benchmark")
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--serve", action="store_true", help="run the serving stream instead of the step benchmark")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-rate", type=float, default=20.0, help="mean arrivals per second")
+    ap.add_argument("--serve-sides", default="32,96", help="grid side range of the 3D requests")
+    ap.add_argument("--serve-budget-gb", type=float, default=120.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.batched:
+        batched_arm(args)
+        return
+    if args.serve:
+        serve_arm(args)
         return
 
     import numpy as np
@@ -311,6 +498,39 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     achieved = apply_bytes / (apply_ms / 1000.0) / 1e9
 
+    # ---- the plain FP64 factor at the same accuracy (same inputs, same steps) ----
+    f64 = None
+    if prec != _lib.HS_PREC_F64 and not args.no_f64_arm:
+        x_mixed, _, _, _ = G.pcg(bs[args.warmup], rtol=1e-10, maxit=1000)
+        G64 = _lib.Factor(rp, ci, vals[0], pb0.perm, pb0.leaf_ptr, eps, _lib.HS_GC_CONSTANT, _lib.HS_PREC_F64)
+        it64, rr64 = [], []
+        for k in range(args.warmup):
+            G64.refactor(vals[k])
+            G64.pcg(bs[k], rtol=1e-10, maxit=1000)
+        torch.cuda.synchronize()
+        e2.record(stream)
+        for k in range(args.warmup, nsteps):
+            G64.refactor(vals[k])
+            x64, it, rr, code = G64.pcg(bs[k], rtol=1e-10, maxit=1000, raise_on_fail=False)
+            if code != _lib.HS_OK:
+                raise RuntimeError(f"FP64-factor PCG did not converge: iters {it}, relres {rr}")
+            it64.append(int(it.max()))
+            rr64.append(float(np.max(rr)))
+        e3.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e2.elapsed_time(e3)
+        e2.record(stream)
+        G64.refactor(vals[args.warmup])
+        e3.record(stream)
+        torch.cuda.synchronize()
+        f64_factor_ms = e2.elapsed_time(e3)
+        x64, _, _, _ = G64.pcg(bs[args.warmup], rtol=1e-10, maxit=1000)
+        diff = float(torch.linalg.norm(x_mixed - x64) / torch.linalg.norm(x64))
+        f64 = {"value": args.steps * args.nrhs / (ms64 / 1000.0), "unit": "solves/s", "ms_per_step": ms64 / args.steps,
+               "factor_ms": f64_factor_ms, "iterations_timed": it64, "max_relres": max(rr64),
+               "x_rel_diff_mixed_vs_f64": diff, "factor_bytes": G64.info()["factor_bytes"]}
+        G64.close()
+
     # ---- end to end through the C ABI with host buffers (H2D values + rhs, D2H x) ----
     hv = [torch.empty(pb0.nnz, dtype=torch.float64, pin_memory=True) for _ in range(2)]
     hb = [torch.empty(bs[0].shape, dtype=torch.float64, pin_memory=True) for _ in range(2)]
@@ -351,29 +571,60 @@ def main():
         except Exception as ex:  # the baseline must not hide the GPU number
             cpu = {"error": str(ex)[:200]}
 
+    # ---- the large-node truncation (tridiagonal eigen path): plain FP32/FP64 ALU work ----
+    # nominal eigen-solve flops (4/3 m^3 + 2 m^2 k per node) over the device time
+    # of its launches (CUDA events on the factor stream, inside the library)
+    info_f = G.info()
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    if args.prec == "f32":
+        alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock
+        alu_src = f"derived: 152 SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz"
+    else:
+        alu_peak = 1.25                                   # nominal GB300 FP64 rate
+        alu_src = "nominal GB300 FP64 (1.25 TFLOP/s)"
+    tb_ms = info_f["trunc_big_ms"]
+    tb_launches = max(info_f["trunc_big_launches"], 1)
+    tb_ach = info_f["trunc_big_flops"] / (tb_ms / 1000.0) / 1e12 if tb_ms > 0 else 0.0
+    roof_trunc = {"bound": "alu", "kernel": "k_trunc_big (large-node truncation: tridiagonalisation, "
+                  "bisection, inverse iteration, back-transformation)",
+                  "achieved": tb_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": tb_ach / alu_peak,
+                  "peak_source": alu_src, "traffic": None,
+                  "algorithmic_flops_per_launch": info_f["trunc_big_flops"] / tb_launches,
+                  "launch_ms": tb_ms / tb_launches, "launches_per_factor": info_f["trunc_big_launches"],
+                  "share_of_step": tb_ms / ms_per_step}
+    roof_apply = {"bound": "hbm", "kernel": "apply (Algorithm 2: k_f1, k_f2, k_b1, k_b2, k_root)",
+                  "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                  "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
+                  "traffic": None, "algorithmic_bytes": apply_bytes, "launch_ms": apply_ms,
+                  "share_of_step": apply_ms * int(it1.max()) / ms_per_step}
+    # the dominant kernel of the step is the one with the larger share of its time
+    dominant, other = ((roof_trunc, roof_apply) if roof_trunc["share_of_step"] >= roof_apply["share_of_step"]
+                       else (roof_apply, roof_trunc))
+
     if rank == 0:
         line = {
             "metric": "solves/s to rel-res 1e-10 (factor + PCG solve; mixed vs FP64 factor)",
             "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.prec == "f32" else "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "grid": WORKLOADS[args.workload][0], "n": n,
-                       "s": WORKLOADS[args.workload][1], "eps": WORKLOADS[args.workload][2],
-                       "leaf": WORKLOADS[args.workload][3], "variant": "GC-constant",
+            "config": {"workload": args.workload, "dim": WORKLOADS[args.workload][0],
+                       "grid": WORKLOADS[args.workload][1], "n": n,
+                       "s": WORKLOADS[args.workload][2], "eps": WORKLOADS[args.workload][3],
+                       "leaf": WORKLOADS[args.workload][4], "variant": "GC-constant",
                        "factor_prec": args.prec, "pcg": "fp64", "rtol": 1e-10, "nrhs": args.nrhs,
                        "l2": "inputs larger than L2 (factor records > 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
-            "roofline": {"bound": "hbm", "kernel": "apply (Algorithm 2: k_f1, k_f2, k_b1, k_b2, k_root)",
-                         "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                         "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
-                         "traffic": None, "algorithmic_bytes": apply_bytes, "launch_ms": apply_ms},
+            "roofline": dominant,
+            "roofline_other": other,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": 8 * (pb0.nnz + n * args.nrhs),
                     "d2h_bytes_per_step": 8 * n * args.nrhs},
+            "fp64_factor": f64,
             "gpu_launches": launches,
             "launches_before_timed": l0,
             "clocks": clk,
             "factor_ms": factor_ms, "solve_ms": solve_ms, "pcg_iterations": int(it1.max()),
+            "factor_host_ms": info_f["host_ms"], "factor_wait_ms": info_f["wait_ms"],
             "iterations_timed": iters_seen[args.warmup:], "max_relres": max(rrs),
             "factor_info": {k: info[k] for k in ("levels", "waves", "super_nodes", "root_size", "max_rank",
                                                  "max_super", "factor_bytes", "device_bytes", "factor_flops")},

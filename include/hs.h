@@ -106,8 +106,16 @@ typedef struct {
   int64_t device_bytes;      /* device memory held by the handle                  */
   int64_t factor_bytes;      /* bytes one hs_apply reads from the factor records  */
   double factor_flops;       /* algorithmic flops of the factorization            */
-  double eig_flops;          /* flops spent in eigen-solves (reported apart)      */
+  double eig_flops;          /* nominal eigen-solve flops, reported apart: per
+                                truncated node 4/3 m^3 + 2 m^2 k                  */
   double factor_ms;          /* device time of the last factorization             */
+  double trunc_big_ms;       /* device time of the large-node truncation launches
+                                (tridiagonal eigen path), CUDA events             */
+  double trunc_big_flops;    /* nominal eigen-solve flops of those nodes          */
+  int32_t trunc_big_launches;/* waves that ran the large-node truncation (one
+                                launch per thread-count class in each)            */
+  double host_ms;            /* host wall time of the factorization call          */
+  double wait_ms;            /* of which waiting for the device (rank reads)      */
 } hs_info;
 
 typedef struct hs_factor_s *hs_factor;
@@ -126,6 +134,41 @@ int hs_factor_create(const hs_csr *A, const hs_clustering *cl, const hs_opts *op
  * The previous factorization is released.  On error the handle holds no valid
  * factorization until the next successful refactor. */
 int hs_factor_refactor(hs_factor f, const double *val, void *stream);
+
+/* hs_factor_create_batch: `count` independent systems factored together.
+ * The paper factors one matrix; this batched form has no counterpart there.
+ * Each problem follows Algorithm 1 exactly as hs_factor_create would do it
+ * alone.  The problems advance in lock step: at every step (a level counted
+ * from the leaves, then a wave of that level) the work of every problem that
+ * has the step runs in the same kernel launches, with one read of the new
+ * ranks for all of them.
+ *   A, cl: arrays of `count` problems (the same layout and ownership as in
+ *     hs_factor_create).
+ *   opts: one set for all problems (eps, variant, factor_prec).  opts->phi is
+ *     ignored.
+ *   phi: per-problem preserved vectors (HOST, n_p doubles each) for
+ *     HS_GC_USER; otherwise it may be NULL.
+ *   out: `count` handles, each used and destroyed like one from
+ *     hs_factor_create.
+ *   status: NULL, or `count` ints that receive each problem's own result.
+ * Results are those of factoring each problem alone, bit for bit.
+ * Errors:
+ *   - A problem whose pivot block is not positive definite leaves the lock
+ *     step: status[p] = HS_ERR_NOT_SPD and out[p] = NULL.  The others are
+ *     finished and returned.  The call then returns HS_ERR_NOT_SPD with the
+ *     first failed problem named in hs_last_error.
+ *   - Any other error fails the whole call and returns no handle. */
+int hs_factor_create_batch(int32_t count, const hs_csr *A, const hs_clustering *cl,
+                           const hs_opts *opts, const double *const *phi, void *stream,
+                           hs_factor *out, int32_t *status);
+
+/* hs_factor_refactor_batch: hs_factor_refactor of `count` distinct handles in
+ * lock step, as in hs_factor_create_batch.  val[p] are DEVICE values of
+ * handle f[p]'s pattern.  status: as in hs_factor_create_batch.  A handle
+ * whose refactor failed holds no valid factorization until its next
+ * successful refactor. */
+int hs_factor_refactor_batch(int32_t count, hs_factor *f, const double *const *val, void *stream,
+                             int32_t *status);
 
 /* hs_apply: z = A_H^{-1} r (Appendix A, Algorithm 2: forward substitution,
  * restriction, parent solve, prolongation, backward substitution).

@@ -37,7 +37,8 @@ STATUS_NAMES = {
 
 # every symbol include/hs.h declares
 EXPORTS = [
-    "hs_factor_create", "hs_factor_refactor", "hs_launch_count", "hs_apply", "hs_apply_static", "hs_pcg", "hs_factor_info", "hs_factor_ranks",
+    "hs_factor_create", "hs_factor_refactor", "hs_factor_create_batch", "hs_factor_refactor_batch",
+    "hs_launch_count", "hs_apply", "hs_apply_static", "hs_pcg", "hs_factor_info", "hs_factor_ranks",
     "hs_factor_destroy", "hs_last_error", "hs_plan_create", "hs_plan_level_waves",
     "hs_plan_super_lists", "hs_plan_destroy",
 ]
@@ -67,7 +68,9 @@ class HsInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("levels", C.c_int32), ("waves", C.c_int32),
                 ("super_nodes", C.c_int32), ("root_size", C.c_int32), ("max_rank", C.c_int32),
                 ("max_super", C.c_int32), ("device_bytes", C.c_int64), ("factor_bytes", C.c_int64),
-                ("factor_flops", C.c_double), ("eig_flops", C.c_double), ("factor_ms", C.c_double)]
+                ("factor_flops", C.c_double), ("eig_flops", C.c_double), ("factor_ms", C.c_double),
+                ("trunc_big_ms", C.c_double), ("trunc_big_flops", C.c_double), ("trunc_big_launches", C.c_int32),
+                ("host_ms", C.c_double), ("wait_ms", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -87,6 +90,9 @@ def lib():
         L.hs_factor_create.argtypes = [C.POINTER(HsCsr), C.POINTER(HsClustering), C.POINTER(HsOpts), vp,
                                        C.POINTER(vp)]
         L.hs_factor_refactor.argtypes = [vp, vp, vp]
+        L.hs_factor_create_batch.argtypes = [i32, C.POINTER(HsCsr), C.POINTER(HsClustering), C.POINTER(HsOpts),
+                                             vp, vp, C.POINTER(vp), vp]
+        L.hs_factor_refactor_batch.argtypes = [i32, C.POINTER(vp), vp, vp, vp]
         L.hs_launch_count.argtypes = []
         L.hs_apply.argtypes = [vp, vp, vp, i32, i64, vp]
         L.hs_apply_static.argtypes = [vp, vp, vp, i32, i64, vp]
@@ -258,3 +264,61 @@ class Factor:
             self.close()
         except Exception:
             pass
+
+
+def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=None, stream=None):
+    """hs_factor_create_batch over `problems`: a list of (rowptr, col, val,
+    perm, leaf_ptr) with rowptr/col int32 and val float64 CUDA tensors and
+    perm/leaf_ptr host arrays.  Returns (factors, status): one Factor per
+    problem (None where its status is HS_ERR_NOT_SPD) and the status array."""
+    import torch
+
+    k = len(problems)
+    A = (HsCsr * k)()
+    cl = (HsClustering * k)()
+    keep = []
+    for p, (rp, ci, va, perm, lp) in enumerate(problems):
+        assert rp.is_cuda and ci.is_cuda and va.is_cuda
+        assert rp.dtype == torch.int32 and ci.dtype == torch.int32 and va.dtype == torch.float64
+        pe = np.ascontiguousarray(perm, dtype=np.int32)
+        lpa = np.ascontiguousarray(lp, dtype=np.int32)
+        keep += [pe, lpa]
+        A[p] = HsCsr(int(rp.numel() - 1), int(ci.numel()), rp.data_ptr(), ci.data_ptr(), va.data_ptr())
+        cl[p] = HsClustering(_ptr(pe), _ptr(lpa), len(lpa) - 1)
+    phi_arr = None
+    if phis is not None:
+        ph = [np.ascontiguousarray(x, dtype=np.float64) for x in phis]
+        keep += ph
+        phi_arr = (C.c_void_p * k)(*[_ptr(x) for x in ph])
+    o = HsOpts(float(eps), int(variant), int(prec), None)
+    out = (C.c_void_p * k)()
+    status = np.zeros(k, dtype=np.int32)
+    code = lib().hs_factor_create_batch(k, A, cl, C.byref(o), phi_arr, _stream_ptr(stream), out, _ptr(status))
+    if code not in (HS_OK, HS_ERR_NOT_SPD):
+        check(code)
+    fs = []
+    for p, (rp, ci, va, perm, lp) in enumerate(problems):
+        if status[p] != HS_OK:
+            fs.append(None)
+            continue
+        f = Factor.__new__(Factor)
+        f.n = int(rp.numel() - 1)
+        f._perm = keep[2 * p]
+        f._lp = keep[2 * p + 1]
+        f._phi = None
+        f._h = C.c_void_p(out[p])
+        fs.append(f)
+    return fs, status
+
+
+def refactor_batch(factors, vals, stream=None):
+    """hs_factor_refactor_batch: new values (float64 CUDA tensors) for each
+    handle.  Returns the per-problem status array (HS_OK or HS_ERR_NOT_SPD)."""
+    k = len(factors)
+    hs = (C.c_void_p * k)(*[f._h.value for f in factors])
+    vs = (C.c_void_p * k)(*[v.data_ptr() for v in vals])
+    status = np.zeros(k, dtype=np.int32)
+    code = lib().hs_factor_refactor_batch(k, hs, vs, _stream_ptr(stream), _ptr(status))
+    if code not in (HS_OK, HS_ERR_NOT_SPD):
+        check(code)
+    return status

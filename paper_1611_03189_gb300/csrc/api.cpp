@@ -66,8 +66,9 @@ X *upload_vec(const std::vector<X> &v, cudaStream_t st) {
 }
 
 // Values -> permuted CSR, numeric factorization, apply schedule to the device,
-// counters.  Used by hs_factor_create and hs_factor_refactor.
-void numeric_factor(FactorHandle &h, const double *val, const double *phi_host, cudaStream_t st) {
+// counters.  Used by hs_factor_create and hs_factor_refactor (one handle) and
+// their batched forms (several handles factored in lock step).
+void numeric_pre(FactorHandle &h, const double *val, cudaStream_t st) {
   h.stream = st;
   h.drop_graphs();   // the schedule and the record pointers change
   launch_gather_values(val, h.d_src, h.nnz, h.d_val, st);
@@ -79,32 +80,20 @@ void numeric_factor(FactorHandle &h, const double *val, const double *phi_host, 
   h.d_nbrs = nullptr;
   h.d_targets = nullptr;
   h.d_contribs = nullptr;
-  cudaEvent_t e0, e1;
-  HS_CUDA(cudaEventCreate(&e0));
-  HS_CUDA(cudaEventCreate(&e1));
-  HS_CUDA(cudaEventRecord(e0, st));
-  try {
-    factorize(h, hs_csr{}, hs_opts{}, phi_host);
-  } catch (...) {
-    cudaStreamSynchronize(st);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    h.nodes.clear();
-    h.waves.clear();
-    h.levels.clear();
-    h.root_m = 0;
-    throw;
-  }
-  HS_CUDA(cudaEventRecord(e1, st));
+}
+
+void numeric_failed(FactorHandle &h) {
+  h.nodes.clear();
+  h.waves.clear();
+  h.levels.clear();
+  h.root_m = 0;
+}
+
+void numeric_post(FactorHandle &h, float ms, cudaStream_t st) {
   h.d_nodes = upload_vec(h.nodes, st);
   h.d_nbrs = upload_vec(h.nbrs, st);
   h.d_targets = upload_vec(h.targets, st);
   h.d_contribs = upload_vec(h.contribs, st);
-  HS_CUDA(cudaStreamSynchronize(st));
-  float ms = 0.f;
-  HS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   hs_info &in = h.info;
   in.n = h.plan.n;
   in.levels = h.plan.L;
@@ -116,6 +105,84 @@ void numeric_factor(FactorHandle &h, const double *val, const double *phi_host, 
   fb += (double)h.root_m * h.root_m;
   in.factor_bytes = (int64_t)(fb * tb);
   in.device_bytes = (int64_t)(h.pers->reserved() + h.scratch->reserved());
+}
+
+// Numeric factorization of one or more handles on stream st (lock step when
+// more than one); factor_ms is the device time of the whole call.  status
+// (optional): per-problem result of a batch (HS_OK or HS_ERR_NOT_SPD, message
+// in msg); failed problems hold no valid factorization.
+void numeric_factor_all(const std::vector<FactorHandle *> &hs, const std::vector<const double *> &vals,
+                        const std::vector<const double *> &phis, cudaStream_t st,
+                        std::vector<int> *status = nullptr, std::vector<std::string> *msg = nullptr) {
+  for (size_t p = 0; p < hs.size(); ++p) numeric_pre(*hs[p], vals[p], st);
+  cudaEvent_t e0, e1;
+  HS_CUDA(cudaEventCreate(&e0));
+  HS_CUDA(cudaEventCreate(&e1));
+  HS_CUDA(cudaEventRecord(e0, st));
+  std::vector<int> stat;
+  std::vector<std::string> msgs;
+  try {
+    factorize_batch(hs, phis, st, &stat, &msgs);
+  } catch (...) {
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (FactorHandle *h : hs) numeric_failed(*h);
+    throw;
+  }
+  HS_CUDA(cudaEventRecord(e1, st));
+  HS_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  HS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (size_t p = 0; p < hs.size(); ++p) {
+    if (stat[p] == HS_OK)
+      numeric_post(*hs[p], ms, st);
+    else
+      numeric_failed(*hs[p]);
+  }
+  HS_CUDA(cudaStreamSynchronize(st));
+  if (status) *status = stat;
+  if (msg) *msg = msgs;
+}
+
+void numeric_factor(FactorHandle &h, const double *val, const double *phi_host, cudaStream_t st) {
+  numeric_factor_all({&h}, {val}, {phi_host}, st);
+}
+
+// checks and planning of hs_factor_create; the handle is left ready for numeric_factor
+void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, const hs_opts *o, cudaStream_t st) {
+  if (!A || !cl) fail(HS_ERR_INVALID, "null argument");
+  if (A->n <= 0 || A->nnz <= 0 || !A->rowptr || !A->col || !A->val) fail(HS_ERR_INVALID, "bad CSR");
+  if (!cl->perm || !cl->leaf_ptr) fail(HS_ERR_INVALID, "bad clustering");
+  HS_CUDA(cudaGetDevice(&h.device));
+  h.stream = st;
+  h.prec = o->factor_prec;
+  h.variant = o->variant;
+  h.eps = o->eps;
+  // pattern to the host for the planner
+  std::vector<int32_t> rp(A->n + 1), ci(A->nnz);
+  HS_CUDA(cudaMemcpyAsync(rp.data(), A->rowptr, sizeof(int32_t) * (A->n + 1), cudaMemcpyDeviceToHost, st));
+  HS_CUDA(cudaMemcpyAsync(ci.data(), A->col, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost, st));
+  HS_CUDA(cudaStreamSynchronize(st));
+  if (rp[A->n] != A->nnz) fail(HS_ERR_INVALID, "rowptr[n] != nnz");
+  build_plan(A->n, rp.data(), ci.data(), cl->perm, cl->leaf_ptr, cl->nleaf, h.plan);
+  // permuted CSR on the device; values gathered there
+  h.d_rowptr = upload_vec(h.plan.prow, st);
+  h.d_col = upload_vec(h.plan.pcol, st);
+  h.d_perm = upload_vec(h.plan.perm, st);
+  h.d_src = upload_vec(h.plan.psrc, st);
+  h.nnz = A->nnz;
+  HS_CUDA(cudaMalloc(&h.d_val, sizeof(double) * A->nnz));
+}
+
+void check_opts(const hs_opts *o) {
+  if (!o) fail(HS_ERR_INVALID, "null argument");
+  if (!(o->eps >= 0.0) || !std::isfinite(o->eps)) fail(HS_ERR_INVALID, "eps must be finite and >= 0");
+  if (o->eps > 0.0 && o->eps < 1e-6) fail(HS_ERR_INVALID, "0 < eps < 1e-6 is not supported");
+  if (o->variant < HS_LORASP || o->variant > HS_GC_USER) fail(HS_ERR_INVALID, "unknown variant");
+  if (o->factor_prec != HS_PREC_F64 && o->factor_prec != HS_PREC_F32) fail(HS_ERR_INVALID, "unknown factor_prec");
 }
 
 }  // namespace
@@ -140,39 +207,57 @@ int hs_factor_create(const hs_csr *A, const hs_clustering *cl, const hs_opts *o,
   return hs::guarded([&]() -> int {
     if (!A || !cl || !o || !out) fail(HS_ERR_INVALID, "null argument");
     *out = nullptr;
-    if (!(o->eps >= 0.0) || !std::isfinite(o->eps)) fail(HS_ERR_INVALID, "eps must be finite and >= 0");
-    if (o->eps > 0.0 && o->eps < 1e-6) fail(HS_ERR_INVALID, "0 < eps < 1e-6 is not supported");
-    if (o->variant < HS_LORASP || o->variant > HS_GC_USER) fail(HS_ERR_INVALID, "unknown variant");
+    hs::check_opts(o);
     if (o->variant == HS_GC_USER && !o->phi) fail(HS_ERR_INVALID, "HS_GC_USER needs phi");
-    if (o->factor_prec != HS_PREC_F64 && o->factor_prec != HS_PREC_F32) fail(HS_ERR_INVALID, "unknown factor_prec");
-    if (A->n <= 0 || A->nnz <= 0 || !A->rowptr || !A->col || !A->val) fail(HS_ERR_INVALID, "bad CSR");
-    if (!cl->perm || !cl->leaf_ptr) fail(HS_ERR_INVALID, "bad clustering");
     hs::require_device();
     cudaStream_t st = (cudaStream_t)stream;
     std::unique_ptr<hs_factor_s> f(new hs_factor_s());
-    hs::FactorHandle &h = f->h;
-    HS_CUDA(cudaGetDevice(&h.device));
-    h.stream = st;
-    h.prec = o->factor_prec;
-    h.variant = o->variant;
-    h.eps = o->eps;
-    // pattern to the host for the planner
-    std::vector<int32_t> rp(A->n + 1), ci(A->nnz);
-    HS_CUDA(cudaMemcpyAsync(rp.data(), A->rowptr, sizeof(int32_t) * (A->n + 1), cudaMemcpyDeviceToHost, st));
-    HS_CUDA(cudaMemcpyAsync(ci.data(), A->col, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost, st));
-    HS_CUDA(cudaStreamSynchronize(st));
-    if (rp[A->n] != A->nnz) fail(HS_ERR_INVALID, "rowptr[n] != nnz");
-    hs::build_plan(A->n, rp.data(), ci.data(), cl->perm, cl->leaf_ptr, cl->nleaf, h.plan);
-    // permuted CSR on the device; values gathered there
-    h.d_rowptr = hs::upload_vec(h.plan.prow, st);
-    h.d_col = hs::upload_vec(h.plan.pcol, st);
-    h.d_perm = hs::upload_vec(h.plan.perm, st);
-    h.d_src = hs::upload_vec(h.plan.psrc, st);
-    h.nnz = A->nnz;
-    HS_CUDA(cudaMalloc(&h.d_val, sizeof(double) * A->nnz));
-    hs::numeric_factor(h, A->val, o->phi, st);
-    h.valid = true;
+    hs::setup_handle(f->h, A, cl, o, st);
+    hs::numeric_factor(f->h, A->val, o->phi, st);
+    f->h.valid = true;
     *out = f.release();
+    return HS_OK;
+  });
+}
+
+int hs_factor_create_batch(int32_t count, const hs_csr *A, const hs_clustering *cl, const hs_opts *o,
+                           const double *const *phi, void *stream, hs_factor *out, int32_t *status) {
+  return hs::guarded([&]() -> int {
+    if (count < 1 || !A || !cl || !o || !out) fail(HS_ERR_INVALID, "null argument or count < 1");
+    for (int32_t p = 0; p < count; ++p) out[p] = nullptr;
+    hs::check_opts(o);
+    if (o->variant == HS_GC_USER && !phi) fail(HS_ERR_INVALID, "HS_GC_USER needs phi");
+    hs::require_device();
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<std::unique_ptr<hs_factor_s>> fs;
+    std::vector<hs::FactorHandle *> hs_;
+    std::vector<const double *> vals, phis;
+    for (int32_t p = 0; p < count; ++p) {
+      if (o->variant == HS_GC_USER && !phi[p]) fail(HS_ERR_INVALID, "HS_GC_USER needs phi for every problem");
+      fs.emplace_back(new hs_factor_s());
+      try {
+        hs::setup_handle(fs.back()->h, &A[p], &cl[p], o, st);
+      } catch (hs::Error &e) {
+        throw hs::Error{e.code, "problem " + std::to_string(p) + ": " + e.msg};
+      }
+      hs_.push_back(&fs.back()->h);
+      vals.push_back(A[p].val);
+      phis.push_back(o->variant == HS_GC_USER ? phi[p] : nullptr);
+    }
+    std::vector<int> stat;
+    std::vector<std::string> msgs;
+    hs::numeric_factor_all(hs_, vals, phis, st, &stat, &msgs);
+    int first = -1;
+    for (int32_t p = 0; p < count; ++p) {
+      if (status) status[p] = stat[p];
+      if (stat[p] == HS_OK) {
+        fs[p]->h.valid = true;
+        out[p] = fs[p].release();
+      } else if (first < 0) {
+        first = p;
+      }
+    }
+    if (first >= 0) fail(stat[first], msgs[first]);   // the others are returned
     return HS_OK;
   });
 }
@@ -184,6 +269,36 @@ int hs_factor_refactor(hs_factor f, const double *val, void *stream) {
     f->h.valid = false;
     hs::numeric_factor(f->h, val, nullptr, (cudaStream_t)stream);
     f->h.valid = true;
+    return HS_OK;
+  });
+}
+
+int hs_factor_refactor_batch(int32_t count, hs_factor *f, const double *const *val, void *stream,
+                             int32_t *status) {
+  return hs::guarded([&]() -> int {
+    if (count < 1 || !f || !val) fail(HS_ERR_INVALID, "null argument or count < 1");
+    std::vector<hs::FactorHandle *> hs_;
+    std::vector<const double *> vals, phis;
+    for (int32_t p = 0; p < count; ++p) {
+      if (!f[p] || !val[p]) fail(HS_ERR_INVALID, "null handle or values");
+      for (int32_t q = 0; q < p; ++q)
+        if (f[q] == f[p]) fail(HS_ERR_INVALID, "a handle appears twice in the batch");
+      hs_.push_back(&f[p]->h);
+      vals.push_back(val[p]);
+      phis.push_back(nullptr);
+    }
+    hs::require_device();
+    for (auto *h : hs_) h->valid = false;
+    std::vector<int> stat;
+    std::vector<std::string> msgs;
+    hs::numeric_factor_all(hs_, vals, phis, (cudaStream_t)stream, &stat, &msgs);
+    int first = -1;
+    for (int32_t p = 0; p < count; ++p) {
+      if (status) status[p] = stat[p];
+      hs_[p]->valid = stat[p] == HS_OK;
+      if (stat[p] != HS_OK && first < 0) first = p;
+    }
+    if (first >= 0) fail(stat[first], msgs[first]);
     return HS_OK;
   });
 }

@@ -16,8 +16,10 @@
 // M_ss = A_ss^-1 - P_ss^T S P_ss = L^-T (I - Q Q^T) L^-1, and
 // A_ns M_ss A_sn' is the Schur term of ~~A_nn' (eq. eliminated).
 #include <algorithm>
+#include <chrono>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <unordered_map>
 
@@ -228,12 +230,14 @@ struct Tag {
   int kind;   // 0 A_ss, 1 S (first CholQR pass), 2 S (second pass), 3 U^T U, 4 root block
   int level;
   int s;
+  int prob;   // problem of a batched factorization (-1: a single one)
 };
 
 inline std::string describe(const Tag &t) {
   static const char *names[] = {"A_ss", "S (first CholQR pass)", "S (second CholQR pass)", "U^T U", "root block"};
-  if (t.kind == 4) return "root block";
-  return "level " + std::to_string(t.level) + " super node " + std::to_string(t.s) + ": " + names[t.kind];
+  const std::string pre = t.prob >= 0 ? "problem " + std::to_string(t.prob) + ": " : std::string();
+  if (t.kind == 4) return pre + "root block";
+  return pre + "level " + std::to_string(t.level) + " super node " + std::to_string(t.s) + ": " + names[t.kind];
 }
 
 template <typename T>
@@ -286,21 +290,126 @@ struct PendingStatus {
   std::vector<Tag> what;
 };
 
+// What the launches of one factorization step share: the stream, an arena for
+// task descriptors, the pinned staging buffers, the status words to check and
+// the host buffer of the per-wave rank read.  One Exec drives one problem, or
+// many independent problems whose steps are batched into the same launches.
+struct Exec {
+  cudaStream_t st = nullptr;
+  DevArena scr{16ull << 20};
+  Staging sg;
+  std::vector<PendingStatus> pending;
+  DevArena stat{1ull << 20};   // status words: kept until the sync_check that reads them
+  int *hbuf = nullptr;
+  size_t hbuf_cap = 0;
+  cudaEvent_t ev_big[2] = {nullptr, nullptr};
+  // batched: a problem whose pivot fails is marked here and leaves the lock
+  // step; the others go on (single: the failure is an error of the call)
+  std::vector<int> prob_status;
+  std::vector<std::string> prob_msg;
+  // host time spent waiting for the device (sync_check), in ms
+  double wait_ms = 0.0;
+  explicit Exec(cudaStream_t s) : st(s) {
+    HS_CUDA(cudaEventCreate(&ev_big[0]));
+    HS_CUDA(cudaEventCreate(&ev_big[1]));
+  }
+  ~Exec() {
+    // copies from the pinned staging buffers may still be in flight after an error
+    cudaStreamSynchronize(st);
+    cudaFreeHost(hbuf);
+    cudaEventDestroy(ev_big[0]);
+    cudaEventDestroy(ev_big[1]);
+  }
+  int *host_ints(size_t n) {
+    if (n > hbuf_cap) {
+      cudaFreeHost(hbuf);
+      hbuf = nullptr;
+      hbuf_cap = std::max(n, (size_t)1 << 16);
+      HS_CUDA(cudaMallocHost(&hbuf, hbuf_cap * sizeof(int)));
+    }
+    return hbuf;
+  }
+  bool mark_failed(const Tag &t, int pivot) {
+    const std::string msg = describe(t) + " is not positive definite (pivot " + std::to_string(pivot) + ")";
+    if (t.prob < 0 || t.prob >= (int)prob_status.size()) fail(HS_ERR_NOT_SPD, msg);
+    if (prob_status[t.prob] == HS_OK) {
+      prob_status[t.prob] = HS_ERR_NOT_SPD;
+      prob_msg[t.prob] = msg;
+    }
+    return true;
+  }
+  bool ok(int prob) const { return prob < 0 || prob >= (int)prob_status.size() || prob_status[prob] == HS_OK; }
+  // waits for the stream, then checks the pending status words
+  void sync_check() {
+    const auto t0 = std::chrono::steady_clock::now();
+    HS_CUDA(cudaStreamSynchronize(st));
+    wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (auto &ps : pending) {
+      std::vector<int> hv(ps.what.size());
+      HS_CUDA(cudaMemcpy(hv.data(), ps.d, ps.what.size() * sizeof(int), cudaMemcpyDeviceToHost));
+      for (size_t i = 0; i < ps.what.size(); ++i)
+        if (hv[i] != 0) mark_failed(ps.what[i], hv[i] - 1);
+    }
+    pending.clear();
+    stat.reset();
+  }
+  // Cholesky-inverse batch whose statuses are checked at the next sync_check
+  template <typename T>
+  void chol_checked(CholBatch<T> &cb) {
+    if (cb.tasks.empty()) return;
+    PendingStatus ps;
+    ps.d = (int *)stat.alloc(sizeof(int) * cb.tasks.size());
+    ps.what = cb.what;
+    Uploader u;
+    const size_t o = u.add(cb.tasks);
+    char *d = u.upload(scr, sg, st);
+    launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)cb.tasks.size(), ps.d, cb.max_m, st);
+    pending.push_back(ps);
+  }
+};
+
+// The batched launches of one wave step, shared by the problems taking part.
+template <typename T>
+struct WaveBatches {
+  // phase A: gather, Cholesky of A_ss, Gram, truncation (statuses and ranks read back)
+  SumBatch<T> gather;
+  GemmBatch<T> gram;
+  CholBatch<T> chol;
+  std::vector<TruncTask<T>> trunc, trunc_big;
+  int max_trunc_m = 0, max_big_m = 0;
+  // large-path re-orthonormalisation of U (CholQR2)
+  GemmBatch<T> o1, o2, o3, o4;
+  CholBatch<T> oc1, oc2;
+  // phase B and the Schur update
+  GemmBatch<T> g1, g2, g3, g4, g5, g6, g7, g8;
+  CholBatch<T> c1, c2;
+  SumBatch<T> schur;
+};
+
 template <typename T>
 class Run {
  public:
-  Run(FactorHandle &h, const double *phi_host) : h_(h), P_(h.plan), st_(h.stream) {
+  Run(FactorHandle &h, const double *phi_host, Exec &ex, int prob)
+      : h_(h), P_(h.plan), ex_(ex), st_(ex.st), prob_(prob) {
     use_phi_ = h.variant != HS_LORASP;
     phi_host_ = phi_host;
-    HS_CUDA(cudaMallocHost(&hbuf_, hbuf_cap_ * sizeof(int)));
-  }
-  ~Run() {
-    // copies from the pinned staging buffers may still be in flight after an error
-    cudaStreamSynchronize(st_);
-    cudaFreeHost(hbuf_);
+    h.stream = ex.st;
   }
 
-  void run();
+  bool ok() const { return ex_.ok(prob_); }
+  int levels() const { return (int)P_.levels.size(); }
+  int waves(int li) const { return li < levels() ? (int)P_.levels[li].waves.size() : 0; }
+  FactorHandle &handle() { return h_; }
+
+  void begin();                                  // outputs cleared, leaf blocks
+  void level_begin(int li, SumBatch<T> &sb);     // merge into the level's super nodes
+  void wave_a(int li, int widx, WaveBatches<T> &B);
+  void wave_b(const int *hb, size_t nchol, size_t ntrunc, double big_ms, WaveBatches<T> &B);
+  void wave_c(WaveBatches<T> &B);
+  void level_end(int li);
+  void root_a(SumBatch<T> &sb);                  // merge of the last red nodes
+  void root_b(CholBatch<T> &cb, GemmBatch<T> &g);
+  void finish();
 
  private:
   struct Sup {
@@ -315,16 +424,15 @@ class Run {
   };
 
   void leaf_setup();
-  void merge(int nred, int key_base);
-  void wave(const PlanLevel &lv, int li, int widx);
+  void merge(int nred, int key_base, SumBatch<T> &sb);
   void end_level(const PlanLevel &lv, int li);
-  void root();
-  void sync_check();
-  int *host_ints(size_t n);
+  Tag tag(int kind, int level, int s) const { return Tag{kind, level, s, prob_}; }
 
   FactorHandle &h_;
   const Plan &P_;
+  Exec &ex_;
   cudaStream_t st_;
+  int prob_;
   bool use_phi_ = false;
   const double *phi_host_ = nullptr;
 
@@ -332,6 +440,7 @@ class Run {
   std::vector<int> size_;      // by key of the current level
   std::vector<T *> phi_;       // by key
   int nsup_ = 0;
+  int nred_ = 0;               // red nodes entering the current level
   // vector layout of the apply workspace
   int64_t seg_off_ = 0;             // segment of the current level's red/super nodes
   std::vector<int64_t> red_off_;    // red node offsets inside that segment (by red index)
@@ -344,38 +453,19 @@ class Run {
     std::vector<int> N;
   };
   std::vector<Rec> recs_;
-  std::vector<PendingStatus> pending_;
-  Staging sg_;
-  int *hbuf_ = nullptr;
-  size_t hbuf_cap_ = 1 << 16;
+  // the wave in progress: its super nodes and its slices of the shared batches
+  const PlanLevel *lv_ = nullptr;
+  std::vector<Sup> cur_;
+  std::vector<int> trunc_sup_, big_sup_;      // super nodes of this run's truncation tasks
+  size_t chol_first_ = 0, chol_count_ = 0, trunc_first_ = 0, big_first_ = 0;
   double flops_ = 0.0;
-  int lv_level_hint_ = 0;
+  // device time (of the launches taken part in) and nominal eigen-solve flops
+  // of the large-node truncations
+  double big_ms_ = 0.0, big_flops_ = 0.0, eig_flops_ = 0.0;
+  int big_launches_ = 0;
+  // root records waiting for root_b
+  T *root_linv_ = nullptr, *root_ainv_ = nullptr;
 };
-
-template <typename T>
-int *Run<T>::host_ints(size_t n) {
-  if (n > hbuf_cap_) {
-    cudaFreeHost(hbuf_);
-    hbuf_cap_ = std::max(n, 2 * hbuf_cap_);
-    HS_CUDA(cudaMallocHost(&hbuf_, hbuf_cap_ * sizeof(int)));
-  }
-  return hbuf_;
-}
-
-template <typename T>
-void Run<T>::sync_check() {
-  HS_CUDA(cudaStreamSynchronize(st_));
-  for (auto &ps : pending_) {
-    std::vector<int> hv(ps.what.size());
-    int *hb = hv.data();
-    HS_CUDA(cudaMemcpy(hb, ps.d, ps.what.size() * sizeof(int), cudaMemcpyDeviceToHost));
-    for (size_t i = 0; i < ps.what.size(); ++i)
-      if (hb[i] != 0)
-        fail(HS_ERR_NOT_SPD, describe(ps.what[i]) + " is not positive definite (pivot " +
-                                 std::to_string(hb[i] - 1) + ")");
-  }
-  pending_.clear();
-}
 
 // Leaf red nodes and their blocks from the permuted CSR (Sec. 2.1: blocks
 // A_{I_i I_j} of the leaf partition).  Entries below the block diagonal are
@@ -453,7 +543,7 @@ void Run<T>::leaf_setup() {
 // Merge the red nodes (keys key_base + i, i < nred) pairwise into super nodes
 // (Sec. 3: I^s_i = I^r_{2i-1} u I^r_{2i}); blocks are assembled 2 x 2.
 template <typename T>
-void Run<T>::merge(int nred, int key_base) {
+void Run<T>::merge(int nred, int key_base, SumBatch<T> &sb) {
   const int nsup = std::max(1, nred / 2);
   std::vector<int> rsize(2 * nsup, -1);
   for (int i = 0; i < nred; ++i) rsize[i] = size_[key_base + i];
@@ -494,7 +584,6 @@ void Run<T>::merge(int nred, int key_base) {
     br.rowkey = IJ.first;
     nb[bkey(IJ.first, IJ.second)] = br;
   }
-  SumBatch<T> sb;
   for (auto &kv : blocks_) {
     const int a = std::min((int)(kv.first >> 32), (int)(kv.first & 0xffffffffu)) - key_base;
     const int b = std::max((int)(kv.first >> 32), (int)(kv.first & 0xffffffffu)) - key_base;
@@ -523,7 +612,6 @@ void Run<T>::merge(int nred, int key_base) {
       o += ssize[j];
     }
   }
-  sb.launch(*h_.scratch, sg_, st_);
   blocks_.swap(nb);
   phi_.swap(nphi);
   size_.assign(2 * nsup, -1);
@@ -540,20 +628,21 @@ void Run<T>::merge(int nred, int key_base) {
 }
 
 template <typename T>
-void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
-  (void)li;
+void Run<T>::wave_a(int li, int widx, WaveBatches<T> &B) {
+  const PlanLevel &lv = P_.levels[li];
+  lv_ = &lv;
   DevArena &scr = *h_.scratch;
   DevArena &per = *h_.pers;
   const std::vector<int> &wl = lv.waves[widx];
-  std::vector<Sup> S(wl.size());
-  SumBatch<T> gather;
-  GemmBatch<T> gram;
-  CholBatch<T> chol;
-  std::vector<TruncTask<T>> trunc, trunc_big;
-  int max_trunc_m = 0, max_big_m = 0;
-  std::vector<int> trunc_sup, big_sup;
+  cur_.assign(wl.size(), Sup());
+  trunc_sup_.clear();
+  big_sup_.clear();
+  chol_first_ = B.chol.tasks.size();
+  trunc_first_ = B.trunc.size();
+  big_first_ = B.trunc_big.size();
+  const double f0 = B.chol.flops + B.gram.flops;
   for (size_t q = 0; q < wl.size(); ++q) {
-    Sup &x = S[q];
+    Sup &x = cur_[q];
     const int s = wl[q];
     const PlanSuper &ps = lv.sup[s];
     x.s = s;
@@ -576,7 +665,7 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
       auto it = blocks_.find(bkey(row, other));
       if (it == blocks_.end()) fail(HS_ERR_INVALID, "internal: missing block");
       const BlockRef<T> &b = it->second;
-      gather.copy(dst, ld, size_[row], cols, b.ptr, b.ld, b.rowkey == row ? 0 : 1);
+      B.gather.copy(dst, ld, size_[row], cols, b.ptr, b.ld, b.rowkey == row ? 0 : 1);
     };
     for (size_t j = 0; j < ps.N.size(); ++j) oriented(s, ps.N[j], x.AsN + x.Noff[j], x.dN, size_[ps.N[j]]);
     if (x.red) {
@@ -588,15 +677,15 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
         x.phiW = talloc<T>(scr, x.dW);
         x.a = talloc<T>(scr, m);
         for (size_t j = 0; j < ps.W.size(); ++j)
-          if (size_[ps.W[j]] > 0) gather.copy(x.phiW + x.Woff[j], 1, size_[ps.W[j]], 1, phi_[ps.W[j]], 1, 0);
+          if (size_[ps.W[j]] > 0) B.gather.copy(x.phiW + x.Woff[j], 1, size_[ps.W[j]], 1, phi_[ps.W[j]], 1, 0);
       }
     }
     auto dit = blocks_.find(bkey(s, s));
     if (dit == blocks_.end()) fail(HS_ERR_INVALID, "internal: missing diagonal block");
-    chol.add(dit->second.ptr, dit->second.ld, x.Linv, m, Tag{0, lv.level, s});
+    B.chol.add(dit->second.ptr, dit->second.ld, x.Linv, m, tag(0, lv.level, s));
     if (x.red && m > 0) {
-      gram.add(x.AsW, x.dW, 0, x.AsW, x.dW, 1, x.G, m, m, m, x.dW, T(1), T(0));
-      if (use_phi_) gram.add(x.AsW, x.dW, 0, x.phiW, 1, 0, x.a, 1, m, 1, x.dW, T(1), T(0));
+      B.gram.add(x.AsW, x.dW, 0, x.AsW, x.dW, 1, x.G, m, m, m, x.dW, T(1), T(0));
+      if (use_phi_) B.gram.add(x.AsW, x.dW, 0, x.phiW, 1, 0, x.a, 1, m, 1, x.dW, T(1), T(0));
       TruncTask<T> tt;
       tt.G = x.G;
       tt.a = x.a;
@@ -605,61 +694,49 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
       tt.work = nullptr;
       tt.m = m;
       if (m <= eig_small_max<T>()) {
-        tt.k_idx = (int)trunc.size();
-        trunc.push_back(tt);
-        trunc_sup.push_back((int)q);
-        max_trunc_m = std::max(max_trunc_m, m);
+        B.trunc.push_back(tt);
+        trunc_sup_.push_back((int)q);
+        B.max_trunc_m = std::max(B.max_trunc_m, m);
       } else {
         tt.work = talloc<T>(scr, trunc_big_work_elems<T>(m));
-        big_sup.push_back((int)q);
-        max_big_m = std::max(max_big_m, m);
-        trunc_big.push_back(tt);
+        big_sup_.push_back((int)q);
+        B.max_big_m = std::max(B.max_big_m, m);
+        B.trunc_big.push_back(tt);
       }
     }
   }
-  for (size_t i = 0; i < trunc_big.size(); ++i) trunc_big[i].k_idx = (int)(trunc.size() + i);
-  gather.launch(scr, sg_, st_);
-  // phase A kernels
-  int *d_stat = (int *)scr.alloc(sizeof(int) * (chol.tasks.size() + trunc.size() + trunc_big.size() + 1));
-  int *d_k = d_stat + chol.tasks.size();
-  if (!chol.tasks.empty()) {
-    Uploader u;
-    const size_t o = u.add(chol.tasks);
-    char *d = u.upload(scr, sg_, st_);
-    launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)chol.tasks.size(), d_stat, chol.max_m, st_);
+  flops_ += B.chol.flops + B.gram.flops - f0;
+  chol_count_ = B.chol.tasks.size() - chol_first_;
+}
+
+template <typename T>
+void Run<T>::wave_b(const int *hb, size_t nchol, size_t ntrunc, double big_ms, WaveBatches<T> &B) {
+  DevArena &scr = *h_.scratch;
+  // this run's slices of the statuses and ranks read after phase A
+  std::vector<Sup> &S = cur_;
+  bool bad = false;
+  for (size_t i = chol_first_; i < chol_first_ + chol_count_; ++i)
+    if (hb[i] != 0) bad = ex_.mark_failed(B.chol.what[i], hb[i] - 1);
+  if (bad) return;   // this problem leaves the lock step
+  for (size_t i = 0; i < trunc_sup_.size(); ++i) S[trunc_sup_[i]].k = hb[nchol + trunc_first_ + i];
+  for (size_t i = 0; i < big_sup_.size(); ++i) S[big_sup_[i]].k = hb[nchol + ntrunc + big_first_ + i];
+  // nominal eigen-solve work of a node: Householder tridiagonalisation
+  // (4/3 m^3) and back-transformation of the k kept vectors (2 m^2 k)
+  auto eig_work = [](double m, double k) { return 4.0 / 3.0 * m * m * m + 2.0 * m * m * k; };
+  for (size_t i = 0; i < trunc_sup_.size(); ++i) eig_flops_ += eig_work(S[trunc_sup_[i]].m, S[trunc_sup_[i]].k);
+  if (!big_sup_.empty()) {
+    big_ms_ += big_ms;
+    ++big_launches_;
+    for (int q : big_sup_) {
+      const double w = eig_work(S[q].m, S[q].k);
+      big_flops_ += w;
+      eig_flops_ += w;
+    }
   }
-  flops_ += chol.flops + gram.flops;
-  gram.launch(scr, sg_, st_);
-  if (!trunc.empty()) {
-    Uploader u;
-    const size_t o = u.add(trunc);
-    char *d = u.upload(scr, sg_, st_);
-    launch_trunc<T>((const TruncTask<T> *)(d + o), (int)trunc.size(), d_k, h_.eps, h_.variant,
-                    max_trunc_m, st_);
-  }
-  if (!trunc_big.empty()) {
-    Uploader u;
-    const size_t o = u.add(trunc_big);
-    char *d = u.upload(scr, sg_, st_);
-    launch_trunc_big<T>((const TruncTask<T> *)(d + o), (int)trunc_big.size(), d_k, h_.eps, h_.variant,
-                        max_big_m, st_);
-  }
-  // one read of the statuses and ranks
-  const size_t nread = chol.tasks.size() + trunc.size() + trunc_big.size();
-  int *hb = host_ints(nread + 1);
-  if (nread) HS_CUDA(cudaMemcpyAsync(hb, d_stat, sizeof(int) * nread, cudaMemcpyDeviceToHost, st_));
-  sync_check();
-  for (size_t i = 0; i < chol.tasks.size(); ++i)
-    if (hb[i] != 0)
-      fail(HS_ERR_NOT_SPD, describe(chol.what[i]) + " is not positive definite (pivot " + std::to_string(hb[i] - 1) + ")");
-  for (size_t i = 0; i < trunc.size(); ++i) S[trunc_sup[i]].k = hb[chol.tasks.size() + i];
-  for (size_t i = 0; i < trunc_big.size(); ++i) S[big_sup[i]].k = hb[chol.tasks.size() + trunc.size() + i];
-  if (!big_sup.empty()) {
+  if (!big_sup_.empty()) {
     // U of the large path: re-orthonormalise by CholQR2 (same span)
-    GemmBatch<T> o1, o2, o3, o4;
-    CholBatch<T> oc1, oc2;
     std::vector<T *> U1s(S.size(), nullptr), U2s(S.size(), nullptr);
-    for (int q : big_sup) {
+    for (int q : big_sup_) {
       Sup &x = S[q];
       const int m = x.m, k = x.k;
       if (k <= 0) continue;
@@ -667,37 +744,27 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
       T *Sg2 = talloc<T>(scr, (size_t)k * k), *Lg2 = talloc<T>(scr, (size_t)k * k);
       U1s[q] = talloc<T>(scr, (size_t)m * m);
       U2s[q] = talloc<T>(scr, (size_t)m * m);
-      o1.add(x.U, m, 1, x.U, m, 0, Sg, k, k, k, m, T(1), T(0));
-      oc1.add(Sg, k, Lg, k, Tag{3, lv.level, x.s});
-      o2.add(x.U, m, 0, Lg, k, 1, U1s[q], m, m, k, k, T(1), T(0));
-      o3.add(U1s[q], m, 1, U1s[q], m, 0, Sg2, k, k, k, m, T(1), T(0));
-      oc2.add(Sg2, k, Lg2, k, Tag{3, lv.level, x.s});
-      o4.add(U1s[q], m, 0, Lg2, k, 1, U2s[q], m, m, k, k, T(1), T(0));
+      B.o1.add(x.U, m, 1, x.U, m, 0, Sg, k, k, k, m, T(1), T(0));
+      B.oc1.add(Sg, k, Lg, k, tag(3, lv_->level, x.s));
+      B.o2.add(x.U, m, 0, Lg, k, 1, U1s[q], m, m, k, k, T(1), T(0));
+      B.o3.add(U1s[q], m, 1, U1s[q], m, 0, Sg2, k, k, k, m, T(1), T(0));
+      B.oc2.add(Sg2, k, Lg2, k, tag(3, lv_->level, x.s));
+      B.o4.add(U1s[q], m, 0, Lg2, k, 1, U2s[q], m, m, k, k, T(1), T(0));
     }
-    auto chol_now = [&](CholBatch<T> &cb) {
-      if (cb.tasks.empty()) return;
-      PendingStatus ps;
-      ps.d = (int *)per.alloc(sizeof(int) * cb.tasks.size());
-      ps.what = cb.what;
-      Uploader u;
-      const size_t o = u.add(cb.tasks);
-      char *d = u.upload(scr, sg_, st_);
-      launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)cb.tasks.size(), ps.d, cb.max_m, st_);
-      pending_.push_back(ps);
-    };
-    o1.launch(scr, sg_, st_);
-    chol_now(oc1);
-    o2.launch(scr, sg_, st_);
-    o3.launch(scr, sg_, st_);
-    chol_now(oc2);
-    o4.launch(scr, sg_, st_);
-    for (int q : big_sup)
+    for (int q : big_sup_)
       if (U2s[q]) S[q].U = U2s[q];
   }
 
+}
+
+template <typename T>
+void Run<T>::wave_c(WaveBatches<T> &B) {
+  DevArena &scr = *h_.scratch;
+  DevArena &per = *h_.pers;
   // phase B
-  GemmBatch<T> g1, g2, g3, g4, g5, g6, g7, g8;
-  CholBatch<T> c1, c2;
+  std::vector<Sup> &S = cur_;
+  const double f0 = B.c1.flops + B.c2.flops + B.g1.flops + B.g2.flops + B.g3.flops + B.g4.flops + B.g5.flops +
+                    B.g6.flops + B.g7.flops + B.g8.flops;
   for (auto &x : S) {
     const int m = x.m, k = x.k, dN = x.dN;
     if (k > m || k < 0) fail(HS_ERR_INVALID, "internal: rank out of range");
@@ -724,63 +791,41 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
       x.phir = use_phi_ ? talloc<T>(per, k) : nullptr;
     }
     // L^-1 U and its CholQR2
-    g1.add(x.Linv, m, 0, x.U, m, 0, x.Ut, k, m, k, m, T(1), T(0));
-    g2.add(x.Ut, k, 1, x.Ut, k, 0, x.S1, k, k, k, m, T(1), T(0));
-    c1.add(x.S1, k, x.L1, k, Tag{1, lv.level, x.s});
-    g3.add(x.Ut, k, 0, x.L1, k, 1, x.Q1, k, m, k, k, T(1), T(0));
-    g4.add(x.Q1, k, 1, x.Q1, k, 0, x.S2, k, k, k, m, T(1), T(0));
-    c2.add(x.S2, k, x.L2, k, Tag{2, lv.level, x.s});
-    g5.add(x.Q1, k, 0, x.L2, k, 1, x.Q, k, m, k, k, T(1), T(0));
-    g5.add(x.L1, k, 1, x.L2, k, 1, x.Rinv, k, k, k, k, T(1), T(0));
+    B.g1.add(x.Linv, m, 0, x.U, m, 0, x.Ut, k, m, k, m, T(1), T(0));
+    B.g2.add(x.Ut, k, 1, x.Ut, k, 0, x.S1, k, k, k, m, T(1), T(0));
+    B.c1.add(x.S1, k, x.L1, k, tag(1, lv_->level, x.s));
+    B.g3.add(x.Ut, k, 0, x.L1, k, 1, x.Q1, k, m, k, k, T(1), T(0));
+    B.g4.add(x.Q1, k, 1, x.Q1, k, 0, x.S2, k, k, k, m, T(1), T(0));
+    B.c2.add(x.S2, k, x.L2, k, tag(2, lv_->level, x.s));
+    B.g5.add(x.Q1, k, 0, x.L2, k, 1, x.Q, k, m, k, k, T(1), T(0));
+    B.g5.add(x.L1, k, 1, x.L2, k, 1, x.Rinv, k, k, k, k, T(1), T(0));
     // quantities needing Q / L^-1
-    g6.add(x.Linv, m, 1, x.Q, k, 0, x.Wt, k, m, k, m, T(1), T(0));          // L^-T Q
-    g6.add(x.Linv, m, 0, x.AsN, dN, 0, x.Gt, dN, m, dN, m, T(1), T(0));       // L^-1 A_sN
-    g6.add(x.Linv, m, 1, x.Linv, m, 0, x.M, m, m, m, m, T(1), T(0));          // L^-T L^-1
+    B.g6.add(x.Linv, m, 1, x.Q, k, 0, x.Wt, k, m, k, m, T(1), T(0));          // L^-T Q
+    B.g6.add(x.Linv, m, 0, x.AsN, dN, 0, x.Gt, dN, m, dN, m, T(1), T(0));       // L^-1 A_sN
+    B.g6.add(x.Linv, m, 1, x.Linv, m, 0, x.M, m, m, m, m, T(1), T(0));          // L^-T L^-1
     if (x.red) {
-      g6.add(x.U, m, 1, x.AsW, x.dW, 0, x.ArW, x.dW, k, x.dW, m, T(1), T(0));  // U^T A_sW
-      if (use_phi_) g6.add(x.U, m, 1, phi_[x.s], 1, 0, x.phir, 1, k, 1, m, T(1), T(0));
+      B.g6.add(x.U, m, 1, x.AsW, x.dW, 0, x.ArW, x.dW, k, x.dW, m, T(1), T(0));  // U^T A_sW
+      if (use_phi_) B.g6.add(x.U, m, 1, phi_[x.s], 1, 0, x.phir, 1, k, 1, m, T(1), T(0));
     }
-    g7.add(x.Rinv, k, 0, x.Wt, k, 1, x.Pm, m, k, m, k, T(1), T(0));           // P_ss = R^-1 (L^-T Q)^T
-    g7.add(x.Wt, k, 0, x.Wt, k, 1, x.M, m, m, m, k, T(-1), T(1));             // M_ss -= W W^T
-    g7.add(x.Q, k, 1, x.Gt, dN, 0, x.Tm, dN, k, dN, m, T(1), T(0));           // Q^T L^-1 A_sN
-    g7.add(x.Gt, dN, 1, x.Gt, dN, 0, x.Z, dN, dN, dN, m, T(1), T(0));         // (L^-1 A_sN)^T (L^-1 A_sN)
-    g8.add(x.Tm, dN, 1, x.Tm, dN, 0, x.Z, dN, dN, dN, k, T(-1), T(1));        // - T^T T
+    B.g7.add(x.Rinv, k, 0, x.Wt, k, 1, x.Pm, m, k, m, k, T(1), T(0));           // P_ss = R^-1 (L^-T Q)^T
+    B.g7.add(x.Wt, k, 0, x.Wt, k, 1, x.M, m, m, m, k, T(-1), T(1));             // M_ss -= W W^T
+    B.g7.add(x.Q, k, 1, x.Gt, dN, 0, x.Tm, dN, k, dN, m, T(1), T(0));           // Q^T L^-1 A_sN
+    B.g7.add(x.Gt, dN, 1, x.Gt, dN, 0, x.Z, dN, dN, dN, m, T(1), T(0));         // (L^-1 A_sN)^T (L^-1 A_sN)
+    B.g8.add(x.Tm, dN, 1, x.Tm, dN, 0, x.Z, dN, dN, dN, k, T(-1), T(1));        // - T^T T
     if (x.red) {
-      g8.add(x.Tm, dN, 1, x.Rinv, k, 1, x.ANr, k, dN, k, k, T(1), T(0));      // A_Nr = T^T R^-T
-      g8.add(x.Rinv, k, 0, x.Rinv, k, 1, x.Arr, k, k, k, k, T(1), T(0));      // A_rr = R^-1 R^-T
+      B.g8.add(x.Tm, dN, 1, x.Rinv, k, 1, x.ANr, k, dN, k, k, T(1), T(0));      // A_Nr = T^T R^-T
+      B.g8.add(x.Rinv, k, 0, x.Rinv, k, 1, x.Arr, k, k, k, k, T(1), T(0));      // A_rr = R^-1 R^-T
     }
   }
-  auto run_chol = [&](CholBatch<T> &cb) {
-    if (cb.tasks.empty()) return;
-    PendingStatus ps;
-    // read at the next synchronisation, after the scratch arena was reset
-    ps.d = (int *)per.alloc(sizeof(int) * cb.tasks.size());
-    ps.what = cb.what;
-    Uploader u;
-    const size_t o = u.add(cb.tasks);
-    char *d = u.upload(scr, sg_, st_);
-    launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)cb.tasks.size(), ps.d, cb.max_m, st_);
-    pending_.push_back(ps);
-    flops_ += cb.flops;
-  };
-  for (GemmBatch<T> *g : {&g1, &g2, &g3, &g4, &g5, &g6, &g7, &g8}) flops_ += g->flops;
-  g1.launch(scr, sg_, st_);
-  g2.launch(scr, sg_, st_);
-  run_chol(c1);
-  g3.launch(scr, sg_, st_);
-  g4.launch(scr, sg_, st_);
-  run_chol(c2);
-  g5.launch(scr, sg_, st_);
-  g6.launch(scr, sg_, st_);
-  g7.launch(scr, sg_, st_);
-  g8.launch(scr, sg_, st_);
+  flops_ += B.c1.flops + B.c2.flops + B.g1.flops + B.g2.flops + B.g3.flops + B.g4.flops + B.g5.flops +
+            B.g6.flops + B.g7.flops + B.g8.flops - f0;
 
   // register the red nodes' blocks and gather the Schur update by target
   std::unordered_map<uint64_t, std::vector<std::pair<int, int>>> tgt;  // target -> (sup idx, pair)
   std::vector<uint64_t> tgt_order;
   for (size_t q = 0; q < S.size(); ++q) {
     const Sup &x = S[q];
-    const PlanSuper &ps = lv.sup[x.s];
+    const PlanSuper &ps = lv_->sup[x.s];
     for (size_t i = 0; i < ps.N.size(); ++i)
       for (size_t j = i; j < ps.N.size(); ++j) {
         const uint64_t key = bkey(ps.N[i], ps.N[j]);
@@ -815,30 +860,28 @@ void Run<T>::wave(const PlanLevel &lv, int li, int widx) {
       }
     }
   }
-  SumBatch<T> schur;
   for (uint64_t key : tgt_order) {
     const BlockRef<T> &dst = blocks_[key];
     const int a = (int)(key >> 32), b = (int)(key & 0xffffffffu);
     const int rk = dst.rowkey, ck = (rk == a) ? b : a;
-    schur.begin(dst.ptr, dst.ld, size_[rk], size_[ck], T(-1), T(1));
+    B.schur.begin(dst.ptr, dst.ld, size_[rk], size_[ck], T(-1), T(1));
     for (auto &c : tgt[key]) {
       const Sup &x = S[c.first];
-      const PlanSuper &ps = lv.sup[x.s];
+      const PlanSuper &ps = lv_->sup[x.s];
       // offsets of the row key and column key inside s's neighbour list
       int orow = -1, ocol = -1;
       for (size_t i = 0; i < ps.N.size(); ++i) {
         if (ps.N[i] == rk) orow = x.Noff[i];
         if (ps.N[i] == ck) ocol = x.Noff[i];
       }
-      schur.src(x.Z + (int64_t)orow * x.dN + ocol, x.dN, 0);
+      B.schur.src(x.Z + (int64_t)orow * x.dN + ocol, x.dN, 0);
     }
-    schur.end();
+    B.schur.end();
   }
-  schur.launch(scr, sg_, st_);
 
   // new red nodes, removal of the eliminated super nodes, apply records
   for (auto &x : S) {
-    const PlanSuper &ps = lv.sup[x.s];
+    const PlanSuper &ps = lv_->sup[x.s];
     if (x.red) {
       const int r = nsup_ + x.s;
       size_[r] = x.k;
@@ -1002,44 +1045,7 @@ void Run<T>::end_level(const PlanLevel &lv, int li) {
 }
 
 template <typename T>
-void Run<T>::root() {
-  // the remaining red nodes (level 1, or the single leaf) form the root
-  const int nred = (int)size_.size();
-  bool any = false;
-  for (int s : size_) any = any || s > 0;
-  h_.root_m = 0;
-  if (!any) {
-    h_.ws_size = seg_off_ + seg_size_;
-    return;
-  }
-  merge(nred, 0);
-  const int m = size_[0];
-  h_.root_m = m;
-  h_.root_off = seg_off_ + sup_off_[0];
-  h_.ws_size = seg_off_ + seg_size_;
-  const BlockRef<T> &b = blocks_.at(bkey(0, 0));
-  T *Linv = talloc<T>(*h_.scratch, (size_t)m * m);
-  T *Ainv = talloc<T>(*h_.pers, (size_t)m * m);
-  CholBatch<T> cb;
-  cb.add(b.ptr, b.ld, Linv, m, Tag{4, 0, 0});
-  PendingStatus ps;
-  ps.d = (int *)h_.pers->alloc(sizeof(int));
-  ps.what = cb.what;
-  Uploader u;
-  const size_t o = u.add(cb.tasks);
-  char *d = u.upload(*h_.scratch, sg_, st_);
-  launch_chol_inv<T>((const CholTask<T> *)(d + o), 1, ps.d, m, st_);
-  pending_.push_back(ps);
-  GemmBatch<T> g;
-  g.add(Linv, m, 1, Linv, m, 0, Ainv, m, m, m, m, T(1), T(0));
-  flops_ += cb.flops + g.flops;
-  g.launch(*h_.scratch, sg_, st_);
-  h_.root_inv = Ainv;
-  h_.info.root_size = m;
-}
-
-template <typename T>
-void Run<T>::run() {
+void Run<T>::begin() {
   h_.nodes.clear();
   h_.nbrs.clear();
   h_.targets.clear();
@@ -1049,27 +1055,233 @@ void Run<T>::run() {
   h_.ranks.clear();
   h_.tmax = 0;
   leaf_setup();
-  int nred = P_.nleaf;
-  for (size_t li = 0; li < P_.levels.size(); ++li) {
-    const PlanLevel &lv = P_.levels[li];
-    lv_level_hint_ = lv.level;
-    merge(nred, 0);
-    for (int j = 0; j < lv.nsup; ++j)
-      if ((size_[j] >= 0) != (bool)lv.exists[j]) fail(HS_ERR_INVALID, "internal: plan/executor mismatch");
-    h_.ranks.emplace_back(lv.nsup, -1);
-    for (int w = 0; w < (int)lv.waves.size(); ++w) {
-      h_.scratch->reset();
-      sg_.next_wave();
-      wave(lv, (int)li, w);
-    }
-    end_level(lv, (int)li);
-    nred = lv.nsup;
+  nred_ = P_.nleaf;
+}
+
+template <typename T>
+void Run<T>::level_begin(int li, SumBatch<T> &sb) {
+  const PlanLevel &lv = P_.levels[li];
+  merge(nred_, 0, sb);
+  for (int j = 0; j < lv.nsup; ++j)
+    if ((size_[j] >= 0) != (bool)lv.exists[j]) fail(HS_ERR_INVALID, "internal: plan/executor mismatch");
+  h_.ranks.emplace_back(lv.nsup, -1);
+}
+
+template <typename T>
+void Run<T>::level_end(int li) {
+  end_level(P_.levels[li], li);
+  nred_ = P_.levels[li].nsup;
+}
+
+// the remaining red nodes (level 1, or the single leaf) form the root
+template <typename T>
+void Run<T>::root_a(SumBatch<T> &sb) {
+  const int nred = (int)size_.size();
+  bool any = false;
+  for (int s : size_) any = any || s > 0;
+  h_.root_m = 0;
+  root_linv_ = root_ainv_ = nullptr;
+  if (!any) {
+    h_.ws_size = seg_off_ + seg_size_;
+    return;
   }
-  h_.scratch->reset();
-  sg_.next_wave();
-  root();
-  sync_check();
+  merge(nred, 0, sb);
+  const int m = size_[0];
+  h_.root_m = m;
+  h_.root_off = seg_off_ + sup_off_[0];
+  h_.ws_size = seg_off_ + seg_size_;
+  root_linv_ = talloc<T>(*h_.scratch, (size_t)m * m);
+  root_ainv_ = talloc<T>(*h_.pers, (size_t)m * m);
+}
+
+template <typename T>
+void Run<T>::root_b(CholBatch<T> &cb, GemmBatch<T> &g) {
+  if (!root_ainv_) return;
+  const int m = h_.root_m;
+  const BlockRef<T> &b = blocks_.at(bkey(0, 0));
+  const double f0 = cb.flops + g.flops;
+  cb.add(b.ptr, b.ld, root_linv_, m, tag(4, 0, 0));
+  g.add(root_linv_, m, 1, root_linv_, m, 0, root_ainv_, m, m, m, m, T(1), T(0));
+  flops_ += cb.flops + g.flops - f0;
+  h_.root_inv = root_ainv_;
+  h_.info.root_size = m;
+}
+
+template <typename T>
+void Run<T>::finish() {
   h_.info.factor_flops = flops_;
+  h_.info.eig_flops = eig_flops_;
+  h_.info.trunc_big_ms = big_ms_;
+  h_.info.trunc_big_flops = big_flops_;
+  h_.info.trunc_big_launches = big_launches_;
+}
+
+// Runs the factorizations of `runs` in lock step: at every step (level counted
+// from the leaves, wave index) the work of all problems that have that step
+// goes into one launch per kernel kind, with one read of the new ranks.
+template <typename T>
+void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
+  const auto t_start = std::chrono::steady_clock::now();
+  for (auto &r : runs) {
+    r->handle().scratch->reset();
+    r->begin();
+  }
+  int maxL = 0;
+  for (auto &r : runs) maxL = std::max(maxL, r->levels());
+  for (int li = 0; li < maxL; ++li) {
+    std::vector<Run<T> *> part;
+    for (auto &r : runs)
+      if (li < r->levels() && r->ok()) part.push_back(r.get());
+    {
+      ex.scr.reset();
+      ex.sg.next_wave();
+      SumBatch<T> sb;
+      for (Run<T> *r : part) {
+        r->handle().scratch->reset();
+        r->level_begin(li, sb);
+      }
+      sb.launch(ex.scr, ex.sg, ex.st);
+    }
+    int nw = 0;
+    for (Run<T> *r : part) nw = std::max(nw, r->waves(li));
+    for (int w = 0; w < nw; ++w) {
+      std::vector<Run<T> *> wp;
+      for (Run<T> *r : part)
+        if (w < r->waves(li) && r->ok()) wp.push_back(r);
+      if (wp.empty()) continue;
+      ex.scr.reset();
+      ex.sg.next_wave();
+      for (Run<T> *r : wp) r->handle().scratch->reset();
+      WaveBatches<T> B;
+      // phase A
+      for (Run<T> *r : wp) r->wave_a(li, w, B);
+      const size_t nchol = B.chol.tasks.size(), ntrunc = B.trunc.size(), nbig = B.trunc_big.size();
+      for (size_t i = 0; i < ntrunc; ++i) B.trunc[i].k_idx = (int)i;
+      for (size_t i = 0; i < nbig; ++i) B.trunc_big[i].k_idx = (int)(ntrunc + i);
+      B.gather.launch(ex.scr, ex.sg, ex.st);
+      int *d_stat = (int *)ex.scr.alloc(sizeof(int) * (nchol + ntrunc + nbig + 1));
+      int *d_k = d_stat + nchol;
+      if (nchol) {
+        Uploader u;
+        const size_t o = u.add(B.chol.tasks);
+        char *d = u.upload(ex.scr, ex.sg, ex.st);
+        launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)nchol, d_stat, B.chol.max_m, ex.st);
+      }
+      B.gram.launch(ex.scr, ex.sg, ex.st);
+      const double eps = wp[0]->handle().eps;
+      const int variant = wp[0]->handle().variant;
+      if (ntrunc) {
+        Uploader u;
+        const size_t o = u.add(B.trunc);
+        char *d = u.upload(ex.scr, ex.sg, ex.st);
+        launch_trunc<T>((const TruncTask<T> *)(d + o), (int)ntrunc, d_k, eps, variant, B.max_trunc_m, ex.st);
+      }
+      if (nbig) {
+        // one launch per thread-count class (k_idx keeps each rank's slot)
+        std::vector<TruncTask<T>> cls[2];
+        int cmax[2] = {0, 0};
+        for (const TruncTask<T> &t : B.trunc_big) {
+          const int c = t.m <= kTruncBigMidMax ? 0 : 1;
+          cls[c].push_back(t);
+          cmax[c] = std::max(cmax[c], t.m);
+        }
+        Uploader u;
+        const size_t o0 = u.add(cls[0]);
+        const size_t o1 = u.add(cls[1]);
+        char *d = u.upload(ex.scr, ex.sg, ex.st);
+        HS_CUDA(cudaEventRecord(ex.ev_big[0], ex.st));
+        launch_trunc_big<T>((const TruncTask<T> *)(d + o0), (int)cls[0].size(), d_k, eps, variant, cmax[0], ex.st);
+        launch_trunc_big<T>((const TruncTask<T> *)(d + o1), (int)cls[1].size(), d_k, eps, variant, cmax[1], ex.st);
+        HS_CUDA(cudaEventRecord(ex.ev_big[1], ex.st));
+      }
+      // one read of the statuses and ranks
+      const size_t nread = nchol + ntrunc + nbig;
+      int *hb = ex.host_ints(nread + 1);
+      if (nread) HS_CUDA(cudaMemcpyAsync(hb, d_stat, sizeof(int) * nread, cudaMemcpyDeviceToHost, ex.st));
+      ex.sync_check();
+      float big_ms = 0.f;
+      if (nbig) HS_CUDA(cudaEventElapsedTime(&big_ms, ex.ev_big[0], ex.ev_big[1]));
+      for (Run<T> *r : wp)
+        if (r->ok()) r->wave_b(hb, nchol, ntrunc, big_ms, B);
+      // U of the large path: CholQR2
+      B.o1.launch(ex.scr, ex.sg, ex.st);
+      ex.chol_checked(B.oc1);
+      B.o2.launch(ex.scr, ex.sg, ex.st);
+      B.o3.launch(ex.scr, ex.sg, ex.st);
+      ex.chol_checked(B.oc2);
+      B.o4.launch(ex.scr, ex.sg, ex.st);
+      // phase B and the Schur update
+      for (Run<T> *r : wp)
+        if (r->ok()) r->wave_c(B);
+      B.g1.launch(ex.scr, ex.sg, ex.st);
+      B.g2.launch(ex.scr, ex.sg, ex.st);
+      ex.chol_checked(B.c1);
+      B.g3.launch(ex.scr, ex.sg, ex.st);
+      B.g4.launch(ex.scr, ex.sg, ex.st);
+      ex.chol_checked(B.c2);
+      B.g5.launch(ex.scr, ex.sg, ex.st);
+      B.g6.launch(ex.scr, ex.sg, ex.st);
+      B.g7.launch(ex.scr, ex.sg, ex.st);
+      B.g8.launch(ex.scr, ex.sg, ex.st);
+      B.schur.launch(ex.scr, ex.sg, ex.st);
+    }
+    for (Run<T> *r : part)
+      if (r->ok()) r->level_end(li);
+  }
+  // the roots
+  ex.scr.reset();
+  ex.sg.next_wave();
+  {
+    SumBatch<T> sb;
+    for (auto &r : runs)
+      if (r->ok()) {
+        r->handle().scratch->reset();
+        r->root_a(sb);
+      }
+    sb.launch(ex.scr, ex.sg, ex.st);
+    CholBatch<T> cb;
+    GemmBatch<T> g;
+    for (auto &r : runs)
+      if (r->ok()) r->root_b(cb, g);
+    ex.chol_checked(cb);
+    g.launch(ex.scr, ex.sg, ex.st);
+  }
+  ex.sync_check();
+  const double total =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  for (auto &r : runs)
+    if (r->ok()) {
+      r->finish();
+      r->handle().info.host_ms = total;
+      r->handle().info.wait_ms = ex.wait_ms;
+    }
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+void factorize_t(const std::vector<FactorHandle *> &hs, const std::vector<const double *> &phis,
+                 cudaStream_t st, std::vector<int> *status, std::vector<std::string> *msg) {
+  Exec ex(st);
+  if (hs.size() > 1) {
+    ex.prob_status.assign(hs.size(), HS_OK);
+    ex.prob_msg.assign(hs.size(), std::string());
+  }
+  std::vector<std::unique_ptr<Run<T>>> runs;
+  for (size_t p = 0; p < hs.size(); ++p) {
+    FactorHandle &h = *hs[p];
+    if (!h.pers) h.pers.reset(new DevArena(256ull << 20));
+    if (!h.scratch) h.scratch.reset(new DevArena(64ull << 20));
+    h.pers->reset();     // a refactorization reuses the previous factor's memory
+    h.scratch->reset();
+    h.info = hs_info{};
+    runs.emplace_back(new Run<T>(h, phis[p], ex, hs.size() > 1 ? (int)p : -1));
+  }
+  execute<T>(ex, runs);
+  if (status) *status = ex.prob_status.empty() ? std::vector<int>(hs.size(), HS_OK) : ex.prob_status;
+  if (msg) *msg = ex.prob_msg.empty() ? std::vector<std::string>(hs.size()) : ex.prob_msg;
 }
 
 }  // namespace
@@ -1077,18 +1289,20 @@ void Run<T>::run() {
 void factorize(FactorHandle &h, const hs_csr &A, const hs_opts &o, const double *phi_host) {
   (void)A;
   (void)o;
-  if (!h.pers) h.pers.reset(new DevArena(256ull << 20));
-  if (!h.scratch) h.scratch.reset(new DevArena(64ull << 20));
-  h.pers->reset();     // a refactorization reuses the previous factor's memory
-  h.scratch->reset();
-  h.info = hs_info{};
-  if (h.prec == HS_PREC_F64) {
-    Run<double> r(h, phi_host);
-    r.run();
-  } else {
-    Run<float> r(h, phi_host);
-    r.run();
-  }
+  factorize_batch({&h}, {phi_host}, h.stream, nullptr, nullptr);
+}
+
+void factorize_batch(const std::vector<FactorHandle *> &hs, const std::vector<const double *> &phis,
+                     cudaStream_t st, std::vector<int> *status, std::vector<std::string> *msg) {
+  if (hs.empty()) return;
+  const int prec = hs[0]->prec;
+  for (FactorHandle *h : hs)
+    if (h->prec != prec || h->eps != hs[0]->eps || h->variant != hs[0]->variant)
+      fail(HS_ERR_INVALID, "a batched factorization needs one precision, tolerance and variant");
+  if (prec == HS_PREC_F64)
+    factorize_t<double>(hs, phis, st, status, msg);
+  else
+    factorize_t<float>(hs, phis, st, status, msg);
 }
 
 }  // namespace hs

@@ -163,6 +163,11 @@ struct FactorHandle {
 
 // factor.cu
 void factorize(FactorHandle &h, const hs_csr &A, const hs_opts &o, const double *phi_host);
+// Independent problems factored in lock step, their steps batched into shared
+// launches.  With more than one problem, a failed pivot (not SPD) takes only
+// that problem out: status[p] = HS_ERR_NOT_SPD and msg[p] say so.
+void factorize_batch(const std::vector<FactorHandle *> &hs, const std::vector<const double *> &phis,
+                     cudaStream_t st, std::vector<int> *status, std::vector<std::string> *msg);
 
 // solve.cu
 void apply_solve(FactorHandle &h, const double *r, double *z, int nrhs, int64_t ld,

@@ -153,6 +153,10 @@ template <typename T>
 void launch_trunc(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant,
                   int max_m, cudaStream_t st);
 // large super nodes (kernels_eig.cu): tridiagonalisation / bisection / inverse iteration
+// Large-node truncations of m <= kTruncBigMidMax run 256 threads per node,
+// larger ones 1024; launch_trunc_big takes tasks of one class at a time.
+constexpr int kTruncBigMidMax = 128;
+
 template <typename T>
 size_t trunc_big_work_elems(int m);
 template <typename T>

@@ -2,7 +2,8 @@
 // symmetric eigen-decomposition of the Gram matrix by Householder
 // tridiagonalisation, Sturm-sequence bisection and inverse iteration.
 //
-// One CTA (1024 threads) per super node:
+// One CTA per super node: 256 threads for m <= 128, 1024 above (a function of
+// m alone, so a node gets the same arithmetic in any batch):
 //   1. GC basis U_1 = orth[phi_s, A_sw phi_w] (Sec. 6), as in the Jacobi path.
 //   2. ||A_sw||_2^2 = lambda_max(G).  LoRaSp: top eigenvalue of T below.  GC:
 //      G = J + (rank <= 4 terms in span{U_1, G U_1}), so lambda_max(G) follows
@@ -28,7 +29,6 @@ namespace hs {
 
 namespace {
 
-constexpr int BT = 1024;  // threads per CTA
 
 __device__ double bsum(double v, double *red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -426,8 +426,8 @@ __device__ int count_above_lowrank(const R *d, const R *e, int m, const R *Z, in
   return pos - k1;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(BT) k_trunc_big(const TruncTask<T> *__restrict__ tasks, int *__restrict__ kout,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict__ tasks, int *__restrict__ kout,
                                                  double eps, int variant, int tile_cap, int vec_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
@@ -763,23 +763,33 @@ size_t trunc_big_work_elems(int m) {
   return (bytes + sizeof(T) - 1) / sizeof(T);
 }
 
-template <typename T>
-void launch_trunc_big(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant, int max_m,
-                      cudaStream_t st) {
+template <typename T, int NT>
+void launch_trunc_big_nt(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant, int max_m,
+                         cudaStream_t st) {
   if (ntasks == 0) return;
   // the per-node vectors go to shared memory while they leave room for a
-  // tile of at least 64 x 64; the rest of the budget is the tile
+  // tile of at least 64 x 64; the rest of the budget is the tile, no larger
+  // than the largest node needs
   const size_t budget = 200 * 1024;
   size_t fixed = trunc_big_vec_bytes<T>(max_m) + 32;
   const int vec_smem = fixed + 64 * 64 * sizeof(T) <= budget ? 1 : 0;
   if (!vec_smem) fixed = 32;
   int cap = 0;
-  while ((size_t)(cap + 1) * (cap + 1) * sizeof(T) + fixed <= budget) ++cap;
+  while (cap < max_m && (size_t)(cap + 1) * (cap + 1) * sizeof(T) + fixed <= budget) ++cap;
   const size_t sm = fixed + (size_t)cap * cap * sizeof(T);
-  check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc_big<T>>(), "k_trunc_big");
-  k_trunc_big<T><<<ntasks, BT, sm, st>>>(d_tasks, d_k, eps, variant, cap, vec_smem);
+  check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc_big<T, NT>>(), "k_trunc_big");
+  k_trunc_big<T, NT><<<ntasks, NT, sm, st>>>(d_tasks, d_k, eps, variant, cap, vec_smem);
   count_launch();
   HS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_trunc_big(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant, int max_m,
+                      cudaStream_t st) {
+  if (max_m <= kTruncBigMidMax)
+    launch_trunc_big_nt<T, 256>(d_tasks, ntasks, d_k, eps, variant, max_m, st);
+  else
+    launch_trunc_big_nt<T, 1024>(d_tasks, ntasks, d_k, eps, variant, max_m, st);
 }
 
 template size_t trunc_big_work_elems<double>(int);
