@@ -279,6 +279,19 @@ int eig_small_max() {
   return v;
 }
 
+// Smallest super node whose truncation takes the multi-CTA path (tridiagonal
+// steps spread over the GPU, reflector products by batches of columns); below
+// it one CTA per node does everything.  HS_GRID_TRIDIAG_MIN (environment)
+// moves the limit, which lets small test problems exercise the path.
+inline int grid_tridiag_min() {
+  static const int v = [] {
+    const char *e = std::getenv("HS_GRID_TRIDIAG_MIN");
+    const int x = e ? std::atoi(e) : 0;
+    return x > 3 ? x : 384;
+  }();
+  return v;
+}
+
 template <typename T>
 T *talloc(DevArena &a, size_t n) {
   return (T *)a.alloc(sizeof(T) * std::max<size_t>(n, 1));
@@ -1116,6 +1129,67 @@ void Run<T>::finish() {
   h_.info.trunc_big_launches = big_launches_;
 }
 
+// Truncation of very large nodes across the whole GPU: k_trunc_big up to J
+// (TB_PREP), the tridiagonal steps (two launches per step over all the nodes'
+// CTAs), Z = Q^T [U1, X] (GC), k_trunc_big from T to its eigenvectors
+// (TB_POST), then U_2 = Q Y by batches of columns.
+template <typename T>
+void trunc_grid(Exec &ex, const std::vector<TruncTask<T>> &tasks, const TruncTask<T> *d_tasks, int *d_k,
+                double eps, int variant, int max_m) {
+  const int n = (int)tasks.size();
+  launch_trunc_big_mode<T>(d_tasks, n, d_k, eps, variant, max_m, 1 /* TB_PREP */, ex.st);
+  std::vector<GridTri<T>> gt(n);
+  int blocks = 0;
+  for (int q = 0; q < n; ++q) {
+    const TruncTask<T> &t = tasks[q];
+    const BigLayout<T> L = big_layout<T>(t.work, t.m);
+    GridTri<T> &g = gt[q];
+    g.A = L.A;
+    g.X = L.Y;                 // the step vectors live in Y until TB_POST
+    g.P = L.Y + t.m;
+    g.V = L.Y + 2 * (size_t)t.m;
+    g.px = L.Y + 3 * (size_t)t.m;
+    g.ppv = L.Y + 4 * (size_t)t.m;
+    g.d = L.d;
+    g.e = L.e;
+    g.tau = L.tau;
+    g.m = t.m;
+    g.nblk = (t.m + kTriRows - 1) / kTriRows;
+    g.blk0 = blocks;
+    blocks += g.nblk;
+  }
+  Uploader u;
+  const size_t og = u.add(gt);
+  char *dg = u.upload(ex.scr, ex.sg, ex.st);
+  const GridTri<T> *d_gt = (const GridTri<T> *)(dg + og);
+  for (int k = 0; k + 2 <= max_m; ++k) {
+    launch_tri_step<T>(d_gt, n, blocks, k, 0, ex.st);
+    if (k + 3 <= max_m) launch_tri_step<T>(d_gt, n, blocks, k, 1, ex.st);
+  }
+  const int nb = refl_batch<T>(max_m);
+  if (variant != HS_LORASP) {
+    std::vector<ReflTask<T>> zf;
+    for (const TruncTask<T> &t : tasks) {
+      const BigLayout<T> L = big_layout<T>(t.work, t.m);
+      zf.push_back(ReflTask<T>{L.A, L.tau, L.LS, t.U, L.sc_int, t.m, 0, 1});
+    }
+    Uploader uz;
+    const size_t oz = uz.add(zf);
+    char *dz = uz.upload(ex.scr, ex.sg, ex.st);
+    launch_refl<T>((const ReflTask<T> *)(dz + oz), (int)zf.size(), std::min(nb, 4), max_m, ex.st);
+  }
+  launch_trunc_big_mode<T>(d_tasks, n, d_k, eps, variant, max_m, 2 /* TB_POST */, ex.st);
+  std::vector<ReflTask<T>> yb;
+  for (const TruncTask<T> &t : tasks) {
+    const BigLayout<T> L = big_layout<T>(t.work, t.m);
+    for (int j0 = 0; j0 < t.m; j0 += nb) yb.push_back(ReflTask<T>{L.A, L.tau, L.Y, t.U, L.sc_int, t.m, j0, 0});
+  }
+  Uploader uy;
+  const size_t oy = uy.add(yb);
+  char *dy = uy.upload(ex.scr, ex.sg, ex.st);
+  launch_refl<T>((const ReflTask<T> *)(dy + oy), (int)yb.size(), nb, max_m, ex.st);
+}
+
 // Runs the factorizations of `runs` in lock step: at every step (level counted
 // from the leaves, wave index) the work of all problems that have that step
 // goes into one launch per kernel kind, with one read of the new ranks.
@@ -1177,21 +1251,25 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
         launch_trunc<T>((const TruncTask<T> *)(d + o), (int)ntrunc, d_k, eps, variant, B.max_trunc_m, ex.st);
       }
       if (nbig) {
-        // one launch per thread-count class (k_idx keeps each rank's slot)
-        std::vector<TruncTask<T>> cls[2];
-        int cmax[2] = {0, 0};
+        // one launch per class (k_idx keeps each rank's slot): 256 or 1024
+        // threads per node, or the multi-CTA path for very large nodes
+        std::vector<TruncTask<T>> cls[3];
+        int cmax[3] = {0, 0, 0};
         for (const TruncTask<T> &t : B.trunc_big) {
-          const int c = t.m <= kTruncBigMidMax ? 0 : 1;
+          const int c = (eps > 0.0 && t.m >= grid_tridiag_min()) ? 2 : t.m <= kTruncBigMidMax ? 0 : 1;
           cls[c].push_back(t);
           cmax[c] = std::max(cmax[c], t.m);
         }
         Uploader u;
         const size_t o0 = u.add(cls[0]);
         const size_t o1 = u.add(cls[1]);
+        const size_t o2 = u.add(cls[2]);
         char *d = u.upload(ex.scr, ex.sg, ex.st);
         HS_CUDA(cudaEventRecord(ex.ev_big[0], ex.st));
         launch_trunc_big<T>((const TruncTask<T> *)(d + o0), (int)cls[0].size(), d_k, eps, variant, cmax[0], ex.st);
         launch_trunc_big<T>((const TruncTask<T> *)(d + o1), (int)cls[1].size(), d_k, eps, variant, cmax[1], ex.st);
+        if (!cls[2].empty())
+          trunc_grid<T>(ex, cls[2], (const TruncTask<T> *)(d + o2), d_k, eps, variant, cmax[2]);
         HS_CUDA(cudaEventRecord(ex.ev_big[1], ex.st));
       }
       // one read of the statuses and ranks

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stddef.h>
 
 #include <mutex>
 #include <string>
@@ -153,6 +154,96 @@ template <typename T>
 void launch_trunc(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant,
                   int max_m, cudaStream_t st);
 // large super nodes (kernels_eig.cu): tridiagonalisation / bisection / inverse iteration
+// Global work area of one large-truncation node (offsets from TruncTask::work;
+// the host computes the same addresses for the multi-CTA kernels):
+//   A (m^2 T)   Gram / J, then the Householder reflectors in its rows
+//   Y (m^2 T)   eigenvectors of T; before that the multi-CTA tridiagonalisation
+//               keeps its step vectors here
+//   LU (4 m^2 T), LS (164 m T), FL (m^2 bytes): inverse iteration and Z
+//   VG          the per-node vectors (d, e, pw in FP64; dt, et, lam, v, tau, wt,
+//               redt in T) when they are not in shared memory
+//   SC          persistent scalars between the kernels of the multi-CTA path:
+//               k1, k2 (ints), then c = U1^T G U1 (4 doubles)
+template <typename T>
+struct BigLayout {
+  T *A, *Y, *LU, *LS;
+  unsigned char *FL, *VG;
+  double *d, *e, *pw;
+  T *dt, *et, *lam, *v, *tau, *wt, *redt;
+  int *sc_int;
+  double *sc_c;
+};
+
+template <typename T>
+__host__ __device__ inline size_t big_vec_bytes(int m) {
+  return 3 * sizeof(double) * (size_t)m + 6 * sizeof(T) * (size_t)((m + 1) & ~1) + 34 * sizeof(T) + 16;
+}
+
+template <typename T>
+__host__ __device__ inline BigLayout<T> big_layout(T *work, int m) {
+  BigLayout<T> L;
+  L.A = work;
+  L.Y = work + (size_t)m * m;
+  L.LU = L.Y + (size_t)m * m;
+  L.LS = L.LU + 4 * (size_t)m * m;
+  L.FL = (unsigned char *)(L.LS + 164 * (size_t)m);
+  L.VG = (unsigned char *)(((uintptr_t)(L.FL + (size_t)m * m) + 15) & ~(uintptr_t)15);
+  const size_t me = (size_t)((m + 1) & ~1);
+  unsigned char *p = L.VG;
+  L.d = (double *)p;
+  p += sizeof(double) * m;
+  L.e = (double *)p;
+  p += sizeof(double) * m;
+  L.pw = (double *)p;
+  p += sizeof(double) * m;
+  L.dt = (T *)p;
+  p += sizeof(T) * me;
+  L.et = (T *)p;
+  p += sizeof(T) * me;
+  L.lam = (T *)p;
+  p += sizeof(T) * me;
+  L.v = (T *)p;
+  p += sizeof(T) * me;
+  L.tau = (T *)p;
+  p += sizeof(T) * me;
+  L.wt = (T *)p;
+  p += sizeof(T) * me;
+  L.redt = (T *)p;
+  unsigned char *sc = (unsigned char *)(((uintptr_t)(L.VG + big_vec_bytes<T>(m)) + 15) & ~(uintptr_t)15);
+  L.sc_int = (int *)sc;
+  L.sc_c = (double *)(sc + 16);
+  return L;
+}
+
+// One node of the multi-CTA tridiagonalisation (very large super nodes): its
+// matrix A (m x m, ld m) and step vectors in the node's work area, the
+// tridiagonal d, e and the reflector coefficients tau.  The node owns nblk =
+// ceil(m / kTriRows) consecutive CTAs starting at blk0.
+constexpr int kTriRows = 8;   // rows per CTA, one warp each
+template <typename T>
+struct GridTri {
+  T *A;
+  T *X, *P, *V;      // column k, p, v of the current step
+  T *px, *ppv;       // per-CTA partial sums (|x|^2, p.v)
+  double *d, *e;
+  T *tau;
+  int m, nblk, blk0;
+};
+
+// Products with Q = H_0 ... H_{m-3} of a node's reflectors: forward (Q^T, the
+// 2 k1 columns of Z, in place) or backward (Q Y into U columns k1..).  A task is
+// one batch of columns [j0, j0 + nb) of one node; k1, k2 come from the node's
+// scalar area (sc).
+template <typename T>
+struct ReflTask {
+  const T *A;
+  const T *tau;
+  T *cols;           // column-major, ld m
+  T *U;              // backward: output, row-major m x m
+  const int *sc;
+  int m, j0, fwd;
+};
+
 // Large-node truncations of m <= kTruncBigMidMax run 256 threads per node,
 // larger ones 1024; launch_trunc_big takes tasks of one class at a time.
 constexpr int kTruncBigMidMax = 128;
@@ -162,6 +253,21 @@ size_t trunc_big_work_elems(int m);
 template <typename T>
 void launch_trunc_big(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant,
                       int max_m, cudaStream_t st);
+// the multi-CTA path: k_trunc_big in one of its modes (TB_PREP = 1, TB_POST = 2)
+template <typename T>
+void launch_trunc_big_mode(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant, int max_m,
+                           int mode, cudaStream_t st);
+// one step k of the multi-CTA tridiagonalisation over `total_blocks` CTAs
+// (phase 0: apply step k-1's update and take column k; phase 1: reflector
+// and p = tau A v)
+template <typename T>
+void launch_tri_step(const GridTri<T> *d_tasks, int ntasks, int total_blocks, int k, int phase, cudaStream_t st);
+// reflector products (one CTA per task); nb columns per task
+template <typename T>
+void launch_refl(const ReflTask<T> *d_tasks, int ntasks, int nb, int m_max, cudaStream_t st);
+// columns per reflector task that fit the shared-memory budget for nodes of size m
+template <typename T>
+int refl_batch(int m);
 // largest m handled by the shared-memory Jacobi truncation
 template <typename T>
 constexpr int jacobi_cap() {

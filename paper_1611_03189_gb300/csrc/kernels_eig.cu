@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "hs_internal.h"
 #include "trunc_common.cuh"
 
@@ -426,9 +428,16 @@ __device__ int count_above_lowrank(const R *d, const R *e, int m, const R *Z, in
   return pos - k1;
 }
 
+// mode: TB_FULL does all steps in this CTA.  The multi-CTA path for very large
+// nodes splits it: TB_PREP stops before the tridiagonalisation (A = J, Z saved,
+// k1 and c stored in SC); the step kernels tridiagonalise; TB_POST takes d, e
+// and the reflectors from global memory and stops after the eigenvectors of T
+// (Y, k2 in SC) -- the reflector kernels do the two products with Q.
+enum { TB_FULL = 0, TB_PREP = 1, TB_POST = 2 };
+
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict__ tasks, int *__restrict__ kout,
-                                                 double eps, int variant, int tile_cap, int vec_smem) {
+                                                 double eps, int variant, int tile_cap, int vec_smem, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
   __shared__ int s_k2;
@@ -439,12 +448,13 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
   // 4 m, then per-thread inverse-iteration slots when the shared tile is too
   // small); then flags (m^2 bytes); then the per-node vectors when they do not
   // fit in shared memory (vec_smem == 0)
-  T *A = t.work;
-  T *Y = t.work + (size_t)m * m;
-  T *LU = Y + (size_t)m * m;
-  T *LS = LU + 4 * (size_t)m * m;
-  unsigned char *FL = (unsigned char *)(LS + 164 * (size_t)m);
-  unsigned char *VG = (unsigned char *)(((uintptr_t)(FL + (size_t)m * m) + 15) & ~(uintptr_t)15);
+  const BigLayout<T> L = big_layout<T>(t.work, m);
+  T *A = L.A;
+  T *Y = L.Y;
+  T *LU = L.LU;
+  T *LS = L.LS;
+  unsigned char *FL = L.FL;
+  unsigned char *VG = L.VG;
   // vector layout (shared memory, or global at VG), then the shared tile
   Big<T> b;
   unsigned char *p = vec_smem ? smem_raw : VG;
@@ -522,7 +532,11 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
   double lmax = 0.0;
   T cmat[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
   // ---- J
-  if (!gc) {
+  if (mode == TB_POST) {
+    // J, Z and c were made by TB_PREP; Z is already Q^T [U1, X]
+    for (int a = 0; a < 2; ++a)
+      for (int bb = 0; bb < 2; ++bb) cmat[a][bb] = (T)L.sc_c[2 * a + bb];
+  } else if (!gc) {
     for (int64_t q = tid; q < (int64_t)m * m; q += nt) A[q] = t.G[q];
   } else if (eps > 0.0) {
     // X = G U1 in Y's first columns, c = U1^T X; one warp per row of G
@@ -577,7 +591,7 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
   __syncthreads();
   // X = G U1 (Y columns 0..k1-1) is needed again below: move it next to U1 first
   T *Zb = LS;  // Z = Q^T [U1, X], 2 k1 <= 4 columns of m
-  if (gc && eps > 0.0) {
+  if (gc && eps > 0.0 && mode != TB_POST) {
     for (int64_t q = tid; q < (int64_t)m * k1; q += nt) {
       const int a = (int)(q / m), i = (int)(q % m);
       Zb[(size_t)a * m + i] = t.U[(int64_t)i * m + a];
@@ -585,7 +599,35 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
     }
   }
   __syncthreads();
-  tridiag<T>(A, m, b);
+  if (mode == TB_PREP) {
+    if (tid == 0) {
+      L.sc_int[0] = k1;
+      for (int a = 0; a < 2; ++a)
+        for (int bb = 0; bb < 2; ++bb) L.sc_c[2 * a + bb] = (double)cmat[a][bb];
+    }
+    return;
+  }
+  if (mode == TB_POST) {
+    // the step kernels left d, e, tau for k < m - 2 and the updated trailing 2 x 2 block
+    if (tid == 0) {
+      if (m >= 2) {
+        b.d[m - 2] = (double)A[(int64_t)(m - 2) * m + m - 2];
+        b.e[m - 2] = (double)A[(int64_t)(m - 1) * m + m - 2];
+        b.tau[m - 2] = T(0);
+      }
+      b.d[m - 1] = (double)A[(int64_t)(m - 1) * m + m - 1];
+      b.e[m - 1] = 0.0;
+      b.tau[m - 1] = T(0);
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += nt) {
+      b.dt[i] = (T)b.d[i];
+      b.et[i] = (T)b.e[i];
+    }
+    __syncthreads();
+  } else {
+    tridiag<T>(A, m, b);
+  }
   const Gersh<T> g = gershgorin<T>(b.dt, b.et, m);
   double thr;
   __shared__ double s_lmax;
@@ -599,7 +641,7 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
     thr = eps * eps * lmax;
   } else if (eps > 0.0) {
     // Z = Q^T [U1, X]: reflectors in forward order, one warp per column
-    {
+    if (mode != TB_POST) {
       const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
       for (int j = warp; j < 2 * k1; j += nw) {
         T *z = Zb + (size_t)j * m;
@@ -704,6 +746,15 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
     }
   }
   __syncthreads();
+  if (mode == TB_POST) {
+    // U_2 = Q Y is left to the reflector kernel
+    if (tid == 0) {
+      L.sc_int[0] = k1;
+      L.sc_int[1] = k2;
+      kout[t.k_idx] = k1 + k2;
+    }
+    return;
+  }
   // ---- back-transformation U_2 = Q Y (reflectors in reverse order): columns
   // staged in shared memory in batches, one warp per column
   {
@@ -745,13 +796,235 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
   if (tid == 0) kout[t.k_idx] = k1 + k2;
 }
 
+// ---------------------------------------------------------------------------
+// Multi-CTA tridiagonalisation of very large nodes.  One CTA per node cannot
+// use more than one SM, and its traffic grows as m^3: here each step is spread
+// over ceil(m / kTriRows) CTAs per node, one warp per row.  Step k:
+//   phase 0 (k_tri_update): rows i >= k get the rank-2 update of step k - 1,
+//     A_ij -= v_i w_j + w_i v_j (w = p - K v, K = tau p.v / 2 from the CTAs'
+//     partials in block order); then x_i = A_ik for i > k and d_k = A_kk, with
+//     per-CTA partials of |x|^2.
+//   phase 1 (k_tri_symv): every CTA forms the reflector of x from the partials
+//     (same arithmetic in every CTA), v_i for its rows, p_i = tau sum_j A_ij v_j,
+//     and per-CTA partials of p.v; v is also kept in row k of A for the later
+//     products with Q (as the one-CTA path stores it).
+// Reductions run in a fixed order, so results do not depend on scheduling.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ int tri_task(const GridTri<T> *tasks, int ntasks, int b) {
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].blk0 <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// fixed-order sum of n partials by one warp (every lane gets it)
+template <typename T>
+__device__ __forceinline__ T warp_sum_parts(const T *part, int n, int lane) {
+  T s = T(0);
+  for (int c = lane; c < n; c += 32) s += part[c];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTriRows * 32) k_tri_update(const GridTri<T> *__restrict__ tasks, int ntasks,
+                                                               int k) {
+  __shared__ T sK;
+  __shared__ T wpart[kTriRows];
+  const GridTri<T> t = tasks[tri_task(tasks, ntasks, blockIdx.x)];
+  const int m = t.m;
+  if (k > m - 2) return;
+  const int rb = blockIdx.x - t.blk0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = rb * kTriRows + warp;
+  if (k >= 1) {
+    if (warp == 0) {
+      const T s = warp_sum_parts<T>(t.ppv, t.nblk, lane);
+      if (lane == 0) sK = T(0.5) * t.tau[k - 1] * s;
+    }
+    __syncthreads();
+  }
+  T part = T(0);
+  if (i >= k && i < m) {
+    T *row = t.A + (int64_t)i * m;
+    if (k >= 1) {
+      const T K = sK;
+      const T vi = t.V[i];
+      const T wi = fma(-K, vi, t.P[i]);
+      for (int j = k + lane; j < m; j += 32) {
+        const T vj = t.V[j];
+        const T wj = fma(-K, vj, t.P[j]);
+        row[j] = fma(-vi, wj, fma(-wi, vj, row[j]));
+      }
+      __syncwarp();
+    }
+    if (k <= m - 3 && lane == 0) {
+      const T x = row[k];
+      if (i == k) {
+        t.d[k] = (double)x;
+      } else {
+        t.X[i] = x;
+        part = x * x;
+      }
+    }
+  }
+  if (lane == 0) wpart[warp] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T s = T(0);
+    for (int w = 0; w < kTriRows; ++w) s += wpart[w];
+    t.px[rb] = s;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTriRows * 32) k_tri_symv(const GridTri<T> *__restrict__ tasks, int ntasks,
+                                                             int k) {
+  __shared__ double s_scale, s_tau;
+  __shared__ T wpart[kTriRows];
+  const GridTri<T> t = tasks[tri_task(tasks, ntasks, blockIdx.x)];
+  const int m = t.m;
+  if (k > m - 3) return;
+  const int rb = blockIdx.x - t.blk0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    // the reflector of x = A[k+1.., k] (as in the one-CTA tridiagonalisation)
+    const double xn2 = (double)warp_sum_parts<T>(t.px, t.nblk, lane);
+    if (lane == 0) {
+      const double alpha = (double)t.X[k + 1];
+      const double sig = xn2 - alpha * alpha;
+      double tau = 0.0, beta = alpha, scale = 0.0;
+      if (sig > 0.0) {
+        beta = -copysign(sqrt(xn2), alpha);
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      s_scale = scale;
+      s_tau = tau;
+      if (rb == 0) {
+        t.e[k] = beta;
+        t.tau[k] = (T)tau;
+      }
+    }
+  }
+  __syncthreads();
+  const T scale_t = (T)s_scale, tau_t = (T)s_tau;
+  const int i = rb * kTriRows + warp;
+  T pv = T(0);
+  if (i >= k + 1 && i < m) {
+    const T vi = (i == k + 1) ? T(1) : t.X[i] * scale_t;
+    T p = T(0);
+    if (s_tau != 0.0) {
+      const T *row = t.A + (int64_t)i * m;
+      const T *X = t.X;
+      auto vj = [&](int j) { return j == k + 1 ? T(1) : X[j] * scale_t; };
+      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+      int j = k + 1 + lane;
+      for (; j + 96 < m; j += 128) {
+        a0 = fma(row[j], vj(j), a0);
+        a1 = fma(row[j + 32], vj(j + 32), a1);
+        a2 = fma(row[j + 64], vj(j + 64), a2);
+        a3 = fma(row[j + 96], vj(j + 96), a3);
+      }
+      for (; j < m; j += 32) a0 = fma(row[j], vj(j), a0);
+      T acc = (a0 + a1) + (a2 + a3);
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      p = tau_t * acc;
+    }
+    if (lane == 0) {
+      t.V[i] = vi;
+      t.P[i] = p;
+      pv = p * vi;
+      if (i >= k + 2) t.A[(int64_t)k * m + i] = vi;   // reflector k kept in row k
+    }
+  }
+  if (lane == 0) wpart[warp] = pv;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T s = T(0);
+    for (int w = 0; w < kTriRows; ++w) s += wpart[w];
+    t.ppv[rb] = s;
+  }
+}
+
+// Products with the reflectors of a node, one CTA per batch of columns held in
+// shared memory: for each reflector the block forms all the batch's dot
+// products (fixed-order reduction), then updates the columns.
+constexpr int RT = 256;
+constexpr int RNB = 16;   // most columns per task
+
+template <typename T>
+__global__ void __launch_bounds__(RT) k_refl(const ReflTask<T> *__restrict__ tasks, int nb) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T red[RT / 32][RNB];
+  __shared__ T tot[RNB];
+  const ReflTask<T> t = tasks[blockIdx.x];
+  const int m = t.m;
+  const int k1 = t.sc[0];
+  const int ncol = t.fwd ? 2 * k1 : t.sc[1];
+  if (t.j0 >= ncol) return;
+  const int nc = min(nb, ncol - t.j0);
+  T *Ys = (T *)smem_raw;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int64_t q = tid; q < (int64_t)nc * m; q += RT) Ys[q] = t.cols[(size_t)t.j0 * m + q];
+  __syncthreads();
+  for (int kk = 0; kk + 2 < m; ++kk) {
+    const int k = t.fwd ? kk : m - 3 - kk;
+    const T tk = t.tau[k];
+    if (tk == T(0)) continue;
+    const int n1 = m - k - 1;
+    const T *vrow = t.A + (int64_t)k * m + k + 1;   // v[0] = 1 implicit
+    T s[RNB];
+#pragma unroll
+    for (int c = 0; c < RNB; ++c) s[c] = T(0);
+    for (int i = tid; i < n1; i += RT) {
+      const T vi = i == 0 ? T(1) : vrow[i];
+#pragma unroll
+      for (int c = 0; c < RNB; ++c)
+        if (c < nc) s[c] = fma(vi, Ys[(size_t)c * m + k + 1 + i], s[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < RNB; ++c) {
+      T x = s[c];
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) red[warp][c] = x;
+    }
+    __syncthreads();
+    if (tid < nc) {
+      T x = T(0);
+      for (int w = 0; w < RT / 32; ++w) x += red[w][tid];
+      tot[tid] = tk * x;
+    }
+    __syncthreads();
+    for (int i = tid; i < n1; i += RT) {
+      const T vi = i == 0 ? T(1) : vrow[i];
+      for (int c = 0; c < nc; ++c) Ys[(size_t)c * m + k + 1 + i] -= tot[c] * vi;
+    }
+    __syncthreads();
+  }
+  if (t.fwd) {
+    for (int64_t q = tid; q < (int64_t)nc * m; q += RT) t.cols[(size_t)t.j0 * m + q] = Ys[q];
+  } else {
+    for (int64_t q = tid; q < (int64_t)m * nc; q += RT) {
+      const int i = (int)(q / nc), c = (int)(q % nc);
+      t.U[(int64_t)i * m + k1 + t.j0 + c] = Ys[(size_t)c * m + i];
+    }
+  }
+}
+
 }  // namespace
 
 // bytes of the per-node vectors of k_trunc_big (d, e, pw in FP64; six m-vectors
 // and 34 reduction slots in T), 16-byte aligned
 template <typename T>
 size_t trunc_big_vec_bytes(int m) {
-  return 3 * sizeof(double) * (size_t)m + 6 * sizeof(T) * (size_t)((m + 1) & ~1) + 34 * sizeof(T) + 16;
+  return big_vec_bytes<T>(m);
 }
 
 template <typename T>
@@ -759,7 +1032,7 @@ size_t trunc_big_work_elems(int m) {
   // A, Y, LU (6 m^2 T) + LS (164 m T) + flags (m^2 bytes) + the vectors (when
   // they do not fit in shared memory); Y also holds 2 m doubles of scratch
   const size_t bytes = sizeof(T) * (6 * (size_t)m * m + 164 * (size_t)m) + (size_t)m * m + 16 +
-                       trunc_big_vec_bytes<T>(m) + 64;
+                       trunc_big_vec_bytes<T>(m) + 16 + 64 + 64;
   return (bytes + sizeof(T) - 1) / sizeof(T);
 }
 
@@ -778,7 +1051,7 @@ void launch_trunc_big_nt(const TruncTask<T> *d_tasks, int ntasks, int *d_k, doub
   while (cap < max_m && (size_t)(cap + 1) * (cap + 1) * sizeof(T) + fixed <= budget) ++cap;
   const size_t sm = fixed + (size_t)cap * cap * sizeof(T);
   check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc_big<T, NT>>(), "k_trunc_big");
-  k_trunc_big<T, NT><<<ntasks, NT, sm, st>>>(d_tasks, d_k, eps, variant, cap, vec_smem);
+  k_trunc_big<T, NT><<<ntasks, NT, sm, st>>>(d_tasks, d_k, eps, variant, cap, vec_smem, TB_FULL);
   count_launch();
   HS_CUDA(cudaGetLastError());
 }
@@ -792,6 +1065,60 @@ void launch_trunc_big(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double 
     launch_trunc_big_nt<T, 1024>(d_tasks, ntasks, d_k, eps, variant, max_m, st);
 }
 
+template <typename T>
+void launch_trunc_big_mode(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps, int variant, int max_m,
+                           int mode, cudaStream_t st) {
+  if (ntasks == 0) return;
+  // per-node vectors in global memory (the step kernels write d, e, tau there);
+  // the whole budget is the tile
+  const size_t budget = 200 * 1024;
+  int cap = 0;
+  while (cap < max_m && (size_t)(cap + 1) * (cap + 1) * sizeof(T) + 32 <= budget) ++cap;
+  const size_t sm = 32 + (size_t)cap * cap * sizeof(T);
+  check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc_big<T, 1024>>(), "k_trunc_big");
+  k_trunc_big<T, 1024><<<ntasks, 1024, sm, st>>>(d_tasks, d_k, eps, variant, cap, 0, mode);
+  count_launch();
+  HS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void launch_tri_step(const GridTri<T> *d_tasks, int ntasks, int total_blocks, int k, int phase, cudaStream_t st) {
+  if (ntasks == 0 || total_blocks == 0) return;
+  if (phase == 0)
+    k_tri_update<T><<<total_blocks, kTriRows * 32, 0, st>>>(d_tasks, ntasks, k);
+  else
+    k_tri_symv<T><<<total_blocks, kTriRows * 32, 0, st>>>(d_tasks, ntasks, k);
+  count_launch();
+  HS_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+int refl_batch(int m) {
+  const size_t budget = 200 * 1024;
+  const int nb = (int)(budget / (sizeof(T) * (size_t)std::max(m, 1)));
+  return std::max(1, std::min(nb, RNB));
+}
+
+template <typename T>
+void launch_refl(const ReflTask<T> *d_tasks, int ntasks, int nb, int m_max, cudaStream_t st) {
+  if (ntasks == 0) return;
+  const size_t sm = sizeof(T) * (size_t)nb * m_max;
+  check_dynamic_smem(sm, allow_max_dynamic_smem<&k_refl<T>>(), "k_refl");
+  k_refl<T><<<ntasks, RT, sm, st>>>(d_tasks, nb);
+  count_launch();
+  HS_CUDA(cudaGetLastError());
+}
+
+template void launch_trunc_big_mode<double>(const TruncTask<double> *, int, int *, double, int, int, int,
+                                            cudaStream_t);
+template void launch_trunc_big_mode<float>(const TruncTask<float> *, int, int *, double, int, int, int,
+                                           cudaStream_t);
+template void launch_tri_step<double>(const GridTri<double> *, int, int, int, int, cudaStream_t);
+template void launch_tri_step<float>(const GridTri<float> *, int, int, int, int, cudaStream_t);
+template int refl_batch<double>(int);
+template int refl_batch<float>(int);
+template void launch_refl<double>(const ReflTask<double> *, int, int, int, cudaStream_t);
+template void launch_refl<float>(const ReflTask<float> *, int, int, int, cudaStream_t);
 template size_t trunc_big_work_elems<double>(int);
 template size_t trunc_big_work_elems<float>(int);
 template void launch_trunc_big<double>(const TruncTask<double> *, int, int *, double, int, int, cudaStream_t);

@@ -271,3 +271,43 @@ def test_large_super_nodes_match_oracle(name, maker):
     assert rel(z32, Z) <= 1e-3
     x, it, rr, _ = G32.pcg(torch.as_tensor(B[:, 0].copy(), device="cuda"), rtol=1e-10, maxit=200)
     assert rr[0] <= 1e-10
+
+
+@pytest.mark.parametrize("name,maker", TRIDIAG_CASES, ids=[c[0] for c in TRIDIAG_CASES])
+@pytest.mark.parametrize("variant", [H.LORASP, H.GC_CONSTANT])
+def test_multi_cta_truncation_path_matches_oracle(name, maker, variant):
+    """Every super node of 16 or more unknowns through the multi-CTA path
+    (tridiagonal steps spread over the GPU, reflector products by column
+    batches): ranks and apply match the oracle."""
+    import os
+    import subprocess
+    import sys
+
+    need_gpu()
+    here = os.path.dirname(os.path.abspath(__file__))
+    code = f"""
+import sys, numpy as np, torch
+sys.path.insert(0, {os.path.dirname(here)!r})
+sys.path.insert(0, {here!r})
+from gpu_util import gpu_factor, oracle_factor, rel
+from oracle import hsolver as H
+from paper_1611_03189_gb300 import problems as P
+import test_gpu_parity as T
+pb = [c for c in T.CASES if c[0] == {name!r}][0][1]()
+for eps in (1e-1, 1e-2):
+    F = oracle_factor(pb, eps, {variant})
+    G = gpu_factor(pb, eps, {variant})
+    assert T._ranks_match(F, G) == [], T._ranks_match(F, G)[:5]
+    B = P.rhs(pb.n, 7, nrhs=2)
+    Z = H.apply(F, B)
+    zg = G.apply(torch.as_tensor(B.T.copy(), device='cuda')).cpu().numpy().T
+    e = rel(zg, Z)
+    assert e <= 1e-10, e
+    G32 = gpu_factor(pb, eps, {variant}, prec=1)
+    e32 = rel(G32.apply(torch.as_tensor(B.T.copy(), device='cuda')).cpu().numpy().T, Z)
+    assert e32 <= 1e-3, e32
+print('ok')
+"""
+    env = dict(os.environ, HS_EIG_SMALL_MAX="8", HS_GRID_TRIDIAG_MIN="16")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-3000:]
