@@ -78,7 +78,9 @@ struct BlockRef {
 
 // Pinned host staging for descriptor uploads, two buffers used in alternate
 // waves: a wave's host->device copies have completed by the next wave's
-// synchronisation, so a buffer is rewritten only two waves later.
+// synchronisation, so a buffer is rewritten only two waves later.  Callers
+// flip (next_wave) once per synchronised step and never twice between two
+// synchronisations.
 struct Staging {
   char *buf[2] = {nullptr, nullptr};
   size_t cap[2] = {0, 0};
@@ -1207,8 +1209,10 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
     for (auto &r : runs)
       if (li < r->levels() && r->ok()) part.push_back(r.get());
     {
+      // the merge's descriptors go into the staging buffer in use: flipping
+      // to the other one here would make the next wave step flip back to a
+      // buffer whose copies may still be pending (no synchronisation between)
       ex.scr.reset();
-      ex.sg.next_wave();
       SumBatch<T> sb;
       for (Run<T> *r : part) {
         r->handle().scratch->reset();
@@ -1223,6 +1227,8 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       for (Run<T> *r : part)
         if (w < r->waves(li) && r->ok()) wp.push_back(r);
       if (wp.empty()) continue;
+      // one flip of the staging buffers per wave step: the other buffer's
+      // copies were enqueued before the previous step's synchronisation
       ex.scr.reset();
       ex.sg.next_wave();
       for (Run<T> *r : wp) r->handle().scratch->reset();
@@ -1306,7 +1312,8 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
     for (Run<T> *r : part)
       if (r->ok()) r->level_end(li);
   }
-  // the roots
+  // the roots (one flip: the last wave step synchronised after the other
+  // buffer's copies)
   ex.scr.reset();
   ex.sg.next_wave();
   {
