@@ -38,6 +38,9 @@ design notes):
      A red node exists iff its super node had a well-separated block.
   R6 the top of the tree: the last super node (level 1) is factored densely.
   R7 Algorithm 1 writes "compress A_sn, A_ns"; the compressed block is A_sw.
+  R11 adaptive tolerance (Sec. 7): the paper's level l runs from the root to
+     l_max at the leaves; here the super nodes of level l (l = L for the pairs of
+     leaves, down to 2) take eps_level[l], so l_max = L.
 
 Node keys inside a level: super node i -> i, red node made from super node i ->
 nsup + i.  Blocks are stored in both orientations, kept consistent.
@@ -221,13 +224,30 @@ def canonical_waves(supers, has_block):
 # factorization (Algorithm 1)
 # ---------------------------------------------------------------------------
 
+def eps_schedule_gc(eps: float, L: int) -> list:
+    """Adaptive tolerance of the GC variant (Sec. 7, Table 3): eps_l =
+    eps 2^((l - l_max)/3), constant eps at the leaf level l_max = L and smaller
+    towards the root.  Entry l is the tolerance of the super nodes of level l
+    (R11); entries 0 and 1 are not used."""
+    return [eps * 2.0 ** ((l - L) / 3.0) for l in range(L + 1)]
+
+
+def eps_schedule_lorasp(eps: float, L: int, h: float) -> list:
+    """Adaptive tolerance of LoRaSp in Sec. 7 (the HChols-like choice with one
+    factor h dropped): eps_l = eps h 2^((l_max - l)/3), small at the leaves and
+    growing towards the root; h is the grid spacing."""
+    return [eps * h * 2.0 ** ((L - l) / 3.0) for l in range(L + 1)]
+
+
 def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None,
-           order="waves", keep_U=False) -> Factor:
+           order="waves", keep_U=False, eps_level=None) -> Factor:
     """Hierarchical factorization.
 
     n, rowptr, col, val: CSR of the SPD matrix A in original ordering.
     perm, leaf_ptr: clustering; perm[p] = original index of unknown p.
     eps: truncation tolerance (R2).  variant: LORASP, GC_CONSTANT or GC_USER.
+    eps_level: optional per-level tolerances (Sec. 7 adaptive choice): entry l
+        (0..L) is used for the super nodes of level l instead of eps.
     phi: for GC_USER, the vector to preserve (original ordering).
     order: "waves" (R4), "waves-reversed" (same waves, each eliminated in
         descending order) or "sequential" (ascending super index, one at a time).
@@ -252,8 +272,11 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
     red_phi = {i: phi_perm[leaf_ptr[i]:leaf_ptr[i + 1]].copy() for i in range(nleaf)}
     levels = []
 
+    if eps_level is not None and len(eps_level) < L + 1:
+        raise ValueError("eps_level needs L + 1 entries (one per level)")
     for lev in range(L, 1, -1):
         nsup = 2 ** (lev - 1)
+        eps_l = float(eps_level[lev]) if eps_level is not None else eps
         # leaf sets of the super nodes: union of the leaf sets of the red nodes that
         # exist (a red node inherits the leaf set of its super node, Sec. 3.2)
         owner = {}
@@ -321,7 +344,7 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
             # within a wave the eliminations are independent (R4); "waves-reversed"
             # eliminates each wave in descending order to test exactly that
             for s in (reversed(wave) if order == "waves-reversed" else wave):
-                rec = _eliminate(s, nsup, blocks, nbr_of, size, vphi, adjacent, eps,
+                rec = _eliminate(s, nsup, blocks, nbr_of, size, vphi, adjacent, eps_l,
                                  variant, use_phi, widx, keep_U)
                 records.append(rec)
                 if rec.wsep:

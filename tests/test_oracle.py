@@ -347,3 +347,76 @@ def test_not_spd_is_genuine():
     F0 = _factor(pb, 0.1, H.LORASP)
     Z0 = H.apply(F0, np.eye(pb.n))
     assert np.linalg.eigvalsh(0.5 * (Z0 + Z0.T))[0] > 0
+
+
+# ---------------------------------------------------------------------------
+# adaptive per-level tolerance (Sec. 7, Table 3)
+# ---------------------------------------------------------------------------
+
+def _ranks(F):
+    return {(lv.level, r.key): (r.k if r.wsep else -1) for lv in F.levels for r in lv.supers}
+
+
+def test_eps_level_constant_equals_scalar_eps():
+    pb = P.diffusion2d(32, 1.0, 0, leaf_size=8)
+    L = int(np.log2(len(pb.leaf_ptr) - 1))
+    Fa = _factor(pb, 1e-2, H.GC_CONSTANT)
+    Fb = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, 0.5, H.GC_CONSTANT,
+                  eps_level=[1e-2] * (L + 1))
+    assert _ranks(Fa) == _ranks(Fb)
+    b = P.rhs(pb.n, 1)
+    assert np.array_equal(H.apply(Fa, b), H.apply(Fb, b))
+
+
+def test_eps_level_zero_everywhere_is_exact():
+    pb = P.poisson2d(16, leaf_size=4)
+    L = int(np.log2(len(pb.leaf_ptr) - 1))
+    F = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, 0.3, H.GC_CONSTANT,
+                 eps_level=[0.0] * (L + 1))
+    A = pb.to_scipy().toarray()
+    b = P.rhs(pb.n, 2)
+    x = H.apply(F, b)
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) <= 1e-11 * np.linalg.norm(x)
+
+
+def test_eps_level_index_is_the_level():
+    """The leaf-most level's truncation sees only the matrix, so its ranks must
+    equal those of a scalar-eps factorization with that level's tolerance; the
+    next level's ranks then follow the two-level schedule.  A shifted or
+    reversed index would use the wrong tolerance at level L."""
+    pb = P.diffusion2d(32, 1.0, 3, leaf_size=8)
+    L = int(np.log2(len(pb.leaf_ptr) - 1))
+    sched = [0.0, 0.0] + [0.3 if l == L else 1e-3 for l in range(2, L + 1)]
+    F = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, 0.5, H.GC_CONSTANT, eps_level=sched)
+    Fa = _factor(pb, 0.3, H.GC_CONSTANT)
+    Fb = _factor(pb, 1e-3, H.GC_CONSTANT)
+    top = {key: k for key, k in _ranks(F).items() if key[0] == L}
+    assert top == {key: k for key, k in _ranks(Fa).items() if key[0] == L}
+    assert top != {key: k for key, k in _ranks(Fb).items() if key[0] == L}
+
+
+def test_adaptive_gc_schedule_matches_the_paper_definition():
+    s = H.eps_schedule_gc(0.3, 9)
+    assert s[9] == 0.3                                # constant eps at the leaf level
+    assert abs(s[6] - 0.15) < 1e-15                   # halves every three levels
+    assert all(s[l] < s[l + 1] for l in range(9))     # smaller towards the root
+    t = H.eps_schedule_lorasp(0.3, 9, 1.0 / 64)
+    assert abs(t[9] - 0.3 / 64) < 1e-15 and all(t[l] > t[l + 1] for l in range(9))
+
+
+def test_adaptive_gc_keeps_iterations_nearly_constant():
+    """Sec. 7: with the adaptive tolerance the GC iteration count stays roughly
+    constant as the grid is refined, where a constant tolerance lets it grow
+    (Table 3 trend; 2D Poisson, eps = 0.1 at the leaves)."""
+    const, adapt = [], []
+    for side in (16, 32, 64):
+        pb = P.poisson2d(side, leaf_size=8)
+        L = int(np.log2(len(pb.leaf_ptr) - 1))
+        b = P.rhs(pb.n, 0)
+        for sched, out in ((None, const), (H.eps_schedule_gc(0.1, L), adapt)):
+            F = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, 0.1, H.GC_CONSTANT,
+                         eps_level=sched)
+            x, it, rr = H.pcg(F, pb.rowptr, pb.col, pb.val, b, rtol=1e-10, maxit=500)
+            out.append(it)
+    assert max(adapt) - min(adapt) <= 2, adapt
+    assert const[-1] - const[0] >= 4, const
