@@ -86,12 +86,20 @@ typedef struct {
  *   eigen-solve cannot resolve singular values that small.
  * variant: HS_LORASP, HS_GC_CONSTANT or HS_GC_USER.
  * phi: HOST pointer, n doubles in the ORIGINAL ordering, used by HS_GC_USER.
- * factor_prec: HS_PREC_F64 or HS_PREC_F32. */
+ * factor_prec: HS_PREC_F64 or HS_PREC_F32.
+ * eps_level: NULL, or a HOST array of tolerances per level for the adaptive
+ *   choice of Sec. 7 (Table 3).  Entry j replaces eps for the super nodes j
+ *   levels above the leaves (j = 0: the pairs of leaves); a problem with 2^L
+ *   leaves reads entries 0 .. L-2, and n_eps_level must cover them.  Each
+ *   entry obeys the rules of eps.  The same list serves problems of different
+ *   depth in hs_factor_create_batch. */
 typedef struct {
   double eps;
   int32_t variant;
   int32_t factor_prec;
   const double *phi;
+  const double *eps_level;
+  int32_t n_eps_level;
 } hs_opts;
 
 /* Sizes and counters of a factorization (all host values). */

@@ -40,7 +40,9 @@ design notes):
   R7 Algorithm 1 writes "compress A_sn, A_ns"; the compressed block is A_sw.
   R11 adaptive tolerance (Sec. 7): the paper's level l runs from the root to
      l_max at the leaves; here the super nodes of level l (l = L for the pairs of
-     leaves, down to 2) take eps_level[l], so l_max = L.
+     leaves, down to 2) play level l with l_max = L, and the tolerance list is
+     indexed by j = L - l (levels above the leaves), so one list serves problems
+     of different depth.
 
 Node keys inside a level: super node i -> i, red node made from super node i ->
 nsup + i.  Blocks are stored in both orientations, kept consistent.
@@ -226,17 +228,18 @@ def canonical_waves(supers, has_block):
 
 def eps_schedule_gc(eps: float, L: int) -> list:
     """Adaptive tolerance of the GC variant (Sec. 7, Table 3): eps_l =
-    eps 2^((l - l_max)/3), constant eps at the leaf level l_max = L and smaller
-    towards the root.  Entry l is the tolerance of the super nodes of level l
-    (R11); entries 0 and 1 are not used."""
-    return [eps * 2.0 ** ((l - L) / 3.0) for l in range(L + 1)]
+    eps 2^((l - l_max)/3), constant eps at the leaf level and smaller towards
+    the root.  Entry j is the tolerance of the super nodes j levels above the
+    leaves (level L - j, R11); L - 1 entries cover levels L..2."""
+    return [eps * 2.0 ** (-j / 3.0) for j in range(L - 1)]
 
 
 def eps_schedule_lorasp(eps: float, L: int, h: float) -> list:
     """Adaptive tolerance of LoRaSp in Sec. 7 (the HChols-like choice with one
     factor h dropped): eps_l = eps h 2^((l_max - l)/3), small at the leaves and
-    growing towards the root; h is the grid spacing."""
-    return [eps * h * 2.0 ** ((L - l) / 3.0) for l in range(L + 1)]
+    growing towards the root; h is the grid spacing.  Indexed like
+    eps_schedule_gc."""
+    return [eps * h * 2.0 ** (j / 3.0) for j in range(L - 1)]
 
 
 def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None,
@@ -246,8 +249,9 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
     n, rowptr, col, val: CSR of the SPD matrix A in original ordering.
     perm, leaf_ptr: clustering; perm[p] = original index of unknown p.
     eps: truncation tolerance (R2).  variant: LORASP, GC_CONSTANT or GC_USER.
-    eps_level: optional per-level tolerances (Sec. 7 adaptive choice): entry l
-        (0..L) is used for the super nodes of level l instead of eps.
+    eps_level: optional per-level tolerances (Sec. 7 adaptive choice): entry j
+        is used instead of eps for the super nodes j levels above the leaves
+        (level L - j); it needs L - 1 entries.
     phi: for GC_USER, the vector to preserve (original ordering).
     order: "waves" (R4), "waves-reversed" (same waves, each eliminated in
         descending order) or "sequential" (ascending super index, one at a time).
@@ -272,11 +276,11 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
     red_phi = {i: phi_perm[leaf_ptr[i]:leaf_ptr[i + 1]].copy() for i in range(nleaf)}
     levels = []
 
-    if eps_level is not None and len(eps_level) < L + 1:
-        raise ValueError("eps_level needs L + 1 entries (one per level)")
+    if eps_level is not None and len(eps_level) < L - 1:
+        raise ValueError("eps_level needs L - 1 entries (levels L..2)")
     for lev in range(L, 1, -1):
         nsup = 2 ** (lev - 1)
-        eps_l = float(eps_level[lev]) if eps_level is not None else eps
+        eps_l = float(eps_level[L - lev]) if eps_level is not None else eps
         # leaf sets of the super nodes: union of the leaf sets of the red nodes that
         # exist (a red node inherits the leaf set of its super node, Sec. 3.2)
         owner = {}

@@ -61,7 +61,7 @@ class HsClustering(C.Structure):
 
 class HsOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("variant", C.c_int32), ("factor_prec", C.c_int32),
-                ("phi", C.c_void_p)]
+                ("phi", C.c_void_p), ("eps_level", C.c_void_p), ("n_eps_level", C.c_int32)]
 
 
 class HsInfo(C.Structure):
@@ -191,7 +191,7 @@ class Factor:
     """
 
     def __init__(self, rowptr, col, val, perm, leaf_ptr, eps, variant=HS_GC_CONSTANT,
-                 prec=HS_PREC_F64, phi=None, stream=None):
+                 prec=HS_PREC_F64, phi=None, stream=None, eps_level=None):
         import torch
 
         assert rowptr.is_cuda and col.is_cuda and val.is_cuda
@@ -202,7 +202,9 @@ class Factor:
         self._phi = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
         A = HsCsr(self.n, int(col.numel()), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
         cl = HsClustering(_ptr(self._perm), _ptr(self._lp), len(self._lp) - 1)
-        o = HsOpts(float(eps), int(variant), int(prec), None if self._phi is None else _ptr(self._phi))
+        self._epsl = None if eps_level is None else np.ascontiguousarray(eps_level, dtype=np.float64)
+        o = HsOpts(float(eps), int(variant), int(prec), None if self._phi is None else _ptr(self._phi),
+                   None if self._epsl is None else _ptr(self._epsl), 0 if self._epsl is None else len(self._epsl))
         h = C.c_void_p()
         self._h = None
         check(lib().hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), _stream_ptr(stream), C.byref(h)))
@@ -266,7 +268,8 @@ class Factor:
             pass
 
 
-def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=None, stream=None):
+def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=None, stream=None,
+                 eps_level=None):
     """hs_factor_create_batch over `problems`: a list of (rowptr, col, val,
     perm, leaf_ptr) with rowptr/col int32 and val float64 CUDA tensors and
     perm/leaf_ptr host arrays.  Returns (factors, status): one Factor per
@@ -290,7 +293,10 @@ def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=N
         ph = [np.ascontiguousarray(x, dtype=np.float64) for x in phis]
         keep += ph
         phi_arr = (C.c_void_p * k)(*[_ptr(x) for x in ph])
-    o = HsOpts(float(eps), int(variant), int(prec), None)
+    epsl = None if eps_level is None else np.ascontiguousarray(eps_level, dtype=np.float64)
+    keep.append(epsl)
+    o = HsOpts(float(eps), int(variant), int(prec), None, None if epsl is None else _ptr(epsl),
+               0 if epsl is None else len(epsl))
     out = (C.c_void_p * k)()
     status = np.zeros(k, dtype=np.int32)
     code = lib().hs_factor_create_batch(k, A, cl, C.byref(o), phi_arr, _stream_ptr(stream), out, _ptr(status))

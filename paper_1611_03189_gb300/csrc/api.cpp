@@ -2,6 +2,7 @@
 // C++ exception) and turns it into a status code plus a thread-local message.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -161,6 +162,7 @@ void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, con
   h.prec = o->factor_prec;
   h.variant = o->variant;
   h.eps = o->eps;
+  h.eps_level.clear();
   // pattern to the host for the planner
   std::vector<int32_t> rp(A->n + 1), ci(A->nnz);
   HS_CUDA(cudaMemcpyAsync(rp.data(), A->rowptr, sizeof(int32_t) * (A->n + 1), cudaMemcpyDeviceToHost, st));
@@ -168,6 +170,13 @@ void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, con
   HS_CUDA(cudaStreamSynchronize(st));
   if (rp[A->n] != A->nnz) fail(HS_ERR_INVALID, "rowptr[n] != nnz");
   build_plan(A->n, rp.data(), ci.data(), cl->perm, cl->leaf_ptr, cl->nleaf, h.plan);
+  if (o->eps_level) {
+    const int need = std::max(h.plan.L - 1, 0);
+    if (o->n_eps_level < need)
+      fail(HS_ERR_INVALID, "eps_level has " + std::to_string(o->n_eps_level) + " entries; this clustering needs " +
+                               std::to_string(need));
+    h.eps_level.assign(o->eps_level, o->eps_level + need);
+  }
   // permuted CSR on the device; values gathered there
   h.d_rowptr = upload_vec(h.plan.prow, st);
   h.d_col = upload_vec(h.plan.pcol, st);
@@ -183,6 +192,14 @@ void check_opts(const hs_opts *o) {
   if (o->eps > 0.0 && o->eps < 1e-6) fail(HS_ERR_INVALID, "0 < eps < 1e-6 is not supported");
   if (o->variant < HS_LORASP || o->variant > HS_GC_USER) fail(HS_ERR_INVALID, "unknown variant");
   if (o->factor_prec != HS_PREC_F64 && o->factor_prec != HS_PREC_F32) fail(HS_ERR_INVALID, "unknown factor_prec");
+  if (o->eps_level) {
+    if (o->n_eps_level < 0) fail(HS_ERR_INVALID, "n_eps_level < 0");
+    for (int j = 0; j < o->n_eps_level; ++j) {
+      const double e = o->eps_level[j];
+      if (!(e >= 0.0) || !std::isfinite(e)) fail(HS_ERR_INVALID, "eps_level entries must be finite and >= 0");
+      if (e > 0.0 && e < 1e-6) fail(HS_ERR_INVALID, "0 < eps_level[j] < 1e-6 is not supported");
+    }
+  }
 }
 
 }  // namespace

@@ -442,6 +442,11 @@ class Run {
   void merge(int nred, int key_base, SumBatch<T> &sb);
   void end_level(const PlanLevel &lv, int li);
   Tag tag(int kind, int level, int s) const { return Tag{kind, level, s, prob_}; }
+  // tolerance of the super nodes of a level (adaptive list indexed from the leaves)
+  double level_eps(int level) const {
+    const int j = P_.L - level;
+    return (j >= 0 && j < (int)h_.eps_level.size()) ? h_.eps_level[j] : h_.eps;
+  }
 
   FactorHandle &h_;
   const Plan &P_;
@@ -707,6 +712,7 @@ void Run<T>::wave_a(int li, int widx, WaveBatches<T> &B) {
       tt.phi = phi_[s];
       tt.U = x.U;
       tt.work = nullptr;
+      tt.eps = level_eps(lv.level);
       tt.m = m;
       if (m <= eig_small_max<T>()) {
         B.trunc.push_back(tt);
@@ -1262,7 +1268,7 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
         std::vector<TruncTask<T>> cls[3];
         int cmax[3] = {0, 0, 0};
         for (const TruncTask<T> &t : B.trunc_big) {
-          const int c = (eps > 0.0 && t.m >= grid_tridiag_min()) ? 2 : t.m <= kTruncBigMidMax ? 0 : 1;
+          const int c = (t.eps > 0.0 && t.m >= grid_tridiag_min()) ? 2 : t.m <= kTruncBigMidMax ? 0 : 1;
           cls[c].push_back(t);
           cmax[c] = std::max(cmax[c], t.m);
         }

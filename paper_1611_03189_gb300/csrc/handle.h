@@ -97,6 +97,7 @@ struct FactorHandle {
   int prec = HS_PREC_F64;
   int variant = HS_GC_CONSTANT;
   double eps = 0.0;
+  std::vector<double> eps_level;       // per level above the leaves (empty: eps everywhere)
   cudaStream_t stream = nullptr;
   int device = 0;
   bool valid = false;                  // holds a usable factorization

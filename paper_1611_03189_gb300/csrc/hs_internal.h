@@ -134,6 +134,7 @@ struct TruncTask {
   const T *phi;
   T *U;
   T *work;
+  double eps;  // truncation tolerance of this node's level
   int m;
   int k_idx;  // index into the rank array
 };

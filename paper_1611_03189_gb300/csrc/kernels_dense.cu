@@ -451,13 +451,13 @@ __device__ int select_columns(const T *A, const T *V, int m, double thr, T *U, i
 
 template <typename T, bool SMEM>
 __global__ void __launch_bounds__(TRUNC_THREADS) k_trunc(const TruncTask<T> *__restrict__ tasks,
-                                                        int *__restrict__ kout, double eps,
-                                                        int variant) {
+                                                        int *__restrict__ kout, int variant) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
   __shared__ int flag;
   __shared__ double u1n[2];
   const TruncTask<T> t = tasks[blockIdx.x];
+  const double eps = t.eps;
   const int m = t.m;
   const int mp = m + (m & 1);
   const int np = mp / 2 > 0 ? mp / 2 : 1;
@@ -686,11 +686,11 @@ void launch_trunc(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps,
   if (max_m <= trunc_smem_cap<T>()) {
     const size_t sm = 2 * sizeof(T) * (size_t)max_m * max_m + trunc_small_arrays<T>(max_m);
     check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc<T, true>>(), "k_trunc");
-    k_trunc<T, true><<<ntasks, TRUNC_THREADS, sm, st>>>(d_tasks, d_k, eps, variant);
+    k_trunc<T, true><<<ntasks, TRUNC_THREADS, sm, st>>>(d_tasks, d_k, variant);
   } else {
     const size_t sm = trunc_small_arrays<T>(max_m);
     check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc<T, false>>(), "k_trunc");
-    k_trunc<T, false><<<ntasks, TRUNC_THREADS, sm, st>>>(d_tasks, d_k, eps, variant);
+    k_trunc<T, false><<<ntasks, TRUNC_THREADS, sm, st>>>(d_tasks, d_k, variant);
   }
   count_launch();
   HS_CUDA(cudaGetLastError());

@@ -437,11 +437,12 @@ enum { TB_FULL = 0, TB_PREP = 1, TB_POST = 2 };
 
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict__ tasks, int *__restrict__ kout,
-                                                 double eps, int variant, int tile_cap, int vec_smem, int mode) {
+                                                 int variant, int tile_cap, int vec_smem, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
   __shared__ int s_k2;
   const TruncTask<T> t = tasks[blockIdx.x];
+  const double eps = t.eps;
   const int m = t.m;
   const int tid = threadIdx.x, nt = blockDim.x;
   // global work, all T: A (m^2), Y (m^2), LU (4 m^2), LS (164 m: Z = Q^T [U1, X] in
@@ -1051,7 +1052,7 @@ void launch_trunc_big_nt(const TruncTask<T> *d_tasks, int ntasks, int *d_k, doub
   while (cap < max_m && (size_t)(cap + 1) * (cap + 1) * sizeof(T) + fixed <= budget) ++cap;
   const size_t sm = fixed + (size_t)cap * cap * sizeof(T);
   check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc_big<T, NT>>(), "k_trunc_big");
-  k_trunc_big<T, NT><<<ntasks, NT, sm, st>>>(d_tasks, d_k, eps, variant, cap, vec_smem, TB_FULL);
+  k_trunc_big<T, NT><<<ntasks, NT, sm, st>>>(d_tasks, d_k, variant, cap, vec_smem, TB_FULL);
   count_launch();
   HS_CUDA(cudaGetLastError());
 }
@@ -1076,7 +1077,7 @@ void launch_trunc_big_mode(const TruncTask<T> *d_tasks, int ntasks, int *d_k, do
   while (cap < max_m && (size_t)(cap + 1) * (cap + 1) * sizeof(T) + 32 <= budget) ++cap;
   const size_t sm = 32 + (size_t)cap * cap * sizeof(T);
   check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc_big<T, 1024>>(), "k_trunc_big");
-  k_trunc_big<T, 1024><<<ntasks, 1024, sm, st>>>(d_tasks, d_k, eps, variant, cap, 0, mode);
+  k_trunc_big<T, 1024><<<ntasks, 1024, sm, st>>>(d_tasks, d_k, variant, cap, 0, mode);
   count_launch();
   HS_CUDA(cudaGetLastError());
 }

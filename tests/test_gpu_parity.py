@@ -14,7 +14,7 @@ from oracle import hsolver as H
 from paper_1611_03189_gb300 import _lib
 from paper_1611_03189_gb300 import problems as P
 
-from gpu_util import gpu_factor, need_gpu, oracle_factor, rel
+from gpu_util import gpu_factor, need_gpu, oracle_factor, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -311,3 +311,25 @@ print('ok')
     env = dict(os.environ, HS_EIG_SMALL_MAX="8", HS_GRID_TRIDIAG_MIN="16")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-3000:]
+
+
+@pytest.mark.parametrize("name,maker", [CASES[1], CASES[3]], ids=[CASES[1][0], CASES[3][0]])
+@pytest.mark.parametrize("variant", [H.LORASP, H.GC_CONSTANT])
+def test_adaptive_eps_level_matches_oracle(name, maker, variant):
+    """Per-level tolerances (Sec. 7 adaptive choice) through hs_opts.eps_level:
+    ranks and apply equal the oracle's with the same schedule."""
+    torch = need_gpu()
+    pb = maker()
+    L = int(np.log2(len(pb.leaf_ptr) - 1))
+    if variant == H.GC_CONSTANT:
+        sched = H.eps_schedule_gc(0.1, L)
+    else:
+        sched = H.eps_schedule_lorasp(0.5, L, 1.0 / np.sqrt(pb.n))
+    F = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, 0.3, variant, eps_level=sched)
+    rp, ci, va = to_dev(pb)
+    G = _lib.Factor(rp, ci, va, pb.perm, pb.leaf_ptr, 0.3, variant, 0, eps_level=sched)
+    assert _ranks_match(F, G) == []
+    B = P.rhs(pb.n, 5, nrhs=2)
+    zg = G.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
+    assert rel(zg, H.apply(F, B)) <= 1e-10
+    G.close()

@@ -362,7 +362,7 @@ def test_eps_level_constant_equals_scalar_eps():
     L = int(np.log2(len(pb.leaf_ptr) - 1))
     Fa = _factor(pb, 1e-2, H.GC_CONSTANT)
     Fb = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, 0.5, H.GC_CONSTANT,
-                  eps_level=[1e-2] * (L + 1))
+                  eps_level=[1e-2] * (L - 1))
     assert _ranks(Fa) == _ranks(Fb)
     b = P.rhs(pb.n, 1)
     assert np.array_equal(H.apply(Fa, b), H.apply(Fb, b))
@@ -372,7 +372,7 @@ def test_eps_level_zero_everywhere_is_exact():
     pb = P.poisson2d(16, leaf_size=4)
     L = int(np.log2(len(pb.leaf_ptr) - 1))
     F = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, 0.3, H.GC_CONSTANT,
-                 eps_level=[0.0] * (L + 1))
+                 eps_level=[0.0] * (L - 1))
     A = pb.to_scipy().toarray()
     b = P.rhs(pb.n, 2)
     x = H.apply(F, b)
@@ -386,7 +386,7 @@ def test_eps_level_index_is_the_level():
     reversed index would use the wrong tolerance at level L."""
     pb = P.diffusion2d(32, 1.0, 3, leaf_size=8)
     L = int(np.log2(len(pb.leaf_ptr) - 1))
-    sched = [0.0, 0.0] + [0.3 if l == L else 1e-3 for l in range(2, L + 1)]
+    sched = [0.3] + [1e-3] * (L - 2)       # entry 0: the leaf-most level L
     F = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, 0.5, H.GC_CONSTANT, eps_level=sched)
     Fa = _factor(pb, 0.3, H.GC_CONSTANT)
     Fb = _factor(pb, 1e-3, H.GC_CONSTANT)
@@ -397,11 +397,11 @@ def test_eps_level_index_is_the_level():
 
 def test_adaptive_gc_schedule_matches_the_paper_definition():
     s = H.eps_schedule_gc(0.3, 9)
-    assert s[9] == 0.3                                # constant eps at the leaf level
-    assert abs(s[6] - 0.15) < 1e-15                   # halves every three levels
-    assert all(s[l] < s[l + 1] for l in range(9))     # smaller towards the root
+    assert len(s) == 8 and s[0] == 0.3                # levels 9..2; constant eps at the leaves
+    assert abs(s[3] - 0.15) < 1e-15                   # halves every three levels
+    assert all(s[j + 1] < s[j] for j in range(7))     # smaller towards the root
     t = H.eps_schedule_lorasp(0.3, 9, 1.0 / 64)
-    assert abs(t[9] - 0.3 / 64) < 1e-15 and all(t[l] > t[l + 1] for l in range(9))
+    assert abs(t[0] - 0.3 / 64) < 1e-15 and all(t[j + 1] > t[j] for j in range(7))
 
 
 def test_adaptive_gc_keeps_iterations_nearly_constant():
