@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 def _problems():
     # uneven sizes and depths: 2D sides 20..72 (levels 5..9) and one 3D grid
-    pbs = [P.diffusion2d(side, 2.0, seed, leaf_size=16) for seed, side in enumerate((20, 72, 33, 48, 64))]
+    pbs = [P.diffusion2d(side, 1.0, seed, leaf_size=16) for seed, side in enumerate((20, 72, 33, 48, 64))]
     pbs.append(P.poisson3d(12, leaf_size=64))
     return pbs
 
