@@ -470,6 +470,12 @@ def main():
     e3.record(stream)
     torch.cuda.synchronize()
     factor_ms = e2.elapsed_time(e3)
+    # one more refactor with the library's per-phase device timing (event pairs)
+    _lib.profile_phases(True)
+    G.refactor(vals[args.warmup])
+    torch.cuda.synchronize()
+    _lib.profile_phases(False)
+    phase_ms = G.info()["phase_ms"]
     e2.record(stream)
     _, it1, _, _ = G.pcg(bs[args.warmup], rtol=1e-10, maxit=1000)
     e3.record(stream)
@@ -625,6 +631,7 @@ def main():
             "clocks": clk,
             "factor_ms": factor_ms, "solve_ms": solve_ms, "pcg_iterations": int(it1.max()),
             "factor_host_ms": info_f["host_ms"], "factor_wait_ms": info_f["wait_ms"],
+            "factor_phase_ms": phase_ms,
             "iterations_timed": iters_seen[args.warmup:], "max_relres": max(rrs),
             "factor_info": {k: info[k] for k in ("levels", "waves", "super_nodes", "root_size", "max_rank",
                                                  "max_super", "factor_bytes", "device_bytes", "factor_flops")},

@@ -124,6 +124,12 @@ typedef struct {
                                 launch per thread-count class in each)            */
   double host_ms;            /* host wall time of the factorization call          */
   double wait_ms;            /* of which waiting for the device (rank reads)      */
+  double phase_ms[10];       /* with hs_profile_phases(1): device time of the
+                                factor's launch groups -- 0 merge, 1 gather of
+                                A_sN/A_sW, 2 Cholesky of A_ss, 3 Gram, 4 small
+                                truncation, 5 large truncation, 6 CholQR of the
+                                large-path U, 7 extension GEMMs and CholQR, 8
+                                Schur scatter, 9 root; otherwise zeros          */
 } hs_info;
 
 typedef struct hs_factor_s *hs_factor;
@@ -227,6 +233,12 @@ int hs_factor_ranks(hs_factor f, int32_t level, int32_t *ranks, int32_t cap, int
 
 /* hs_factor_destroy: release the handle and its device memory (NULL is OK). */
 int hs_factor_destroy(hs_factor f);
+
+/* hs_profile_phases: on != 0 makes later factorizations (all handles, all
+ * threads) time their launch groups with CUDA events into hs_info.phase_ms;
+ * 0 turns it off (the default).  A measurement aid; the paper has no
+ * counterpart.  Returns HS_OK. */
+int hs_profile_phases(int32_t on);
 
 /* hs_last_error: message of the last failing call on this thread. */
 const char *hs_last_error(void);

@@ -38,7 +38,7 @@ STATUS_NAMES = {
 # every symbol include/hs.h declares
 EXPORTS = [
     "hs_factor_create", "hs_factor_refactor", "hs_factor_create_batch", "hs_factor_refactor_batch",
-    "hs_launch_count", "hs_apply", "hs_apply_static", "hs_pcg", "hs_factor_info", "hs_factor_ranks",
+    "hs_launch_count", "hs_profile_phases", "hs_apply", "hs_apply_static", "hs_pcg", "hs_factor_info", "hs_factor_ranks",
     "hs_factor_destroy", "hs_last_error", "hs_plan_create", "hs_plan_level_waves",
     "hs_plan_super_lists", "hs_plan_destroy",
 ]
@@ -70,10 +70,15 @@ class HsInfo(C.Structure):
                 ("max_super", C.c_int32), ("device_bytes", C.c_int64), ("factor_bytes", C.c_int64),
                 ("factor_flops", C.c_double), ("eig_flops", C.c_double), ("factor_ms", C.c_double),
                 ("trunc_big_ms", C.c_double), ("trunc_big_flops", C.c_double), ("trunc_big_launches", C.c_int32),
-                ("host_ms", C.c_double), ("wait_ms", C.c_double)]
+                ("host_ms", C.c_double), ("wait_ms", C.c_double), ("phase_ms", C.c_double * 10)]
+
+    PHASES = ("merge", "gather", "chol_Ass", "gram", "trunc_small", "trunc_large", "cholqr_large",
+              "extension", "schur", "root")
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "phase_ms"}
+        d["phase_ms"] = dict(zip(self.PHASES, list(self.phase_ms)))
+        return d
 
 
 _lib = None
@@ -94,6 +99,7 @@ def lib():
                                              vp, vp, C.POINTER(vp), vp]
         L.hs_factor_refactor_batch.argtypes = [i32, C.POINTER(vp), vp, vp, vp]
         L.hs_launch_count.argtypes = []
+        L.hs_profile_phases.argtypes = [i32]
         L.hs_apply.argtypes = [vp, vp, vp, i32, i64, vp]
         L.hs_apply_static.argtypes = [vp, vp, vp, i32, i64, vp]
         L.hs_pcg.argtypes = [vp, vp, vp, i32, i64, dbl, i32, vp, vp, vp]
@@ -328,3 +334,8 @@ def refactor_batch(factors, vals, stream=None):
     if code not in (HS_OK, HS_ERR_NOT_SPD):
         check(code)
     return status
+
+
+def profile_phases(on: bool) -> None:
+    """hs_profile_phases: per-phase device times of later factorizations."""
+    check(lib().hs_profile_phases(1 if on else 0))

@@ -322,6 +322,11 @@ int hs_factor_refactor_batch(int32_t count, hs_factor *f, const double *const *v
 
 int64_t hs_launch_count(void) { return hs::g_launches.load(); }
 
+int hs_profile_phases(int32_t on) {
+  hs::set_phase_profiling(on != 0);
+  return HS_OK;
+}
+
 int hs_apply(hs_factor f, const double *r, double *z, int32_t nrhs, int64_t ld, void *stream) {
   return hs::guarded([&]() -> int {
     if (!f || !r || !z) fail(HS_ERR_INVALID, "null argument");

@@ -16,6 +16,7 @@
 // M_ss = A_ss^-1 - P_ss^T S P_ss = L^-T (I - Q Q^T) L^-1, and
 // A_ns M_ss A_sn' is the Schur term of ~~A_nn' (eq. eliminated).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
@@ -285,6 +286,9 @@ int eig_small_max() {
 // steps spread over the GPU, reflector products by batches of columns); below
 // it one CTA per node does everything.  HS_GRID_TRIDIAG_MIN (environment)
 // moves the limit, which lets small test problems exercise the path.
+std::atomic<int> g_phase_prof{0};
+bool phase_profiling() { return g_phase_prof.load() != 0; }
+
 inline int grid_tridiag_min() {
   static const int v = [] {
     const char *e = std::getenv("HS_GRID_TRIDIAG_MIN");
@@ -324,6 +328,33 @@ struct Exec {
   std::vector<std::string> prob_msg;
   // host time spent waiting for the device (sync_check), in ms
   double wait_ms = 0.0;
+  // optional device time per phase (hs_profile_phases): event pairs around
+  // each launch group, read after the final synchronisation
+  bool prof = false;
+  struct Span {
+    int phase;
+    cudaEvent_t e0, e1;
+  };
+  std::vector<Span> spans;
+  int open_phase = -1;
+  void begin(int phase) {
+    if (!prof) return;
+    Span sp{phase, nullptr, nullptr};
+    HS_CUDA(cudaEventCreate(&sp.e0));
+    HS_CUDA(cudaEventCreate(&sp.e1));
+    HS_CUDA(cudaEventRecord(sp.e0, st));
+    spans.push_back(sp);
+  }
+  void end() {
+    if (!prof || spans.empty()) return;
+    HS_CUDA(cudaEventRecord(spans.back().e1, st));
+  }
+  void phase_times(double *ms, int nphase) {
+    for (Span &sp : spans) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, sp.e0, sp.e1) == cudaSuccess && sp.phase < nphase) ms[sp.phase] += t;
+    }
+  }
   explicit Exec(cudaStream_t s) : st(s) {
     HS_CUDA(cudaEventCreate(&ev_big[0]));
     HS_CUDA(cudaEventCreate(&ev_big[1]));
@@ -331,6 +362,10 @@ struct Exec {
   ~Exec() {
     // copies from the pinned staging buffers may still be in flight after an error
     cudaStreamSynchronize(st);
+    for (Span &sp : spans) {
+      cudaEventDestroy(sp.e0);
+      cudaEventDestroy(sp.e1);
+    }
     cudaFreeHost(hbuf);
     cudaEventDestroy(ev_big[0]);
     cudaEventDestroy(ev_big[1]);
@@ -1224,7 +1259,9 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
         r->handle().scratch->reset();
         r->level_begin(li, sb);
       }
+      ex.begin(0);
       sb.launch(ex.scr, ex.sg, ex.st);
+      ex.end();
     }
     int nw = 0;
     for (Run<T> *r : part) nw = std::max(nw, r->waves(li));
@@ -1244,23 +1281,31 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       const size_t nchol = B.chol.tasks.size(), ntrunc = B.trunc.size(), nbig = B.trunc_big.size();
       for (size_t i = 0; i < ntrunc; ++i) B.trunc[i].k_idx = (int)i;
       for (size_t i = 0; i < nbig; ++i) B.trunc_big[i].k_idx = (int)(ntrunc + i);
+      ex.begin(1);
       B.gather.launch(ex.scr, ex.sg, ex.st);
+      ex.end();
       int *d_stat = (int *)ex.scr.alloc(sizeof(int) * (nchol + ntrunc + nbig + 1));
       int *d_k = d_stat + nchol;
       if (nchol) {
         Uploader u;
         const size_t o = u.add(B.chol.tasks);
         char *d = u.upload(ex.scr, ex.sg, ex.st);
+        ex.begin(2);
         launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)nchol, d_stat, B.chol.max_m, ex.st);
+        ex.end();
       }
+      ex.begin(3);
       B.gram.launch(ex.scr, ex.sg, ex.st);
+      ex.end();
       const double eps = wp[0]->handle().eps;
       const int variant = wp[0]->handle().variant;
       if (ntrunc) {
         Uploader u;
         const size_t o = u.add(B.trunc);
         char *d = u.upload(ex.scr, ex.sg, ex.st);
+        ex.begin(4);
         launch_trunc<T>((const TruncTask<T> *)(d + o), (int)ntrunc, d_k, eps, variant, B.max_trunc_m, ex.st);
+        ex.end();
       }
       if (nbig) {
         // one launch per class (k_idx keeps each rank's slot): 256 or 1024
@@ -1277,12 +1322,14 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
         const size_t o1 = u.add(cls[1]);
         const size_t o2 = u.add(cls[2]);
         char *d = u.upload(ex.scr, ex.sg, ex.st);
+        ex.begin(5);
         HS_CUDA(cudaEventRecord(ex.ev_big[0], ex.st));
         launch_trunc_big<T>((const TruncTask<T> *)(d + o0), (int)cls[0].size(), d_k, eps, variant, cmax[0], ex.st);
         launch_trunc_big<T>((const TruncTask<T> *)(d + o1), (int)cls[1].size(), d_k, eps, variant, cmax[1], ex.st);
         if (!cls[2].empty())
           trunc_grid<T>(ex, cls[2], (const TruncTask<T> *)(d + o2), d_k, eps, variant, cmax[2]);
         HS_CUDA(cudaEventRecord(ex.ev_big[1], ex.st));
+        ex.end();
       }
       // one read of the statuses and ranks
       const size_t nread = nchol + ntrunc + nbig;
@@ -1294,15 +1341,18 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       for (Run<T> *r : wp)
         if (r->ok()) r->wave_b(hb, nchol, ntrunc, big_ms, B);
       // U of the large path: CholQR2
+      ex.begin(6);
       B.o1.launch(ex.scr, ex.sg, ex.st);
       ex.chol_checked(B.oc1);
       B.o2.launch(ex.scr, ex.sg, ex.st);
       B.o3.launch(ex.scr, ex.sg, ex.st);
       ex.chol_checked(B.oc2);
       B.o4.launch(ex.scr, ex.sg, ex.st);
+      ex.end();
       // phase B and the Schur update
       for (Run<T> *r : wp)
         if (r->ok()) r->wave_c(B);
+      ex.begin(7);
       B.g1.launch(ex.scr, ex.sg, ex.st);
       B.g2.launch(ex.scr, ex.sg, ex.st);
       ex.chol_checked(B.c1);
@@ -1313,7 +1363,10 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       B.g6.launch(ex.scr, ex.sg, ex.st);
       B.g7.launch(ex.scr, ex.sg, ex.st);
       B.g8.launch(ex.scr, ex.sg, ex.st);
+      ex.end();
+      ex.begin(8);
       B.schur.launch(ex.scr, ex.sg, ex.st);
+      ex.end();
     }
     for (Run<T> *r : part)
       if (r->ok()) r->level_end(li);
@@ -1329,6 +1382,7 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
         r->handle().scratch->reset();
         r->root_a(sb);
       }
+    ex.begin(9);
     sb.launch(ex.scr, ex.sg, ex.st);
     CholBatch<T> cb;
     GemmBatch<T> g;
@@ -1336,6 +1390,7 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       if (r->ok()) r->root_b(cb, g);
     ex.chol_checked(cb);
     g.launch(ex.scr, ex.sg, ex.st);
+    ex.end();
   }
   ex.sync_check();
   const double total =
@@ -1345,6 +1400,7 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       r->finish();
       r->handle().info.host_ms = total;
       r->handle().info.wait_ms = ex.wait_ms;
+      ex.phase_times(r->handle().info.phase_ms, 10);
     }
 }
 
@@ -1356,6 +1412,7 @@ template <typename T>
 void factorize_t(const std::vector<FactorHandle *> &hs, const std::vector<const double *> &phis,
                  cudaStream_t st, std::vector<int> *status, std::vector<std::string> *msg) {
   Exec ex(st);
+  ex.prof = phase_profiling();
   if (hs.size() > 1) {
     ex.prob_status.assign(hs.size(), HS_OK);
     ex.prob_msg.assign(hs.size(), std::string());
@@ -1376,6 +1433,8 @@ void factorize_t(const std::vector<FactorHandle *> &hs, const std::vector<const 
 }
 
 }  // namespace
+
+void set_phase_profiling(bool on) { g_phase_prof.store(on ? 1 : 0); }
 
 void factorize(FactorHandle &h, const hs_csr &A, const hs_opts &o, const double *phi_host) {
   (void)A;

@@ -164,6 +164,8 @@ struct FactorHandle {
 
 // factor.cu
 void factorize(FactorHandle &h, const hs_csr &A, const hs_opts &o, const double *phi_host);
+// device time per factor phase into hs_info.phase_ms (event pairs; small cost)
+void set_phase_profiling(bool on);
 // Independent problems factored in lock step, their steps batched into shared
 // launches.  With more than one problem, a failed pivot (not SPD) takes only
 // that problem out: status[p] = HS_ERR_NOT_SPD and msg[p] say so.
