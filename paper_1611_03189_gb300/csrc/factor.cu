@@ -293,7 +293,7 @@ inline int grid_tridiag_min() {
   static const int v = [] {
     const char *e = std::getenv("HS_GRID_TRIDIAG_MIN");
     const int x = e ? std::atoi(e) : 0;
-    return x > 3 ? x : 384;
+    return x > 3 ? x : 200;
   }();
   return v;
 }
@@ -410,11 +410,131 @@ struct Exec {
     PendingStatus ps;
     ps.d = (int *)stat.alloc(sizeof(int) * cb.tasks.size());
     ps.what = cb.what;
-    Uploader u;
-    const size_t o = u.add(cb.tasks);
-    char *d = u.upload(scr, sg, st);
-    launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)cb.tasks.size(), ps.d, cb.max_m, st);
+    chol_inv_any<T>(cb.tasks, ps.d);
     pending.push_back(ps);
+  }
+
+  // L^-1 of A = L L^T for every task; status[t.status_idx] = 0 or failing
+  // pivot + 1.  Matrices that fit in shared memory take one CTA each; larger
+  // ones the blocked path below.
+  template <typename T>
+  void chol_inv_any(const std::vector<CholTask<T>> &tasks, int *status) {
+    std::vector<CholTask<T>> small, large;
+    int small_max = 0;
+    for (const CholTask<T> &t : tasks) {
+      if (t.m <= chol_smem_cap<T>()) {
+        small.push_back(t);
+        small_max = std::max(small_max, t.m);
+      } else {
+        large.push_back(t);
+      }
+    }
+    if (!small.empty()) {
+      Uploader u;
+      const size_t o = u.add(small);
+      char *d = u.upload(scr, sg, st);
+      launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)small.size(), status, small_max, st);
+    }
+    if (!large.empty()) chol_inv_blocked<T>(large, status);
+  }
+
+  // Blocked right-looking Cholesky with the block-triangular inverse, for
+  // matrices too large for one CTA (at the top levels of 3D problems the
+  // pivot blocks reach thousands of unknowns).  Block columns of kCholNb:
+  //   D_b = L_bb^-1 (one CTA, shared memory), panel L_ib = W_ib D_b^T,
+  //   trailing update W_ik -= L_ib L_kb^T (batched GEMMs over the GPU);
+  // then block rows of X = L^-1: X_ii = D_i, X_i,0:i = -D_i (L_i,0:i X_0:i,0:i).
+  // All large tasks of the batch advance together, one launch per kind and
+  // block step.
+  template <typename T>
+  void chol_inv_blocked(const std::vector<CholTask<T>> &tasks, int *status) {
+    constexpr int nb = 128;
+    struct Work {
+      CholTask<T> t;
+      T *W, *Lf, *D, *Tb;
+      int nblk;
+      int *bs;
+    };
+    std::vector<Work> w;
+    int maxblk = 0, nbs = 0;
+    for (const CholTask<T> &t : tasks) {
+      Work x;
+      x.t = t;
+      const size_t m = (size_t)t.m;
+      x.W = (T *)scr.alloc(sizeof(T) * m * m);
+      x.Lf = (T *)scr.alloc(sizeof(T) * m * m);
+      x.nblk = (t.m + nb - 1) / nb;
+      x.D = (T *)scr.alloc(sizeof(T) * (size_t)x.nblk * nb * nb);
+      x.Tb = (T *)scr.alloc(sizeof(T) * (size_t)nb * m);
+      x.bs = nullptr;
+      nbs += x.nblk;
+      maxblk = std::max(maxblk, x.nblk);
+      w.push_back(x);
+    }
+    int *bs = (int *)stat.alloc(sizeof(int) * nbs);
+    {
+      int off = 0;
+      SumBatch<T> cp;
+      for (Work &x : w) {
+        x.bs = bs + off;
+        off += x.nblk;
+        cp.copy(x.W, x.t.m, x.t.m, x.t.m, x.t.A, x.t.lda, 0);
+        // the inverse is lower triangular with a zero strict upper part
+        HS_CUDA(cudaMemsetAsync(x.t.Linv, 0, sizeof(T) * (size_t)x.t.m * x.t.m, st));
+      }
+      cp.launch(scr, sg, st);
+    }
+    for (int b = 0; b < maxblk; ++b) {
+      std::vector<CholTask<T>> dc;
+      GemmBatch<T> pan, trl;
+      for (Work &x : w) {
+        if (b >= x.nblk) continue;
+        const int m = x.t.m, j0 = b * nb, jb = std::min(nb, m - j0), rest = m - j0 - jb;
+        T *Db = x.D + (size_t)b * nb * nb;
+        CholTask<T> c;
+        c.A = x.W + (size_t)j0 * m + j0;
+        c.lda = m;
+        c.Linv = Db;
+        c.ldl = jb;
+        c.m = jb;
+        c.status_idx = (int)(x.bs - bs) + b;
+        dc.push_back(c);
+        if (rest > 0) {
+          T *Lp = x.Lf + (size_t)(j0 + jb) * m + j0;
+          pan.add(x.W + (size_t)(j0 + jb) * m + j0, m, 0, Db, jb, 1, Lp, m, rest, jb, jb, T(1), T(0));
+          trl.add(Lp, m, 0, Lp, m, 1, x.W + (size_t)(j0 + jb) * m + j0 + jb, m, rest, rest, jb, T(-1), T(1));
+        }
+      }
+      Uploader u;
+      const size_t o = u.add(dc);
+      char *d = u.upload(scr, sg, st);
+      launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)dc.size(), bs, nb, st);
+      pan.launch(scr, sg, st);
+      trl.launch(scr, sg, st);
+    }
+    for (int b = 0; b < maxblk; ++b) {
+      GemmBatch<T> g1, g2;
+      SumBatch<T> dg;
+      for (Work &x : w) {
+        if (b >= x.nblk) continue;
+        const int m = x.t.m, i0 = b * nb, jb = std::min(nb, m - i0);
+        const T *Db = x.D + (size_t)b * nb * nb;
+        if (b > 0) {
+          g1.add(x.Lf + (size_t)i0 * m, m, 0, x.t.Linv, m, 0, x.Tb, m, jb, i0, i0, T(1), T(0));
+          g2.add(Db, jb, 0, x.Tb, m, 0, x.t.Linv + (size_t)i0 * m, m, jb, i0, jb, T(-1), T(0));
+        }
+        dg.copy(x.t.Linv + (size_t)i0 * m + i0, m, jb, jb, Db, jb, 0);
+      }
+      g1.launch(scr, sg, st);
+      g2.launch(scr, sg, st);
+      dg.launch(scr, sg, st);
+    }
+    std::vector<StatusMerge> sm;
+    for (Work &x : w) sm.push_back(StatusMerge{x.bs, x.nblk, nb, status + x.t.status_idx});
+    Uploader u;
+    const size_t o = u.add(sm);
+    char *d = u.upload(scr, sg, st);
+    launch_status_merge((const StatusMerge *)(d + o), (int)sm.size(), st);
   }
 };
 
@@ -1287,11 +1407,8 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       int *d_stat = (int *)ex.scr.alloc(sizeof(int) * (nchol + ntrunc + nbig + 1));
       int *d_k = d_stat + nchol;
       if (nchol) {
-        Uploader u;
-        const size_t o = u.add(B.chol.tasks);
-        char *d = u.upload(ex.scr, ex.sg, ex.st);
         ex.begin(2);
-        launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)nchol, d_stat, B.chol.max_m, ex.st);
+        ex.chol_inv_any<T>(B.chol.tasks, d_stat);
         ex.end();
       }
       ex.begin(3);

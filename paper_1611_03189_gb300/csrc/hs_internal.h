@@ -148,6 +148,18 @@ void launch_gemm(const GemmTask<T> *d_tasks, const int *d_tile_start, int ntasks
 template <typename T>
 void launch_sum(const SumTask<T> *d_tasks, const SumSrc<T> *d_srcs, const int *d_tile_start,
                 int ntasks, int total_tiles, cudaStream_t st);
+// largest m the Cholesky kernel keeps in shared memory (larger ones are
+// factored blockwise by the host-driven multi-CTA path)
+template <typename T>
+int chol_smem_cap();
+// per large task of a blocked Cholesky: its diagonal-block statuses (bs,
+// nblk blocks of nb) merged into *out = first failing pivot + 1, else 0
+struct StatusMerge {
+  const int *bs;
+  int nblk, nb;
+  int *out;
+};
+void launch_status_merge(const StatusMerge *d_tasks, int ntasks, cudaStream_t st);
 template <typename T>
 void launch_chol_inv(const CholTask<T> *d_tasks, int ntasks, int *d_status, int max_m,
                      cudaStream_t st);

@@ -652,6 +652,16 @@ void launch_sum(const SumTask<T> *d_tasks, const SumSrc<T> *d_srcs, const int *d
   HS_CUDA(cudaGetLastError());
 }
 
+// first failing pivot over the diagonal blocks of a blocked Cholesky
+static __global__ void k_status_merge(const StatusMerge *__restrict__ t, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int r = 0;
+  for (int b = 0; b < t[i].nblk && !r; ++b)
+    if (t[i].bs[b]) r = b * t[i].nb + t[i].bs[b];
+  *t[i].out = r;
+}
+
 template <typename T>
 int chol_smem_cap() {
   return sizeof(T) == 8 ? 160 : 224;
@@ -715,11 +725,19 @@ void launch_gather_values(const double *val, const int32_t *src, int64_t nnz, do
   HS_CUDA(cudaGetLastError());
 }
 
+void launch_status_merge(const StatusMerge *d_tasks, int ntasks, cudaStream_t st) {
+  if (ntasks == 0) return;
+  k_status_merge<<<(ntasks + 127) / 128, 128, 0, st>>>(d_tasks, ntasks);
+  count_launch();
+  HS_CUDA(cudaGetLastError());
+}
+
 #define HS_INST(T)                                                                            \
   template void launch_gemm<T>(const GemmTask<T> *, const int *, int, int, cudaStream_t);     \
   template void launch_sum<T>(const SumTask<T> *, const SumSrc<T> *, const int *, int, int,   \
                               cudaStream_t);                                                  \
   template void launch_chol_inv<T>(const CholTask<T> *, int, int *, int, cudaStream_t);       \
+  template int chol_smem_cap<T>();                                                            \
   template void launch_trunc<T>(const TruncTask<T> *, int, int *, double, int, int,           \
                                 cudaStream_t);                                                \
   template void launch_scatter_values<T>(const double *, const int64_t *, int64_t, T *,       \
