@@ -124,12 +124,15 @@ typedef struct {
                                 launch per thread-count class in each)            */
   double host_ms;            /* host wall time of the factorization call          */
   double wait_ms;            /* of which waiting for the device (rank reads)      */
-  double phase_ms[10];       /* with hs_profile_phases(1): device time of the
+  double phase_ms[16];       /* with hs_profile_phases(1): device time of the
                                 factor's launch groups -- 0 merge, 1 gather of
                                 A_sN/A_sW, 2 Cholesky of A_ss, 3 Gram, 4 small
                                 truncation, 5 large truncation, 6 CholQR of the
                                 large-path U, 7 extension GEMMs and CholQR, 8
-                                Schur scatter, 9 root; otherwise zeros          */
+                                Schur scatter, 9 root; within 5, the multi-CTA
+                                path: 10 prepare, 11 tridiagonal steps, 12 Q^T Z,
+                                13 eigenvectors of T, 14 Q Y; 15 unused;
+                                otherwise zeros                                 */
 } hs_info;
 
 typedef struct hs_factor_s *hs_factor;

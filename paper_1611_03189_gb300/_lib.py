@@ -70,10 +70,11 @@ class HsInfo(C.Structure):
                 ("max_super", C.c_int32), ("device_bytes", C.c_int64), ("factor_bytes", C.c_int64),
                 ("factor_flops", C.c_double), ("eig_flops", C.c_double), ("factor_ms", C.c_double),
                 ("trunc_big_ms", C.c_double), ("trunc_big_flops", C.c_double), ("trunc_big_launches", C.c_int32),
-                ("host_ms", C.c_double), ("wait_ms", C.c_double), ("phase_ms", C.c_double * 10)]
+                ("host_ms", C.c_double), ("wait_ms", C.c_double), ("phase_ms", C.c_double * 16)]
 
     PHASES = ("merge", "gather", "chol_Ass", "gram", "trunc_small", "trunc_large", "cholqr_large",
-              "extension", "schur", "root")
+              "extension", "schur", "root", "grid_prepare", "grid_tridiag_steps", "grid_qtz",
+              "grid_eigvec_T", "grid_qy", "unused")
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "phase_ms"}

@@ -336,18 +336,20 @@ struct Exec {
     cudaEvent_t e0, e1;
   };
   std::vector<Span> spans;
-  int open_phase = -1;
+  std::vector<size_t> open;     // spans begun and not yet ended (nesting)
   void begin(int phase) {
     if (!prof) return;
     Span sp{phase, nullptr, nullptr};
     HS_CUDA(cudaEventCreate(&sp.e0));
     HS_CUDA(cudaEventCreate(&sp.e1));
     HS_CUDA(cudaEventRecord(sp.e0, st));
+    open.push_back(spans.size());
     spans.push_back(sp);
   }
   void end() {
-    if (!prof || spans.empty()) return;
-    HS_CUDA(cudaEventRecord(spans.back().e1, st));
+    if (!prof || open.empty()) return;
+    HS_CUDA(cudaEventRecord(spans[open.back()].e1, st));
+    open.pop_back();
   }
   void phase_times(double *ms, int nphase) {
     for (Span &sp : spans) {
@@ -1300,7 +1302,10 @@ template <typename T>
 void trunc_grid(Exec &ex, const std::vector<TruncTask<T>> &tasks, const TruncTask<T> *d_tasks, int *d_k,
                 double eps, int variant, int max_m) {
   const int n = (int)tasks.size();
+  // nested spans (phases 10-14) inside the large-truncation span (5)
+  ex.begin(10);
   launch_trunc_big_mode<T>(d_tasks, n, d_k, eps, variant, max_m, 1 /* TB_PREP */, ex.st);
+  ex.end();
   std::vector<GridTri<T>> gt(n);
   int blocks = 0;
   for (int q = 0; q < n; ++q) {
@@ -1325,10 +1330,12 @@ void trunc_grid(Exec &ex, const std::vector<TruncTask<T>> &tasks, const TruncTas
   const size_t og = u.add(gt);
   char *dg = u.upload(ex.scr, ex.sg, ex.st);
   const GridTri<T> *d_gt = (const GridTri<T> *)(dg + og);
+  ex.begin(11);
   for (int k = 0; k + 2 <= max_m; ++k) {
     launch_tri_step<T>(d_gt, n, blocks, k, 0, ex.st);
     if (k + 3 <= max_m) launch_tri_step<T>(d_gt, n, blocks, k, 1, ex.st);
   }
+  ex.end();
   const int nb = refl_batch<T>(max_m);
   if (variant != HS_LORASP) {
     std::vector<ReflTask<T>> zf;
@@ -1339,9 +1346,13 @@ void trunc_grid(Exec &ex, const std::vector<TruncTask<T>> &tasks, const TruncTas
     Uploader uz;
     const size_t oz = uz.add(zf);
     char *dz = uz.upload(ex.scr, ex.sg, ex.st);
+    ex.begin(12);
     launch_refl<T>((const ReflTask<T> *)(dz + oz), (int)zf.size(), std::min(nb, 4), max_m, ex.st);
+    ex.end();
   }
+  ex.begin(13);
   launch_trunc_big_mode<T>(d_tasks, n, d_k, eps, variant, max_m, 2 /* TB_POST */, ex.st);
+  ex.end();
   std::vector<ReflTask<T>> yb;
   for (const TruncTask<T> &t : tasks) {
     const BigLayout<T> L = big_layout<T>(t.work, t.m);
@@ -1350,7 +1361,9 @@ void trunc_grid(Exec &ex, const std::vector<TruncTask<T>> &tasks, const TruncTas
   Uploader uy;
   const size_t oy = uy.add(yb);
   char *dy = uy.upload(ex.scr, ex.sg, ex.st);
+  ex.begin(14);
   launch_refl<T>((const ReflTask<T> *)(dy + oy), (int)yb.size(), nb, max_m, ex.st);
+  ex.end();
 }
 
 // Runs the factorizations of `runs` in lock step: at every step (level counted
@@ -1517,7 +1530,7 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       r->finish();
       r->handle().info.host_ms = total;
       r->handle().info.wait_ms = ex.wait_ms;
-      ex.phase_times(r->handle().info.phase_ms, 10);
+      ex.phase_times(r->handle().info.phase_ms, 16);
     }
 }
 

@@ -858,11 +858,22 @@ __global__ void __launch_bounds__(kTriRows * 32) k_tri_update(const GridTri<T> *
       const T K = sK;
       const T vi = t.V[i];
       const T wi = fma(-K, vi, t.P[i]);
-      for (int j = k + lane; j < m; j += 32) {
-        const T vj = t.V[j];
-        const T wj = fma(-K, vj, t.P[j]);
-        row[j] = fma(-vi, wj, fma(-wi, vj, row[j]));
+      const T *V = t.V, *P = t.P;
+      auto upd = [&](T a, int j) {
+        const T vj = V[j];
+        return fma(-vi, fma(-K, vj, P[j]), fma(-wi, vj, a));
+      };
+      // four independent row elements in flight per lane (the step is a
+      // stream over the trailing rows)
+      int j = k + lane;
+      for (; j + 96 < m; j += 128) {
+        const T a0 = row[j], a1 = row[j + 32], a2 = row[j + 64], a3 = row[j + 96];
+        row[j] = upd(a0, j);
+        row[j + 32] = upd(a1, j + 32);
+        row[j + 64] = upd(a2, j + 64);
+        row[j + 96] = upd(a3, j + 96);
       }
+      for (; j < m; j += 32) row[j] = upd(row[j], j);
       __syncwarp();
     }
     if (k <= m - 3 && lane == 0) {
