@@ -284,11 +284,16 @@ __device__ __forceinline__ float hash_unit(uint32_t a, uint32_t b) {
 // T - lam I with partial pivoting (rows i, i+1 interchanged when the
 // sub-diagonal dominates), three solves from a fixed pseudo-random start,
 // modified Gram-Schmidt against `nprev` previous vectors of the same cluster
-// of close eigenvalues.  y: output (length m); lu: 4 m of scratch; flags: m bytes.
+// of close eigenvalues.  y: output (length m); lu: 4 m of scratch; flags: m
+// bytes; element i of y, lu's four arrays and flags sits at index i * st (st >
+// 1 interleaves the scratch of several threads, so that their accesses to
+// global memory coalesce).
 template <typename R>
 __device__ void inverse_iteration(const R *d, const R *e, int m, R lam, R tnorm, R *y, const R *prev,
-                                  int nprev, R *lu, unsigned char *flags, uint32_t seed) {
-  R *u0 = lu, *u1 = lu + m, *u2 = lu + 2 * m, *l = lu + 3 * m;
+                                  int nprev, R *lu, unsigned char *flags, uint32_t seed, int st = 1) {
+  const size_t sm = (size_t)m * st;
+  R *u0 = lu, *u1 = lu + sm, *u2 = lu + 2 * sm, *l = lu + 3 * sm;
+  auto I = [st](int i) { return (size_t)i * st; };
   const R small = unit_round<R>() * tnorm + R(1e-30);
   R a = d[0] - lam, c = (m > 1) ? e[0] : R(0);
   for (int i = 0; i + 1 < m; ++i) {
@@ -298,60 +303,60 @@ __device__ void inverse_iteration(const R *d, const R *e, int m, R lam, R tnorm,
     if (fabs(a) >= fabs(bsub)) {
       const R piv = (a == R(0)) ? small : a;
       const R mult = bsub / piv;
-      u0[i] = piv;
-      u1[i] = c;
-      u2[i] = R(0);
-      l[i] = mult;
-      flags[i] = 0;
+      u0[I(i)] = piv;
+      u1[I(i)] = c;
+      u2[I(i)] = R(0);
+      l[I(i)] = mult;
+      flags[I(i)] = 0;
       a = an - mult * c;
       c = cn;
     } else {
       const R mult = a / bsub;
-      u0[i] = bsub;
-      u1[i] = an;
-      u2[i] = cn;
-      l[i] = mult;
-      flags[i] = 1;
+      u0[I(i)] = bsub;
+      u1[I(i)] = an;
+      u2[I(i)] = cn;
+      l[I(i)] = mult;
+      flags[I(i)] = 1;
       a = c - mult * an;
       c = -mult * cn;
     }
   }
-  u0[m - 1] = a;
+  u0[I(m - 1)] = a;
   for (int i = 0; i < m; ++i)
-    if (fabs(u0[i]) < small) u0[i] = copysign(small, u0[i]);
-  for (int i = 0; i < m; ++i) y[i] = (R)hash_unit(seed, (uint32_t)i);
+    if (fabs(u0[I(i)]) < small) u0[I(i)] = copysign(small, u0[I(i)]);
+  for (int i = 0; i < m; ++i) y[I(i)] = (R)hash_unit(seed, (uint32_t)i);
   for (int it = 0; it < 3; ++it) {
     for (int i = 0; i + 1 < m; ++i) {
-      if (flags[i]) {
-        const R t = y[i];
-        y[i] = y[i + 1];
-        y[i + 1] = t - l[i] * y[i];
+      if (flags[I(i)]) {
+        const R t = y[I(i)];
+        y[I(i)] = y[I(i + 1)];
+        y[I(i + 1)] = t - l[I(i)] * y[I(i)];
       } else {
-        y[i + 1] -= l[i] * y[i];
+        y[I(i + 1)] -= l[I(i)] * y[I(i)];
       }
     }
     for (int i = m - 1; i >= 0; --i) {
-      R s = y[i];
-      if (i + 1 < m) s -= u1[i] * y[i + 1];
-      if (i + 2 < m) s -= u2[i] * y[i + 2];
-      y[i] = s / u0[i];
+      R s = y[I(i)];
+      if (i + 1 < m) s -= u1[I(i)] * y[I(i + 1)];
+      if (i + 2 < m) s -= u2[I(i)] * y[I(i + 2)];
+      y[I(i)] = s / u0[I(i)];
     }
     for (int pass = 0; pass < 2; ++pass)
       for (int p = 0; p < nprev; ++p) {
         const R *q = prev + (size_t)p * m;
         R dot = R(0);
-        for (int i = 0; i < m; ++i) dot += q[i] * y[i];
-        for (int i = 0; i < m; ++i) y[i] -= dot * q[i];
+        for (int i = 0; i < m; ++i) dot += q[i] * y[I(i)];
+        for (int i = 0; i < m; ++i) y[I(i)] -= dot * q[i];
       }
     // normalise, scaling by the largest entry first to keep the sum in range
     R big = R(0);
-    for (int i = 0; i < m; ++i) big = fmax(big, fabs(y[i]));
+    for (int i = 0; i < m; ++i) big = fmax(big, fabs(y[I(i)]));
     const R sc = big > R(0) ? R(1) / big : R(0);
     R nrm = R(0);
-    for (int i = 0; i < m; ++i) nrm += (y[i] * sc) * (y[i] * sc);
+    for (int i = 0; i < m; ++i) nrm += (y[I(i)] * sc) * (y[I(i)] * sc);
     nrm = sqrt(nrm);
     const R inv = nrm > R(0) ? sc / nrm : R(0);
-    for (int i = 0; i < m; ++i) y[i] *= inv;
+    for (int i = 0; i < m; ++i) y[I(i)] *= inv;
   }
 }
 
@@ -723,25 +728,40 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
     // tile holds fewer than 8 slots
     const size_t tile_bytes = (size_t)b.tile_cap * b.tile_cap * sizeof(T);
     const size_t slot_bytes = ((5 * (size_t)m * sizeof(T) + (size_t)m + 15) / 16) * 16;
-    unsigned char *slot_base = (unsigned char *)b.tile;
     int nslot = (int)(tile_bytes / slot_bytes);
-    const int nslot_g = (int)((164 * (size_t)m * sizeof(T) - 16) / slot_bytes);   // 31 or more
-    if (nslot < 8 && nslot < nslot_g) {
-      slot_base = (unsigned char *)(((uintptr_t)LS + 15) & ~(uintptr_t)15);
-      nslot = nslot_g;
+    // too few slots in the tile: up to one per thread in the (otherwise unused)
+    // LU and FL regions of global memory, interleaved so that the threads'
+    // accesses coalesce (5 m T per slot in LU's 4 m^2, m flags in FL's m^2)
+    const bool glob = nslot < 32;
+    int ns_g = 0;
+    if (glob) {
+      ns_g = (int)((4 * (size_t)m * m) / (5 * (size_t)m));
+      if (ns_g > nt) ns_g = nt;
+      if (ns_g < 1) ns_g = 1;
+      nslot = ns_g;
     }
     if (nslot > nt) nslot = nt;
     if (tid < nslot) {
-      unsigned char *slot = slot_base + (size_t)tid * slot_bytes;
-      T *lu = (T *)slot;
-      T *ys = lu + 4 * (size_t)m;
-      unsigned char *fl = (unsigned char *)(ys + m);
+      T *lu, *ys;
+      unsigned char *fl;
+      int st = 1;
+      if (glob) {
+        lu = LU + tid;
+        ys = LU + 4 * (size_t)m * ns_g + tid;
+        fl = FL + tid;
+        st = ns_g;
+      } else {
+        unsigned char *slot = (unsigned char *)b.tile + (size_t)tid * slot_bytes;
+        lu = (T *)slot;
+        ys = lu + 4 * (size_t)m;
+        fl = (unsigned char *)(ys + m);
+      }
       for (int c = tid; c < nc; c += nslot) {
         const int j0 = starts[c], j1 = starts[c + 1];
         for (int q = j0; q < j1; ++q) {
           inverse_iteration<T>(b.dt, b.et, m, b.lam[q], g.tnorm, ys, Y + (size_t)j0 * m, q - j0, lu, fl,
-                               (uint32_t)(q * 7919 + 17));
-          for (int i = 0; i < m; ++i) Y[(size_t)q * m + i] = ys[i];
+                               (uint32_t)(q * 7919 + 17), st);
+          for (int i = 0; i < m; ++i) Y[(size_t)q * m + i] = ys[(size_t)i * st];
         }
       }
     }
