@@ -729,10 +729,10 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
     const size_t tile_bytes = (size_t)b.tile_cap * b.tile_cap * sizeof(T);
     const size_t slot_bytes = ((5 * (size_t)m * sizeof(T) + (size_t)m + 15) / 16) * 16;
     int nslot = (int)(tile_bytes / slot_bytes);
-    // too few slots in the tile: up to one per thread in the (otherwise unused)
+    // fewer than 8 slots in the tile: up to one per thread in the (otherwise unused)
     // LU and FL regions of global memory, interleaved so that the threads'
     // accesses coalesce (5 m T per slot in LU's 4 m^2, m flags in FL's m^2)
-    const bool glob = nslot < 32;
+    const bool glob = nslot < 8;
     int ns_g = 0;
     if (glob) {
       ns_g = (int)((4 * (size_t)m * m) / (5 * (size_t)m));
