@@ -55,6 +55,28 @@ def make_problem(name: str, seed: int):
     return P.diffusion2d(side, s, seed, leaf_size=leaf), eps
 
 
+def replica_seed(rank: int, k: int) -> int:
+    """Coefficient-field seed of step k on replica `rank`: replicas solve
+    different systems (the path has no data exchange; weak scaling)."""
+    return rank * 1000 + k
+
+
+def max_over_ranks(ms: float, dist, device=None) -> float:
+    """The slowest rank's time: every rank contributes its own, all get the max."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, steps: int, nrhs: int, ms: float) -> float:
+    """Solves per second of the whole job: all replicas' solves over the slowest time."""
+    return world * steps * nrhs / (ms / 1000.0)
+
+
 def sample_for(name: str):
     """(sample workload, unknowns of the workload / unknowns of the sample)."""
     sample = CPU_SAMPLE.get(name, name)
@@ -404,7 +426,7 @@ def main():
     # inputs resident in HBM: one matrix (new coefficient field) and rhs block per step
     pbs = []
     for k in range(nsteps):
-        pb, eps = make_problem(args.workload, seed=rank * 1000 + k)
+        pb, eps = make_problem(args.workload, seed=replica_seed(rank, k))
         pbs.append(pb)
     pb0 = pbs[0]
     rp = torch.as_tensor(pb0.rowptr, device=dev)
@@ -453,13 +475,9 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     ms_per_step = ms / args.steps
-    value = world * args.steps * args.nrhs / (ms / 1000.0)
+    value = whole_job_rate(world, args.steps, args.nrhs, ms)
     info = G.info()
 
     # ---- factor-only and solve-only splits (resident factor), for context ----
@@ -558,12 +576,8 @@ def main():
         hx[k % 2].copy_(x, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e2.elapsed_time(e3)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_val = world * args.steps * args.nrhs / (e2e_ms / 1000.0)
+    e2e_ms = max_over_ranks(e2.elapsed_time(e3), dist, dev)
+    e2e_val = whole_job_rate(world, args.steps, args.nrhs, e2e_ms)
 
     if args.profile and rank == 0:
         print(json.dumps({"plan_and_first_factor_s": t_plan, "factor_ms": factor_ms, "solve_ms": solve_ms,
