@@ -449,7 +449,7 @@ enum { TB_FULL = 0, TB_PREP = 1, TB_POST = 2 };
 
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict__ tasks, int *__restrict__ kout,
-                                                 int variant, int tile_cap, int vec_smem, int mode, int post_copy) {
+                                                 int variant, int tile_cap, int vec_smem, int mode) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
   __shared__ int s_k2;
@@ -499,8 +499,7 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
   // them at every step; from global memory each step waited on L2)
   const int me_post = (m + 1) & ~1;
   T *post_dt = (T *)smem_raw, *post_et = post_dt + me_post, *post_z = post_et + me_post;
-  const bool copies = mode == TB_POST && post_copy;
-  if (copies) b.tile = (T *)(smem_raw + post_smem_bytes<T>(m));
+  if (mode == TB_POST) b.tile = (T *)(smem_raw + post_smem_bytes<T>(m));
   b.tile_cap = tile_cap;
   b.red = red;
   if (m == 0) {
@@ -640,18 +639,13 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
       b.tau[m - 1] = T(0);
     }
     __syncthreads();
-    if (!copies) {
-      post_dt = b.dt;
-      post_et = b.et;
-      post_z = LS;
-    }
     for (int i = tid; i < m; i += nt) {
       post_dt[i] = (T)b.d[i];
       post_et[i] = (T)b.e[i];
     }
     b.dt = post_dt;
     b.et = post_et;
-    if (copies && gc && eps > 0.0)
+    if (gc && eps > 0.0)
       for (int64_t q = tid; q < 2 * (int64_t)k1 * m; q += nt) post_z[q] = LS[q];
     __syncthreads();
   } else {
@@ -1108,7 +1102,7 @@ void launch_trunc_big_nt(const TruncTask<T> *d_tasks, int ntasks, int *d_k, doub
   while (cap < max_m && (size_t)(cap + 1) * (cap + 1) * sizeof(T) + fixed <= budget) ++cap;
   const size_t sm = fixed + (size_t)cap * cap * sizeof(T);
   check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc_big<T, NT>>(), "k_trunc_big");
-  k_trunc_big<T, NT><<<ntasks, NT, sm, st>>>(d_tasks, d_k, variant, cap, vec_smem, TB_FULL, 0);
+  k_trunc_big<T, NT><<<ntasks, NT, sm, st>>>(d_tasks, d_k, variant, cap, vec_smem, TB_FULL);
   count_launch();
   HS_CUDA(cudaGetLastError());
 }
@@ -1129,15 +1123,13 @@ void launch_trunc_big_mode(const TruncTask<T> *d_tasks, int ntasks, int *d_k, do
   // per-node vectors in global memory (the step kernels write d, e, tau there);
   // TB_POST first takes its copies of T and Z, the rest of the budget is the tile
   const size_t budget = 200 * 1024;
-  // (when they fit with room for a 32 x 32 tile; otherwise they stay global)
-  size_t pre = mode == 2 ? post_smem_bytes<T>(max_m) : 0;
-  const int post_copy = (mode == 2 && pre + 32 * 32 * sizeof(T) + 32 <= budget) ? 1 : 0;
-  if (!post_copy) pre = 0;
+  const size_t pre = mode == 2 ? post_smem_bytes<T>(max_m) : 0;
+  if (pre + 32 > budget) fail(HS_ERR_CAPACITY, "super node too large for the eigenvector kernel's shared memory");
   int cap = 0;
   while (cap < max_m && (size_t)(cap + 1) * (cap + 1) * sizeof(T) + 32 + pre <= budget) ++cap;
   const size_t sm = 32 + pre + (size_t)cap * cap * sizeof(T);
   check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc_big<T, 1024>>(), "k_trunc_big");
-  k_trunc_big<T, 1024><<<ntasks, 1024, sm, st>>>(d_tasks, d_k, variant, cap, 0, mode, post_copy);
+  k_trunc_big<T, 1024><<<ntasks, 1024, sm, st>>>(d_tasks, d_k, variant, cap, 0, mode);
   count_launch();
   HS_CUDA(cudaGetLastError());
 }
