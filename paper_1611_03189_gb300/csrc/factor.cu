@@ -15,6 +15,12 @@
 // Identities: S = U^T A_ss^-1 U = R^T R, P_ss = S^-1 U^T A_ss^-1,
 // M_ss = A_ss^-1 - P_ss^T S P_ss = L^-T (I - Q Q^T) L^-1, and
 // A_ns M_ss A_sn' is the Schur term of ~~A_nn' (eq. eliminated).
+//
+// One executor (execute) drives one problem or many independent ones in lock
+// step: at every step (level from the leaves, wave) all problems that have it
+// share the launches.  Truncations of nodes with m >= 200 spread their
+// tridiagonalisation over the GPU (trunc_grid); Cholesky factors above the
+// shared-memory limit are blocked (Exec::chol_inv_blocked).
 #include <algorithm>
 #include <atomic>
 #include <chrono>
