@@ -433,13 +433,6 @@ __device__ int count_above_lowrank(const R *d, const R *e, int m, const R *Z, in
   return pos - k1;
 }
 
-// shared bytes of TB_POST's copies of T (dt, et) and Z (up to 4 columns), 16-aligned
-template <typename T>
-__host__ __device__ inline size_t post_smem_bytes(int m) {
-  const size_t me = (size_t)((m + 1) & ~1);
-  return ((6 * me * sizeof(T)) + 15) & ~(size_t)15;
-}
-
 // mode: TB_FULL does all steps in this CTA.  The multi-CTA path for very large
 // nodes splits it: TB_PREP stops before the tridiagonalisation (A = J, Z saved,
 // k1 and c stored in SC); the step kernels tridiagonalise; TB_POST takes d, e
@@ -494,12 +487,6 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
   p += sizeof(T) * 34;
   p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
   b.tile = (T *)(vec_smem ? p : smem_raw);
-  // TB_POST keeps its own copies of T and Z at the start of shared memory (the
-  // bisection, the Sturm and inertia counts and the inverse iteration read
-  // them at every step; from global memory each step waited on L2)
-  const int me_post = (m + 1) & ~1;
-  T *post_dt = (T *)smem_raw, *post_et = post_dt + me_post, *post_z = post_et + me_post;
-  if (mode == TB_POST) b.tile = (T *)(smem_raw + post_smem_bytes<T>(m));
   b.tile_cap = tile_cap;
   b.red = red;
   if (m == 0) {
@@ -640,13 +627,9 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
     }
     __syncthreads();
     for (int i = tid; i < m; i += nt) {
-      post_dt[i] = (T)b.d[i];
-      post_et[i] = (T)b.e[i];
+      b.dt[i] = (T)b.d[i];
+      b.et[i] = (T)b.e[i];
     }
-    b.dt = post_dt;
-    b.et = post_et;
-    if (gc && eps > 0.0)
-      for (int64_t q = tid; q < 2 * (int64_t)k1 * m; q += nt) post_z[q] = LS[q];
     __syncthreads();
   } else {
     tridiag<T>(A, m, b);
@@ -691,9 +674,7 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
       T lo = lmaxT, hi = fmax(trace, lmaxT) * T(1.0001) + T(1e-30);
       for (int round = 0; round < 40 && hi - lo > T(4) * unit_round<T>() * hi; ++round) {
         const T sig = lo + (hi - lo) * T(tid + 1) / T(33);
-        const int c = k1 > 0 ? count_above_lowrank<T>(b.dt, b.et, m, mode == TB_POST ? post_z : Zb, k1, cmat,
-                                                       sig)
-                             : 0;
+        const int c = k1 > 0 ? count_above_lowrank<T>(b.dt, b.et, m, Zb, k1, cmat, sig) : 0;
         const unsigned above = __ballot_sync(0xffffffffu, c >= 1);
         const int l = above ? 31 - __clz(above) : -1;   // highest sigma with an eigenvalue above it
         const T nlo = l >= 0 ? lo + (hi - lo) * T(l + 1) / T(33) : lo;
@@ -1121,13 +1102,11 @@ void launch_trunc_big_mode(const TruncTask<T> *d_tasks, int ntasks, int *d_k, do
                            int mode, cudaStream_t st) {
   if (ntasks == 0) return;
   // per-node vectors in global memory (the step kernels write d, e, tau there);
-  // TB_POST first takes its copies of T and Z, the rest of the budget is the tile
+  // the whole budget is the tile
   const size_t budget = 200 * 1024;
-  const size_t pre = mode == 2 ? post_smem_bytes<T>(max_m) : 0;
-  if (pre + 32 > budget) fail(HS_ERR_CAPACITY, "super node too large for the eigenvector kernel's shared memory");
   int cap = 0;
-  while (cap < max_m && (size_t)(cap + 1) * (cap + 1) * sizeof(T) + 32 + pre <= budget) ++cap;
-  const size_t sm = 32 + pre + (size_t)cap * cap * sizeof(T);
+  while (cap < max_m && (size_t)(cap + 1) * (cap + 1) * sizeof(T) + 32 <= budget) ++cap;
+  const size_t sm = 32 + (size_t)cap * cap * sizeof(T);
   check_dynamic_smem(sm, allow_max_dynamic_smem<&k_trunc_big<T, 1024>>(), "k_trunc_big");
   k_trunc_big<T, 1024><<<ntasks, 1024, sm, st>>>(d_tasks, d_k, variant, cap, 0, mode);
   count_launch();
