@@ -1358,6 +1358,31 @@ void trunc_grid(Exec &ex, const std::vector<TruncTask<T>> &tasks, const TruncTas
   }
   ex.begin(13);
   launch_trunc_big_mode<T>(d_tasks, n, d_k, eps, variant, max_m, 2 /* TB_POST */, ex.st);
+  {
+    // eigenvectors of T: clusters spread over many CTAs (at most m per node)
+    const int spc = invit_slots<T>(max_m);
+    std::vector<InvitTask<T>> it;
+    int iblocks = 0;
+    for (const TruncTask<T> &t : tasks) {
+      const BigLayout<T> L = big_layout<T>(t.work, t.m);
+      InvitTask<T> x;
+      x.dt = L.dt;
+      x.et = L.et;
+      x.lam = L.lam;
+      x.starts = (const int *)L.pw;
+      x.sc = L.sc_int;
+      x.tnorm = L.sc_tnorm;
+      x.Y = L.Y;
+      x.m = t.m;
+      x.blk0 = iblocks;
+      iblocks += (t.m + spc - 1) / spc;
+      it.push_back(x);
+    }
+    Uploader ui;
+    const size_t oi = ui.add(it);
+    char *di = ui.upload(ex.scr, ex.sg, ex.st);
+    launch_invit<T>((const InvitTask<T> *)(di + oi), (int)it.size(), iblocks, spc, max_m, ex.st);
+  }
   ex.end();
   std::vector<ReflTask<T>> yb;
   for (const TruncTask<T> &t : tasks) {

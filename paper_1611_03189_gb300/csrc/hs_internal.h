@@ -183,8 +183,9 @@ struct BigLayout {
   unsigned char *FL, *VG;
   double *d, *e, *pw;
   T *dt, *et, *lam, *v, *tau, *wt, *redt;
-  int *sc_int;
-  double *sc_c;
+  int *sc_int;        // k1, k2, number of eigenvalue clusters
+  double *sc_c;       // c = U1^T G U1 (4 doubles)
+  double *sc_tnorm;   // norm bound of T (inverse-iteration tolerance)
 };
 
 template <typename T>
@@ -225,6 +226,7 @@ __host__ __device__ inline BigLayout<T> big_layout(T *work, int m) {
   unsigned char *sc = (unsigned char *)(((uintptr_t)(L.VG + big_vec_bytes<T>(m)) + 15) & ~(uintptr_t)15);
   L.sc_int = (int *)sc;
   L.sc_c = (double *)(sc + 16);
+  L.sc_tnorm = (double *)(sc + 48);
   return L;
 }
 
@@ -241,6 +243,19 @@ struct GridTri {
   double *d, *e;
   T *tau;
   int m, nblk, blk0;
+};
+
+// Inverse iteration of a node's selected eigenvalues (multi-CTA path): the
+// clusters of close eigenvalues (starts, count in sc[2]) are spread one per
+// thread over many CTAs, each thread's LU and vector in shared memory.
+template <typename T>
+struct InvitTask {
+  const T *dt, *et, *lam;
+  const int *starts;
+  const int *sc;
+  const double *tnorm;
+  T *Y;              // eigenvectors of T, column q at Y + q m
+  int m, blk0;
 };
 
 // Products with Q = H_0 ... H_{m-3} of a node's reflectors: forward (Q^T, the
@@ -275,6 +290,12 @@ void launch_trunc_big_mode(const TruncTask<T> *d_tasks, int ntasks, int *d_k, do
 // and p = tau A v)
 template <typename T>
 void launch_tri_step(const GridTri<T> *d_tasks, int ntasks, int total_blocks, int k, int phase, cudaStream_t st);
+// inverse iteration over total_blocks CTAs of `spc` slots each
+template <typename T>
+void launch_invit(const InvitTask<T> *d_tasks, int ntasks, int total_blocks, int spc, int m_max, cudaStream_t st);
+// slots per CTA of launch_invit for nodes of size up to m
+template <typename T>
+int invit_slots(int m);
 // reflector products (one CTA per task); nb columns per task
 template <typename T>
 void launch_refl(const ReflTask<T> *d_tasks, int ntasks, int nb, int m_max, cudaStream_t st);

@@ -722,10 +722,15 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
   }
   __syncthreads();
   const int nc = s_nc;
-  {
+  if (mode == TB_POST) {
+    // the eigenvectors of T come from k_invit, spread over many CTAs
+    if (tid == 0) {
+      L.sc_int[2] = nc;
+      *L.sc_tnorm = (double)g.tnorm;
+    }
+  } else {
     // each worker thread owns a slot: u0,u1,u2,l,y (5 m T) + m flags, in the
-    // shared tile, or in the global LS region (Z is no longer needed) when the
-    // tile holds fewer than 8 slots
+    // shared tile (see below for the global fallback)
     const size_t tile_bytes = (size_t)b.tile_cap * b.tile_cap * sizeof(T);
     const size_t slot_bytes = ((5 * (size_t)m * sizeof(T) + (size_t)m + 15) / 16) * 16;
     int nslot = (int)(tile_bytes / slot_bytes);
@@ -985,6 +990,48 @@ __global__ void __launch_bounds__(kTriRows * 32) k_tri_symv(const GridTri<T> *__
   }
 }
 
+// Inverse iteration of the multi-CTA path: one warp per CTA, `spc` of its
+// threads active, each with a slot (LU of T - lam I and the vector: 5 m T and m
+// flags) in shared memory, taking one cluster of close eigenvalues.  Same
+// arithmetic as the one-CTA kernel; each step of the recurrence stays on chip.
+template <typename T>
+__device__ __forceinline__ int invit_task(const InvitTask<T> *tasks, int ntasks, int b) {
+  int lo = 0, hi = ntasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].blk0 <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__host__ __device__ inline size_t invit_slot_bytes(int m) {
+  return ((5 * (size_t)m * sizeof(T) + (size_t)m + 15) / 16) * 16;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32) k_invit(const InvitTask<T> *__restrict__ tasks, int ntasks, int spc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const InvitTask<T> t = tasks[invit_task(tasks, ntasks, blockIdx.x)];
+  const int m = t.m;
+  const int c = (blockIdx.x - t.blk0) * spc + threadIdx.x;
+  if ((int)threadIdx.x >= spc || c >= t.sc[2]) return;
+  unsigned char *slot = smem_raw + (size_t)threadIdx.x * invit_slot_bytes<T>(m);
+  T *lu = (T *)slot;
+  T *ys = lu + 4 * (size_t)m;
+  unsigned char *fl = (unsigned char *)(ys + m);
+  const T tnorm = (T)*t.tnorm;
+  const int j0 = t.starts[c], j1 = t.starts[c + 1];
+  for (int q = j0; q < j1; ++q) {
+    inverse_iteration<T>(t.dt, t.et, m, t.lam[q], tnorm, ys, t.Y + (size_t)j0 * m, q - j0, lu, fl,
+                         (uint32_t)(q * 7919 + 17));
+    for (int i = 0; i < m; ++i) t.Y[(size_t)q * m + i] = ys[i];
+  }
+}
+
 // Products with the reflectors of a node, one CTA per batch of columns held in
 // shared memory: for each reflector the block forms all the batch's dot
 // products (fixed-order reduction), then updates the columns.
@@ -1141,6 +1188,27 @@ void launch_refl(const ReflTask<T> *d_tasks, int ntasks, int nb, int m_max, cuda
   HS_CUDA(cudaGetLastError());
 }
 
+template <typename T>
+int invit_slots(int m) {
+  const size_t budget = 200 * 1024;
+  const int spc = (int)(budget / invit_slot_bytes<T>(std::max(m, 1)));
+  return std::max(1, std::min(spc, 32));
+}
+
+template <typename T>
+void launch_invit(const InvitTask<T> *d_tasks, int ntasks, int total_blocks, int spc, int m_max, cudaStream_t st) {
+  if (ntasks == 0 || total_blocks == 0) return;
+  const size_t sm = (size_t)spc * invit_slot_bytes<T>(m_max);
+  check_dynamic_smem(sm, allow_max_dynamic_smem<&k_invit<T>>(), "k_invit");
+  k_invit<T><<<total_blocks, 32, sm, st>>>(d_tasks, ntasks, spc);
+  count_launch();
+  HS_CUDA(cudaGetLastError());
+}
+
+template int invit_slots<double>(int);
+template int invit_slots<float>(int);
+template void launch_invit<double>(const InvitTask<double> *, int, int, int, int, cudaStream_t);
+template void launch_invit<float>(const InvitTask<float> *, int, int, int, int, cudaStream_t);
 template void launch_trunc_big_mode<double>(const TruncTask<double> *, int, int *, double, int, int, int,
                                             cudaStream_t);
 template void launch_trunc_big_mode<float>(const TruncTask<float> *, int, int *, double, int, int, int,
