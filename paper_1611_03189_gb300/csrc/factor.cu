@@ -18,7 +18,7 @@
 //
 // One executor (execute) drives one problem or many independent ones in lock
 // step: at every step (level from the leaves, wave) all problems that have it
-// share the launches.  Truncations of nodes with m >= 200 spread their
+// share the launches.  Truncations of nodes with m >= 128 spread their
 // tridiagonalisation over the GPU (trunc_grid); Cholesky factors above the
 // shared-memory limit are blocked (Exec::chol_inv_blocked).
 #include <algorithm>
@@ -299,7 +299,7 @@ inline int grid_tridiag_min() {
   static const int v = [] {
     const char *e = std::getenv("HS_GRID_TRIDIAG_MIN");
     const int x = e ? std::atoi(e) : 0;
-    return x > 3 ? x : 200;
+    return x > 3 ? x : 128;
   }();
   return v;
 }
