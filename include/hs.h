@@ -250,6 +250,13 @@ const char *hs_last_error(void);
  * process so far (all handles, all threads). */
 int64_t hs_launch_count(void);
 
+/* hs_abi_sizes: sizeof of the ABI structs as this library was compiled --
+ * sizes[0] hs_csr, [1] hs_clustering, [2] hs_opts, [3] hs_info -- so that a
+ * binding can check its own struct layouts (no device needed).  Writes
+ * min(cap, 4) entries and returns the number of structs (4).  A build check;
+ * the paper has no counterpart. */
+int hs_abi_sizes(int64_t *sizes, int32_t cap);
+
 /* ---------------------------------------------------------------------------
  * Symbolic planner (host only; no device needed).  The elimination order is
  * "a given ordering" of super nodes (Sec. 3.2); this library uses canonical

@@ -38,7 +38,7 @@ STATUS_NAMES = {
 # every symbol include/hs.h declares
 EXPORTS = [
     "hs_factor_create", "hs_factor_refactor", "hs_factor_create_batch", "hs_factor_refactor_batch",
-    "hs_launch_count", "hs_profile_phases", "hs_apply", "hs_apply_static", "hs_pcg", "hs_factor_info", "hs_factor_ranks",
+    "hs_launch_count", "hs_profile_phases", "hs_abi_sizes", "hs_apply", "hs_apply_static", "hs_pcg", "hs_factor_info", "hs_factor_ranks",
     "hs_factor_destroy", "hs_last_error", "hs_plan_create", "hs_plan_level_waves",
     "hs_plan_super_lists", "hs_plan_destroy",
 ]
@@ -101,6 +101,7 @@ def lib():
         L.hs_factor_refactor_batch.argtypes = [i32, C.POINTER(vp), vp, vp, vp]
         L.hs_launch_count.argtypes = []
         L.hs_profile_phases.argtypes = [i32]
+        L.hs_abi_sizes.argtypes = [vp, i32]
         L.hs_apply.argtypes = [vp, vp, vp, i32, i64, vp]
         L.hs_apply_static.argtypes = [vp, vp, vp, i32, i64, vp]
         L.hs_pcg.argtypes = [vp, vp, vp, i32, i64, dbl, i32, vp, vp, vp]

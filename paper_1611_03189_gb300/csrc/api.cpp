@@ -322,6 +322,13 @@ int hs_factor_refactor_batch(int32_t count, hs_factor *f, const double *const *v
 
 int64_t hs_launch_count(void) { return hs::g_launches.load(); }
 
+int hs_abi_sizes(int64_t *sizes, int32_t cap) {
+  const int64_t v[4] = {(int64_t)sizeof(hs_csr), (int64_t)sizeof(hs_clustering), (int64_t)sizeof(hs_opts),
+                        (int64_t)sizeof(hs_info)};
+  for (int32_t i = 0; i < cap && i < 4 && sizes; ++i) sizes[i] = v[i];
+  return 4;
+}
+
 int hs_profile_phases(int32_t on) {
   hs::set_phase_profiling(on != 0);
   return HS_OK;

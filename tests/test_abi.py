@@ -34,6 +34,18 @@ def test_exports_every_declared_symbol(lib):
         assert hasattr(lib, name)
 
 
+def test_binding_structs_match_the_compiled_abi(lib):
+    """The ctypes mirrors of hs_csr, hs_clustering, hs_opts and hs_info have the
+    sizes the library was compiled with (a field added on one side only would
+    shift every later field)."""
+    import ctypes as C
+
+    sizes = np.zeros(4, dtype=np.int64)
+    assert lib.hs_abi_sizes(sizes.ctypes.data, 4) == 4
+    mine = [C.sizeof(_lib.HsCsr), C.sizeof(_lib.HsClustering), C.sizeof(_lib.HsOpts), C.sizeof(_lib.HsInfo)]
+    assert sizes.tolist() == mine
+
+
 PLAN_CASES = [
     ("poisson2d 32 leaf8", lambda: P.poisson2d(32, leaf_size=8)),
     ("poisson2d 64 leaf16", lambda: P.poisson2d(64, leaf_size=16)),
