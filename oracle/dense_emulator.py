@@ -20,32 +20,47 @@ import math
 
 import numpy as np
 
-LORASP, GC_CONSTANT, GC_USER = 0, 1, 2
+LORASP, GC_CONSTANT, GC_USER, GC_PROJ = 0, 1, 2, 3
 
 
 def _orth_phi(phi_s, a):
+    # candidates: every column of phi_s, then every column of a (Sec. 6, one or
+    # several preserved vectors)
+    m = len(phi_s)
+    cand = list(np.reshape(phi_s, (m, -1)).T) + list(np.reshape(a, (m, -1)).T)
     cols = []
-    if np.linalg.norm(phi_s) > 0:
-        cols.append(phi_s / np.linalg.norm(phi_s))
-    na = np.linalg.norm(a)
-    if na > 0:
-        v = a.copy()
-        for _ in range(2):
-            for u in cols:
-                v -= u * (u @ v)
-        if np.linalg.norm(v) > 1e-12 * na:
+    for c in cand:
+        nc = np.linalg.norm(c)
+        if nc == 0:
+            continue
+        v = np.array(c, dtype=float)
+        if cols:
+            for _ in range(2):
+                for u in cols:
+                    v -= u * (u @ v)
+        if np.linalg.norm(v) > 1e-12 * nc:
             cols.append(v / np.linalg.norm(v))
-    return np.array(cols).T.reshape(len(phi_s), len(cols))
+    return np.array(cols).T.reshape(m, len(cols))
 
 
-def _truncate(B, eps, variant, phi_s, phi_w):
+def _proj_phi(phi_s, a, eps1):
+    # Appendix B, one-sided projection: dominant left singular subspace of [X_s, A_sw X_w]
+    m = len(phi_s)
+    C = np.hstack([np.reshape(phi_s, (m, -1)), np.reshape(a, (m, -1))])
+    u, sv, _ = np.linalg.svd(C, full_matrices=False)
+    if sv[0] == 0:
+        return np.zeros((m, 0))
+    return u[:, : int(np.sum(sv > max(eps1, 1e-12) * sv[0]))]
+
+
+def _truncate(B, eps, variant, phi_s, phi_w, eps1=0.0):
     m = B.shape[0]
     if variant == LORASP:
         if eps == 0:
             return np.eye(m)
         u, sv, _ = np.linalg.svd(B)
         return u[:, : int(np.sum(sv > eps * sv[0]))]
-    U1 = _orth_phi(phi_s, B @ phi_w)
+    U1 = _proj_phi(phi_s, B @ phi_w, eps1) if variant == GC_PROJ else _orth_phi(phi_s, B @ phi_w)
     if eps == 0:
         q, _ = np.linalg.qr(np.hstack([U1, np.eye(m)]))
         return np.hstack([U1, q[:, U1.shape[1]:m]])
@@ -58,7 +73,7 @@ def _truncate(B, eps, variant, phi_s, phi_w):
 class DenseEmulator:
     """Dense extended-system factorization; `solve(b)` returns A_H^-1 b."""
 
-    def __init__(self, A_dense, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None):
+    def __init__(self, A_dense, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None, eps1=0.0):
         n = A_dense.shape[0]
         perm = np.asarray(perm)
         self.perm = perm
@@ -73,7 +88,8 @@ class DenseEmulator:
             return bool(pattern[np.ix_(np.concatenate([cells[a] for a in la]),
                                        np.concatenate([cells[b] for b in lb]))].any())
 
-        phi0 = np.ones(n) if variant != GC_USER else np.asarray(phi)[perm]
+        self.eps1 = eps1
+        phi0 = np.asarray(phi, dtype=float)[perm] if variant in (GC_USER, GC_PROJ) else np.ones(n)
         # current system: matrix K over unknowns; groups: key -> (index list, leaf set)
         K = Ap.copy()
         vphi = phi0.copy()
@@ -123,7 +139,7 @@ class DenseEmulator:
         rest = [i for i in range(total) if i not in set(Is)]
         if W:
             B = K[np.ix_(Is, Iw)]
-            U = _truncate(B, eps, variant, vphi[Is], vphi[Iw])
+            U = _truncate(B, eps, variant, vphi[Is], vphi[Iw], self.eps1)
         else:
             U = np.zeros((m, 0))
         k = U.shape[1]

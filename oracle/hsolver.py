@@ -29,7 +29,9 @@ design notes):
      truncation: the red node keeps a complete orthonormal basis (k = m).
   R3 GC basis: modified Gram-Schmidt with one re-orthogonalisation;
      u_1 = phi_s/||phi_s||, u_2 added only when the remainder of A_sw phi_w
-     exceeds 1e-12 ||A_sw phi_w||.
+     exceeds 1e-12 ||A_sw phi_w||.  With several preserved vectors (phi an
+     m x p matrix) the candidates are the columns of phi_s, then those of
+     A_sw phi_w, each kept under the same rule.
   R4 elimination order ("a given ordering", Sec. 3.2): canonical waves.  Within
      a level, repeatedly take, in ascending super-node index, a maximal set of
      super nodes no two of which share a block; eliminate that set, repeat.
@@ -43,6 +45,13 @@ design notes):
      leaves, down to 2) play level l with l_max = L, and the tolerance list is
      indexed by j = L - l (levels above the leaves), so one list serves problems
      of different depth.
+  R12 Appendix B, first-order one-sided projection (variant GC_PROJ): U_1 are
+     the left singular vectors of C = [X_s, A_sw X_w] with
+     sigma_i > max(eps1, 1e-12) sigma_1(C) (the 1e-12 floor drops the
+     rounding-level directions of dependent columns, as R3 does); U_2 and the
+     threshold eps ||A_sw||_2 are those of GC.  The appendix does not say what
+     the parent red node keeps of X: as in Sec. 6, X_r = U^T X_s.  The caller
+     passes the columns of X already scaled (e_i / lambda_i in the appendix).
 
 Node keys inside a level: super node i -> i, red node made from super node i ->
 nsup + i.  Blocks are stored in both orientations, kept consistent.
@@ -58,6 +67,7 @@ import scipy.linalg as sla
 LORASP = 0
 GC_CONSTANT = 1
 GC_USER = 2
+GC_PROJ = 3  # Appendix B, first-order one-sided projection (R12)
 
 MGS_DROP = 1e-12  # R3
 
@@ -70,25 +80,50 @@ class NotSPD(RuntimeError):
 # compression (Sec. 3.2 eq. local_compression; Sec. 6 eq. preserve)
 # ---------------------------------------------------------------------------
 
+def _columns(x) -> np.ndarray:
+    """A vector or an m x p matrix as an m x p matrix."""
+    x = np.asarray(x, dtype=np.float64)
+    return x.reshape(x.shape[0], -1)
+
+
 def gc_basis(phi_s: np.ndarray, a: np.ndarray) -> np.ndarray:
-    """Orthonormal U_1 spanning [phi_s, a] by MGS with one re-orthogonalisation (R3)."""
-    m = phi_s.shape[0]
+    """Orthonormal U_1 spanning [phi_s, a] by MGS with one re-orthogonalisation (R3).
+
+    phi_s and a = A_sw phi_w are vectors, or m x p matrices when p vectors are
+    preserved; the candidates are phi_s's columns, then a's, and one is kept
+    when its remainder exceeds MGS_DROP times its norm."""
+    P = _columns(phi_s)
+    m = P.shape[0]
     cols = []
-    nphi = float(np.linalg.norm(phi_s))
-    if nphi > 0.0:
-        cols.append(phi_s / nphi)
-    na = float(np.linalg.norm(a))
-    if na > 0.0:
-        v = a.copy()
-        for _ in range(2):
+    for c in np.hstack([P, _columns(a)]).T:
+        nc = float(np.linalg.norm(c))
+        if nc == 0.0:
+            continue
+        v = c.copy()
+        for _ in range(2 if cols else 0):
             for u in cols:
                 v = v - u * float(u @ v)
         nv = float(np.linalg.norm(v))
-        if nv > MGS_DROP * na:
+        if nv > MGS_DROP * nc:
             cols.append(v / nv)
     if not cols:
         return np.zeros((m, 0))
     return np.column_stack(cols)
+
+
+def proj_basis(C: np.ndarray, eps1: float) -> np.ndarray:
+    """Appendix B (first-order one-sided projection), first truncated SVD: the
+    left singular vectors of C = [X_s, A_sw X_w] with
+    sigma_i > max(eps1, MGS_DROP) sigma_1(C) (R12)."""
+    C = _columns(C)
+    m = C.shape[0]
+    if C.size == 0:
+        return np.zeros((m, 0))
+    Uc, sc, _ = np.linalg.svd(C, full_matrices=False)
+    if sc[0] == 0.0:
+        return np.zeros((m, 0))
+    k = int(np.count_nonzero(sc > max(eps1, MGS_DROP) * sc[0]))
+    return Uc[:, :k].copy()
 
 
 def complete_basis(U1: np.ndarray, m: int) -> np.ndarray:
@@ -99,12 +134,14 @@ def complete_basis(U1: np.ndarray, m: int) -> np.ndarray:
     return V[:, w > 0.5]
 
 
-def compress(B: np.ndarray, eps: float, variant: int, phi_s=None, phi_w=None):
+def compress(B: np.ndarray, eps: float, variant: int, phi_s=None, phi_w=None, eps1: float = 0.0):
     """Return U (m x k, orthonormal columns) for the well-separated block B = A_sw.
 
     LoRaSp: leading left singular vectors of B with sigma_i > eps ||B||_2.
     GC: U = [U_1, U_2], U_1 = orth[phi_s, B phi_w], U_2 = leading left singular
     vectors of (I - U_1 U_1^T) B with sigma_i > eps ||B||_2.
+    GC_PROJ (Appendix B): as GC, with U_1 the left singular vectors of
+    [phi_s, B phi_w] above eps1 times its norm (R12).
     """
     m = B.shape[0]
     if m == 0:
@@ -116,7 +153,10 @@ def compress(B: np.ndarray, eps: float, variant: int, phi_s=None, phi_w=None):
         normB = sb[0] if sb.size else 0.0
         k = int(np.count_nonzero(sb > eps * normB))
         return Ub[:, :k].copy()
-    U1 = gc_basis(phi_s, B @ phi_w)
+    if variant == GC_PROJ:
+        U1 = proj_basis(np.hstack([_columns(phi_s), _columns(B @ phi_w)]), eps1)
+    else:
+        U1 = gc_basis(phi_s, B @ phi_w)
     if eps == 0.0:
         return np.hstack([U1, complete_basis(U1, m)])
     normB = float(np.linalg.svd(B, compute_uv=False)[0]) if B.size else 0.0
@@ -243,16 +283,18 @@ def eps_schedule_lorasp(eps: float, L: int, h: float) -> list:
 
 
 def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None,
-           order="waves", keep_U=False, eps_level=None) -> Factor:
+           order="waves", keep_U=False, eps_level=None, eps1=0.0) -> Factor:
     """Hierarchical factorization.
 
     n, rowptr, col, val: CSR of the SPD matrix A in original ordering.
     perm, leaf_ptr: clustering; perm[p] = original index of unknown p.
-    eps: truncation tolerance (R2).  variant: LORASP, GC_CONSTANT or GC_USER.
+    eps: truncation tolerance (R2).  variant: LORASP, GC_CONSTANT, GC_USER or
+        GC_PROJ (Appendix B; eps1 is its first tolerance, R12).
     eps_level: optional per-level tolerances (Sec. 7 adaptive choice): entry j
         is used instead of eps for the super nodes j levels above the leaves
         (level L - j); it needs L - 1 entries.
-    phi: for GC_USER, the vector to preserve (original ordering).
+    phi: for GC_USER and GC_PROJ, the vector to preserve (original ordering),
+        or an n x p array of p vectors.
     order: "waves" (R4), "waves-reversed" (same waves, each eliminated in
         descending order) or "sequential" (ascending super index, one at a time).
     """
@@ -264,8 +306,8 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
     if 2 ** L != nleaf:
         raise ValueError("number of leaves must be a power of two")
     blocks, leaf_adj = _leaf_blocks(n, rowptr, col, val, perm, leaf_ptr)
-    use_phi = variant in (GC_CONSTANT, GC_USER)
-    if variant == GC_USER:
+    use_phi = variant in (GC_CONSTANT, GC_USER, GC_PROJ)
+    if variant in (GC_USER, GC_PROJ):
         phi_perm = np.asarray(phi, dtype=np.float64)[perm]
     else:
         phi_perm = np.ones(n)
@@ -349,7 +391,7 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
             # eliminates each wave in descending order to test exactly that
             for s in (reversed(wave) if order == "waves-reversed" else wave):
                 rec = _eliminate(s, nsup, blocks, nbr_of, size, vphi, adjacent, eps_l,
-                                 variant, use_phi, widx, keep_U)
+                                 variant, use_phi, widx, keep_U, eps1)
                 records.append(rec)
                 if rec.wsep:
                     new_red_size[s] = rec.k
@@ -400,7 +442,7 @@ def _set_block(blocks, nbr_of, x, y, blk):
 
 
 def _eliminate(s, nsup, blocks, nbr_of, size, vphi, adjacent, eps, variant, use_phi, widx,
-               keep_U):
+               keep_U, eps1=0.0):
     """Compress, extend and eliminate super node s (Sec. 3.2)."""
     m = size[s]
     others = sorted(nbr_of.get(s, ()))
@@ -413,7 +455,7 @@ def _eliminate(s, nsup, blocks, nbr_of, size, vphi, adjacent, eps, variant, use_
         B = np.hstack([blocks[(s, w)] for w in W]) if m else np.zeros((0, sum(size[w] for w in W)))
         if use_phi:
             phi_w = np.concatenate([vphi[w] for w in W])
-            U = compress(B, eps, variant, vphi[s], phi_w)
+            U = compress(B, eps, variant, vphi[s], phi_w, eps1)
         else:
             U = compress(B, eps, variant)
     else:

@@ -1,0 +1,181 @@
+"""Pins of the oracle for several preserved vectors (Sec. 6 with p > 1) and the
+Appendix B first-order one-sided projection (variant GC_PROJ).
+
+* Several vectors (Sec. 6): every preserved vector phi_i with A phi_i =
+  lambda_i phi_i comes back exactly, A_H^-1 phi_i = phi_i / lambda_i; a vector
+  that was not preserved does not.
+* The dense extended-system emulator, which recomputes every compression from
+  its own dense blocks, gives the same A_H^-1 with several vectors and with the
+  projection variant.
+* Appendix B bounds of the one-sided projection on a random block: the
+  inequalities the appendix derives for B - B~ on X_s and on X_w, and the
+  eps_2 bound on the whole block.
+* eps1 = 0 keeps the whole span of [X_s, A_sw X_w]: the projection variant then
+  preserves its vectors exactly and equals GC with the same vectors.
+"""
+import numpy as np
+import pytest
+
+from oracle import hsolver as H
+from oracle.dense_emulator import DenseEmulator
+from paper_1611_03189_gb300 import problems as P
+
+MODES = [(1, 1), (2, 1), (1, 2)]
+
+
+def _factor(pb, eps, variant, **kw):
+    return H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, eps, variant, **kw)
+
+
+def _eig(nx, modes=MODES):
+    """Columns: the (j, k) eigenvectors of the 5-point Laplacian; their eigenvalues."""
+    V = np.column_stack([P.laplacian_eigvec_2d(nx, nx, j, k) for j, k in modes])
+    lam = np.array([P.laplacian_eigval_2d(nx, nx, j, k) for j, k in modes])
+    return V, lam
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_gc_user_preserves_several_eigenvectors():
+    nx = 24
+    pb = P.poisson2d(nx, leaf_size=8)
+    V, lam = _eig(nx)
+    F = _factor(pb, 0.2, H.GC_USER, phi=V)
+    Z = H.apply(F, V)
+    for i in range(V.shape[1]):
+        assert _rel(Z[:, i], V[:, i] / lam[i]) <= 1e-11
+    # negative control: preserving only the first one leaves the others approximate
+    F1 = _factor(pb, 0.2, H.GC_USER, phi=V[:, 0])
+    Z1 = H.apply(F1, V)
+    assert _rel(Z1[:, 0], V[:, 0] / lam[0]) <= 1e-11
+    assert _rel(Z1[:, 1], V[:, 1] / lam[1]) > 1e-6
+    assert _rel(Z1[:, 2], V[:, 2] / lam[2]) > 1e-6
+
+
+def test_constant_and_eigenvector_together():
+    nx = 16
+    pb = P.poisson2d(nx, leaf_size=4)
+    V, lam = _eig(nx, [(1, 1)])
+    Phi = np.column_stack([np.ones(pb.n), V[:, 0]])
+    F = _factor(pb, 0.3, H.GC_USER, phi=Phi)
+    A = pb.to_scipy()
+    assert np.linalg.norm(H.apply(F, A @ np.ones(pb.n)) - 1.0) <= 1e-11 * np.sqrt(pb.n)
+    assert _rel(H.apply(F, V[:, 0]), V[:, 0] / lam[0]) <= 1e-11
+
+
+def test_one_column_matrix_is_the_vector():
+    nx = 16
+    pb = P.poisson2d(nx, leaf_size=4)
+    v = P.laplacian_eigvec_2d(nx, nx)
+    b = P.rhs(pb.n, 3)
+    z1 = H.apply(_factor(pb, 0.1, H.GC_USER, phi=v), b)
+    z2 = H.apply(_factor(pb, 0.1, H.GC_USER, phi=v[:, None]), b)
+    assert _rel(z2, z1) <= 1e-13
+
+
+@pytest.mark.parametrize("variant,eps1", [(H.GC_USER, 0.0), (H.GC_PROJ, 0.05)])
+def test_emulator_several_vectors(variant, eps1):
+    nx = 12
+    pb = P.poisson2d(nx, leaf_size=4)
+    V, lam = _eig(nx)
+    X = V / lam if variant == H.GC_PROJ else V
+    A = pb.to_scipy().toarray()
+    F = _factor(pb, 0.2, variant, phi=X, eps1=eps1)
+    E = DenseEmulator(A, pb.perm, pb.leaf_ptr, 0.2, variant, phi=X, eps1=eps1)
+    I = np.eye(pb.n)
+    Z1 = H.apply(F, I)
+    Z2 = np.column_stack([E.solve(e) for e in I])
+    assert np.abs(Z1 - Z2).max() <= 1e-12 * np.abs(Z1).max()
+    assert np.abs(Z1 @ A - I).max() > 1e-6
+
+
+def test_gc_basis_several_vectors_drops_dependent_columns():
+    m = 8
+    rng = np.random.default_rng(5)
+    phi = np.column_stack([np.ones(m), rng.standard_normal(m)])
+    # a's first column lies in span(phi): dropped; its second is new
+    a = np.column_stack([2.0 * phi[:, 0] - phi[:, 1], rng.standard_normal(m)])
+    U1 = H.gc_basis(phi, a)
+    assert U1.shape == (m, 3)
+    assert np.allclose(U1.T @ U1, np.eye(3), atol=1e-14)
+    for c in np.hstack([phi, a]).T:
+        assert np.linalg.norm(c - U1 @ (U1.T @ c)) <= 1e-13 * np.linalg.norm(c)
+    # zero columns are skipped
+    assert H.gc_basis(np.zeros((m, 2)), a[:, 1:]).shape == (m, 1)
+
+
+def _lowrankish(m, w, seed, decay=0.7):
+    rng = np.random.default_rng(seed)
+    Q1, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((w, m)))
+    return (Q1 * decay ** np.arange(m)) @ Q2.T
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("eps1,eps2", [(1e-2, 1e-1), (1e-3, 1e-2), (0.05, 0.3)])
+def test_one_sided_projection_bounds(seed, eps1, eps2):
+    """Appendix B, first-order one-sided projection, with B = A_sw here (the
+    appendix's B^T): U = [U_1, U_2] satisfies
+      ||(I - U_1 U_1^T) C|| <= eps1 ||C||, C = [X_s, A_sw X_w], minimal;
+      ||A_sw - U U^T A_sw|| <= eps2 ||A_sw||;
+      ||(I - U U^T) A_sw X_w|| <= min(eps1 ||C||, eps2 ||A_sw|| ||X_w||);
+      ||A_sw^T (I - U U^T) X_s|| <= eps1 eps2 ||A_sw|| ||C||."""
+    rng = np.random.default_rng(200 + seed)
+    m, w = 20, 50
+    B = _lowrankish(m, w, seed)
+    Xs = rng.standard_normal((m, 3)) / np.array([1.0, 3.0, 10.0])
+    Xw = rng.standard_normal((w, 3)) / np.array([1.0, 3.0, 10.0])
+    C = np.hstack([Xs, B @ Xw])
+    nC, nB = np.linalg.norm(C, 2), np.linalg.norm(B, 2)
+    U1 = H.proj_basis(C, eps1)
+    sv = np.linalg.svd(C, compute_uv=False)
+    assert U1.shape[1] == int(np.sum(sv > eps1 * sv[0]))
+    assert np.linalg.norm(C - U1 @ (U1.T @ C), 2) <= eps1 * nC * (1 + 1e-12)
+    U = H.compress(B, eps2, H.GC_PROJ, Xs, Xw, eps1)
+    k = U.shape[1]
+    assert np.allclose(U.T @ U, np.eye(k), atol=1e-13)
+    assert np.allclose(U[:, : U1.shape[1]].T @ U1 @ U1.T @ U[:, : U1.shape[1]], np.eye(U1.shape[1]), atol=1e-12)
+    R = np.eye(m) - U @ U.T
+    tol = 1 + 1e-10
+    assert np.linalg.norm(R @ B, 2) <= eps2 * nB * tol
+    assert np.linalg.norm(R @ B @ Xw, 2) <= min(eps1 * nC, eps2 * nB * np.linalg.norm(Xw, 2)) * tol
+    assert np.linalg.norm(B.T @ R @ Xs, 2) <= eps1 * eps2 * nB * nC * tol
+
+
+def test_projection_eps1_zero_is_gc_with_the_same_vectors():
+    nx = 24
+    pb = P.poisson2d(nx, leaf_size=8)
+    V, lam = _eig(nx, [(1, 1), (2, 1)])
+    X = V / lam
+    Fp = _factor(pb, 0.2, H.GC_PROJ, phi=X, eps1=0.0)
+    Fg = _factor(pb, 0.2, H.GC_USER, phi=X)
+    b = P.rhs(pb.n, 6)
+    assert _rel(H.apply(Fp, b), H.apply(Fg, b)) <= 1e-10
+    Z = H.apply(Fp, V)
+    for i in range(2):
+        assert _rel(Z[:, i], V[:, i] / lam[i]) <= 1e-11
+
+
+def test_projection_improves_low_modes_over_lorasp():
+    """With eps1 > 0 the low modes are only approximately kept, but far better
+    than by LoRaSp at the same eps (the appendix's purpose), and PCG needs
+    fewer iterations."""
+    nx = 32
+    pb = P.poisson2d(nx, leaf_size=8)
+    V, lam = _eig(nx)
+    Fp = _factor(pb, 0.1, H.GC_PROJ, phi=V / lam, eps1=0.05)
+    Fl = _factor(pb, 0.1, H.LORASP)
+    errs = []
+    for i in range(V.shape[1]):
+        ep = _rel(H.apply(Fp, V[:, i]), V[:, i] / lam[i])
+        el = _rel(H.apply(Fl, V[:, i]), V[:, i] / lam[i])
+        assert ep < 0.1 * el
+        errs.append(ep)
+    # eps1 = 0.05 does truncate: the modes are kept approximately, not exactly
+    assert max(errs) > 1e-8
+    b = P.rhs(pb.n, 1)
+    ip = H.pcg(Fp, pb.rowptr, pb.col, pb.val, b)[1]
+    il = H.pcg(Fl, pb.rowptr, pb.col, pb.val, b)[1]
+    assert ip < il
