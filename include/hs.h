@@ -45,8 +45,13 @@ typedef enum {
 enum {
   HS_LORASP = 0,       /* truncated SVD of A_sw only (Sec. 3.2)                  */
   HS_GC_CONSTANT = 1,  /* GC: also preserve the constant vector (Sec. 6, Sec. 7) */
-  HS_GC_USER = 2       /* GC: preserve a caller-supplied vector phi (Sec. 6)     */
+  HS_GC_USER = 2,      /* GC: preserve caller-supplied vectors phi (Sec. 6)      */
+  HS_GC_PROJ = 3       /* Appendix B, first-order one-sided projection: U_1 from
+                          the truncated SVD of [X_s, A_sw X_w] at eps1, then GC */
 };
+
+/* Most preserved vectors per problem (n_phi) for HS_GC_USER and HS_GC_PROJ. */
+#define HS_MAX_PHI 4
 
 /* Arithmetic of the factorization (north of the factor: the PCG is always FP64). */
 enum {
@@ -84,15 +89,24 @@ typedef struct {
  *   truncation (every red node keeps a complete basis; the factorization is
  *   then exact).  0 < eps < 1e-6 is rejected (HS_ERR_INVALID): the Gram-matrix
  *   eigen-solve cannot resolve singular values that small.
- * variant: HS_LORASP, HS_GC_CONSTANT or HS_GC_USER.
- * phi: HOST pointer, n doubles in the ORIGINAL ordering, used by HS_GC_USER.
+ * variant: HS_LORASP, HS_GC_CONSTANT, HS_GC_USER or HS_GC_PROJ.
+ * phi: HOST pointer, n_phi vectors of n doubles each (vector j at phi + j*n),
+ *   in the ORIGINAL ordering; used by HS_GC_USER (vectors preserved exactly,
+ *   Sec. 6) and HS_GC_PROJ (the scaled vectors X of Appendix B, e.g.
+ *   e_i / lambda_i, kept approximately).  Required by both.
  * factor_prec: HS_PREC_F64 or HS_PREC_F32.
  * eps_level: NULL, or a HOST array of tolerances per level for the adaptive
  *   choice of Sec. 7 (Table 3).  Entry j replaces eps for the super nodes j
  *   levels above the leaves (j = 0: the pairs of leaves); a problem with 2^L
  *   leaves reads entries 0 .. L-2, and n_eps_level must cover them.  Each
  *   entry obeys the rules of eps.  The same list serves problems of different
- *   depth in hs_factor_create_batch. */
+ *   depth in hs_factor_create_batch.
+ * n_phi: number of vectors in phi, 1 .. HS_MAX_PHI (0 reads as 1); must be
+ *   1 or 0 for HS_LORASP and HS_GC_CONSTANT.
+ * eps1: HS_GC_PROJ's first tolerance (Appendix B, eps_1 <= eps_2 = eps): U_1
+ *   keeps the left singular vectors of [X_s, A_sw X_w] with
+ *   sigma_i > max(eps1, 1e-12) * sigma_1.  Finite and >= 0; ignored by the
+ *   other variants. */
 typedef struct {
   double eps;
   int32_t variant;
@@ -100,6 +114,8 @@ typedef struct {
   const double *phi;
   const double *eps_level;
   int32_t n_eps_level;
+  int32_t n_phi;
+  double eps1;
 } hs_opts;
 
 /* Sizes and counters of a factorization (all host values). */
@@ -163,8 +179,9 @@ int hs_factor_refactor(hs_factor f, const double *val, void *stream);
  *     hs_factor_create).
  *   opts: one set for all problems (eps, variant, factor_prec).  opts->phi is
  *     ignored.
- *   phi: per-problem preserved vectors (HOST, n_p doubles each) for
- *     HS_GC_USER; otherwise it may be NULL.
+ *   phi: per-problem preserved vectors (HOST, opts->n_phi vectors of n_p
+ *     doubles each, laid out as opts->phi) for HS_GC_USER and HS_GC_PROJ;
+ *     otherwise it may be NULL.
  *   out: `count` handles, each used and destroyed like one from
  *     hs_factor_create.
  *   status: NULL, or `count` ints that receive each problem's own result.

@@ -26,6 +26,8 @@ HS_ERR_CUDA = 7
 HS_LORASP = 0
 HS_GC_CONSTANT = 1
 HS_GC_USER = 2
+HS_GC_PROJ = 3
+HS_MAX_PHI = 4
 
 HS_PREC_F64 = 0
 HS_PREC_F32 = 1
@@ -61,7 +63,17 @@ class HsClustering(C.Structure):
 
 class HsOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("variant", C.c_int32), ("factor_prec", C.c_int32),
-                ("phi", C.c_void_p), ("eps_level", C.c_void_p), ("n_eps_level", C.c_int32)]
+                ("phi", C.c_void_p), ("eps_level", C.c_void_p), ("n_eps_level", C.c_int32),
+                ("n_phi", C.c_int32), ("eps1", C.c_double)]
+
+
+def _phi_block(phi):
+    """Preserved vectors as hs_opts wants them: an n-vector, or an n x p array
+    (one vector per column) -> (p x n C-contiguous float64, p)."""
+    a = np.asarray(phi, dtype=np.float64)
+    if a.ndim == 1:
+        return np.ascontiguousarray(a), 1
+    return np.ascontiguousarray(a.T), int(a.shape[1])
 
 
 class HsInfo(C.Structure):
@@ -195,11 +207,13 @@ class Factor:
     """hs_factor_create / hs_apply / hs_pcg on torch CUDA tensors.
 
     rowptr, col: int32 CUDA tensors; val: float64 CUDA tensor (original order).
-    perm, leaf_ptr: host int32 arrays (clustering).  phi: host float64 (GC user).
+    perm, leaf_ptr: host int32 arrays (clustering).  phi: host float64, an
+    n-vector or n x p (p <= HS_MAX_PHI vectors), for HS_GC_USER / HS_GC_PROJ.
+    eps1: HS_GC_PROJ's first tolerance.
     """
 
     def __init__(self, rowptr, col, val, perm, leaf_ptr, eps, variant=HS_GC_CONSTANT,
-                 prec=HS_PREC_F64, phi=None, stream=None, eps_level=None):
+                 prec=HS_PREC_F64, phi=None, stream=None, eps_level=None, eps1=0.0):
         import torch
 
         assert rowptr.is_cuda and col.is_cuda and val.is_cuda
@@ -207,12 +221,13 @@ class Factor:
         self.n = int(rowptr.numel() - 1)
         self._perm = np.ascontiguousarray(perm, dtype=np.int32)
         self._lp = np.ascontiguousarray(leaf_ptr, dtype=np.int32)
-        self._phi = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+        self._phi, nphi = (None, 0) if phi is None else _phi_block(phi)
         A = HsCsr(self.n, int(col.numel()), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
         cl = HsClustering(_ptr(self._perm), _ptr(self._lp), len(self._lp) - 1)
         self._epsl = None if eps_level is None else np.ascontiguousarray(eps_level, dtype=np.float64)
         o = HsOpts(float(eps), int(variant), int(prec), None if self._phi is None else _ptr(self._phi),
-                   None if self._epsl is None else _ptr(self._epsl), 0 if self._epsl is None else len(self._epsl))
+                   None if self._epsl is None else _ptr(self._epsl), 0 if self._epsl is None else len(self._epsl),
+                   nphi, float(eps1))
         h = C.c_void_p()
         self._h = None
         check(lib().hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), _stream_ptr(stream), C.byref(h)))
@@ -277,7 +292,7 @@ class Factor:
 
 
 def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=None, stream=None,
-                 eps_level=None):
+                 eps_level=None, eps1=0.0):
     """hs_factor_create_batch over `problems`: a list of (rowptr, col, val,
     perm, leaf_ptr) with rowptr/col int32 and val float64 CUDA tensors and
     perm/leaf_ptr host arrays.  Returns (factors, status): one Factor per
@@ -297,14 +312,18 @@ def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=N
         A[p] = HsCsr(int(rp.numel() - 1), int(ci.numel()), rp.data_ptr(), ci.data_ptr(), va.data_ptr())
         cl[p] = HsClustering(_ptr(pe), _ptr(lpa), len(lpa) - 1)
     phi_arr = None
+    nphi = 0
     if phis is not None:
-        ph = [np.ascontiguousarray(x, dtype=np.float64) for x in phis]
+        blocks = [_phi_block(x) for x in phis]
+        nphi = blocks[0][1]
+        assert all(b[1] == nphi for b in blocks), "every problem needs the same number of vectors"
+        ph = [b[0] for b in blocks]
         keep += ph
         phi_arr = (C.c_void_p * k)(*[_ptr(x) for x in ph])
     epsl = None if eps_level is None else np.ascontiguousarray(eps_level, dtype=np.float64)
     keep.append(epsl)
     o = HsOpts(float(eps), int(variant), int(prec), None, None if epsl is None else _ptr(epsl),
-               0 if epsl is None else len(epsl))
+               0 if epsl is None else len(epsl), nphi, float(eps1))
     out = (C.c_void_p * k)()
     status = np.zeros(k, dtype=np.int32)
     code = lib().hs_factor_create_batch(k, A, cl, C.byref(o), phi_arr, _stream_ptr(stream), out, _ptr(status))

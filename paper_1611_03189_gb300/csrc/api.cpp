@@ -162,6 +162,8 @@ void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, con
   h.prec = o->factor_prec;
   h.variant = o->variant;
   h.eps = o->eps;
+  h.nphi = (o->variant == HS_GC_USER || o->variant == HS_GC_PROJ) ? std::max(o->n_phi, 1) : 1;
+  h.eps1 = o->variant == HS_GC_PROJ ? o->eps1 : 0.0;
   h.eps_level.clear();
   // pattern to the host for the planner
   std::vector<int32_t> rp(A->n + 1), ci(A->nnz);
@@ -190,7 +192,12 @@ void check_opts(const hs_opts *o) {
   if (!o) fail(HS_ERR_INVALID, "null argument");
   if (!(o->eps >= 0.0) || !std::isfinite(o->eps)) fail(HS_ERR_INVALID, "eps must be finite and >= 0");
   if (o->eps > 0.0 && o->eps < 1e-6) fail(HS_ERR_INVALID, "0 < eps < 1e-6 is not supported");
-  if (o->variant < HS_LORASP || o->variant > HS_GC_USER) fail(HS_ERR_INVALID, "unknown variant");
+  if (o->variant < HS_LORASP || o->variant > HS_GC_PROJ) fail(HS_ERR_INVALID, "unknown variant");
+  const bool user = o->variant == HS_GC_USER || o->variant == HS_GC_PROJ;
+  if (o->n_phi < 0 || o->n_phi > (user ? HS_MAX_PHI : 1))
+    fail(HS_ERR_INVALID, user ? "n_phi must be 0 .. HS_MAX_PHI" : "n_phi > 1 needs HS_GC_USER or HS_GC_PROJ");
+  if (o->variant == HS_GC_PROJ && (!(o->eps1 >= 0.0) || !std::isfinite(o->eps1)))
+    fail(HS_ERR_INVALID, "eps1 must be finite and >= 0");
   if (o->factor_prec != HS_PREC_F64 && o->factor_prec != HS_PREC_F32) fail(HS_ERR_INVALID, "unknown factor_prec");
   if (o->eps_level) {
     if (o->n_eps_level < 0) fail(HS_ERR_INVALID, "n_eps_level < 0");
@@ -225,7 +232,8 @@ int hs_factor_create(const hs_csr *A, const hs_clustering *cl, const hs_opts *o,
     if (!A || !cl || !o || !out) fail(HS_ERR_INVALID, "null argument");
     *out = nullptr;
     hs::check_opts(o);
-    if (o->variant == HS_GC_USER && !o->phi) fail(HS_ERR_INVALID, "HS_GC_USER needs phi");
+    if ((o->variant == HS_GC_USER || o->variant == HS_GC_PROJ) && !o->phi)
+      fail(HS_ERR_INVALID, "HS_GC_USER and HS_GC_PROJ need phi");
     hs::require_device();
     cudaStream_t st = (cudaStream_t)stream;
     std::unique_ptr<hs_factor_s> f(new hs_factor_s());
@@ -243,14 +251,15 @@ int hs_factor_create_batch(int32_t count, const hs_csr *A, const hs_clustering *
     if (count < 1 || !A || !cl || !o || !out) fail(HS_ERR_INVALID, "null argument or count < 1");
     for (int32_t p = 0; p < count; ++p) out[p] = nullptr;
     hs::check_opts(o);
-    if (o->variant == HS_GC_USER && !phi) fail(HS_ERR_INVALID, "HS_GC_USER needs phi");
+    const bool user = o->variant == HS_GC_USER || o->variant == HS_GC_PROJ;
+    if (user && !phi) fail(HS_ERR_INVALID, "HS_GC_USER and HS_GC_PROJ need phi");
     hs::require_device();
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<std::unique_ptr<hs_factor_s>> fs;
     std::vector<hs::FactorHandle *> hs_;
     std::vector<const double *> vals, phis;
     for (int32_t p = 0; p < count; ++p) {
-      if (o->variant == HS_GC_USER && !phi[p]) fail(HS_ERR_INVALID, "HS_GC_USER needs phi for every problem");
+      if (user && !phi[p]) fail(HS_ERR_INVALID, "HS_GC_USER and HS_GC_PROJ need phi for every problem");
       fs.emplace_back(new hs_factor_s());
       try {
         hs::setup_handle(fs.back()->h, &A[p], &cl[p], o, st);
@@ -259,7 +268,7 @@ int hs_factor_create_batch(int32_t count, const hs_csr *A, const hs_clustering *
       }
       hs_.push_back(&fs.back()->h);
       vals.push_back(A[p].val);
-      phis.push_back(o->variant == HS_GC_USER ? phi[p] : nullptr);
+      phis.push_back(user ? phi[p] : nullptr);
     }
     std::vector<int> stat;
     std::vector<std::string> msgs;

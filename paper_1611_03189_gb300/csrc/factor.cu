@@ -692,12 +692,16 @@ void Run<T>::leaf_setup() {
     HS_CUDA(cudaMemcpyAsync(h_.d_leaf_dest, dest.data(), sizeof(int64_t) * P_.nnz, cudaMemcpyHostToDevice, st_));
     h_.leaf_total = total;
     if (use_phi_) {
-      // preserved vector of the leaves (GC): ones, or the caller's phi permuted
-      std::vector<T> ph(P_.n);
+      // preserved vectors of the leaves (GC): ones, or the caller's vectors
+      // permuted; n x nphi row-major (a node's rows are contiguous)
+      const int np = h_.nphi;
+      const bool user = h_.variant == HS_GC_USER || h_.variant == HS_GC_PROJ;
+      std::vector<T> ph((size_t)P_.n * np);
       for (int64_t p = 0; p < P_.n; ++p)
-        ph[p] = (h_.variant == HS_GC_USER) ? (T)phi_host_[P_.perm[p]] : T(1);
-      HS_CUDA(cudaMalloc(&h_.d_phi0, sizeof(T) * P_.n));
-      HS_CUDA(cudaMemcpyAsync(h_.d_phi0, ph.data(), sizeof(T) * P_.n, cudaMemcpyHostToDevice, st_));
+        for (int j = 0; j < np; ++j)
+          ph[(size_t)p * np + j] = user ? (T)phi_host_[(size_t)j * P_.n + P_.perm[p]] : T(1);
+      HS_CUDA(cudaMalloc(&h_.d_phi0, sizeof(T) * ph.size()));
+      HS_CUDA(cudaMemcpyAsync(h_.d_phi0, ph.data(), sizeof(T) * ph.size(), cudaMemcpyHostToDevice, st_));
     }
   }
   const int64_t total = h_.leaf_total;
@@ -715,7 +719,7 @@ void Run<T>::leaf_setup() {
   }
   phi_.assign(nleaf, nullptr);
   if (use_phi_)
-    for (int i = 0; i < nleaf; ++i) phi_[i] = (T *)h_.d_phi0 + lp[i];
+    for (int i = 0; i < nleaf; ++i) phi_[i] = (T *)h_.d_phi0 + (size_t)lp[i] * h_.nphi;
   // vector layout: level L segment = the permuted unknowns
   seg_off_ = 0;
   red_off_.assign(nleaf, 0);
@@ -780,18 +784,19 @@ void Run<T>::merge(int nred, int key_base, SumBatch<T> &sb) {
       sb.copy(sbk.ptr + (int64_t)coff[b] * sbk.ld + coff[a], sbk.ld, rsize[b], rsize[a], rb.ptr, rb.ld,
               1 - ta);
   }
-  // preserved vectors: contiguous per level
+  // preserved vectors (m x nphi row-major per node): contiguous per level
   std::vector<T *> nphi(2 * nsup, nullptr);
   if (use_phi_) {
+    const int np = h_.nphi;
     int64_t tot = 0;
     for (int j = 0; j < nsup; ++j) tot += std::max(ssize[j], 0);
-    T *v = talloc<T>(*h_.pers, tot);
+    T *v = talloc<T>(*h_.pers, tot * np);
     int64_t o = 0;
     for (int j = 0; j < nsup; ++j) {
       if (ssize[j] < 0) continue;
-      nphi[j] = v + o;
+      nphi[j] = v + o * np;
       for (int c = 2 * j; c <= 2 * j + 1; ++c)
-        if (rsize[c] > 0) sb.copy(v + o + coff[c], 1, rsize[c], 1, phi_[key_base + c], 1, 0);
+        if (rsize[c] > 0) sb.copy(v + (o + coff[c]) * np, np, rsize[c], np, phi_[key_base + c], np, 0);
       o += ssize[j];
     }
   }
@@ -857,10 +862,12 @@ void Run<T>::wave_a(int li, int widx, WaveBatches<T> &B) {
       x.G = talloc<T>(scr, (size_t)m * m);
       x.U = talloc<T>(scr, (size_t)m * m);
       if (use_phi_) {
-        x.phiW = talloc<T>(scr, x.dW);
-        x.a = talloc<T>(scr, m);
+        const int np = h_.nphi;
+        x.phiW = talloc<T>(scr, (size_t)x.dW * np);
+        x.a = talloc<T>(scr, (size_t)m * np);
         for (size_t j = 0; j < ps.W.size(); ++j)
-          if (size_[ps.W[j]] > 0) B.gather.copy(x.phiW + x.Woff[j], 1, size_[ps.W[j]], 1, phi_[ps.W[j]], 1, 0);
+          if (size_[ps.W[j]] > 0)
+            B.gather.copy(x.phiW + (size_t)x.Woff[j] * np, np, size_[ps.W[j]], np, phi_[ps.W[j]], np, 0);
       }
     }
     auto dit = blocks_.find(bkey(s, s));
@@ -868,11 +875,13 @@ void Run<T>::wave_a(int li, int widx, WaveBatches<T> &B) {
     B.chol.add(dit->second.ptr, dit->second.ld, x.Linv, m, tag(0, lv.level, s));
     if (x.red && m > 0) {
       B.gram.add(x.AsW, x.dW, 0, x.AsW, x.dW, 1, x.G, m, m, m, x.dW, T(1), T(0));
-      if (use_phi_) B.gram.add(x.AsW, x.dW, 0, x.phiW, 1, 0, x.a, 1, m, 1, x.dW, T(1), T(0));
+      if (use_phi_) B.gram.add(x.AsW, x.dW, 0, x.phiW, h_.nphi, 0, x.a, h_.nphi, m, h_.nphi, x.dW, T(1), T(0));
       TruncTask<T> tt;
       tt.G = x.G;
       tt.a = x.a;
       tt.phi = phi_[s];
+      tt.np = use_phi_ ? h_.nphi : 0;
+      tt.eps1 = h_.eps1;
       tt.U = x.U;
       tt.work = nullptr;
       tt.eps = level_eps(lv.level);
@@ -972,7 +981,7 @@ void Run<T>::wave_c(WaveBatches<T> &B) {
       x.ANr = talloc<T>(per, (size_t)dN * k);
       x.Arr = talloc<T>(per, (size_t)k * k);
       x.ArW = talloc<T>(per, (size_t)k * x.dW);
-      x.phir = use_phi_ ? talloc<T>(per, k) : nullptr;
+      x.phir = use_phi_ ? talloc<T>(per, (size_t)k * h_.nphi) : nullptr;
     }
     // L^-1 U and its CholQR2
     B.g1.add(x.Linv, m, 0, x.U, m, 0, x.Ut, k, m, k, m, T(1), T(0));
@@ -989,7 +998,7 @@ void Run<T>::wave_c(WaveBatches<T> &B) {
     B.g6.add(x.Linv, m, 1, x.Linv, m, 0, x.M, m, m, m, m, T(1), T(0));          // L^-T L^-1
     if (x.red) {
       B.g6.add(x.U, m, 1, x.AsW, x.dW, 0, x.ArW, x.dW, k, x.dW, m, T(1), T(0));  // U^T A_sW
-      if (use_phi_) B.g6.add(x.U, m, 1, phi_[x.s], 1, 0, x.phir, 1, k, 1, m, T(1), T(0));
+      if (use_phi_) B.g6.add(x.U, m, 1, phi_[x.s], h_.nphi, 0, x.phir, h_.nphi, k, h_.nphi, m, T(1), T(0));
     }
     B.g7.add(x.Rinv, k, 0, x.Wt, k, 1, x.Pm, m, k, m, k, T(1), T(0));           // P_ss = R^-1 (L^-T Q)^T
     B.g7.add(x.Wt, k, 0, x.Wt, k, 1, x.M, m, m, m, k, T(-1), T(1));             // M_ss -= W W^T
@@ -1344,16 +1353,19 @@ void trunc_grid(Exec &ex, const std::vector<TruncTask<T>> &tasks, const TruncTas
   ex.end();
   const int nb = refl_batch<T>(max_m);
   if (variant != HS_LORASP) {
+    // Z = Q^T [U_1, G U_1] has 2 k1 <= 4 np columns, in batches of up to 4
+    const int nbz = std::min(nb, 4);
     std::vector<ReflTask<T>> zf;
     for (const TruncTask<T> &t : tasks) {
       const BigLayout<T> L = big_layout<T>(t.work, t.m);
-      zf.push_back(ReflTask<T>{L.A, L.tau, L.LS, t.U, L.sc_int, t.m, 0, 1});
+      for (int j0 = 0; j0 < 4 * std::max(t.np, 1); j0 += nbz)
+        zf.push_back(ReflTask<T>{L.A, L.tau, L.LS, t.U, L.sc_int, t.m, j0, 1});
     }
     Uploader uz;
     const size_t oz = uz.add(zf);
     char *dz = uz.upload(ex.scr, ex.sg, ex.st);
     ex.begin(12);
-    launch_refl<T>((const ReflTask<T> *)(dz + oz), (int)zf.size(), std::min(nb, 4), max_m, ex.st);
+    launch_refl<T>((const ReflTask<T> *)(dz + oz), (int)zf.size(), nbz, max_m, ex.st);
     ex.end();
   }
   ex.begin(13);

@@ -98,6 +98,8 @@ struct FactorHandle {
   int variant = HS_GC_CONSTANT;
   double eps = 0.0;
   std::vector<double> eps_level;       // per level above the leaves (empty: eps everywhere)
+  int nphi = 1;                        // preserved vectors per node (GC family)
+  double eps1 = 0.0;                   // first tolerance of HS_GC_PROJ (Appendix B)
   cudaStream_t stream = nullptr;
   int device = 0;
   bool valid = false;                  // holds a usable factorization
@@ -133,7 +135,7 @@ struct FactorHandle {
   std::vector<std::pair<int, int>> leaf_blocks;   // leaf block list, in storage order
   std::vector<int64_t> leaf_block_off;
   int64_t leaf_total = 0;
-  void *d_phi0 = nullptr;              // leaf preserved vector (GC), factor precision
+  void *d_phi0 = nullptr;              // leaf preserved vectors (GC): n x nphi row-major, factor precision
   int64_t nnz = 0;
 
   // solve buffers (grown on demand)

@@ -124,8 +124,14 @@ struct CholTask {
   int status_idx;
 };
 
-// Truncation of one super node (Sec. 3.2 compression, Sec. 6 GC basis).
-// G = A_sw A_sw^T (m x m, ld m), a = A_sw phi_w (m), phi = phi_s (m).
+// Preserved vectors per node (GC family, HS_MAX_PHI) and the size of the GC
+// basis U_1 they give: the columns of phi_s and of A_sw phi_w.
+constexpr int kMaxPhi = 4;
+constexpr int kMaxK1 = 2 * kMaxPhi;
+
+// Truncation of one super node (Sec. 3.2 compression, Sec. 6 GC basis,
+// Appendix B projection).  G = A_sw A_sw^T (m x m, ld m); a = A_sw phi_w and
+// phi = phi_s, both m x np row-major (np = 0 for LoRaSp).
 // Outputs U (m x k, row-major, ld m) and k.  Work: 2 m^2 T.
 template <typename T>
 struct TruncTask {
@@ -134,9 +140,11 @@ struct TruncTask {
   const T *phi;
   T *U;
   T *work;
-  double eps;  // truncation tolerance of this node's level
+  double eps;   // truncation tolerance of this node's level
+  double eps1;  // HS_GC_PROJ: tolerance of the SVD of [phi_s, A_sw phi_w]
   int m;
-  int k_idx;  // index into the rank array
+  int np;       // preserved vectors (columns of phi and a)
+  int k_idx;    // index into the rank array
 };
 
 // ---------------------------------------------------------------------------
@@ -176,7 +184,8 @@ void launch_trunc(const TruncTask<T> *d_tasks, int ntasks, int *d_k, double eps,
 //   VG          the per-node vectors (d, e, pw in FP64; dt, et, lam, v, tau, wt,
 //               redt in T) when they are not in shared memory
 //   SC          persistent scalars between the kernels of the multi-CTA path:
-//               k1, k2 (ints), then c = U1^T G U1 (4 doubles)
+//               k1, k2, cluster count (ints), the norm bound of T, then
+//               c = U1^T G U1 (kMaxK1 x kMaxK1 doubles)
 template <typename T>
 struct BigLayout {
   T *A, *Y, *LU, *LS;
@@ -184,7 +193,7 @@ struct BigLayout {
   double *d, *e, *pw;
   T *dt, *et, *lam, *v, *tau, *wt, *redt;
   int *sc_int;        // k1, k2, number of eigenvalue clusters
-  double *sc_c;       // c = U1^T G U1 (4 doubles)
+  double *sc_c;       // c = U1^T G U1 (kMaxK1 x kMaxK1 doubles, ld kMaxK1)
   double *sc_tnorm;   // norm bound of T (inverse-iteration tolerance)
 };
 
@@ -192,6 +201,9 @@ template <typename T>
 __host__ __device__ inline size_t big_vec_bytes(int m) {
   return 3 * sizeof(double) * (size_t)m + 6 * sizeof(T) * (size_t)((m + 1) & ~1) + 34 * sizeof(T) + 16;
 }
+
+// bytes of the SC area (after its 16-byte alignment)
+constexpr size_t kBigScBytes = 24 + sizeof(double) * kMaxK1 * kMaxK1;
 
 template <typename T>
 __host__ __device__ inline BigLayout<T> big_layout(T *work, int m) {
@@ -225,8 +237,8 @@ __host__ __device__ inline BigLayout<T> big_layout(T *work, int m) {
   L.redt = (T *)p;
   unsigned char *sc = (unsigned char *)(((uintptr_t)(L.VG + big_vec_bytes<T>(m)) + 15) & ~(uintptr_t)15);
   L.sc_int = (int *)sc;
-  L.sc_c = (double *)(sc + 16);
-  L.sc_tnorm = (double *)(sc + 48);
+  L.sc_tnorm = (double *)(sc + 16);
+  L.sc_c = (double *)(sc + 24);
   return L;
 }
 

@@ -455,7 +455,9 @@ __global__ void __launch_bounds__(TRUNC_THREADS) k_trunc(const TruncTask<T> *__r
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
   __shared__ int flag;
-  __shared__ double u1n[2];
+  __shared__ double s_gR[kMaxK1 * 2 * kMaxPhi], s_gW[kMaxK1 * kMaxK1 + kMaxK1];
+  __shared__ int s_gk;
+  __shared__ T s_c[kMaxK1 * kMaxK1];
   const TruncTask<T> t = tasks[blockIdx.x];
   const double eps = t.eps;
   const int m = t.m;
@@ -493,43 +495,12 @@ __global__ void __launch_bounds__(TRUNC_THREADS) k_trunc(const TruncTask<T> *__r
     if (tid == 0) kout[t.k_idx] = m;
     return;
   }
-  // ---- GC basis U_1 = orth[phi_s, A_sw phi_w] (Sec. 6; MGS with one re-orthogonalisation)
+  // ---- GC basis U_1 (Sec. 6: orth[phi_s, A_sw phi_w]; Appendix B: its
+  // dominant left singular vectors), scratch in A and V (2 m^2 T >= m doubles)
   int k1 = 0;
-  if (variant != HS_LORASP) {
-    double s = 0.0;
-    for (int i = tid; i < m; i += nt) s += (double)t.phi[i] * (double)t.phi[i];
-    const double nphi = sqrt(block_sum<T>(s, red));
-    if (nphi > 0.0) {
-      for (int i = tid; i < m; i += nt) t.U[(int64_t)i * m] = (T)((double)t.phi[i] / nphi);
-      k1 = 1;
-    }
-    __syncthreads();
-    s = 0.0;
-    for (int i = tid; i < m; i += nt) s += (double)t.a[i] * (double)t.a[i];
-    const double na = sqrt(block_sum<T>(s, red));
-    if (na > 0.0) {
-      // v = a kept in V's first column as scratch
-      for (int i = tid; i < m; i += nt) V[i] = t.a[i];
-      __syncthreads();
-      for (int pass = 0; pass < 2 && k1 == 1; ++pass) {
-        double d = 0.0;
-        for (int i = tid; i < m; i += nt) d += (double)t.U[(int64_t)i * m] * (double)V[i];
-        d = block_sum<T>(d, red);
-        for (int i = tid; i < m; i += nt) V[i] = (T)((double)V[i] - d * (double)t.U[(int64_t)i * m]);
-        __syncthreads();
-      }
-      double sv = 0.0;
-      for (int i = tid; i < m; i += nt) sv += (double)V[i] * (double)V[i];
-      const double nv = sqrt(block_sum<T>(sv, red));
-      if (nv > 1e-12 * na) {
-        for (int i = tid; i < m; i += nt) t.U[(int64_t)i * m + k1] = (T)((double)V[i] / nv);
-        ++k1;
-      }
-      __syncthreads();
-    }
-    if (tid == 0) u1n[0] = (double)k1;
-    __syncthreads();
-  }
+  if (variant != HS_LORASP)
+    k1 = gc_basis_dev<T>(t.phi, t.a, t.np, m, variant == HS_GC_PROJ, t.eps1, t.U, (double *)A, red, s_gR, s_gW,
+                         &s_gk);
   // ---- ||A_sw||_2^2 = lambda_max(G)
   for (int64_t e = tid; e < (int64_t)m * m; e += nt) A[e] = t.G[e];
   __syncthreads();
@@ -545,8 +516,12 @@ __global__ void __launch_bounds__(TRUNC_THREADS) k_trunc(const TruncTask<T> *__r
     return;
   }
   if (eps == 0.0) {
-    // no truncation: complete the GC basis to all of R^m (closed form)
-    gc_complete<T>(t.U, m, k1, (double *)A, red);
+    // no truncation: complete the GC basis to all of R^m (Householder QR of U_1;
+    // scratch k1 m <= 2 m^2 T in A and V)
+    if (k1 <= 2)
+      gc_complete<T>(t.U, m, k1, (double *)A, red);
+    else
+      gc_complete_n<T>(t.U, m, k1, (double *)A, s_gW, red);
     if (tid == 0) kout[t.k_idx] = m;
     return;
   }
@@ -567,22 +542,41 @@ __global__ void __launch_bounds__(TRUNC_THREADS) k_trunc(const TruncTask<T> *__r
       V[i * m + a] = s;
     }
     __syncthreads();
-    T c[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+    // c = U1^T G U1 (k1 x k1, ld kMaxK1)
     for (int a = 0; a < k1; ++a)
       for (int b = 0; b < k1; ++b) {
         double s = 0.0;
         for (int i = tid; i < m; i += nt) s += (double)(t.U[(int64_t)i * m + a] * V[i * m + b]);
-        c[a][b] = (T)block_sum<T>(s, red);
+        const T cab = (T)block_sum<T>(s, red);
+        if (tid == 0) s_c[a * kMaxK1 + b] = cab;
       }
-    for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
-      const int i = (int)(e / m), j = (int)(e % m);
-      T v = t.G[e];
-      for (int a = 0; a < k1; ++a) {
-        const T ui = t.U[(int64_t)i * m + a], uj = t.U[(int64_t)j * m + a];
-        v = fma(-ui, V[j * m + a], fma(-V[i * m + a], uj, v));
-        for (int b = 0; b < k1; ++b) v = fma(ui * c[a][b], t.U[(int64_t)j * m + b], v);
+    __syncthreads();
+    if (k1 <= 2) {
+      // one or two basis vectors (one preserved vector): c in registers
+      T c[2][2];
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) c[a][b] = (a < k1 && b < k1) ? s_c[a * kMaxK1 + b] : T(0);
+      for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+        const int i = (int)(e / m), j = (int)(e % m);
+        T v = t.G[e];
+        for (int a = 0; a < k1; ++a) {
+          const T ui = t.U[(int64_t)i * m + a], uj = t.U[(int64_t)j * m + a];
+          v = fma(-ui, V[j * m + a], fma(-V[i * m + a], uj, v));
+          for (int b = 0; b < k1; ++b) v = fma(ui * c[a][b], t.U[(int64_t)j * m + b], v);
+        }
+        A[e] = v;
       }
-      A[e] = v;
+    } else {
+      for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
+        const int i = (int)(e / m), j = (int)(e % m);
+        T v = t.G[e];
+        for (int a = 0; a < k1; ++a) {
+          const T ui = t.U[(int64_t)i * m + a], uj = t.U[(int64_t)j * m + a];
+          v = fma(-ui, V[j * m + a], fma(-V[i * m + a], uj, v));
+          for (int b = 0; b < k1; ++b) v = fma(ui * s_c[a * kMaxK1 + b], t.U[(int64_t)j * m + b], v);
+        }
+        A[e] = v;
+      }
     }
     thr = eps * eps * lmax;
   } else {

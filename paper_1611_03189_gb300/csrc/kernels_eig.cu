@@ -4,9 +4,10 @@
 //
 // One CTA per super node: 256 threads for m <= 128, 1024 above (a function of
 // m alone, so a node gets the same arithmetic in any batch):
-//   1. GC basis U_1 = orth[phi_s, A_sw phi_w] (Sec. 6), as in the Jacobi path.
+//   1. GC basis U_1 = orth[phi_s, A_sw phi_w] (Sec. 6; Appendix B: its dominant
+//      left singular vectors), as in the Jacobi path.
 //   2. ||A_sw||_2^2 = lambda_max(G).  LoRaSp: top eigenvalue of T below.  GC:
-//      G = J + (rank <= 4 terms in span{U_1, G U_1}), so lambda_max(G) follows
+//      G = J + (rank <= 2 k1 terms in span{U_1, G U_1}), so lambda_max(G) follows
 //      from the tridiagonal T of J by a warp multisection on the Haynsworth
 //      inertia count of the low-rank correction (no second tridiagonalisation).
 //   3. J = G (LoRaSp), (I - U1 U1^T) G (I - U1 U1^T) (GC) or I - U1 U1^T (GC,
@@ -363,41 +364,43 @@ __device__ void inverse_iteration(const R *d, const R *e, int m, R lam, R tnorm,
 
 // Eigenvalues of G above sigma, for sigma > lambda_max(T), where Q^T G Q = T + Z M Z^T,
 // T = tridiag(d, e) (the tridiagonal of the projected Gram J = P G P), Z = Q^T [U_1, G U_1]
-// (m x 2 k1, column j at Z + j*m) and M = [[-C, I], [I, 0]], C = U_1^T G U_1.
+// (m x 2 k1, column j at Z + j*m) and M = [[-C, I], [I, 0]], C = U_1^T G U_1 (k1 x k1,
+// ld kMaxK1).  NZ >= 2 k1 bounds the small dense parts held per thread.
 // Haynsworth inertia of [[T - sigma I, Z], [Z^T, -M^-1]] gives
 //   #eig(G) > sigma = n_+(-M^-1 - Z^T (T - sigma I)^-1 Z) - n_+(-M^-1),  n_+(-M^-1) = k1,
 // since T - sigma I is negative definite.  With T - sigma I = L D L^T (L unit
 // lower bidiagonal) and W = L^-1 Z, Z^T (T - sigma I)^-1 Z = W^T D^-1 W: one
 // forward sweep with register accumulators, no storage.
-template <typename R>
-__device__ int count_above_lowrank(const R *d, const R *e, int m, const R *Z, int k1, const R (&C)[2][2],
-                                   R sigma) {
+template <typename R, int NZ>
+__device__ int count_above_lowrank(const R *d, const R *e, int m, const R *Z, int k1, const R *C, R sigma) {
   const int nz = 2 * k1;
-  R w[4] = {R(0), R(0), R(0), R(0)};
-  R g[4][4];
-  for (int a = 0; a < 4; ++a)
-    for (int b2 = 0; b2 < 4; ++b2) g[a][b2] = R(0);
+  R w[NZ];
+  R g[NZ][NZ];
+  for (int a = 0; a < NZ; ++a) {
+    w[a] = R(0);
+    for (int b2 = 0; b2 < NZ; ++b2) g[a][b2] = R(0);
+  }
   R dd = R(1), lprev = R(0);
   for (int i = 0; i < m; ++i) {
     dd = (i == 0) ? d[0] - sigma : d[i] - sigma - lprev * e[i - 1];
     const R inv = R(1) / dd;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < NZ; ++a)
       if (a < nz) w[a] = Z[(size_t)a * m + i] - (i == 0 ? R(0) : lprev * w[a]);
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < NZ; ++a)
 #pragma unroll
-      for (int b2 = 0; b2 < 4; ++b2)
+      for (int b2 = 0; b2 < NZ; ++b2)
         if (a < nz && b2 <= a) g[a][b2] = fma(w[a] * inv, w[b2], g[a][b2]);
     lprev = (i + 1 < m) ? e[i] * inv : R(0);
   }
-  R S[4][4];
+  R S[NZ][NZ];
   for (int a = 0; a < nz; ++a)
     for (int b = 0; b < nz; ++b) {
       R v = R(0);
       if (a < k1 && b >= k1 && b - k1 == a) v = R(-1);
       if (b < k1 && a >= k1 && a - k1 == b) v = R(-1);
-      if (a >= k1 && b >= k1) v = -C[a - k1][b - k1];
+      if (a >= k1 && b >= k1) v = -C[(a - k1) * kMaxK1 + (b - k1)];
       S[a][b] = v - (b <= a ? g[a][b] : g[b][a]);
     }
   // symmetrise and count positive eigenvalues by cyclic Jacobi on the small matrix
@@ -407,7 +410,7 @@ __device__ int count_above_lowrank(const R *d, const R *e, int m, const R *Z, in
       S[a][b] = v;
       S[b][a] = v;
     }
-  for (int sweep = 0; sweep < 12; ++sweep)
+  for (int sweep = 0; sweep < (NZ > 4 ? 16 : 12); ++sweep)
     for (int p = 0; p < nz; ++p)
       for (int q = p + 1; q < nz; ++q) {
         const R apq = S[p][q];
@@ -433,6 +436,57 @@ __device__ int count_above_lowrank(const R *d, const R *e, int m, const R *Z, in
   return pos - k1;
 }
 
+// J = G - U1 X^T - X U1^T + U1 c U1^T (the Gram matrix projected off span U_1),
+// X = G U1 in Y's columns (column a at Y + a m), c in shared memory (ld
+// kMaxK1); one warp per row.  KB >= k1 sizes the per-row registers.
+template <typename T, int KB>
+__device__ void build_projected_gram(const T *G, const T *U, const T *Y, const T *s_c, T *A, int m, int k1) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < m; i += nw) {
+    T ui[KB], xi[KB], cu[KB];
+#pragma unroll
+    for (int a = 0; a < KB; ++a) {
+      ui[a] = a < k1 ? U[(int64_t)i * m + a] : T(0);
+      xi[a] = a < k1 ? Y[(size_t)a * m + i] : T(0);
+    }
+#pragma unroll
+    for (int bb = 0; bb < KB; ++bb) {
+      T su = T(0);
+#pragma unroll
+      for (int a = 0; a < KB; ++a)
+        if (a < k1) su = fma(ui[a], s_c[a * kMaxK1 + bb], su);
+      cu[bb] = su;
+    }
+    for (int j = lane; j < m; j += 32) {
+      T v = G[(int64_t)i * m + j];
+#pragma unroll
+      for (int a = 0; a < KB; ++a)
+        if (a < k1) {
+          const T uj = U[(int64_t)j * m + a];
+          v = fma(-ui[a], Y[(size_t)a * m + j], fma(-xi[a], uj, v));
+          v = fma(cu[a], uj, v);
+        }
+      A[(int64_t)i * m + j] = v;
+    }
+  }
+}
+
+// k1 > 2 (several preserved vectors) in a call of its own, off the register
+// allocation of the one-vector path
+template <typename T>
+__device__ __noinline__ void build_projected_gram_wide(const T *G, const T *U, const T *Y, const T *s_c, T *A,
+                                                       int m, int k1) {
+  build_projected_gram<T, kMaxK1>(G, U, Y, s_c, A, m, k1);
+}
+
+// The count for k1 > 2 (several preserved vectors) in a call of its own, so
+// that its 16 x 16 local arrays stay out of the kernel's register allocation.
+template <typename R>
+__device__ __noinline__ int count_above_lowrank_wide(const R *d, const R *e, int m, const R *Z, int k1,
+                                                     const R *C, R sigma) {
+  return count_above_lowrank<R, 2 * kMaxK1>(d, e, m, Z, k1, C, sigma);
+}
+
 // mode: TB_FULL does all steps in this CTA.  The multi-CTA path for very large
 // nodes splits it: TB_PREP stops before the tridiagonalisation (A = J, Z saved,
 // k1 and c stored in SC); the step kernels tridiagonalise; TB_POST takes d, e
@@ -446,6 +500,9 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[33];
   __shared__ int s_k2;
+  __shared__ double s_gR[kMaxK1 * 2 * kMaxPhi], s_gW[kMaxK1 * kMaxK1 + kMaxK1];
+  __shared__ int s_gk;
+  __shared__ T s_c[kMaxK1 * kMaxK1];   // c = U1^T G U1, ld kMaxK1
   const TruncTask<T> t = tasks[blockIdx.x];
   const double eps = t.eps;
   const int m = t.m;
@@ -493,55 +550,28 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
     if (tid == 0) kout[t.k_idx] = 0;
     return;
   }
-  // ---- GC basis U_1 (same rule as the Jacobi path)
+  // ---- GC basis U_1 (same rule as the Jacobi path; scratch b.pw, m doubles)
   int k1 = 0;
-  if (variant != HS_LORASP) {
-    double s = 0.0;
-    for (int i = tid; i < m; i += nt) s += (double)t.phi[i] * (double)t.phi[i];
-    const double nphi = sqrt(bsum(s, red));
-    if (nphi > 0.0) {
-      for (int i = tid; i < m; i += nt) t.U[(int64_t)i * m] = (T)((double)t.phi[i] / nphi);
-      k1 = 1;
-    }
-    __syncthreads();
-    s = 0.0;
-    for (int i = tid; i < m; i += nt) s += (double)t.a[i] * (double)t.a[i];
-    const double na = sqrt(bsum(s, red));
-    if (na > 0.0) {
-      for (int i = tid; i < m; i += nt) b.pw[i] = (double)t.a[i];
-      __syncthreads();
-      for (int pass = 0; pass < 2 && k1 == 1; ++pass) {
-        double dd = 0.0;
-        for (int i = tid; i < m; i += nt) dd += (double)t.U[(int64_t)i * m] * b.pw[i];
-        dd = bsum(dd, red);
-        for (int i = tid; i < m; i += nt) b.pw[i] -= dd * (double)t.U[(int64_t)i * m];
-        __syncthreads();
-      }
-      double sv = 0.0;
-      for (int i = tid; i < m; i += nt) sv += b.pw[i] * b.pw[i];
-      const double nv = sqrt(bsum(sv, red));
-      if (nv > 1e-12 * na) {
-        for (int i = tid; i < m; i += nt) t.U[(int64_t)i * m + k1] = (T)(b.pw[i] / nv);
-        ++k1;
-      }
-      __syncthreads();
-    }
-  }
+  if (variant != HS_LORASP)
+    k1 = gc_basis_dev<T>(t.phi, t.a, t.np, m, variant == HS_GC_PROJ, t.eps1, t.U, b.pw, red, s_gR, s_gW, &s_gk);
   const bool gc = variant != HS_LORASP;
   if (gc && eps == 0.0) {
-    // no truncation: complete the GC basis to all of R^m (closed form)
-    gc_complete<T>(t.U, m, k1, (double *)Y, red);
+    // no truncation: complete the GC basis to all of R^m (Householder QR of
+    // U_1; scratch k1 m doubles in Y and LU, 5 m^2 T)
+    if (k1 <= 2)
+      gc_complete<T>(t.U, m, k1, (double *)Y, red);
+    else
+      gc_complete_n<T>(t.U, m, k1, (double *)Y, s_gW, red);
     if (tid == 0) kout[t.k_idx] = m;
     return;
   }
   // ---- lambda_max(G) (GC) follows from the tridiagonal of the projected Gram below
   double lmax = 0.0;
-  T cmat[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
   // ---- J
   if (mode == TB_POST) {
     // J, Z and c were made by TB_PREP; Z is already Q^T [U1, X]
-    for (int a = 0; a < 2; ++a)
-      for (int bb = 0; bb < 2; ++bb) cmat[a][bb] = (T)L.sc_c[2 * a + bb];
+    for (int q = tid; q < kMaxK1 * kMaxK1; q += nt) s_c[q] = (T)L.sc_c[q];
+    __syncthreads();
   } else if (!gc) {
     for (int64_t q = tid; q < (int64_t)m * m; q += nt) A[q] = t.G[q];
   } else if (eps > 0.0) {
@@ -557,35 +587,21 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
         }
     }
     __syncthreads();
-    T c[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+    for (int q = tid; q < kMaxK1 * kMaxK1; q += nt) s_c[q] = T(0);
+    __syncthreads();
     for (int a = 0; a < k1; ++a)
       for (int bb = 0; bb < k1; ++bb) {
         T s = T(0);
         for (int i = tid; i < m; i += nt) s = fma(t.U[(int64_t)i * m + a], Y[(size_t)bb * m + i], s);
-        c[a][bb] = bsum_t<T>(s, b.redt);
-        cmat[a][bb] = c[a][bb];
+        const T cab = bsum_t<T>(s, b.redt);
+        if (tid == 0) s_c[a * kMaxK1 + bb] = cab;
       }
+    __syncthreads();
     // J = G - U1 X^T - X U1^T + U1 c U1^T, one warp per row
-    {
-      const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-      for (int i = warp; i < m; i += nw) {
-        T ui[2], xi[2], cu[2];
-        for (int a = 0; a < 2; ++a) {
-          ui[a] = a < k1 ? t.U[(int64_t)i * m + a] : T(0);
-          xi[a] = a < k1 ? Y[(size_t)a * m + i] : T(0);
-        }
-        for (int bb = 0; bb < 2; ++bb) cu[bb] = ui[0] * c[0][bb] + ui[1] * c[1][bb];
-        for (int j = lane; j < m; j += 32) {
-          T v = t.G[(int64_t)i * m + j];
-          for (int a = 0; a < k1; ++a) {
-            const T uj = t.U[(int64_t)j * m + a];
-            v = fma(-ui[a], Y[(size_t)a * m + j], fma(-xi[a], uj, v));
-            v = fma(cu[a], uj, v);
-          }
-          A[(int64_t)i * m + j] = v;
-        }
-      }
-    }
+    if (k1 <= 2)
+      build_projected_gram<T, 2>(t.G, t.U, Y, s_c, A, m, k1);
+    else
+      build_projected_gram_wide<T>(t.G, t.U, Y, s_c, A, m, k1);
   } else {
     for (int64_t q = tid; q < (int64_t)m * m; q += nt) {
       const int i = (int)(q / m), j = (int)(q % m);
@@ -596,7 +612,7 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
   }
   __syncthreads();
   // X = G U1 (Y columns 0..k1-1) is needed again below: move it next to U1 first
-  T *Zb = LS;  // Z = Q^T [U1, X], 2 k1 <= 4 columns of m
+  T *Zb = LS;  // Z = Q^T [U1, X], 2 k1 <= 2 kMaxK1 columns of m
   if (gc && eps > 0.0 && mode != TB_POST) {
     for (int64_t q = tid; q < (int64_t)m * k1; q += nt) {
       const int a = (int)(q / m), i = (int)(q % m);
@@ -606,11 +622,8 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
   }
   __syncthreads();
   if (mode == TB_PREP) {
-    if (tid == 0) {
-      L.sc_int[0] = k1;
-      for (int a = 0; a < 2; ++a)
-        for (int bb = 0; bb < 2; ++bb) L.sc_c[2 * a + bb] = (double)cmat[a][bb];
-    }
+    if (tid == 0) L.sc_int[0] = k1;
+    for (int q = tid; q < kMaxK1 * kMaxK1; q += nt) L.sc_c[q] = (double)s_c[q];
     return;
   }
   if (mode == TB_POST) {
@@ -674,7 +687,9 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
       T lo = lmaxT, hi = fmax(trace, lmaxT) * T(1.0001) + T(1e-30);
       for (int round = 0; round < 40 && hi - lo > T(4) * unit_round<T>() * hi; ++round) {
         const T sig = lo + (hi - lo) * T(tid + 1) / T(33);
-        const int c = k1 > 0 ? count_above_lowrank<T>(b.dt, b.et, m, Zb, k1, cmat, sig) : 0;
+        const int c = k1 == 0 ? 0
+                      : k1 <= 2 ? count_above_lowrank<T, 4>(b.dt, b.et, m, Zb, k1, s_c, sig)
+                                : count_above_lowrank_wide<T>(b.dt, b.et, m, Zb, k1, s_c, sig);
         const unsigned above = __ballot_sync(0xffffffffu, c >= 1);
         const int l = above ? 31 - __clz(above) : -1;   // highest sigma with an eigenvalue above it
         const T nlo = l >= 0 ? lo + (hi - lo) * T(l + 1) / T(33) : lo;
@@ -1109,9 +1124,10 @@ size_t trunc_big_vec_bytes(int m) {
 template <typename T>
 size_t trunc_big_work_elems(int m) {
   // A, Y, LU (6 m^2 T) + LS (164 m T) + flags (m^2 bytes) + the vectors (when
-  // they do not fit in shared memory); Y also holds 2 m doubles of scratch
+  // they do not fit in shared memory) + SC; Y and LU also hold k1 m doubles
+  // of scratch
   const size_t bytes = sizeof(T) * (6 * (size_t)m * m + 164 * (size_t)m) + (size_t)m * m + 16 +
-                       trunc_big_vec_bytes<T>(m) + 16 + 64 + 64;
+                       trunc_big_vec_bytes<T>(m) + 16 + kBigScBytes + 64;
   return (bytes + sizeof(T) - 1) / sizeof(T);
 }
 

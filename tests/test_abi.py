@@ -121,3 +121,13 @@ def test_options_are_validated_before_any_device_work(lib):
     for eps, var, prec in ((-1.0, 1, 0), (1e-8, 1, 0), (0.1, 7, 0), (0.1, 1, 5), (0.1, 2, 0)):
         o = _lib.HsOpts(eps, var, prec, None)
         assert lib.hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), None, C.byref(h)) == _lib.HS_ERR_INVALID
+    # several vectors and the Appendix B projection: n_phi in range, only for the
+    # variants that take vectors, eps1 finite and >= 0, phi present
+    phi = np.ones(8)
+    P_ = phi.ctypes.data
+    for var, ptr, nphi, eps1 in ((_lib.HS_GC_USER, P_, 5, 0.0), (_lib.HS_GC_USER, P_, -1, 0.0),
+                                 (_lib.HS_GC_CONSTANT, None, 2, 0.0), (_lib.HS_LORASP, None, 2, 0.0),
+                                 (_lib.HS_GC_PROJ, P_, 1, -1.0), (_lib.HS_GC_PROJ, P_, 1, float("nan")),
+                                 (_lib.HS_GC_PROJ, None, 1, 0.1)):
+        o = _lib.HsOpts(0.1, var, 0, ptr, None, 0, nphi, eps1)
+        assert lib.hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), None, C.byref(h)) == _lib.HS_ERR_INVALID

@@ -1,0 +1,178 @@
+"""Several preserved vectors (Sec. 6 with p > 1) and the Appendix B one-sided
+projection (HS_GC_PROJ) on the GPU, against the FP64 oracle on the same inputs.
+
+Bars as in test_gpu_parity: equal ranks, FP64 apply within 1e-10 relative of
+the oracle, exact preservation A_H^-1 phi_i = phi_i / lambda_i within 1e-11 for
+preserved eigenvectors, FP32 factor within 1e-3 of the oracle.  Every
+truncation path is covered: the shared-memory Jacobi kernel (default for these
+sizes), the one-CTA tridiagonal kernel (HS_EIG_SMALL_MAX=8) and the multi-CTA
+path (also HS_GRID_TRIDIAG_MIN=16), each with U_1 of up to 8 columns.
+"""
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+from oracle import hsolver as H
+from paper_1611_03189_gb300 import _lib
+from paper_1611_03189_gb300 import problems as P
+
+from gpu_util import need_gpu, rel, to_dev
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _eig(nx, modes):
+    V = np.column_stack([P.laplacian_eigvec_2d(nx, nx, j, k) for j, k in modes])
+    lam = np.array([P.laplacian_eigval_2d(nx, nx, j, k) for j, k in modes])
+    return V, lam
+
+
+def _case(name):
+    """(problem, variant, vectors, eigenvalues or None, eps1) of a named case."""
+    if name == "poisson32 3 eigenvectors":
+        V, lam = _eig(32, [(1, 1), (2, 1), (1, 2)])
+        return P.poisson2d(32, leaf_size=8), H.GC_USER, V, lam, 0.0
+    if name == "poisson32 projection":
+        V, lam = _eig(32, [(1, 1), (2, 1), (1, 2)])
+        return P.poisson2d(32, leaf_size=8), H.GC_PROJ, V / lam, None, 0.05
+    if name == "poisson64 4 eigenvectors":
+        V, lam = _eig(64, [(1, 1), (2, 1), (1, 2), (2, 2)])
+        return P.poisson2d(64, leaf_size=16), H.GC_USER, V, lam, 0.0
+    if name == "poisson64 projection 4":
+        V, lam = _eig(64, [(1, 1), (2, 1), (1, 2), (2, 2)])
+        return P.poisson2d(64, leaf_size=16), H.GC_PROJ, V / lam, None, 0.02
+    if name == "diffusion64 2 random vectors":
+        pb = P.diffusion2d(64, 1.0, 0, leaf_size=16)
+        return pb, H.GC_USER, np.random.default_rng(3).standard_normal((pb.n, 2)), None, 0.0
+    raise KeyError(name)
+
+
+NAMES = ["poisson32 3 eigenvectors", "poisson32 projection", "poisson64 4 eigenvectors",
+         "poisson64 projection 4", "diffusion64 2 random vectors"]
+
+
+def _oracle(pb, eps, variant, X, eps1):
+    return H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, eps, variant, phi=X, eps1=eps1)
+
+
+def _gpu(pb, eps, variant, X, eps1, prec=0):
+    rp, ci, va = to_dev(pb)
+    return _lib.Factor(rp, ci, va, pb.perm, pb.leaf_ptr, eps, variant, prec, phi=X, eps1=eps1)
+
+
+def _ranks_equal(F, G):
+    bad = []
+    for lv in F.levels:
+        g = G.ranks(lv.level)
+        for rec in lv.supers:
+            want = rec.k if rec.wsep else -1
+            if g[rec.key] != want:
+                bad.append((lv.level, rec.key, want, int(g[rec.key])))
+    return bad
+
+
+def check_case(name, eps, fp32=True):
+    """Ranks, apply and (for eigenvectors) exact preservation against the oracle."""
+    import torch
+
+    pb, variant, X, lam, eps1 = _case(name)
+    F = _oracle(pb, eps, variant, X, eps1)
+    G = _gpu(pb, eps, variant, X, eps1)
+    bad = _ranks_equal(F, G)
+    assert bad == [], bad[:5]
+    B = P.rhs(pb.n, 7, nrhs=2)
+    zg = G.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
+    assert rel(zg, H.apply(F, B)) <= 1e-10
+    if lam is not None:
+        Z = G.apply(torch.as_tensor(X.T.copy(), device="cuda")).cpu().numpy().T
+        for i in range(X.shape[1]):
+            assert rel(Z[:, i], X[:, i] / lam[i]) <= 1e-11
+    if fp32:
+        G32 = _gpu(pb, eps, variant, X, eps1, prec=1)
+        z32 = G32.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
+        assert rel(z32, H.apply(F, B)) <= 1e-3
+        x, it, rr, _ = G32.pcg(torch.as_tensor(B[:, 0].copy(), device="cuda"), rtol=1e-10, maxit=300)
+        assert rr[0] <= 1e-10
+        G32.close()
+    G.close()
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("eps", [1e-1, 1e-2])
+def test_several_vectors_match_oracle(name, eps):
+    need_gpu()
+    check_case(name, eps)
+
+
+@pytest.mark.parametrize("path,env", [("tridiagonal", {"HS_EIG_SMALL_MAX": "8"}),
+                                      ("multi-CTA", {"HS_EIG_SMALL_MAX": "8", "HS_GRID_TRIDIAG_MIN": "16"})])
+def test_several_vectors_on_the_eigen_paths(path, env):
+    """Every super node through the large-node eigen path (k1 up to 8 columns
+    in the projected Gram, the low-rank inertia count and the reflector
+    products of the multi-CTA path)."""
+    need_gpu()
+    code = f"""
+import sys
+sys.path.insert(0, {os.path.dirname(HERE)!r})
+sys.path.insert(0, {HERE!r})
+import test_gpu_multi_phi as T
+for name in ("poisson32 3 eigenvectors", "poisson32 projection", "poisson64 projection 4"):
+    for eps in (1e-1, 1e-2):
+        T.check_case(name, eps, fp32=(eps == 1e-1))
+print('ok')
+"""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                       env=dict(os.environ, **env))
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-3000:]
+
+
+@pytest.mark.parametrize("small_max", [None, "8"], ids=["jacobi", "tridiagonal"])
+def test_eps0_with_several_vectors_is_exact(small_max):
+    """eps = 0 completes a U_1 of up to 8 columns to a full basis (Householder
+    completion): the factorization is exact."""
+    need_gpu()
+    code = f"""
+import sys, numpy as np, torch, scipy.sparse.linalg as spla
+sys.path.insert(0, {os.path.dirname(HERE)!r})
+sys.path.insert(0, {HERE!r})
+import test_gpu_multi_phi as T
+from gpu_util import rel
+from paper_1611_03189_gb300 import problems as P
+for name in ("poisson32 3 eigenvectors", "poisson32 projection", "diffusion64 2 random vectors"):
+    pb, variant, X, lam, eps1 = T._case(name)
+    G = T._gpu(pb, 0.0, variant, X, eps1)
+    b = P.rhs(pb.n, 2)
+    z = G.apply(torch.as_tensor(b, device='cuda')).cpu().numpy()
+    e = rel(z, spla.spsolve(pb.to_scipy().tocsc(), b))
+    assert e <= 1e-10, (name, e)
+print('ok')
+"""
+    env = dict(os.environ)
+    if small_max:
+        env["HS_EIG_SMALL_MAX"] = small_max
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-3000:]
+
+
+def test_batch_with_several_vectors_equals_each_alone():
+    """Problems of different sizes, each with its own two vectors, factored in
+    lock step: each gets the factorization it gets alone, bit for bit."""
+    torch = need_gpu()
+    pbs = [P.diffusion2d(side, 1.0, seed, leaf_size=16) for seed, side in enumerate((20, 48, 33))]
+    rng = np.random.default_rng(11)
+    Xs = [rng.standard_normal((pb.n, 2)) for pb in pbs]
+    args = [to_dev(pb) + (pb.perm, pb.leaf_ptr) for pb in pbs]
+    for variant, eps1 in ((H.GC_USER, 0.0), (H.GC_PROJ, 0.05)):
+        fs, status = _lib.factor_batch(args, 1e-2, variant, 1, phis=Xs, eps1=eps1)
+        assert list(status) == [0] * len(pbs)
+        for pb, X, f in zip(pbs, Xs, fs):
+            g = _gpu(pb, 1e-2, variant, X, eps1, prec=1)
+            B = torch.as_tensor(P.rhs(pb.n, 5, nrhs=2).T.copy(), device="cuda")
+            assert np.array_equal(f.apply(B).cpu().numpy(), g.apply(B).cpu().numpy())
+            f.close()
+            g.close()
