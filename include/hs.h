@@ -241,6 +241,20 @@ int hs_apply_static(hs_factor f, const double *r, double *z, int32_t nrhs, int64
 int hs_pcg(hs_factor f, const double *b, double *x, int32_t nrhs, int64_t ld, double rtol,
            int32_t maxit, int32_t *iters, double *relres, void *stream);
 
+/* hs_gmres: solve A x = b by GMRES right-preconditioned with A_H^{-1}, the
+ * outer solver of the paper's experiments (Sec. 7, Tables 2-5), x_0 = 0, one
+ * right-hand side, FP64.  Stops when the Arnoldi least-squares residual falls
+ * below rtol ||b||_2 (Sec. 7: relative residual 1e-10), restarting every
+ * `restart` steps (0: no restart).  A is the matrix of the last successful
+ * hs_factor_create / hs_factor_refactor.  b, x: DEVICE, n doubles (original
+ * ordering).  iters, relres: HOST; *iters = Arnoldi steps over all cycles,
+ * *relres = ||b - A x|| / ||b|| recomputed at the end.  The handle keeps the
+ * Krylov basis, (m + 7) n doubles of device memory with m = restart, or maxit
+ * when restart is 0; m must be <= 1000 (HS_ERR_INVALID otherwise).  Returns
+ * HS_ERR_NO_CONVERGENCE (with x, iters, relres filled) after maxit steps. */
+int hs_gmres(hs_factor f, const double *b, double *x, double rtol, int32_t maxit, int32_t restart,
+             int32_t *iters, double *relres, void *stream);
+
 /* hs_factor_info: sizes and counters of a factorization. */
 int hs_factor_info(hs_factor f, hs_info *info);
 

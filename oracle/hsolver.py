@@ -655,26 +655,51 @@ def stationary(F: Factor, rowptr, col, val, x_star, tol=1e-6, maxit=2000):
     return maxit
 
 
-def gmres(F: Factor, rowptr, col, val, b, rtol=1e-10, maxit=300):
-    """Right-preconditioned unrestarted GMRES; iterations to ||b - A x|| < rtol ||b||."""
+def gmres_solve(F: Factor, rowptr, col, val, b, rtol=1e-10, maxit=300, restart=0):
+    """Right-preconditioned GMRES (Sec. 7, Tables 2-5), x_0 = 0: Arnoldi on
+    A A_H^-1 with modified Gram-Schmidt, the Hessenberg least-squares problem
+    solved directly at every step, stop when its residual is below rtol ||b||;
+    restart every `restart` steps (0: never), x += A_H^-1 V y at the end of a
+    cycle.  Returns (x, Arnoldi steps, true relative residual)."""
     b = np.asarray(b, dtype=np.float64)
     nb = float(np.linalg.norm(b))
-    V = [b / nb]
-    Hm = np.zeros((maxit + 1, maxit))
-    Z = []
-    for j in range(maxit):
-        z = apply(F, V[j])
-        Z.append(z)
-        w = csr_matvec(rowptr, col, val, z)
-        for i in range(j + 1):
-            Hm[i, j] = float(V[i] @ w)
-            w = w - Hm[i, j] * V[i]
-        Hm[j + 1, j] = float(np.linalg.norm(w))
-        e1 = np.zeros(j + 2)
-        e1[0] = nb
-        y, *_ = np.linalg.lstsq(Hm[:j + 2, :j + 1], e1, rcond=None)
-        res = float(np.linalg.norm(Hm[:j + 2, :j + 1] @ y - e1))
-        if res < rtol * nb or Hm[j + 1, j] == 0.0:
-            return j + 1
-        V.append(w / Hm[j + 1, j])
-    return maxit
+    x = np.zeros_like(b)
+    if nb == 0.0:
+        return x, 0, 0.0
+    m = restart if 0 < restart < maxit else maxit
+    total = 0
+    done = False
+    while not done and total < maxit:
+        r = b - csr_matvec(rowptr, col, val, x)
+        beta = float(np.linalg.norm(r))
+        if beta < rtol * nb:
+            break
+        V = [r / beta]
+        Hm = np.zeros((m + 1, m))
+        y = np.zeros(0)
+        for j in range(m):
+            if total >= maxit:
+                break
+            w = csr_matvec(rowptr, col, val, apply(F, V[j]))
+            for i in range(j + 1):
+                Hm[i, j] = float(V[i] @ w)
+                w = w - Hm[i, j] * V[i]
+            Hm[j + 1, j] = float(np.linalg.norm(w))
+            total += 1
+            e1 = np.zeros(j + 2)
+            e1[0] = beta
+            y, *_ = np.linalg.lstsq(Hm[:j + 2, :j + 1], e1, rcond=None)
+            res = float(np.linalg.norm(Hm[:j + 2, :j + 1] @ y - e1))
+            if res < rtol * nb or Hm[j + 1, j] == 0.0:
+                done = True
+                break
+            V.append(w / Hm[j + 1, j])
+        if y.size:
+            x = x + apply(F, np.column_stack(V[:y.size]) @ y)
+    rel = float(np.linalg.norm(b - csr_matvec(rowptr, col, val, x))) / nb
+    return x, total, rel
+
+
+def gmres(F: Factor, rowptr, col, val, b, rtol=1e-10, maxit=300):
+    """Right-preconditioned unrestarted GMRES; iterations to ||b - A x|| < rtol ||b||."""
+    return gmres_solve(F, rowptr, col, val, b, rtol, maxit)[1]

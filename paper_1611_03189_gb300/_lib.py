@@ -40,7 +40,7 @@ STATUS_NAMES = {
 # every symbol include/hs.h declares
 EXPORTS = [
     "hs_factor_create", "hs_factor_refactor", "hs_factor_create_batch", "hs_factor_refactor_batch",
-    "hs_launch_count", "hs_profile_phases", "hs_abi_sizes", "hs_apply", "hs_apply_static", "hs_pcg", "hs_factor_info", "hs_factor_ranks",
+    "hs_launch_count", "hs_profile_phases", "hs_abi_sizes", "hs_apply", "hs_apply_static", "hs_pcg", "hs_gmres", "hs_factor_info", "hs_factor_ranks",
     "hs_factor_destroy", "hs_last_error", "hs_plan_create", "hs_plan_level_waves",
     "hs_plan_super_lists", "hs_plan_destroy",
 ]
@@ -117,6 +117,7 @@ def lib():
         L.hs_apply.argtypes = [vp, vp, vp, i32, i64, vp]
         L.hs_apply_static.argtypes = [vp, vp, vp, i32, i64, vp]
         L.hs_pcg.argtypes = [vp, vp, vp, i32, i64, dbl, i32, vp, vp, vp]
+        L.hs_gmres.argtypes = [vp, vp, vp, dbl, i32, i32, vp, vp, vp]
         L.hs_factor_info.argtypes = [vp, C.POINTER(HsInfo)]
         L.hs_factor_ranks.argtypes = [vp, i32, vp, i32, C.POINTER(i32)]
         L.hs_factor_destroy.argtypes = [vp]
@@ -266,6 +267,22 @@ class Factor:
         if code not in (HS_OK, HS_ERR_NO_CONVERGENCE) or (raise_on_fail and code != HS_OK):
             check(code)
         return x, it, rr, code
+
+    def gmres(self, b, rtol=1e-10, maxit=300, restart=0, x=None, stream=None, raise_on_fail=True):
+        """x, iters, relres, status of right-preconditioned GMRES for A x = b;
+        b is (n,) float64 CUDA; restart = 0 runs without restarts."""
+        import torch
+
+        b = b.contiguous()
+        if x is None:
+            x = torch.empty_like(b)
+        it = C.c_int32()
+        rr = C.c_double()
+        code = lib().hs_gmres(self._h, b.data_ptr(), x.data_ptr(), float(rtol), int(maxit), int(restart),
+                              C.byref(it), C.byref(rr), _stream_ptr(stream))
+        if code not in (HS_OK, HS_ERR_NO_CONVERGENCE) or (raise_on_fail and code != HS_OK):
+            check(code)
+        return x, int(it.value), float(rr.value), code
 
     def info(self) -> dict:
         inf = HsInfo()

@@ -381,6 +381,22 @@ int hs_pcg(hs_factor f, const double *b, double *x, int32_t nrhs, int64_t ld, do
   });
 }
 
+int hs_gmres(hs_factor f, const double *b, double *x, double rtol, int32_t maxit, int32_t restart,
+             int32_t *iters, double *relres, void *stream) {
+  return hs::guarded([&]() -> int {
+    if (!f || !b || !x || !iters || !relres) fail(HS_ERR_INVALID, "null argument");
+    if (!(rtol > 0.0) || maxit < 1 || restart < 0) fail(HS_ERR_INVALID, "rtol must be > 0, maxit >= 1, restart >= 0");
+    if ((restart > 0 ? std::min(restart, maxit) : maxit) > 1000)
+      fail(HS_ERR_INVALID, "the Krylov basis is limited to 1000 vectors (restart, or maxit without restart)");
+    hs::require_device();
+    if (!f->h.valid) fail(HS_ERR_INVALID, "the handle holds no valid factorization");
+    int it = 0;
+    const int r = hs::gmres_solve(f->h, b, x, rtol, maxit, restart, &it, relres, (cudaStream_t)stream);
+    *iters = it;
+    return r;
+  });
+}
+
 int hs_factor_info(hs_factor f, hs_info *info) {
   return hs::guarded([&]() -> int {
     if (!f || !info) fail(HS_ERR_INVALID, "null argument");

@@ -143,6 +143,8 @@ struct FactorHandle {
   int64_t ws_cap = 0, t_cap = 0;
   void *d_ws = nullptr, *d_t = nullptr;  // apply workspace and scratch, factor precision
   double *d_pcg = nullptr;             // x, r, p, p2, q, b, z (7 n nrhs), FP64
+  double *d_gm = nullptr;              // GMRES: Krylov basis and vectors, FP64
+  size_t gm_cap = 0;                   // doubles in d_gm
   double *d_part = nullptr;            // per-block partial sums
   double *d_scal = nullptr;            // per-rhs scalars
   int *d_iflags = nullptr;             // per-rhs ints + block counter
@@ -179,6 +181,9 @@ void apply_solve(FactorHandle &h, const double *r, double *z, int nrhs, int64_t 
                  cudaStream_t st);
 int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld, double rtol,
               int maxit, int *iters, double *relres, cudaStream_t st);
+// right-preconditioned restarted GMRES, one right-hand side (hs_gmres)
+int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int maxit, int restart, int *iters,
+                double *relres, cudaStream_t st);
 void apply_static(FactorHandle &h, const double *r, double *z, int nrhs, int64_t ld, cudaStream_t st);
 
 }  // namespace hs

@@ -16,6 +16,8 @@
 // Contributions to one phi_n are summed in a fixed order, so results do not
 // depend on scheduling.
 #include <algorithm>
+#include <cmath>
+#include <vector>
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
@@ -806,6 +808,226 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
 }
 
 // ---------------------------------------------------------------------------
+// GMRES (hs_gmres): the outer solver of the paper's experiments (Sec. 7,
+// Tables 2-5), right-preconditioned by A_H^-1, x_0 = 0, FP64.  Arnoldi on
+// A A_H^-1 with classical Gram-Schmidt applied twice (two fused passes instead
+// of the j + 1 dependent reductions of modified Gram-Schmidt); the Hessenberg
+// least-squares problem by Givens rotations on the host, which reads one
+// column of dot products per step.  At a restart (or the end)
+// x += A_H^-1 (V y).  Reductions run in an order fixed by n alone.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int GT = 256;
+
+int gm_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 4095) / 4096, 128)); }
+
+// part[i * gridDim.x + b] = block b's share of V_i . w, i = blockIdx.y < nv
+__global__ void __launch_bounds__(GT) k_gm_dots(const double *__restrict__ V, int64_t n,
+                                                const double *__restrict__ w, double *__restrict__ part) {
+  __shared__ double ws[GT / 32];
+  const double *v = V + (int64_t)blockIdx.y * n;
+  double s = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)GT + threadIdx.x; k < n; k += (int64_t)gridDim.x * GT)
+    s = fma(v[k], w[k], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < GT / 32; ++q) t += ws[q];
+    part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// h[i] = sum over b of part[i * nb + b], one warp per i
+__global__ void k_gm_sum(const double *__restrict__ part, int nb, int nv, double *__restrict__ h) {
+  const int i = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (i >= nv) return;
+  double s = 0.0;
+  for (int b = lane; b < nb; b += 32) s += part[(int64_t)i * nb + b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) h[i] = s;
+}
+
+// w -= sum_{i < nv} h_i V_i
+__global__ void k_gm_sub(const double *__restrict__ V, int64_t n, int nv, const double *__restrict__ h,
+                         double *__restrict__ w) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double s = w[k];
+    for (int i = 0; i < nv; ++i) s = fma(-h[i], V[(int64_t)i * n + k], s);
+    w[k] = s;
+  }
+}
+
+// u = sum_{i < nv} y_i V_i
+__global__ void k_gm_comb(const double *__restrict__ V, int64_t n, int nv, const double *__restrict__ y,
+                          double *__restrict__ u) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < nv; ++i) s = fma(y[i], V[(int64_t)i * n + k], s);
+    u[k] = s;
+  }
+}
+
+// v = a w ; x += z
+__global__ void k_gm_scale(const double *__restrict__ w, int64_t n, double a, double *__restrict__ v) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    v[k] = a * w[k];
+}
+__global__ void k_gm_add(double *__restrict__ x, const double *__restrict__ z, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    x[k] += z[k];
+}
+
+// y = A x (permuted CSR)
+__global__ void k_spmv(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, const double *__restrict__ va,
+                       int64_t n, const double *__restrict__ x, double *__restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; ++k) acc = fma(va[k], x[ci[k]], acc);
+    y[i] = acc;
+  }
+}
+
+// out[0 .. nv) = V_i . w for i < nv (device), through part
+void gm_dots(const double *V, int64_t n, int nv, const double *w, double *part, double *out, cudaStream_t st) {
+  const int nb = gm_blocks(n);
+  k_gm_dots<<<dim3(nb, nv), GT, 0, st>>>(V, n, w, part);
+  k_gm_sum<<<(nv * 32 + 255) / 256, 256, 0, st>>>(part, nb, nv, out);
+  count_launch(2);
+}
+
+}  // namespace
+
+int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int maxit, int restart, int *iters,
+                double *relres, cudaStream_t st) {
+  ensure_buffers(h, std::max(1, h.nrhs_cap));
+  const int64_t n = h.plan.n;
+  const int mr = std::max(1, (restart > 0 && restart < maxit) ? restart : maxit);
+  // V (mr + 1 vectors), w, u, z, X, B, R; part (mr + 1) x blocks; h1, h2, |w|^2
+  const int nb = gm_blocks(n);
+  const size_t need = (size_t)(mr + 7) * n + (size_t)(mr + 1) * nb + 2 * (size_t)(mr + 1) + 2 + (size_t)(mr + 1);
+  if (h.gm_cap < need) {
+    cudaFree(h.d_gm);
+    h.d_gm = nullptr;
+    h.gm_cap = 0;
+    HS_CUDA(cudaMalloc(&h.d_gm, sizeof(double) * need));
+    h.gm_cap = need;
+  }
+  double *V = h.d_gm, *W = V + (size_t)(mr + 1) * n, *U = W + n, *Zv = U + n, *X = Zv + n, *B = X + n, *R = B + n;
+  double *part = R + n, *hd = part + (size_t)(mr + 1) * nb, *yd = hd + 2 * (size_t)(mr + 1) + 2;
+  const int g = grid_for(n);
+  k_gather_in<double><<<g, 256, 0, st>>>(b, n, h.d_perm, n, 1, 1, B);
+  count_launch();
+  HS_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * n, st));
+  std::vector<double> hh(2 * (size_t)(mr + 1) + 2);
+  auto read = [&](int cnt) {
+    HS_CUDA(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    HS_CUDA(cudaStreamSynchronize(st));
+  };
+  gm_dots(B, n, 1, B, part, hd, st);
+  read(1);
+  const double bnorm = std::sqrt(hh[0]);
+  int total = 0;
+  bool converged = bnorm == 0.0;
+  // Hessenberg (column-major, ld mr + 1), Givens rotations, rotated rhs
+  std::vector<double> H((size_t)(mr + 1) * mr), cs(mr), sn(mr), gv(mr + 1), y(mr);
+  while (!converged && total < maxit) {
+    // r = b - A x; v_0 = r / |r|
+    if (total == 0) {
+      HS_CUDA(cudaMemcpyAsync(R, B, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+      k_residual<<<g, 256, 0, st>>>(h.d_rowptr, h.d_col, h.d_val, n, 1, X, B, R);
+      count_launch();
+    }
+    gm_dots(R, n, 1, R, part, hd, st);
+    read(1);
+    const double beta = std::sqrt(hh[0]);
+    if (beta < rtol * bnorm) {
+      converged = true;
+      break;
+    }
+    k_gm_scale<<<g, 256, 0, st>>>(R, n, 1.0 / beta, V);
+    count_launch();
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int j = 0;
+    for (; j < mr && total < maxit; ++j) {
+      // w = A A_H^-1 v_j
+      apply_pcg(h, V + (size_t)j * n, Zv, 1, st, !graphs_enabled());
+      k_spmv<<<g, 256, 0, st>>>(h.d_rowptr, h.d_col, h.d_val, n, Zv, W);
+      count_launch();
+      // two passes of classical Gram-Schmidt, then |w|^2
+      double *h1 = hd, *h2 = hd + (mr + 1);
+      gm_dots(V, n, j + 1, W, part, h1, st);
+      k_gm_sub<<<g, 256, 0, st>>>(V, n, j + 1, h1, W);
+      gm_dots(V, n, j + 1, W, part, h2, st);
+      k_gm_sub<<<g, 256, 0, st>>>(V, n, j + 1, h2, W);
+      gm_dots(W, n, 1, W, part, hd + 2 * (mr + 1), st);
+      count_launch(2);
+      HS_CUDA(cudaGetLastError());
+      HS_CUDA(cudaMemcpyAsync(hh.data(), hd, sizeof(double) * (2 * (mr + 1) + 1), cudaMemcpyDeviceToHost, st));
+      HS_CUDA(cudaStreamSynchronize(st));
+      double *col = &H[(size_t)j * (mr + 1)];
+      for (int i = 0; i <= j; ++i) col[i] = hh[i] + hh[(mr + 1) + i];
+      const double hn = std::sqrt(hh[2 * (mr + 1)]);
+      col[j + 1] = hn;
+      ++total;
+      // previous rotations, then the one that zeroes col[j + 1]
+      for (int i = 0; i < j; ++i) {
+        const double a = col[i], c = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * c;
+        col[i + 1] = -sn[i] * a + cs[i] * c;
+      }
+      const double den = std::hypot(col[j], col[j + 1]);
+      cs[j] = den > 0.0 ? col[j] / den : 1.0;
+      sn[j] = den > 0.0 ? col[j + 1] / den : 0.0;
+      col[j] = den;
+      col[j + 1] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      if (std::fabs(gv[j + 1]) < rtol * bnorm || hn == 0.0) {
+        converged = true;
+        ++j;
+        break;
+      }
+      if (j + 1 < mr && total < maxit) {
+        k_gm_scale<<<g, 256, 0, st>>>(W, n, 1.0 / hn, V + (size_t)(j + 1) * n);
+        count_launch();
+      }
+    }
+    // y = R^-1 g (upper triangular, j columns); x += A_H^-1 (V y)
+    const int k = j;
+    for (int i = k - 1; i >= 0; --i) {
+      double s = gv[i];
+      for (int c = i + 1; c < k; ++c) s -= H[(size_t)c * (mr + 1) + i] * y[c];
+      const double d = H[(size_t)i * (mr + 1) + i];
+      y[i] = d != 0.0 ? s / d : 0.0;
+    }
+    HS_CUDA(cudaMemcpyAsync(yd, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
+    k_gm_comb<<<g, 256, 0, st>>>(V, n, k, yd, U);
+    count_launch();
+    apply_pcg(h, U, Zv, 1, st, !graphs_enabled());
+    k_gm_add<<<g, 256, 0, st>>>(X, Zv, n);
+    count_launch();
+    HS_CUDA(cudaGetLastError());
+  }
+  // true relative residual, x back to the original order
+  k_residual<<<g, 256, 0, st>>>(h.d_rowptr, h.d_col, h.d_val, n, 1, X, B, R);
+  count_launch();
+  gm_dots(R, n, 1, R, part, hd, st);
+  read(1);
+  k_scatter_out<double><<<g, 256, 0, st>>>(X, h.d_perm, n, 1, 1, x, n);
+  count_launch();
+  HS_CUDA(cudaGetLastError());
+  HS_CUDA(cudaStreamSynchronize(st));
+  *iters = total;
+  *relres = bnorm > 0.0 ? std::sqrt(hh[0]) / bnorm : 0.0;
+  return converged ? HS_OK : HS_ERR_NO_CONVERGENCE;
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free apply (hs_apply_static).  Some callers cannot allocate device
 // memory when they solve: code that records work inside a CUDA stream capture,
 // or a service that fixes its device-memory footprint at start-up.  For them
@@ -889,6 +1111,7 @@ FactorHandle::~FactorHandle() {
   cudaFree(d_ws);
   cudaFree(d_t);
   cudaFree(d_pcg);
+  cudaFree(d_gm);
   cudaFree(d_part);
   cudaFree(d_scal);
   cudaFree(d_iflags);

@@ -121,6 +121,10 @@ def test_options_are_validated_before_any_device_work(lib):
     for eps, var, prec in ((-1.0, 1, 0), (1e-8, 1, 0), (0.1, 7, 0), (0.1, 1, 5), (0.1, 2, 0)):
         o = _lib.HsOpts(eps, var, prec, None)
         assert lib.hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), None, C.byref(h)) == _lib.HS_ERR_INVALID
+    # GMRES: tolerance, step counts and the Krylov basis limit come first
+    it, rr = C.c_int32(), C.c_double()
+    for rtol, maxit, restart in ((0.0, 10, 0), (1e-10, 0, 0), (1e-10, 10, -1), (1e-10, 2000, 0), (1e-10, 5000, 1001)):
+        assert lib.hs_gmres(C.c_void_p(8), 8, 8, rtol, maxit, restart, C.byref(it), C.byref(rr), None) == _lib.HS_ERR_INVALID
     # several vectors and the Appendix B projection: n_phi in range, only for the
     # variants that take vectors, eps1 finite and >= 0, phi present
     phi = np.ones(8)

@@ -179,3 +179,42 @@ def test_projection_improves_low_modes_over_lorasp():
     ip = H.pcg(Fp, pb.rowptr, pb.col, pb.val, b)[1]
     il = H.pcg(Fl, pb.rowptr, pb.col, pb.val, b)[1]
     assert ip < il
+
+
+# --- GMRES (Sec. 7, Tables 2-5) ---------------------------------------------
+
+def test_gmres_with_exact_preconditioner_takes_one_step():
+    pb = P.poisson2d(16, leaf_size=4)
+    F = _factor(pb, 0.0, H.GC_CONSTANT)
+    b = P.rhs(pb.n, 2)
+    x, it, rr = H.gmres_solve(F, pb.rowptr, pb.col, pb.val, b)
+    assert it == 1 and rr <= 1e-12
+    import scipy.sparse.linalg as spla
+
+    assert _rel(x, spla.spsolve(pb.to_scipy().tocsc(), b)) <= 1e-11
+
+
+@pytest.mark.parametrize("variant", [H.LORASP, H.GC_CONSTANT])
+def test_gmres_needs_no_more_steps_than_pcg(variant):
+    """For SPD A and SPD A_H^-1, right-preconditioned GMRES and PCG search the
+    same Krylov space; GMRES minimises the residual over it, so it reaches the
+    residual tolerance in no more steps."""
+    pb = P.diffusion2d(32, 1.0, 4, leaf_size=8)
+    F = _factor(pb, 0.2, variant)
+    b = P.rhs(pb.n, 5)
+    x, itg, rr = H.gmres_solve(F, pb.rowptr, pb.col, pb.val, b)
+    _, itc, _ = H.pcg(F, pb.rowptr, pb.col, pb.val, b)
+    assert rr <= 1e-10
+    assert itg <= itc
+    assert _rel(x, H.pcg(F, pb.rowptr, pb.col, pb.val, b)[0]) <= 1e-8
+
+
+def test_restarted_gmres_converges_and_long_restart_is_unrestarted():
+    pb = P.poisson2d(32, leaf_size=8)
+    F = _factor(pb, 0.3, H.LORASP)
+    b = P.rhs(pb.n, 8)
+    x0, it0, _ = H.gmres_solve(F, pb.rowptr, pb.col, pb.val, b)
+    x1, it1, _ = H.gmres_solve(F, pb.rowptr, pb.col, pb.val, b, restart=it0 + 5)
+    assert it1 == it0 and _rel(x1, x0) <= 1e-13
+    x2, it2, rr2 = H.gmres_solve(F, pb.rowptr, pb.col, pb.val, b, restart=3, maxit=500)
+    assert rr2 <= 1e-10 and it2 >= it0
