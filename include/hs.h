@@ -248,9 +248,12 @@ int hs_pcg(hs_factor f, const double *b, double *x, int32_t nrhs, int64_t ld, do
  * `restart` steps (0: no restart).  A is the matrix of the last successful
  * hs_factor_create / hs_factor_refactor.  b, x: DEVICE, n doubles (original
  * ordering).  iters, relres: HOST; *iters = Arnoldi steps over all cycles,
- * *relres = ||b - A x|| / ||b|| recomputed at the end.  The handle keeps the
- * Krylov basis, (m + 7) n doubles of device memory with m = restart, or maxit
- * when restart is 0; m must be <= 1000 (HS_ERR_INVALID otherwise).  Returns
+ * *relres = ||b - A x|| / ||b|| recomputed at the end.  Flexible form: the
+ * preconditioned vectors are kept and x is updated from them, so an FP32
+ * factor (whose applications round differently) still reaches rtol on the
+ * true residual.  The handle keeps the Krylov basis, (2 m + 6) n doubles of
+ * device memory with m = restart, or maxit when restart is 0; m must be
+ * <= 1000 (HS_ERR_INVALID otherwise).  Returns
  * HS_ERR_NO_CONVERGENCE (with x, iters, relres filled) after maxit steps. */
 int hs_gmres(hs_factor f, const double *b, double *x, double rtol, int32_t maxit, int32_t restart,
              int32_t *iters, double *relres, void *stream);

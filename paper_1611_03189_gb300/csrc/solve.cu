@@ -813,8 +813,12 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
 // A A_H^-1 with classical Gram-Schmidt applied twice (two fused passes instead
 // of the j + 1 dependent reductions of modified Gram-Schmidt); the Hessenberg
 // least-squares problem by Givens rotations on the host, which reads one
-// column of dot products per step.  At a restart (or the end)
-// x += A_H^-1 (V y).  Reductions run in an order fixed by n alone.
+// column of dot products per step.  Flexible form: the preconditioned vectors
+// z_j = A_H^-1 v_j are kept and a cycle ends with x += Z y.  With an FP32
+// factor each application of A_H^-1 rounds differently; x = A_H^-1 (V y)
+// would then miss the Arnoldi relation A Z = V H by that rounding (a true
+// residual near 1e-6 where the estimate says 1e-10), while A Z y stays exact.
+// Reductions run in an order fixed by n alone.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -905,9 +909,10 @@ int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int ma
   ensure_buffers(h, std::max(1, h.nrhs_cap));
   const int64_t n = h.plan.n;
   const int mr = std::max(1, (restart > 0 && restart < maxit) ? restart : maxit);
-  // V (mr + 1 vectors), w, u, z, X, B, R; part (mr + 1) x blocks; h1, h2, |w|^2
+  // V (mr + 1 vectors), Z (mr), w, u, X, B, R; part (mr + 1) x blocks; h1, h2,
+  // |w|^2; y
   const int nb = gm_blocks(n);
-  const size_t need = (size_t)(mr + 7) * n + (size_t)(mr + 1) * nb + 2 * (size_t)(mr + 1) + 2 + (size_t)(mr + 1);
+  const size_t need = (size_t)(2 * mr + 6) * n + (size_t)(mr + 1) * nb + 2 * (size_t)(mr + 1) + 2 + (size_t)(mr + 1);
   if (h.gm_cap < need) {
     cudaFree(h.d_gm);
     h.d_gm = nullptr;
@@ -915,7 +920,8 @@ int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int ma
     HS_CUDA(cudaMalloc(&h.d_gm, sizeof(double) * need));
     h.gm_cap = need;
   }
-  double *V = h.d_gm, *W = V + (size_t)(mr + 1) * n, *U = W + n, *Zv = U + n, *X = Zv + n, *B = X + n, *R = B + n;
+  double *V = h.d_gm, *Zm = V + (size_t)(mr + 1) * n, *W = Zm + (size_t)mr * n, *U = W + n, *X = U + n, *B = X + n,
+         *R = B + n;
   double *part = R + n, *hd = part + (size_t)(mr + 1) * nb, *yd = hd + 2 * (size_t)(mr + 1) + 2;
   const int g = grid_for(n);
   k_gather_in<double><<<g, 256, 0, st>>>(b, n, h.d_perm, n, 1, 1, B);
@@ -954,9 +960,10 @@ int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int ma
     gv[0] = beta;
     int j = 0;
     for (; j < mr && total < maxit; ++j) {
-      // w = A A_H^-1 v_j
-      apply_pcg(h, V + (size_t)j * n, Zv, 1, st, !graphs_enabled());
-      k_spmv<<<g, 256, 0, st>>>(h.d_rowptr, h.d_col, h.d_val, n, Zv, W);
+      // z_j = A_H^-1 v_j ; w = A z_j
+      double *zj = Zm + (size_t)j * n;
+      apply_pcg(h, V + (size_t)j * n, zj, 1, st, !graphs_enabled());
+      k_spmv<<<g, 256, 0, st>>>(h.d_rowptr, h.d_col, h.d_val, n, zj, W);
       count_launch();
       // two passes of classical Gram-Schmidt, then |w|^2
       double *h1 = hd, *h2 = hd + (mr + 1);
@@ -997,7 +1004,7 @@ int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int ma
         count_launch();
       }
     }
-    // y = R^-1 g (upper triangular, j columns); x += A_H^-1 (V y)
+    // y = R^-1 g (upper triangular, j columns); x += Z y
     const int k = j;
     for (int i = k - 1; i >= 0; --i) {
       double s = gv[i];
@@ -1006,10 +1013,9 @@ int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int ma
       y[i] = d != 0.0 ? s / d : 0.0;
     }
     HS_CUDA(cudaMemcpyAsync(yd, y.data(), sizeof(double) * k, cudaMemcpyHostToDevice, st));
-    k_gm_comb<<<g, 256, 0, st>>>(V, n, k, yd, U);
+    k_gm_comb<<<g, 256, 0, st>>>(Zm, n, k, yd, U);
     count_launch();
-    apply_pcg(h, U, Zv, 1, st, !graphs_enabled());
-    k_gm_add<<<g, 256, 0, st>>>(X, Zv, n);
+    k_gm_add<<<g, 256, 0, st>>>(X, U, n);
     count_launch();
     HS_CUDA(cudaGetLastError());
   }
