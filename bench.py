@@ -313,6 +313,63 @@ def batched_arm(args) -> None:
 # ---------------------------------------------------------------------------
 # serving: a Poisson stream of 3D diffusion factor / solve requests
 # ---------------------------------------------------------------------------
+def gmres_table_arm(args) -> None:
+    """The paper's headline experiment on the GPU (Sec. 7.1, Table 2): GMRES
+    iterations to relative residual 1e-10 preconditioned by LoRaSp,
+    GC-constant and GC-eigenvector (the smallest Laplacian eigenvector) at
+    eps = 0.1, 0.2, 0.3, on the 2D constant-coefficient Poisson problem with
+    leaves of 8 unknowns, for growing grids.  PCG iterations of the same
+    factors are reported beside them.  One JSON line."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1611_03189_gb300 import _lib
+    from paper_1611_03189_gb300 import problems as P
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    prec = _lib.HS_PREC_F32 if args.table_prec == "f32" else _lib.HS_PREC_F64
+    rows = []
+    t0 = time.perf_counter()
+    for side in (int(v) for v in args.table_sides.split(",")):
+        pb = P.poisson2d(side, leaf_size=8)
+        rp = torch.as_tensor(pb.rowptr, dtype=torch.int32, device=dev)
+        ci = torch.as_tensor(pb.col, dtype=torch.int32, device=dev)
+        va = torch.as_tensor(pb.val, dtype=torch.float64, device=dev)
+        b = torch.as_tensor(P.rhs(pb.n, 0), device=dev)
+        phi = P.laplacian_eigvec_2d(side, side)
+        row = {"side": side, "n": pb.n, "depth": int(round(math.log2(len(pb.leaf_ptr) - 1)))}
+        worst = 0.0
+        for key, var, ph in (("lorasp", _lib.HS_LORASP, None), ("gc_constant", _lib.HS_GC_CONSTANT, None),
+                             ("gc_eigenvector", _lib.HS_GC_USER, phi)):
+            gm, cg = [], []
+            for eps in (0.1, 0.2, 0.3):
+                try:
+                    G = _lib.Factor(rp, ci, va, pb.perm, pb.leaf_ptr, eps, var, prec, phi=ph)
+                except RuntimeError as e:   # a factorization that fails is reported, not fatal
+                    gm.append(None)
+                    cg.append(None)
+                    row.setdefault("errors", []).append(f"{key} eps={eps}: {e}")
+                    continue
+                _, it, rr, _ = G.gmres(b, rtol=1e-10, maxit=400, raise_on_fail=False)
+                _, itc, rrc, _ = G.pcg(b, rtol=1e-10, maxit=400, raise_on_fail=False)
+                gm.append(it)
+                cg.append(int(itc[0]))
+                worst = max(worst, rr, float(rrc[0]))
+                G.close()
+            row[key] = gm
+            row[key + "_pcg"] = cg
+        row["max_relres"] = worst
+        rows.append(row)
+    print(json.dumps({"table": "GMRES iterations to relative residual 1e-10, 2D constant-coefficient Poisson, "
+                               "leaves of 8 (Sec. 7.1, Table 2); columns eps = 0.1, 0.2, 0.3",
+                      "factor_prec": args.table_prec, "solver": "hs_gmres (flexible, no restart); hs_pcg beside it",
+                      "rhs": "standard normal, seed 0", "rows": rows,
+                      "seconds": round(time.perf_counter() - t0, 1)}), flush=True)
+
+
 def serve_arm(args) -> None:
     """Served latency (p50/p99) and throughput of the continuous-batching loop,
     mixed (FP32) factor against the plain FP64 factor on the same stream."""
@@ -390,6 +447,10 @@ def main():
     ap.add_argument("--serve-sides", default="32,96", help="grid side range of the 3D requests")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--gmres-table", action="store_true",
+                    help="GMRES iteration table of the paper's Table 2 (no timing)")
+    ap.add_argument("--table-sides", default="32,64,128,256,512,1024")
+    ap.add_argument("--table-prec", default="f32", choices=["f32", "f64"])
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -399,6 +460,9 @@ def main():
         return
     if args.serve:
         serve_arm(args)
+        return
+    if args.gmres_table:
+        gmres_table_arm(args)
         return
 
     import numpy as np
