@@ -347,7 +347,7 @@ def gmres_table_arm(args) -> None:
             gm, cg = [], []
             for eps in (0.1, 0.2, 0.3):
                 try:
-                    G = _lib.Factor(rp, ci, va, pb.perm, pb.leaf_ptr, eps, var, prec, phi=ph)
+                    G = _lib.Factor(rp, ci, va, pb.perm, pb.leaf_ptr, eps, var, prec, phi=ph, nbr_dist=args.table_nbr)
                 except RuntimeError as e:   # a factorization that fails is reported, not fatal
                     gm.append(None)
                     cg.append(None)
@@ -363,9 +363,10 @@ def gmres_table_arm(args) -> None:
             row[key + "_pcg"] = cg
         row["max_relres"] = worst
         rows.append(row)
+        print(json.dumps({"row": row}), flush=True)
     print(json.dumps({"table": "GMRES iterations to relative residual 1e-10, 2D constant-coefficient Poisson, "
                                "leaves of 8 (Sec. 7.1, Table 2); columns eps = 0.1, 0.2, 0.3",
-                      "factor_prec": args.table_prec, "solver": "hs_gmres (flexible, no restart); hs_pcg beside it",
+                      "factor_prec": args.table_prec, "nbr_dist": args.table_nbr, "solver": "hs_gmres (flexible, no restart); hs_pcg beside it",
                       "rhs": "standard normal, seed 0", "rows": rows,
                       "seconds": round(time.perf_counter() - t0, 1)}), flush=True)
 
@@ -451,6 +452,8 @@ def main():
                     help="GMRES iteration table of the paper's Table 2 (no timing)")
     ap.add_argument("--table-sides", default="32,64,128,256,512,1024")
     ap.add_argument("--table-prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--table-nbr", type=int, default=1, choices=[1, 2],
+                    help="neighbour rule: 1 edge-joined clusters, 2 also clusters sharing a neighbour")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

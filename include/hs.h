@@ -76,11 +76,19 @@ typedef struct {
  * HOST pointers.  perm[p] = original index of the p-th unknown in cluster
  * order (a permutation of 0..n-1).  Leaf i holds cluster-order unknowns
  * leaf_ptr[i] .. leaf_ptr[i+1]-1; nleaf must be a power of two, leaves must be
- * non-empty and in sibling order (leaves 2j and 2j+1 are merged first). */
+ * non-empty and in sibling order (leaves 2j and 2j+1 are merged first).
+ * nbr_dist: the neighbour rule (Sec. 3.1).  0 or 1: two nodes of a level are
+ * neighbours when their leaf sets are joined by an edge of the original
+ * graph, the paper's algebraic rule; every other block is well separated and
+ * compressed.  2: also the nodes of a level that share a neighbour, an
+ * algebraic stand-in for the geometric rule of the paper's experiments
+ * (Sec. 7: well separated when the distance exceeds the cluster size), which
+ * compresses less.  Other values are HS_ERR_INVALID. */
 typedef struct {
   const int32_t *perm;
   const int32_t *leaf_ptr;
   int32_t nleaf;
+  int32_t nbr_dist;
 } hs_clustering;
 
 /* Factorization options.

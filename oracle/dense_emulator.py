@@ -73,7 +73,7 @@ def _truncate(B, eps, variant, phi_s, phi_w, eps1=0.0):
 class DenseEmulator:
     """Dense extended-system factorization; `solve(b)` returns A_H^-1 b."""
 
-    def __init__(self, A_dense, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None, eps1=0.0):
+    def __init__(self, A_dense, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None, eps1=0.0, nbr_dist=1):
         n = A_dense.shape[0]
         perm = np.asarray(perm)
         self.perm = perm
@@ -84,9 +84,18 @@ class DenseEmulator:
         # leaf adjacency from the original pattern
         pattern = Ap != 0
 
-        def adjacent(la, lb):
+        def touching(la, lb):
             return bool(pattern[np.ix_(np.concatenate([cells[a] for a in la]),
                                        np.concatenate([cells[b] for b in lb]))].any())
+
+        self.level_sets = []     # leaf sets of the current level's super nodes
+
+        def adjacent(la, lb):
+            if touching(la, lb):
+                return True
+            # distance 2: a super node of this level touches both
+            return nbr_dist == 2 and any(touching(la, lz) and touching(lz, lb) and set(lz) != set(la)
+                                         and set(lz) != set(lb) for lz in self.level_sets)
 
         self.eps1 = eps1
         phi0 = np.asarray(phi, dtype=float)[perm] if variant in (GC_USER, GC_PROJ) else np.ones(n)
@@ -109,6 +118,7 @@ class DenseEmulator:
                     del groups[p]
                 groups[("s", lev, i)] = (idx, leaves)
                 supers.append(("s", lev, i))
+            self.level_sets = [groups[s][1] for s in supers]
             new_red = [None] * nsup
 
             def coupled(g, h):

@@ -52,6 +52,11 @@ design notes):
      threshold eps ||A_sw||_2 are those of GC.  The appendix does not say what
      the parent red node keeps of X: as in Sec. 6, X_r = U^T X_s.  The caller
      passes the columns of X already scaled (e_i / lambda_i in the appendix).
+  R14 neighbour rule of the experiments (Sec. 7 uses a geometric rule: well
+     separated when the distance exceeds the cluster size; the C ABI carries
+     no coordinates): with nbr_dist = 2, two super nodes of a level are also
+     neighbours when they share a neighbour at that level (distance 2 in the
+     level's cluster graph).  nbr_dist = 1 is R1.
 
 Node keys inside a level: super node i -> i, red node made from super node i ->
 nsup + i.  Blocks are stored in both orientations, kept consistent.
@@ -283,7 +288,7 @@ def eps_schedule_lorasp(eps: float, L: int, h: float) -> list:
 
 
 def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None,
-           order="waves", keep_U=False, eps_level=None, eps1=0.0) -> Factor:
+           order="waves", keep_U=False, eps_level=None, eps1=0.0, nbr_dist=1) -> Factor:
     """Hierarchical factorization.
 
     n, rowptr, col, val: CSR of the SPD matrix A in original ordering.
@@ -295,6 +300,8 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
         (level L - j); it needs L - 1 entries.
     phi: for GC_USER and GC_PROJ, the vector to preserve (original ordering),
         or an n x p array of p vectors.
+    nbr_dist: 1, neighbours are joined by an edge of the original graph (R1);
+        2, also the nodes of a level that share a neighbour (R14).
     order: "waves" (R4), "waves-reversed" (same waves, each eliminated in
         descending order) or "sequential" (ascending super index, one at a time).
     """
@@ -334,6 +341,13 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
         for a, b in leaf_adj:
             if a in owner and b in owner and owner[a] != owner[b]:
                 coarse_adj.add((owner[a], owner[b]))
+        if nbr_dist == 2:
+            # R14: also the super nodes of this level that share a neighbour
+            direct = {}
+            for x, y in coarse_adj:
+                direct.setdefault(x, set()).add(y)
+            coarse_adj = coarse_adj | {(x, y) for x in direct for z in direct[x] for y in direct.get(z, ())
+                                       if y != x}
 
         def adjacent(x, y):
             return ((x - nsup if x >= nsup else x), (y - nsup if y >= nsup else y)) in coarse_adj

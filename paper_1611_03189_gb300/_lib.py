@@ -58,7 +58,7 @@ class HsCsr(C.Structure):
 
 
 class HsClustering(C.Structure):
-    _fields_ = [("perm", C.c_void_p), ("leaf_ptr", C.c_void_p), ("nleaf", C.c_int32)]
+    _fields_ = [("perm", C.c_void_p), ("leaf_ptr", C.c_void_p), ("nleaf", C.c_int32), ("nbr_dist", C.c_int32)]
 
 
 class HsOpts(C.Structure):
@@ -156,10 +156,10 @@ def _ptr(a: np.ndarray) -> int:
 class Plan:
     """Symbolic planner of the library (host only)."""
 
-    def __init__(self, n, rowptr, col, perm, leaf_ptr):
+    def __init__(self, n, rowptr, col, perm, leaf_ptr, nbr_dist=1):
         self._keep = [np.ascontiguousarray(x, dtype=np.int32) for x in (rowptr, col, perm, leaf_ptr)]
         rp, ci, pe, lp = self._keep
-        cl = HsClustering(_ptr(pe), _ptr(lp), len(lp) - 1)
+        cl = HsClustering(_ptr(pe), _ptr(lp), len(lp) - 1, int(nbr_dist))
         h = C.c_void_p()
         check(lib().hs_plan_create(int(n), _ptr(rp), _ptr(ci), C.byref(cl), C.byref(h)))
         self._h = h
@@ -210,11 +210,12 @@ class Factor:
     rowptr, col: int32 CUDA tensors; val: float64 CUDA tensor (original order).
     perm, leaf_ptr: host int32 arrays (clustering).  phi: host float64, an
     n-vector or n x p (p <= HS_MAX_PHI vectors), for HS_GC_USER / HS_GC_PROJ.
-    eps1: HS_GC_PROJ's first tolerance.
+    eps1: HS_GC_PROJ's first tolerance.  nbr_dist: neighbour rule (1: joined by
+    an edge; 2: also nodes sharing a neighbour).
     """
 
     def __init__(self, rowptr, col, val, perm, leaf_ptr, eps, variant=HS_GC_CONSTANT,
-                 prec=HS_PREC_F64, phi=None, stream=None, eps_level=None, eps1=0.0):
+                 prec=HS_PREC_F64, phi=None, stream=None, eps_level=None, eps1=0.0, nbr_dist=1):
         import torch
 
         assert rowptr.is_cuda and col.is_cuda and val.is_cuda
@@ -224,7 +225,7 @@ class Factor:
         self._lp = np.ascontiguousarray(leaf_ptr, dtype=np.int32)
         self._phi, nphi = (None, 0) if phi is None else _phi_block(phi)
         A = HsCsr(self.n, int(col.numel()), rowptr.data_ptr(), col.data_ptr(), val.data_ptr())
-        cl = HsClustering(_ptr(self._perm), _ptr(self._lp), len(self._lp) - 1)
+        cl = HsClustering(_ptr(self._perm), _ptr(self._lp), len(self._lp) - 1, int(nbr_dist))
         self._epsl = None if eps_level is None else np.ascontiguousarray(eps_level, dtype=np.float64)
         o = HsOpts(float(eps), int(variant), int(prec), None if self._phi is None else _ptr(self._phi),
                    None if self._epsl is None else _ptr(self._epsl), 0 if self._epsl is None else len(self._epsl),
@@ -309,7 +310,7 @@ class Factor:
 
 
 def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=None, stream=None,
-                 eps_level=None, eps1=0.0):
+                 eps_level=None, eps1=0.0, nbr_dist=1):
     """hs_factor_create_batch over `problems`: a list of (rowptr, col, val,
     perm, leaf_ptr) with rowptr/col int32 and val float64 CUDA tensors and
     perm/leaf_ptr host arrays.  Returns (factors, status): one Factor per
@@ -327,7 +328,7 @@ def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=N
         lpa = np.ascontiguousarray(lp, dtype=np.int32)
         keep += [pe, lpa]
         A[p] = HsCsr(int(rp.numel() - 1), int(ci.numel()), rp.data_ptr(), ci.data_ptr(), va.data_ptr())
-        cl[p] = HsClustering(_ptr(pe), _ptr(lpa), len(lpa) - 1)
+        cl[p] = HsClustering(_ptr(pe), _ptr(lpa), len(lpa) - 1, int(nbr_dist))
     phi_arr = None
     nphi = 0
     if phis is not None:

@@ -152,6 +152,12 @@ void numeric_factor(FactorHandle &h, const double *val, const double *phi_host, 
   numeric_factor_all({&h}, {val}, {phi_host}, st);
 }
 
+// neighbour rule of a clustering (0 reads as 1)
+int nbr_rule(int32_t d) {
+  if (d < 0 || d > 2) fail(HS_ERR_INVALID, "nbr_dist must be 0, 1 or 2");
+  return d == 0 ? 1 : d;
+}
+
 // checks and planning of hs_factor_create; the handle is left ready for numeric_factor
 void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, const hs_opts *o, cudaStream_t st) {
   if (!A || !cl) fail(HS_ERR_INVALID, "null argument");
@@ -171,7 +177,7 @@ void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, con
   HS_CUDA(cudaMemcpyAsync(ci.data(), A->col, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost, st));
   HS_CUDA(cudaStreamSynchronize(st));
   if (rp[A->n] != A->nnz) fail(HS_ERR_INVALID, "rowptr[n] != nnz");
-  build_plan(A->n, rp.data(), ci.data(), cl->perm, cl->leaf_ptr, cl->nleaf, h.plan);
+  build_plan(A->n, rp.data(), ci.data(), cl->perm, cl->leaf_ptr, cl->nleaf, h.plan, nbr_rule(cl->nbr_dist));
   if (o->eps_level) {
     const int need = std::max(h.plan.L - 1, 0);
     if (o->n_eps_level < need)
@@ -430,7 +436,7 @@ int hs_plan_create(int64_t n, const int32_t *rowptr, const int32_t *col, const h
     if (!rowptr || !col || !cl || !cl->perm || !cl->leaf_ptr || !out) fail(HS_ERR_INVALID, "null argument");
     *out = nullptr;
     std::unique_ptr<hs_plan_s> p(new hs_plan_s());
-    hs::build_plan(n, rowptr, col, cl->perm, cl->leaf_ptr, cl->nleaf, p->p);
+    hs::build_plan(n, rowptr, col, cl->perm, cl->leaf_ptr, cl->nleaf, p->p, hs::nbr_rule(cl->nbr_dist));
     *out = p.release();
     return HS_OK;
   });

@@ -18,8 +18,9 @@ void check(bool ok, const std::string &msg) {
 }  // namespace
 
 void build_plan(int64_t n, const int32_t *rowptr, const int32_t *col, const int32_t *perm,
-                const int32_t *leaf_ptr, int32_t nleaf, Plan &P) {
+                const int32_t *leaf_ptr, int32_t nleaf, Plan &P, int nbr_dist) {
   check(n > 0, "n must be positive");
+  check(nbr_dist >= 0 && nbr_dist <= 2, "nbr_dist must be 0, 1 or 2");
   check(n < (int64_t)1 << 31, "n must fit in int32");
   check(nleaf >= 1 && (nleaf & (nleaf - 1)) == 0, "nleaf must be a power of two");
   int L = 0;
@@ -131,6 +132,21 @@ void build_plan(int64_t n, const int32_t *rowptr, const int32_t *col, const int3
       auto &v = sadj[i];
       std::sort(v.begin(), v.end());
       v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+    if (nbr_dist == 2) {
+      // also the super nodes that share a neighbour at this level (cluster-graph
+      // distance 2)
+      std::vector<std::vector<int>> s2(nsup);
+      for (int i = 0; i < nsup; ++i) {
+        auto &v = s2[i];
+        v = sadj[i];
+        for (int z : sadj[i])
+          for (int y : sadj[z])
+            if (y != i) v.push_back(y);
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+      }
+      sadj.swap(s2);
     }
     auto base = [nsup](int key) { return key >= nsup ? key - nsup : key; };
     auto adjacent = [&](int x, int y) {

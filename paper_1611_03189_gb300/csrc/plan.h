@@ -50,8 +50,10 @@ struct Plan {
   int total_waves = 0;
 };
 
+// nbr_dist: 0 or 1, neighbours are joined by an edge of the original graph
+// (Sec. 3.1); 2, also the nodes of a level that share a neighbour.
 // Throws hs::fail(HS_ERR_INVALID, ...) on bad input.
 void build_plan(int64_t n, const int32_t *rowptr, const int32_t *col, const int32_t *perm,
-                const int32_t *leaf_ptr, int32_t nleaf, Plan &out);
+                const int32_t *leaf_ptr, int32_t nleaf, Plan &out, int nbr_dist = 1);
 
 }  // namespace hs

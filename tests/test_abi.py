@@ -56,10 +56,11 @@ PLAN_CASES = [
 
 
 @pytest.mark.parametrize("name,maker", PLAN_CASES, ids=[c[0] for c in PLAN_CASES])
-def test_planner_matches_oracle_waves_and_lists(lib, name, maker):
+@pytest.mark.parametrize("nbr_dist", [1, 2])
+def test_planner_matches_oracle_waves_and_lists(lib, name, maker, nbr_dist):
     pb = maker()
-    F = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, 0.3, H.LORASP)
-    plan = _lib.Plan(pb.n, pb.rowptr, pb.col, pb.perm, pb.leaf_ptr)
+    F = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, 0.3, H.LORASP, nbr_dist=nbr_dist)
+    plan = _lib.Plan(pb.n, pb.rowptr, pb.col, pb.perm, pb.leaf_ptr, nbr_dist=nbr_dist)
     try:
         for lv in F.levels:
             wo = plan.waves(lv.level)
@@ -91,6 +92,10 @@ def test_planner_rejects_bad_inputs(lib):
     with pytest.raises(_lib.HsError) as e:
         _lib.Plan(2, rp, ci, np.array([0, 1], np.int32), np.array([0, 1, 2], np.int32))
     assert "symmetric" in str(e.value)
+    for d in (-1, 3):
+        with pytest.raises(_lib.HsError) as e:
+            _lib.Plan(pb.n, pb.rowptr, pb.col, pb.perm, pb.leaf_ptr, nbr_dist=d)
+        assert "nbr_dist" in str(e.value)
 
 
 def test_library_does_not_fall_back_without_a_device(lib):

@@ -218,3 +218,48 @@ def test_restarted_gmres_converges_and_long_restart_is_unrestarted():
     assert it1 == it0 and _rel(x1, x0) <= 1e-13
     x2, it2, rr2 = H.gmres_solve(F, pb.rowptr, pb.col, pb.val, b, restart=3, maxit=500)
     assert rr2 <= 1e-10 and it2 >= it0
+
+
+# --- neighbour rule of the experiments (R14) -------------------------------
+
+@pytest.mark.parametrize("variant", [H.LORASP, H.GC_CONSTANT])
+def test_distance2_rule_matches_the_emulator(variant):
+    """The emulator applies the rule to its own dense leaf sets: same A_H^-1."""
+    pb = P.poisson2d(16, leaf_size=4)
+    A = pb.to_scipy().toarray()
+    F = _factor(pb, 0.2, variant, nbr_dist=2)
+    E = DenseEmulator(A, pb.perm, pb.leaf_ptr, 0.2, variant, nbr_dist=2)
+    I = np.eye(pb.n)
+    Z1 = H.apply(F, I)
+    Z2 = np.column_stack([E.solve(e) for e in I])
+    assert np.abs(Z1 - Z2).max() <= 1e-12 * np.abs(Z1).max()
+    assert np.abs(Z1 @ A - I).max() > 1e-8
+
+
+def test_distance2_rule_keeps_exactness_and_preservation():
+    pb = P.poisson2d(24, leaf_size=8)
+    b = P.rhs(pb.n, 1)
+    import scipy.sparse.linalg as spla
+
+    F0 = _factor(pb, 0.0, H.GC_CONSTANT, nbr_dist=2)
+    assert _rel(H.apply(F0, b), spla.spsolve(pb.to_scipy().tocsc(), b)) <= 1e-11
+    V, lam = _eig(24, [(1, 1), (2, 1)])
+    F = _factor(pb, 0.2, H.GC_USER, phi=V, nbr_dist=2)
+    Z = H.apply(F, V)
+    for i in range(2):
+        assert _rel(Z[:, i], V[:, i] / lam[i]) <= 1e-11
+
+
+def test_distance2_rule_converges_faster():
+    """The GMRES counts come down towards the paper's Table 2 (32 x 32, leaves
+    of 8: 5 / 7 at eps 0.1 / 0.3 for LoRaSp and GC-constant), and GC-constant
+    still needs no more steps than LoRaSp."""
+    pb = P.poisson2d(32, leaf_size=8)
+    b = P.rhs(pb.n, 0)
+    its = {}
+    for d in (1, 2):
+        for var in (H.LORASP, H.GC_CONSTANT):
+            F = _factor(pb, 0.3, var, nbr_dist=d)
+            its[d, var] = H.gmres(F, pb.rowptr, pb.col, pb.val, b)
+    assert its[2, H.LORASP] < its[1, H.LORASP] and its[2, H.LORASP] <= 9
+    assert its[2, H.GC_CONSTANT] <= its[2, H.LORASP]
