@@ -166,16 +166,22 @@ void build_plan(int64_t n, const int32_t *rowptr, const int32_t *col, const int3
     for (int i = 0; i < nsup; ++i)
       if (lv.exists[i]) remaining.push_back(i);
     int widx = 0;
+    // wave members so far (a node conflicts with the wave when one of its
+    // blocks leads to a member): O(blocks) per candidate
+    std::vector<char> inwave(2 * nsup, 0);
     while (!remaining.empty()) {
       std::vector<int> wave;
       for (int s : remaining) {
         bool ok = true;
-        for (int t : wave)
-          if (nb[s].count(t)) {
+        for (int x : nb[s])
+          if (inwave[x]) {
             ok = false;
             break;
           }
-        if (ok) wave.push_back(s);
+        if (ok) {
+          wave.push_back(s);
+          inwave[s] = 1;
+        }
       }
       for (int s : wave) {
         PlanSuper &ps = lv.sup[s];
@@ -202,9 +208,9 @@ void build_plan(int64_t n, const int32_t *rowptr, const int32_t *col, const int3
         }
       }
       std::vector<int> rest;
-      std::set<int> taken(wave.begin(), wave.end());
       for (int s : remaining)
-        if (!taken.count(s)) rest.push_back(s);
+        if (!inwave[s]) rest.push_back(s);
+      for (int s : wave) inwave[s] = 0;
       remaining.swap(rest);
       lv.waves.push_back(wave);
       ++widx;
