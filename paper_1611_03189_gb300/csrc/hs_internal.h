@@ -128,6 +128,7 @@ struct CholTask {
 // basis U_1 they give: the columns of phi_s and of A_sw phi_w.
 constexpr int kMaxPhi = 4;
 constexpr int kMaxK1 = 2 * kMaxPhi;
+static_assert(kMaxPhi == HS_MAX_PHI, "the kernels' vector limit must match the ABI's");
 
 // Truncation of one super node (Sec. 3.2 compression, Sec. 6 GC basis,
 // Appendix B projection).  G = A_sw A_sw^T (m x m, ld m); a = A_sw phi_w and
