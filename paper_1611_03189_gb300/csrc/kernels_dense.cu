@@ -518,10 +518,13 @@ __global__ void __launch_bounds__(TRUNC_THREADS) k_trunc(const TruncTask<T> *__r
   if (eps == 0.0) {
     // no truncation: complete the GC basis to all of R^m (Householder QR of U_1;
     // scratch k1 m <= 2 m^2 T in A and V)
-    if (k1 <= 2)
-      gc_complete<T>(t.U, m, k1, (double *)A, red);
-    else
-      gc_complete_n<T>(t.U, m, k1, (double *)A, s_gW, red);
+    // (nothing to complete when U_1 already spans R^m)
+    if (k1 < m) {
+      if (k1 <= 2)
+        gc_complete<T>(t.U, m, k1, (double *)A, red);
+      else
+        gc_complete_n<T>(t.U, m, k1, (double *)A, s_gW, red);
+    }
     if (tid == 0) kout[t.k_idx] = m;
     return;
   }

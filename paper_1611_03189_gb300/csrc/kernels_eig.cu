@@ -558,10 +558,13 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
   if (gc && eps == 0.0) {
     // no truncation: complete the GC basis to all of R^m (Householder QR of
     // U_1; scratch k1 m doubles in Y and LU, 5 m^2 T)
-    if (k1 <= 2)
-      gc_complete<T>(t.U, m, k1, (double *)Y, red);
-    else
-      gc_complete_n<T>(t.U, m, k1, (double *)Y, s_gW, red);
+    // (nothing to complete when U_1 already spans R^m)
+    if (k1 < m) {
+      if (k1 <= 2)
+        gc_complete<T>(t.U, m, k1, (double *)Y, red);
+      else
+        gc_complete_n<T>(t.U, m, k1, (double *)Y, s_gW, red);
+    }
     if (tid == 0) kout[t.k_idx] = m;
     return;
   }
