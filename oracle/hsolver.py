@@ -139,6 +139,13 @@ def complete_basis(U1: np.ndarray, m: int) -> np.ndarray:
     return V[:, w > 0.5]
 
 
+def _margin(sv: np.ndarray, thr: float) -> float:
+    """min_i |sv_i - thr| / thr (inf for thr = 0 or no values)."""
+    if thr <= 0.0 or sv.size == 0:
+        return math.inf
+    return float(np.min(np.abs(sv - thr)) / thr)
+
+
 def compress(B: np.ndarray, eps: float, variant: int, phi_s=None, phi_w=None, eps1: float = 0.0):
     """Return U (m x k, orthonormal columns) for the well-separated block B = A_sw.
 
@@ -148,27 +155,37 @@ def compress(B: np.ndarray, eps: float, variant: int, phi_s=None, phi_w=None, ep
     GC_PROJ (Appendix B): as GC, with U_1 the left singular vectors of
     [phi_s, B phi_w] above eps1 times its norm (R12).
     """
+    return _compress(B, eps, variant, phi_s, phi_w, eps1)[0]
+
+
+def _compress(B: np.ndarray, eps: float, variant: int, phi_s=None, phi_w=None, eps1: float = 0.0):
+    """compress(), and the margin of its rank decisions (SuperRecord.margin)."""
     m = B.shape[0]
     if m == 0:
-        return np.zeros((0, 0))
+        return np.zeros((0, 0)), math.inf
     if variant == LORASP:
         if eps == 0.0:
-            return np.eye(m)
+            return np.eye(m), math.inf
         Ub, sb, _ = np.linalg.svd(B, full_matrices=False)
         normB = sb[0] if sb.size else 0.0
         k = int(np.count_nonzero(sb > eps * normB))
-        return Ub[:, :k].copy()
+        return Ub[:, :k].copy(), _margin(sb, eps * normB)
+    margin = math.inf
     if variant == GC_PROJ:
-        U1 = proj_basis(np.hstack([_columns(phi_s), _columns(B @ phi_w)]), eps1)
+        C1 = np.hstack([_columns(phi_s), _columns(B @ phi_w)])
+        U1 = proj_basis(C1, eps1)
+        s1 = np.linalg.svd(C1, compute_uv=False)
+        if s1.size and s1[0] > 0.0:
+            margin = _margin(s1, max(eps1, MGS_DROP) * s1[0])
     else:
         U1 = gc_basis(phi_s, B @ phi_w)
     if eps == 0.0:
-        return np.hstack([U1, complete_basis(U1, m)])
+        return np.hstack([U1, complete_basis(U1, m)]), margin
     normB = float(np.linalg.svd(B, compute_uv=False)[0]) if B.size else 0.0
     C = B - U1 @ (U1.T @ B)
     Uc, sc, _ = np.linalg.svd(C, full_matrices=False)
     k2 = int(np.count_nonzero(sc > eps * normB))
-    return np.hstack([U1, Uc[:, :k2]])
+    return np.hstack([U1, Uc[:, :k2]]), min(margin, _margin(sc, eps * normB))
 
 
 # ---------------------------------------------------------------------------
@@ -189,6 +206,10 @@ class SuperRecord:
     P: np.ndarray         # P_ss = S^-1 U^T A_ss^-1          (k x m)
     wsep: list = field(default_factory=list)   # keys of W(s), for inspection
     U: np.ndarray | None = None
+    # smallest relative distance |sigma_i - threshold| / threshold among the
+    # singular values behind this node's rank decisions (inf when none): ranks
+    # from another implementation may differ only where this is tiny
+    margin: float = math.inf
 
 
 @dataclass
@@ -212,6 +233,7 @@ class Factor:
     root_chol: np.ndarray | None
     eps: float
     variant: int
+    partial: bool = False  # only the first levels were factored (no solve)
 
     def ranks(self):
         """{level: {super index: k}} for every super node with a red node."""
@@ -288,7 +310,7 @@ def eps_schedule_lorasp(eps: float, L: int, h: float) -> list:
 
 
 def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None,
-           order="waves", keep_U=False, eps_level=None, eps1=0.0, nbr_dist=1) -> Factor:
+           order="waves", keep_U=False, eps_level=None, eps1=0.0, nbr_dist=1, levels=None) -> Factor:
     """Hierarchical factorization.
 
     n, rowptr, col, val: CSR of the SPD matrix A in original ordering.
@@ -302,6 +324,8 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
         or an n x p array of p vectors.
     nbr_dist: 1, neighbours are joined by an edge of the original graph (R1);
         2, also the nodes of a level that share a neighbour (R14).
+    levels: factor only that many levels above the leaves and return a
+        partial record (ranks and margins to compare; it cannot be applied).
     order: "waves" (R4), "waves-reversed" (same waves, each eliminated in
         descending order) or "sequential" (ascending super index, one at a time).
     """
@@ -323,11 +347,13 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
     red_size = {i: int(leaf_ptr[i + 1] - leaf_ptr[i]) for i in range(nleaf)}
     red_leaves = {i: (i,) for i in range(nleaf)}
     red_phi = {i: phi_perm[leaf_ptr[i]:leaf_ptr[i + 1]].copy() for i in range(nleaf)}
-    levels = []
+    all_levels = []
 
     if eps_level is not None and len(eps_level) < L - 1:
         raise ValueError("eps_level needs L - 1 entries (levels L..2)")
     for lev in range(L, 1, -1):
+        if levels is not None and L - lev >= levels:
+            return Factor(n, perm, leaf_ptr, L, all_levels, -1, None, eps, variant, partial=True)
         nsup = 2 ** (lev - 1)
         eps_l = float(eps_level[L - lev]) if eps_level is not None else eps
         # leaf sets of the super nodes: union of the leaf sets of the red nodes that
@@ -417,7 +443,7 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
             assert x >= nsup and y >= nsup, "super node left uneliminated"
             nxt[(x - nsup, y - nsup)] = blk
         blocks = nxt
-        levels.append(LevelRecord(lev, nsup, sup_size, dict(new_red_size), records, waves))
+        all_levels.append(LevelRecord(lev, nsup, sup_size, dict(new_red_size), records, waves))
         red_size = new_red_size
         red_phi = new_red_phi
         red_leaves = {i: sup_leaves[i] for i in new_red_size}
@@ -444,7 +470,7 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
             root_chol = np.linalg.cholesky(A_root)
         except np.linalg.LinAlgError as e:
             raise NotSPD("root block is not positive definite") from e
-    return Factor(n, perm, leaf_ptr, L, levels, root_size, root_chol, eps, variant)
+    return Factor(n, perm, leaf_ptr, L, all_levels, root_size, root_chol, eps, variant)
 
 
 def _set_block(blocks, nbr_of, x, y, blk):
@@ -469,11 +495,11 @@ def _eliminate(s, nsup, blocks, nbr_of, size, vphi, adjacent, eps, variant, use_
         B = np.hstack([blocks[(s, w)] for w in W]) if m else np.zeros((0, sum(size[w] for w in W)))
         if use_phi:
             phi_w = np.concatenate([vphi[w] for w in W])
-            U = compress(B, eps, variant, vphi[s], phi_w, eps1)
+            U, margin = _compress(B, eps, variant, vphi[s], phi_w, eps1)
         else:
-            U = compress(B, eps, variant)
+            U, margin = _compress(B, eps, variant)
     else:
-        U = np.zeros((m, 0))
+        U, margin = np.zeros((m, 0)), math.inf
     k = U.shape[1]
 
     # elimination of [x_s; y_b] (eq. extended_rearranged, K = L K_2 L^T).
@@ -539,7 +565,7 @@ def _eliminate(s, nsup, blocks, nbr_of, size, vphi, adjacent, eps, variant, use_
         nbr_of[x].discard(s)
     del blocks[(s, s)]
     nbr_of.pop(s, None)
-    return SuperRecord(s, widx, m, k, N, A_sn, M, P, W, U if keep_U else None)
+    return SuperRecord(s, widx, m, k, N, A_sn, M, P, W, U if keep_U else None, margin)
 
 
 # ---------------------------------------------------------------------------
@@ -548,6 +574,8 @@ def _eliminate(s, nsup, blocks, nbr_of, size, vphi, adjacent, eps, variant, use_
 
 def apply(F: Factor, r: np.ndarray) -> np.ndarray:
     """z = A_H^-1 r (r in original ordering; 1-D or 2-D with columns as RHS)."""
+    if F.partial:
+        raise ValueError("a partial factorization (levels=...) cannot be applied")
     r = np.asarray(r, dtype=np.float64)
     vec = r.ndim == 1
     R = r[:, None] if vec else r

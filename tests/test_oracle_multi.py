@@ -302,3 +302,35 @@ def test_table3_3d_counts_are_close_to_the_paper():
         for key, v in got.items():
             assert abs(v - paper[key]) <= 3, (side, key, v, paper[key])
         assert got["ad.3"] <= got["gc.3"]
+
+
+# --- partial factorization and rank margins (full-size checks) --------------
+
+def test_partial_factorization_is_a_prefix_of_the_full_one():
+    pb = P.diffusion2d(32, 1.0, 3, leaf_size=8)
+    F = _factor(pb, 1e-2, H.GC_CONSTANT)
+    Fp = _factor(pb, 1e-2, H.GC_CONSTANT, levels=2)
+    assert Fp.partial and len(Fp.levels) == 2
+    for a, b in zip(Fp.levels, F.levels[:2]):
+        assert a.level == b.level and a.waves == b.waves
+        assert [(r.key, r.k, r.nbrs, r.wsep) for r in a.supers] == [(r.key, r.k, r.nbrs, r.wsep) for r in b.supers]
+    with pytest.raises(ValueError):
+        H.apply(Fp, np.ones(pb.n))
+
+
+def test_rank_margin_is_the_distance_to_the_threshold():
+    """margin = min_i |sigma_i - eps sigma_1| / (eps sigma_1): a tolerance just
+    above the threshold by less than the margin keeps the rank, one beyond it
+    changes it."""
+    B = _lowrankish(16, 40, 2)
+    sv = np.linalg.svd(B, compute_uv=False)
+    eps = 0.05
+    U, margin = H._compress(B, eps, H.LORASP)
+    i = int(np.argmin(np.abs(sv - eps * sv[0])))
+    assert margin == pytest.approx(abs(sv[i] - eps * sv[0]) / (eps * sv[0]))
+    k = U.shape[1]
+    assert H.compress(B, eps * (1 + 0.5 * margin), H.LORASP).shape[1] == k
+    assert H.compress(B, eps * (1 - 0.5 * margin), H.LORASP).shape[1] == k
+    # crossing sigma_i changes the rank by one
+    assert H.compress(B, sv[i] / sv[0] * (1 + 1e-9), H.LORASP).shape[1] != H.compress(
+        B, sv[i] / sv[0] * (1 - 1e-9), H.LORASP).shape[1]
