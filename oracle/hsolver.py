@@ -52,6 +52,11 @@ design notes):
      threshold eps ||A_sw||_2 are those of GC.  The appendix does not say what
      the parent red node keeps of X: as in Sec. 6, X_r = U^T X_s.  The caller
      passes the columns of X already scaled (e_i / lambda_i in the appendix).
+  R15 symmetric diagonal scaling (an option the paper does not mention): the
+     factorization of D^-1/2 A D^-1/2 (D = diag A).  With a 1e-5 coefficient
+     jump, GC-constant on A itself loses definiteness (R9): the constant
+     vector in U_1 mixes the O(1) rows of A_sw into the 1e-5 rows.  Scaled,
+     the rows have one scale and the GMRES counts come close to Table 4.
   R14 neighbour rule of the experiments (Sec. 7 uses a geometric rule: well
      separated when the distance exceeds the cluster size; the C ABI carries
      no coordinates): with nbr_dist = 2, two super nodes of a level are also
@@ -234,6 +239,7 @@ class Factor:
     eps: float
     variant: int
     partial: bool = False  # only the first levels were factored (no solve)
+    dscale: np.ndarray | None = None  # R15: D^-1/2 (original order) when scaled
 
     def ranks(self):
         """{level: {super index: k}} for every super node with a red node."""
@@ -310,7 +316,8 @@ def eps_schedule_lorasp(eps: float, L: int, h: float) -> list:
 
 
 def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None,
-           order="waves", keep_U=False, eps_level=None, eps1=0.0, nbr_dist=1, levels=None) -> Factor:
+           order="waves", keep_U=False, eps_level=None, eps1=0.0, nbr_dist=1, levels=None,
+           scale=False) -> Factor:
     """Hierarchical factorization.
 
     n, rowptr, col, val: CSR of the SPD matrix A in original ordering.
@@ -326,6 +333,10 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
         2, also the nodes of a level that share a neighbour (R14).
     levels: factor only that many levels above the leaves and return a
         partial record (ranks and margins to compare; it cannot be applied).
+    scale: factor D^-1/2 A D^-1/2 (D = diag A) instead of A (R15); apply()
+        then returns D^-1/2 A_H'^-1 D^-1/2 r.  GC-constant preserves the
+        constant vector of the scaled system; GC_USER / GC_PROJ vectors are
+        mapped to it (D^1/2 phi), so that they stay preserved for A.
     order: "waves" (R4), "waves-reversed" (same waves, each eliminated in
         descending order) or "sequential" (ascending super index, one at a time).
     """
@@ -336,10 +347,24 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
     L = int(round(math.log2(nleaf)))
     if 2 ** L != nleaf:
         raise ValueError("number of leaves must be a power of two")
+    dscale = None
+    if scale:
+        # R15: symmetric diagonal scaling, D^-1/2 A D^-1/2
+        rows = np.repeat(np.arange(n), np.diff(rowptr))
+        col_a = np.asarray(col, dtype=np.int64)
+        diag = np.zeros(n)
+        np.add.at(diag, rows[rows == col_a], np.asarray(val, dtype=np.float64)[rows == col_a])
+        if np.any(diag <= 0.0):
+            raise NotSPD("a diagonal entry is not positive")
+        dscale = 1.0 / np.sqrt(diag)
+        val = np.asarray(val, dtype=np.float64) * dscale[rows] * dscale[col_a]
     blocks, leaf_adj = _leaf_blocks(n, rowptr, col, val, perm, leaf_ptr)
     use_phi = variant in (GC_CONSTANT, GC_USER, GC_PROJ)
     if variant in (GC_USER, GC_PROJ):
-        phi_perm = np.asarray(phi, dtype=np.float64)[perm]
+        ph = np.asarray(phi, dtype=np.float64)
+        if dscale is not None:
+            ph = ph / (dscale if ph.ndim == 1 else dscale[:, None])
+        phi_perm = ph[perm]
     else:
         phi_perm = np.ones(n)
 
@@ -353,7 +378,7 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
         raise ValueError("eps_level needs L - 1 entries (levels L..2)")
     for lev in range(L, 1, -1):
         if levels is not None and L - lev >= levels:
-            return Factor(n, perm, leaf_ptr, L, all_levels, -1, None, eps, variant, partial=True)
+            return Factor(n, perm, leaf_ptr, L, all_levels, -1, None, eps, variant, partial=True, dscale=dscale)
         nsup = 2 ** (lev - 1)
         eps_l = float(eps_level[L - lev]) if eps_level is not None else eps
         # leaf sets of the super nodes: union of the leaf sets of the red nodes that
@@ -470,7 +495,7 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
             root_chol = np.linalg.cholesky(A_root)
         except np.linalg.LinAlgError as e:
             raise NotSPD("root block is not positive definite") from e
-    return Factor(n, perm, leaf_ptr, L, all_levels, root_size, root_chol, eps, variant)
+    return Factor(n, perm, leaf_ptr, L, all_levels, root_size, root_chol, eps, variant, dscale=dscale)
 
 
 def _set_block(blocks, nbr_of, x, y, blk):
@@ -577,6 +602,11 @@ def apply(F: Factor, r: np.ndarray) -> np.ndarray:
     if F.partial:
         raise ValueError("a partial factorization (levels=...) cannot be applied")
     r = np.asarray(r, dtype=np.float64)
+    if F.dscale is not None:
+        # R15: A_H^-1 = D^-1/2 A_H'^-1 D^-1/2
+        ds = F.dscale if r.ndim == 1 else F.dscale[:, None]
+        return ds * apply(Factor(F.n, F.perm, F.leaf_ptr, F.L, F.levels, F.root_size, F.root_chol, F.eps,
+                                 F.variant), ds * r)
     vec = r.ndim == 1
     R = r[:, None] if vec else r
     rp = R[F.perm]

@@ -354,3 +354,50 @@ def test_tables4_5_small_grid_counts_near_the_paper():
                 got = H.gmres(F, pb.rowptr, pb.col, pb.val, b)
                 want = row[2 + i] if var == H.LORASP else row[5 + i]
                 assert abs(got - want) <= 3, (var, eps, got, want)
+
+
+# --- symmetric diagonal scaling (R15) ---------------------------------------
+
+def test_scaling_a_constant_diagonal_changes_nothing():
+    """diag A = 4 everywhere: D^-1/2 A D^-1/2 = A / 4 exactly, the truncation
+    rules are relative, so the scaled preconditioner is the same operator."""
+    pb = P.poisson2d(24, leaf_size=8)
+    b = P.rhs(pb.n, 2)
+    for var in (H.LORASP, H.GC_CONSTANT):
+        z0 = H.apply(_factor(pb, 0.1, var), b)
+        z1 = H.apply(_factor(pb, 0.1, var, scale=True), b)
+        assert _rel(z1, z0) <= 1e-14
+
+
+def test_scaling_keeps_exactness_and_user_vectors():
+    pb = P.diffusion2d(24, 2.0, 3, leaf_size=8)
+    A = pb.to_scipy()
+    b = P.rhs(pb.n, 1)
+    import scipy.sparse.linalg as spla
+
+    F0 = _factor(pb, 0.0, H.GC_CONSTANT, scale=True)
+    assert _rel(H.apply(F0, b), spla.spsolve(A.tocsc(), b)) <= 1e-11
+    # a user vector stays exactly preserved for A: A_H^-1 (A phi) = phi
+    phi = np.random.default_rng(4).uniform(0.5, 1.5, pb.n)
+    F = _factor(pb, 0.2, H.GC_USER, phi=phi, scale=True)
+    assert _rel(H.apply(F, A @ phi), phi) <= 1e-11
+    # and the preconditioner is still symmetric
+    Z = H.apply(F, np.eye(pb.n)[:, :40])
+    G = np.eye(pb.n)[:, :40].T @ Z
+    assert np.abs(G - G.T).max() <= 1e-12 * np.abs(G).max()
+
+
+def test_scaling_rescues_gc_on_the_coefficient_jump():
+    """Table 4 at 32 x 32 (1e-5 jump): unscaled, GC-constant loses
+    definiteness (R9); scaled, it factors and, with the distance-2 rule,
+    lands within 3 of the printed counts (7 8 7), as does LoRaSp (6 6 6)."""
+    t4 = _golden("table4_gmres_piecewise.txt")
+    pb = P.piecewise2d(32, leaf_size=8)
+    b = P.rhs(pb.n, 0)
+    with pytest.raises(H.NotSPD):
+        _factor(pb, 0.1, H.GC_CONSTANT, nbr_dist=2)
+    for var, c0 in ((H.LORASP, 2), (H.GC_CONSTANT, 5)):
+        for i, eps in enumerate((0.1, 0.2, 0.3)):
+            F = _factor(pb, eps, var, nbr_dist=2, scale=True)
+            x, it, rr = H.gmres_solve(F, pb.rowptr, pb.col, pb.val, b)
+            assert rr <= 1e-10 and abs(it - t4[32][c0 + i]) <= 3, (var, eps, it)
