@@ -1050,19 +1050,28 @@ namespace {
 std::mutex g_static_mu;
 void *g_static_ptr[64] = {nullptr};
 
-// Device address of the array for the current device; looked up on the first
-// call on each device (with that device current) and cached.
-void *static_ws_for_current_device() {
+// Device address of the array for the current device.  Outside a stream
+// capture it is looked up on every call (with the device current), so a
+// device reset or a new primary context never leaves a stale address behind;
+// while `st` is capturing, the address cached by the last call outside a
+// capture is used, and a device that has none yet is an error.
+void *static_ws_for_current_device(cudaStream_t st) {
   int dev = 0;
   HS_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) fail(HS_ERR_CUDA, "device ordinal out of range for the static apply buffer");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  const cudaError_t ce = cudaStreamIsCapturing(st, &cs);
+  const bool capturing = ce != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+  if (ce != cudaSuccess) cudaGetLastError();   // a query error is not sticky; clear it
   std::lock_guard<std::mutex> lk(g_static_mu);
-  if (!g_static_ptr[dev]) {
+  if (!capturing) {
     void *ptr = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_apply_ws);
     if (e != cudaSuccess || !ptr)
       fail(HS_ERR_CUDA, std::string("cudaGetSymbolAddress of the static apply buffer: ") + cudaGetErrorString(e));
     g_static_ptr[dev] = ptr;
+  } else if (!g_static_ptr[dev]) {
+    fail(HS_ERR_INVALID, "hs_apply_static: the first call on a device must come before any stream capture");
   }
   return g_static_ptr[dev];
 }
@@ -1080,7 +1089,7 @@ void apply_static_t(FactorHandle &h, const double *r, double *z, int nrhs, int64
     fail(HS_ERR_CAPACITY, "hs_apply_static needs " + std::to_string(need) + " bytes of workspace for this factor and " +
                               std::to_string(nrhs) + " right-hand sides; the static buffer holds " +
                               std::to_string(kStaticApplyBytes) + " bytes");
-  unsigned char *base = (unsigned char *)static_ws_for_current_device();
+  unsigned char *base = (unsigned char *)static_ws_for_current_device(st);
   T *ws = (T *)base, *tb = (T *)(base + ws_b), *tb2 = (T *)(base + ws_b + t_b);
   k_gather_in<T><<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, ws);
   count_launch();

@@ -38,3 +38,18 @@ def oracle_factor(pb, eps, variant, phi=None):
 
 def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def elem(a, b):
+    """Element-wise error of a against b, per right-hand side: the largest
+    max_i |a_ij - b_ij| / max_i |b_ij| over the columns j (a vector is one
+    column).  Unlike one global 2-norm ratio, a wrong block of a few entries
+    cannot hide under the norm of the whole vector."""
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if a.shape != b.shape:
+        raise ValueError(f"shapes differ: {a.shape} vs {b.shape}")
+    if b.ndim == 1:
+        a, b = a[:, None], b[:, None]
+    scale = np.maximum(np.max(np.abs(b), axis=0), 1e-300)
+    return float(np.max(np.max(np.abs(a - b), axis=0) / scale))

@@ -19,7 +19,7 @@ from oracle import hsolver as H
 from paper_1611_03189_gb300 import _lib
 from paper_1611_03189_gb300 import problems as P
 
-from gpu_util import need_gpu, rel, to_dev
+from gpu_util import elem, need_gpu, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -87,15 +87,15 @@ def check_case(name, eps, fp32=True):
     assert bad == [], bad[:5]
     B = P.rhs(pb.n, 7, nrhs=2)
     zg = G.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
-    assert rel(zg, H.apply(F, B)) <= 1e-10
+    assert elem(zg, H.apply(F, B)) <= 1e-10
     if lam is not None:
         Z = G.apply(torch.as_tensor(X.T.copy(), device="cuda")).cpu().numpy().T
         for i in range(X.shape[1]):
-            assert rel(Z[:, i], X[:, i] / lam[i]) <= 1e-11
+            assert elem(Z[:, i], X[:, i] / lam[i]) <= 1e-11
     if fp32:
         G32 = _gpu(pb, eps, variant, X, eps1, prec=1)
         z32 = G32.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
-        assert rel(z32, H.apply(F, B)) <= 1e-3
+        assert elem(z32, H.apply(F, B)) <= 1e-3
         x, it, rr, _ = G32.pcg(torch.as_tensor(B[:, 0].copy(), device="cuda"), rtol=1e-10, maxit=300)
         assert rr[0] <= 1e-10
         G32.close()
@@ -141,14 +141,14 @@ import sys, numpy as np, torch, scipy.sparse.linalg as spla
 sys.path.insert(0, {os.path.dirname(HERE)!r})
 sys.path.insert(0, {HERE!r})
 import test_gpu_multi_phi as T
-from gpu_util import rel
+from gpu_util import elem
 from paper_1611_03189_gb300 import problems as P
 for name in ("poisson32 3 eigenvectors", "poisson32 projection", "diffusion64 2 random vectors"):
     pb, variant, X, lam, eps1 = T._case(name)
     G = T._gpu(pb, 0.0, variant, X, eps1)
     b = P.rhs(pb.n, 2)
     z = G.apply(torch.as_tensor(b, device='cuda')).cpu().numpy()
-    e = rel(z, spla.spsolve(pb.to_scipy().tocsc(), b))
+    e = elem(z, spla.spsolve(pb.to_scipy().tocsc(), b))
     assert e <= 1e-10, (name, e)
 print('ok')
 """

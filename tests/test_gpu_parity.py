@@ -1,9 +1,11 @@
 """Parity of the CUDA path with the FP64 oracle on the same seeded inputs.
 
-Bars (derived in the design notes): FP64 apply within 1e-10 relative of the
-oracle's A_H^-1 r; ranks equal except singular values within 1e-10 relative of
-the threshold; PCG iteration counts within +-1 and relative residual <= 1e-10;
-eps = 0 reproduces a direct solve.  The FP32 factor is checked against the
+Bars (derived in the design notes): FP64 apply element by element within
+1e-10 of the oracle's A_H^-1 r (max |z_gpu - z_oracle| <= 1e-10 max |z_oracle|
+per right-hand side); ranks equal except singular values within 1e-10 relative
+of the threshold; PCG iteration counts within +-1, relative residual <= 1e-10
+and the solution within 1e-10 of the oracle's iterate after the same number of
+iterations; eps = 0 reproduces a direct solve.  The FP32 factor is checked against the
 oracle within its own rounding level and must still reach 1e-10 under FP64 PCG.
 """
 import numpy as np
@@ -14,7 +16,7 @@ from oracle import hsolver as H
 from paper_1611_03189_gb300 import _lib
 from paper_1611_03189_gb300 import problems as P
 
-from gpu_util import gpu_factor, need_gpu, oracle_factor, rel, to_dev
+from gpu_util import elem, gpu_factor, need_gpu, oracle_factor, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +55,7 @@ def test_apply_and_ranks_match_oracle_fp64(name, maker, variant, eps):
     B = P.rhs(pb.n, 7, nrhs=3)
     Z = H.apply(F, B)
     zg = G.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
-    assert rel(zg, Z) <= 1e-10
+    assert elem(zg, Z) <= 1e-10
 
 
 @pytest.mark.parametrize("name,maker", CASES[:3], ids=[c[0] for c in CASES[:3]])
@@ -65,7 +67,7 @@ def test_eps0_is_exact_on_gpu(name, maker, variant):
     b = P.rhs(pb.n, 3)
     x = spla.spsolve(pb.to_scipy().tocsc(), b)
     z = G.apply(torch.as_tensor(b, device="cuda")).cpu().numpy()
-    assert rel(z, x) <= 1e-11
+    assert elem(z, x) <= 1e-11
 
 
 @pytest.mark.parametrize("name,maker", CASES, ids=[c[0] for c in CASES])
@@ -83,8 +85,19 @@ def test_pcg_matches_oracle(name, maker):
     assert rr[0] <= 1e-10
     true_rr = np.linalg.norm(b - pb.to_scipy() @ x) / np.linalg.norm(b)
     assert true_rr <= 1e-10 and abs(true_rr - rr[0]) <= 1e-12
-    if int(it[0]) == ito:
-        assert rel(x, xo) <= 1e-9
+    assert rel(x, _oracle_x_after(F, pb, b, int(it[0]), xo, ito)) <= 1e-10
+
+
+def _oracle_x_after(F, pb, b, its, xo, ito):
+    """The oracle's PCG iterate after exactly `its` iterations (the GPU's
+    count): the stopped oracle solve itself when the counts agree, else the
+    oracle run again without its stopping test for that many iterations, so
+    that a count differing by one is still compared iterate for iterate."""
+    if its == ito:
+        return xo
+    x, done, _ = H.pcg(F, pb.rowptr, pb.col, pb.val, b, rtol=1e-300, maxit=its)
+    assert done == its
+    return x
 
 
 def test_gc_preserves_constant_vector_on_gpu():
@@ -93,7 +106,7 @@ def test_gc_preserves_constant_vector_on_gpu():
     G = gpu_factor(pb, 1e-1, H.GC_CONSTANT)
     one = np.ones(pb.n)
     z = G.apply(torch.as_tensor(pb.to_scipy() @ one, device="cuda")).cpu().numpy()
-    assert rel(z, one) <= 1e-11
+    assert elem(z, one) <= 1e-11
     G0 = gpu_factor(pb, 1e-1, H.LORASP)
     z0 = G0.apply(torch.as_tensor(pb.to_scipy() @ one, device="cuda")).cpu().numpy()
     assert rel(z0, one) > 1e-6
@@ -108,9 +121,9 @@ def test_gc_user_vector_on_gpu():
     G = gpu_factor(pb, 0.2, H.GC_USER, phi=phi)
     F = oracle_factor(pb, 0.2, H.GC_USER, phi=phi)
     z = G.apply(torch.as_tensor(phi, device="cuda")).cpu().numpy()
-    assert rel(z, phi / lam) <= 1e-11
+    assert elem(z, phi / lam) <= 1e-11
     b = P.rhs(pb.n, 9)
-    assert rel(G.apply(torch.as_tensor(b, device="cuda")).cpu().numpy(), H.apply(F, b)) <= 1e-10
+    assert elem(G.apply(torch.as_tensor(b, device="cuda")).cpu().numpy(), H.apply(F, b)) <= 1e-10
 
 
 def test_multi_rhs_apply_equals_single():
@@ -145,7 +158,7 @@ def test_fp32_factor_reaches_fp64_accuracy_under_pcg(name, maker):
     G = gpu_factor(pb, 1e-2, H.GC_CONSTANT, prec=_lib.HS_PREC_F32)
     b = P.rhs(pb.n, 1)
     z = G.apply(torch.as_tensor(b, device="cuda")).cpu().numpy()
-    assert rel(z, H.apply(F, b)) <= 1e-3
+    assert elem(z, H.apply(F, b)) <= 1e-3
     x, it, rr, code = G.pcg(torch.as_tensor(b, device="cuda"))
     _, ito, _ = H.pcg(F, pb.rowptr, pb.col, pb.val, b)
     assert code == _lib.HS_OK and rr[0] <= 1e-10
@@ -170,9 +183,9 @@ def test_edge_cases_single_leaf_and_tiny_levels():
             G = gpu_factor(pb, eps, H.GC_CONSTANT)
             F = oracle_factor(pb, eps, H.GC_CONSTANT)
             z = G.apply(torch.as_tensor(b, device="cuda")).cpu().numpy()
-            assert rel(z, H.apply(F, b)) <= 1e-11
+            assert elem(z, H.apply(F, b)) <= 1e-11
             if eps == 0.0:
-                assert rel(z, x) <= 1e-11
+                assert elem(z, x) <= 1e-11
 
 
 def test_refactor_equals_fresh_factor_bitwise():
@@ -217,7 +230,7 @@ def test_tridiagonal_truncation_path_matches_oracle(name, maker, variant):
 import sys, numpy as np, torch
 sys.path.insert(0, {repr(__import__('os').path.dirname(__import__('os').path.dirname(__import__('os').path.abspath(__file__))))})
 sys.path.insert(0, {repr(__import__('os').path.dirname(__import__('os').path.abspath(__file__)))})
-from gpu_util import gpu_factor, oracle_factor, rel
+from gpu_util import elem, gpu_factor, oracle_factor, rel
 from oracle import hsolver as H
 from paper_1611_03189_gb300 import problems as P
 import test_gpu_parity as T
@@ -229,10 +242,10 @@ for eps in (1e-1, 1e-2):
     B = P.rhs(pb.n, 7, nrhs=2)
     Z = H.apply(F, B)
     zg = G.apply(torch.as_tensor(B.T.copy(), device='cuda')).cpu().numpy().T
-    e = rel(zg, Z)
+    e = elem(zg, Z)
     assert e <= 1e-10, e
     G32 = gpu_factor(pb, eps, {variant}, prec=1)
-    e32 = rel(G32.apply(torch.as_tensor(B.T.copy(), device='cuda')).cpu().numpy().T, Z)
+    e32 = elem(G32.apply(torch.as_tensor(B.T.copy(), device='cuda')).cpu().numpy().T, Z)
     assert e32 <= 1e-3, e32
 print('ok')
 """
@@ -265,10 +278,10 @@ def test_large_super_nodes_match_oracle(name, maker):
     B = P.rhs(pb.n, 3, nrhs=2)
     Z = H.apply(F, B)
     zg = G.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
-    assert rel(zg, Z) <= 1e-10
+    assert elem(zg, Z) <= 1e-10
     G32 = gpu_factor(pb, 1e-2, H.GC_CONSTANT, prec=1)
     z32 = G32.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
-    assert rel(z32, Z) <= 1e-3
+    assert elem(z32, Z) <= 1e-3
     x, it, rr, _ = G32.pcg(torch.as_tensor(B[:, 0].copy(), device="cuda"), rtol=1e-10, maxit=200)
     assert rr[0] <= 1e-10
 
@@ -289,7 +302,7 @@ def test_multi_cta_truncation_path_matches_oracle(name, maker, variant):
 import sys, numpy as np, torch
 sys.path.insert(0, {os.path.dirname(here)!r})
 sys.path.insert(0, {here!r})
-from gpu_util import gpu_factor, oracle_factor, rel
+from gpu_util import elem, gpu_factor, oracle_factor, rel
 from oracle import hsolver as H
 from paper_1611_03189_gb300 import problems as P
 import test_gpu_parity as T
@@ -301,10 +314,10 @@ for eps in (1e-1, 1e-2):
     B = P.rhs(pb.n, 7, nrhs=2)
     Z = H.apply(F, B)
     zg = G.apply(torch.as_tensor(B.T.copy(), device='cuda')).cpu().numpy().T
-    e = rel(zg, Z)
+    e = elem(zg, Z)
     assert e <= 1e-10, e
     G32 = gpu_factor(pb, eps, {variant}, prec=1)
-    e32 = rel(G32.apply(torch.as_tensor(B.T.copy(), device='cuda')).cpu().numpy().T, Z)
+    e32 = elem(G32.apply(torch.as_tensor(B.T.copy(), device='cuda')).cpu().numpy().T, Z)
     assert e32 <= 1e-3, e32
 print('ok')
 """
@@ -331,5 +344,5 @@ def test_adaptive_eps_level_matches_oracle(name, maker, variant):
     assert _ranks_match(F, G) == []
     B = P.rhs(pb.n, 5, nrhs=2)
     zg = G.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
-    assert rel(zg, H.apply(F, B)) <= 1e-10
+    assert elem(zg, H.apply(F, B)) <= 1e-10
     G.close()
