@@ -38,8 +38,15 @@ WORKLOADS = {
     "poisson3d_32": (3, 32, 0.0, 1e-2, 64),
     "poisson3d_24": (3, 24, 0.0, 1e-2, 64),
 }
-# the oracle's bounded sample of each workload (10-30 s of one core)
-CPU_SAMPLE = {"diffusion2d_512": "diffusion2d_256", "poisson3d_64": "poisson3d_24", "poisson3d_32": "poisson3d_24"}
+# Workloads whose one-step oracle run exceeds a few minutes of one core are
+# timed on a smaller grid of the same recipe and scaled by the unknown count
+# (the 3D ones: the ranks grow with the grid there, so the scaled figure
+# flatters the oracle and is labelled an estimate).  The 2D workloads are
+# timed on the workload itself.
+CPU_SAMPLE = {"poisson3d_64": "poisson3d_24", "poisson3d_32": "poisson3d_24"}
+METRIC = "solves/s to rel-res 1e-10 (factor + PCG solve; mixed vs FP64 factor)"
+# factor precisions by name (values of HS_PREC_*)
+PRECS = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
 
 
 def make_problem(name: str, seed: int):
@@ -159,6 +166,21 @@ print(json.dumps({{"times": times, "iters": iters}}))
 """
 
 
+def tensor_peak_for(prec: str, peaks: dict):
+    """Dense tensor-core peak (TFLOP/s) for the operand type of a factor
+    precision: the measured sustained BF16 figure (the GEMM runs inside a long
+    step), times the nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s) for TF32."""
+    bf16 = peaks.get("bf16_tflops_sustained")
+    src = "measured sustained bf16 (MEASURED_PEAKS.json)"
+    if not bf16:
+        bf16, src = 1700.0, "fallback sustained bf16"
+    if prec == "tf32":
+        return bf16 * 1.1 / 2.25, src + " x nominal tf32/bf16 ratio 1.1/2.25"
+    if prec in ("f32", "f64"):
+        return bf16, src + " (the contractions' peak if they ran as bf16 on tensor cores)"
+    return bf16, src
+
+
 def run_oracle(name: str, reps: int, seed0: int = 0) -> dict:
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
@@ -173,34 +195,47 @@ def cpu_baseline(workload: str) -> dict:
     sample, scale = sample_for(workload)
     res = run_oracle(sample, 1, seed0=0)
     t = res["times"][0]
-    return {"value": (1.0 / t) / scale, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": (f"one factor + PCG solve (1 rhs) of the same recipe on the smaller grid {sample} "
-                       f"({t:.2f} s, {res['iters'][0]} iterations), scaled by the unknown count "
-                       f"x{scale:g} (linear complexity, Sec. 3)" if scale != 1.0 else
-                       f"one factor + PCG solve (1 rhs) of the workload ({t:.2f} s)"),
-            "sample_seconds": t}
+    if scale == 1.0:
+        what = (f"one step of the workload itself ({workload}: factor of the seed-0 field + PCG solve of "
+                f"1 rhs, {res['iters'][0]} iterations, {t:.1f} s), measured")
+    else:
+        what = (f"one factor + PCG solve (1 rhs) of the same recipe on the smaller grid {sample} "
+                f"({t:.2f} s, {res['iters'][0]} iterations), scaled by the unknown count x{scale:g}: an estimate")
+    return {"value": (1.0 / t) / scale, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": what,
+            "sample_seconds": t, "measured": scale == 1.0}
 
 
 def reference_arm(args) -> None:
+    """The oracle (FP64, one core, in a child process) on the bench's own
+    workload.  Each oracle step of the 2D workload takes about half a minute
+    of one core, so min(steps, 2) steps are timed and no warm-up is run (the
+    oracle has nothing to warm up); the line says so."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     sample, scale = sample_for(args.workload)
-    res = run_oracle(sample, args.warmup + args.steps, seed0=0)
-    times = res["times"][args.warmup:]
+    nsteps = max(1, min(args.steps, 2))
+    res = run_oracle(sample, nsteps, seed0=0)
+    times = res["times"]
     per = sum(times) / len(times)
     value = (1.0 / per) / scale
+    measured = scale == 1.0
+    sample_txt = (f"each step one factor + PCG solve (1 rhs) of the workload itself, {nsteps} steps timed "
+                  f"(no warm-up: the oracle has none)" if measured else
+                  f"each step one factor + PCG solve of the recipe on the smaller grid {sample}, "
+                  f"scaled by the unknown count x{scale:g} (an estimate)")
     line = {
-        "impl": "reference", "metric": "solves/s to rel-res 1e-10 (factor + PCG solve, FP64 oracle)",
-        "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": per * 1000 * scale, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "impl": "reference", "metric": METRIC,
+        "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": nsteps, "warmup": 0,
+        "requested": {"steps": args.steps, "warmup": args.warmup},
+        "ms_per_step": per * 1000 * scale, "ms_per_step_measured": measured,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "nrhs": 1, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": f"each step one factor + PCG solve of the recipe on the smaller grid {sample}, "
-                                   f"scaled by the unknown count x{scale:g}"},
+        "config": {"workload": args.workload, "nrhs": 1, "sample": sample, "factor_prec": "f64 (oracle)"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": sample_txt},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "iterations": res["iters"][args.warmup:],
+        "iterations": res["iters"],
+        "step_seconds": times,
     }
     print(json.dumps(line), flush=True)
 
@@ -234,9 +269,9 @@ def batched_arm(args) -> None:
     devs = [(torch.as_tensor(pb.rowptr, device=dev), torch.as_tensor(pb.col, device=dev),
              torch.as_tensor(pb.val, device=dev)) for pb in pbs]
     rhs = [torch.as_tensor(P.rhs(pb.n, 100 + i, nrhs=nrhs).T.copy(), device=dev) for i, pb in enumerate(pbs)]
-    prec = _lib.HS_PREC_F32 if args.prec == "f32" else _lib.HS_PREC_F64
+    prec = PRECS[args.prec]
     fs, status = _lib.factor_batch([d + (pb.perm, pb.leaf_ptr) for d, pb in zip(devs, pbs)], 1e-2,
-                                   _lib.HS_GC_CONSTANT, prec)
+                                   _lib.HS_GC_CONSTANT, prec, scale=args.scale)
     live = [i for i in range(count) if status[i] == _lib.HS_OK]
     streams = [torch.cuda.Stream(device=dev) for _ in range(8)]
     pool = cf.ThreadPoolExecutor(max_workers=len(streams))
@@ -291,10 +326,11 @@ def batched_arm(args) -> None:
         "metric": "solves/s to rel-res 1e-10 (batched factor + PCG, 4 rhs per problem)",
         "value": solves / (ms / 1000.0), "unit": "rhs solves/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if args.prec == "f32" else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.prec == "f64" else f"{args.prec}+f64", "data": "synthetic",
         "config": {"workload": f"batched_{count}", "problems": count, "sides": "log-uniform [32, 256]",
                    "s": 2.0, "leaf": 16, "eps": 1e-2, "variant": "GC-constant", "nrhs": nrhs,
                    "factor_prec": args.prec, "unknowns_total": int(sum(pb.n for pb in pbs)),
+                   "diagonal_scaling": bool(args.scale),
                    "generation_s": t_gen, "pcg_streams": len(streams),
                    "l2": "inputs larger than L2 (factor records > 129 MB)"},
         "problems_not_spd": int(count - len(live)),
@@ -371,6 +407,134 @@ def gmres_table_arm(args) -> None:
                       "seconds": round(time.perf_counter() - t0, 1)}), flush=True)
 
 
+def sweep_arm(args) -> None:
+    """The 2D variable-coefficient workload over its parameter grid: contrast
+    s in {1, 2, 3} x tolerance eps in {1e-1, 1e-2, 1e-3}, each with and without
+    the symmetric diagonal scaling, in the factor precision --prec.  Per point:
+    one warm-up and --steps timed factor + PCG solves (fields of seeds 0, 1,
+    ...), PCG iterations, the largest relative residual, or the failure
+    (HS_ERR_NOT_SPD when GC-constant loses definiteness).  One JSON line."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1611_03189_gb300 import _lib
+    from paper_1611_03189_gb300 import problems as P
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    side = WORKLOADS[args.workload][1]
+    prec = PRECS[args.prec]
+    rows = []
+    t0 = time.perf_counter()
+    nst = max(args.steps, 1)
+    for s_ in (1.0, 2.0, 3.0):
+        pbs = [P.diffusion2d(side, s_, k, leaf_size=16) for k in range(nst + 1)]
+        rp = torch.as_tensor(pbs[0].rowptr, device=dev)
+        ci = torch.as_tensor(pbs[0].col, device=dev)
+        vals = [torch.as_tensor(pb.val, device=dev) for pb in pbs]
+        bs = [torch.as_tensor(P.rhs(pbs[0].n, 1000 + k), device=dev) for k in range(nst + 1)]
+        for eps in (1e-1, 1e-2, 1e-3):
+            for scale in (False, True):
+                row = {"s": s_, "eps": eps, "scale": scale}
+                try:
+                    G = _lib.Factor(rp, ci, vals[0], pbs[0].perm, pbs[0].leaf_ptr, eps, _lib.HS_GC_CONSTANT, prec,
+                                    scale=scale)
+                except _lib.HsError as e:
+                    row["failed"] = str(e)[:160]
+                    rows.append(row)
+                    print(json.dumps({"point": row}), flush=True)
+                    continue
+                its, rrs, fails = [], [], 0
+                torch.cuda.synchronize()
+                ms = 0.0
+                for k in range(nst + 1):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    try:
+                        if k > 0:
+                            G.refactor(vals[k])
+                        _, it, rr, code = G.pcg(bs[k], rtol=1e-10, maxit=1000, raise_on_fail=False)
+                    except _lib.HsError:
+                        fails += 1
+                        continue
+                    e1.record()
+                    torch.cuda.synchronize()
+                    if k > 0:
+                        ms += e0.elapsed_time(e1)
+                        its.append(int(it[0]))
+                        rrs.append(float(rr[0]))
+                timed = len(its)
+                row.update({"solves_per_s": timed / (ms / 1000.0) if ms > 0 else None, "iterations": its,
+                            "max_relres": max(rrs) if rrs else None, "not_spd_fields": fails,
+                            "fields": nst + 1, "factor_bytes": G.info()["factor_bytes"]})
+                G.close()
+                rows.append(row)
+                print(json.dumps({"point": row}), flush=True)
+    print(json.dumps({"sweep": f"2D diffusion {side}x{side}, leaves of 16, GC-constant, PCG to 1e-10",
+                      "factor_prec": args.prec, "rows": rows, "seconds": round(time.perf_counter() - t0, 1)}),
+          flush=True)
+
+
+def gemm_arm(args) -> None:
+    """The tensor-core GEMM alone (hs_gemm_tc): C = A B with M = N = K =
+    --gemm-size, FP32 operands rounded to --prec (tf32 or bf16), FP32
+    accumulation; each of --steps timed calls after --warmup, CUDA events on
+    the launching stream.  TFLOP/s against the measured bf16 burst peak (times
+    the nominal tf32/bf16 ratio for tf32).  One JSON line."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1611_03189_gb300 import _lib
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    n = args.gemm_size
+    prec = PRECS[args.prec]
+    if prec not in (_lib.HS_PREC_TF32, _lib.HS_PREC_BF16):
+        raise SystemExit("--gemm needs --prec tf32 or bf16")
+    g = torch.Generator(device=dev).manual_seed(0)
+    A = torch.randn((n, n), generator=g, device=dev, dtype=torch.float32)
+    B = torch.randn((n, n), generator=g, device=dev, dtype=torch.float32)
+    C = torch.zeros((n, n), device=dev, dtype=torch.float32)
+    res = {}
+    for bn in (64, 128):
+        for _ in range(max(args.warmup, 1)):
+            _lib.gemm_tc(prec, A, B, C, bn=bn)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(max(args.steps, 1)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _lib.gemm_tc(prec, A, B, C, bn=bn)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        res[bn] = min(ts)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    bf16 = peaks.get("bf16_tflops", 1900.0)
+    peak = bf16 * (1.1 / 2.25 if args.prec == "tf32" else 1.0)
+    flops = 2.0 * n ** 3
+    best = min(res, key=res.get)
+    ach = flops / (res[best] / 1000.0) / 1e12
+    print(json.dumps({"metric": "tensor-core GEMM TFLOP/s (hs_gemm_tc)", "value": ach, "unit": "TFLOP/s",
+                      "prec": args.prec, "m_n_k": n, "ms": res, "best_tile_n": best,
+                      "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                   "frac": ach / peak,
+                                   "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)" +
+                                                  (" x nominal tf32/bf16 ratio 1.1/2.25" if args.prec == "tf32"
+                                                   else "")}}), flush=True)
+
+
 def serve_arm(args) -> None:
     """Served latency (p50/p99) and throughput of the continuous-batching loop,
     mixed (FP32) factor against the plain FP64 factor on the same stream."""
@@ -435,8 +599,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="diffusion2d_512", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--prec", default="f32", choices=["f32", "tf32", "bf16", "f64"])
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--scale", action="store_true", help="factor the diagonally scaled D^-1/2 A D^-1/2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64-arm", action="store_true", help="skip the FP64-factor comparison")
     ap.add_argument("--profile", action="store_true", help="print a phase breakdown to stderr")
@@ -448,6 +613,10 @@ def main():
     ap.add_argument("--serve-sides", default="32,96", help="grid side range of the 3D requests")
     ap.add_argument("--serve-budget-gb", type=float, default=120.0)
     ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--gemm", action="store_true", help="time the tensor-core GEMM alone (one JSON line)")
+    ap.add_argument("--gemm-size", type=int, default=4096)
+    ap.add_argument("--sweep", action="store_true",
+                    help="2D diffusion parameter grid: s x eps x scaling (no oracle, one JSON line)")
     ap.add_argument("--gmres-table", action="store_true",
                     help="GMRES iteration table of the paper's Table 2 (no timing)")
     ap.add_argument("--table-sides", default="32,64,128,256,512,1024")
@@ -466,6 +635,12 @@ def main():
         return
     if args.gmres_table:
         gmres_table_arm(args)
+        return
+    if args.sweep:
+        sweep_arm(args)
+        return
+    if args.gemm:
+        gemm_arm(args)
         return
 
     import numpy as np
@@ -488,7 +663,7 @@ def main():
     from paper_1611_03189_gb300 import problems as P
 
     dev = torch.device("cuda", local)
-    prec = _lib.HS_PREC_F32 if args.prec == "f32" else _lib.HS_PREC_F64
+    prec = PRECS[args.prec]
     nsteps = args.warmup + args.steps
     # inputs resident in HBM: one matrix (new coefficient field) and rhs block per step
     pbs = []
@@ -503,7 +678,7 @@ def main():
           for k in range(nsteps)]
     stream = torch.cuda.current_stream()
     t_plan = time.perf_counter()
-    G = _lib.Factor(rp, ci, vals[0], pb0.perm, pb0.leaf_ptr, eps, _lib.HS_GC_CONSTANT, prec)
+    G = _lib.Factor(rp, ci, vals[0], pb0.perm, pb0.leaf_ptr, eps, _lib.HS_GC_CONSTANT, prec, scale=args.scale)
     t_plan = time.perf_counter() - t_plan
 
     iters_seen = []
@@ -593,7 +768,8 @@ def main():
     f64 = None
     if prec != _lib.HS_PREC_F64 and not args.no_f64_arm:
         x_mixed, _, _, _ = G.pcg(bs[args.warmup], rtol=1e-10, maxit=1000)
-        G64 = _lib.Factor(rp, ci, vals[0], pb0.perm, pb0.leaf_ptr, eps, _lib.HS_GC_CONSTANT, _lib.HS_PREC_F64)
+        G64 = _lib.Factor(rp, ci, vals[0], pb0.perm, pb0.leaf_ptr, eps, _lib.HS_GC_CONSTANT, _lib.HS_PREC_F64,
+                          scale=args.scale)
         it64, rr64 = [], []
         for k in range(args.warmup):
             G64.refactor(vals[k])
@@ -663,7 +839,7 @@ def main():
     # of its launches (CUDA events on the factor stream, inside the library)
     info_f = G.info()
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    if args.prec == "f32":
+    if args.prec != "f64":
         alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12      # FP32 FMA lanes x 2 flops x clock
         alu_src = f"derived: 152 SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz"
     else:
@@ -684,25 +860,50 @@ def main():
                   "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
                   "traffic": None, "algorithmic_bytes": apply_bytes, "launch_ms": apply_ms,
                   "share_of_step": apply_ms * int(it1.max()) / ms_per_step}
-    # the dominant kernel of the step is the one with the larger share of its time
-    dominant, other = ((roof_trunc, roof_apply) if roof_trunc["share_of_step"] >= roof_apply["share_of_step"]
-                       else (roof_apply, roof_trunc))
+    # ---- the tensor-core GEMM of the mixed factors (tcgen05), against the tensor peak ----
+    # flops it executes (2MNK per task) over the device time of its launches
+    # (an event pair around each launch on the factor stream, inside the library)
+    tensor_peak, tensor_src = tensor_peak_for(args.prec, peaks)
+    roofs = [roof_trunc, roof_apply]
+    if info_f["tc_launches"] > 0 and info_f["tc_ms"] > 0:
+        tc_ach = info_f["tc_flops"] / (info_f["tc_ms"] / 1000.0) / 1e12
+        roofs.append({"bound": "tensor", "kernel": f"k_gemm_tc ({args.prec.upper()} operands, FP32 accumulate in TMEM)",
+                      "achieved": tc_ach, "peak": tensor_peak, "unit": "TFLOP/s", "frac": tc_ach / tensor_peak,
+                      "peak_source": tensor_src, "traffic": None,
+                      "algorithmic_flops_per_launch": info_f["tc_flops"] / info_f["tc_launches"],
+                      "launch_ms": info_f["tc_ms"] / info_f["tc_launches"],
+                      "launches_per_factor": info_f["tc_launches"], "share_of_step": info_f["tc_ms"] / ms_per_step})
+    # the dominant kernel of the step is the one with the largest share of its time
+    roofs.sort(key=lambda r: -r["share_of_step"])
+    dominant, others = roofs[0], roofs[1:]
+    # the factorization's algorithmic work (per-node count of the hot-path
+    # table: Gram, R^T, Cholesky, Y, S, G, H, Schur, M_ss / P_ss) over its device
+    # time, against the tensor peak its contractions would run at
+    factor_alg = {"alg_flops": info_f["alg_flops"], "factor_ms": factor_ms,
+                  "achieved_tflops": info_f["alg_flops"] / (factor_ms / 1000.0) / 1e12,
+                  "peak_tflops": tensor_peak, "peak_source": tensor_src,
+                  "frac": info_f["alg_flops"] / (factor_ms / 1000.0) / 1e12 / tensor_peak,
+                  "executed_flops": info_f["factor_flops"], "eig_flops_nominal": info_f["eig_flops"]}
 
     if rank == 0:
         line = {
-            "metric": "solves/s to rel-res 1e-10 (factor + PCG solve; mixed vs FP64 factor)",
+            "metric": METRIC,
             "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if args.prec == "f32" else "f64", "data": "synthetic",
+            "dtype": "f64" if args.prec == "f64" else f"{args.prec}+f64", "data": "synthetic",
             "config": {"workload": args.workload, "dim": WORKLOADS[args.workload][0],
                        "grid": WORKLOADS[args.workload][1], "n": n,
                        "s": WORKLOADS[args.workload][2], "eps": WORKLOADS[args.workload][3],
                        "leaf": WORKLOADS[args.workload][4], "variant": "GC-constant",
                        "factor_prec": args.prec, "pcg": "fp64", "rtol": 1e-10, "nrhs": args.nrhs,
+                       "diagonal_scaling": bool(args.scale),
                        "l2": "inputs larger than L2 (factor records > 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": dominant,
-            "roofline_other": other,
+            "roofline_other": others,
+            "factor_algorithmic": factor_alg,
+            "gemm_autotune": ([{k: r[k] for k in ("max_mn", "k", "route")} for r in _lib.gemm_tune_report(prec)]
+                              if args.prec in ("tf32", "bf16") else None),
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": 8 * (pb0.nnz + n * args.nrhs),
                     "d2h_bytes_per_step": 8 * n * args.nrhs},

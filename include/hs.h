@@ -11,6 +11,8 @@
  *     available from hs_last_error() (thread-local, valid until the next call
  *     on the same thread).  No C++ exception ever crosses this boundary.
  *   - "device" pointers are CUDA global-memory pointers on the current device;
+ *     calls that take a factorization handle must run with the device it
+ *     was created on current (HS_ERR_INVALID otherwise);
  *     "host" pointers are ordinary CPU memory.  Arguments are borrowed for the
  *     duration of the call only; the library keeps no reference to them.
  *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
@@ -50,14 +52,27 @@ enum {
                           the truncated SVD of [X_s, A_sw X_w] at eps1, then GC */
 };
 
+/* Elimination order of the super nodes of a level (hs_opts.order_mode). */
+enum { HS_ORDER_WAVES = 0, HS_ORDER_SEQUENTIAL = 1 };
+
 /* Most preserved vectors per problem (n_phi) for HS_GC_USER and HS_GC_PROJ. */
 #define HS_MAX_PHI 4
 
-/* Arithmetic of the factorization (north of the factor: the PCG is always FP64). */
+/* Arithmetic of the factorization (the PCG is always FP64).  The mixed
+ * precisions keep blocks and factor records in FP32 and run the dense
+ * contractions of the elimination (Sec. 3.2 eqs. extended_rearranged and
+ * eliminated: L^-1 U and its CholQR, L^-1 A_sN, M_ss, P_ss, A_Nr, A_rr, the
+ * Schur update; the blocked Cholesky's panel and trailing updates) on the
+ * tensor cores; the outer FP64 PCG wins the accuracy back. */
 enum {
   HS_PREC_F64 = 0,     /* every factor step in FP64                              */
-  HS_PREC_F32 = 1      /* blocks, Gram, eigen-solves and factor records in FP32;
-                          rank decision taken on the FP32 singular values      */
+  HS_PREC_F32 = 1,     /* blocks, Gram, eigen-solves and factor records in FP32
+                          (CUDA cores); the rank is decided on the FP32
+                          eigenvalues of the Gram matrix                        */
+  HS_PREC_TF32 = 2,    /* contractions on tensor cores with TF32 operands and
+                          FP32 accumulation; the truncation (Gram A_sw A_sw^T,
+                          its eigen-solve and the rank decision) in FP64        */
+  HS_PREC_BF16 = 3     /* as HS_PREC_TF32 with BF16 operands                    */
 };
 
 /* Sparse SPD matrix A in CSR form (Sec. 2: A symmetric positive definite).
@@ -102,7 +117,7 @@ typedef struct {
  *   in the ORIGINAL ordering; used by HS_GC_USER (vectors preserved exactly,
  *   Sec. 6) and HS_GC_PROJ (the scaled vectors X of Appendix B, e.g.
  *   e_i / lambda_i, kept approximately).  Required by both.
- * factor_prec: HS_PREC_F64 or HS_PREC_F32.
+ * factor_prec: HS_PREC_F64, HS_PREC_F32, HS_PREC_TF32 or HS_PREC_BF16.
  * eps_level: NULL, or a HOST array of tolerances per level for the adaptive
  *   choice of Sec. 7 (Table 3).  Entry j replaces eps for the super nodes j
  *   levels above the leaves (j = 0: the pairs of leaves); a problem with 2^L
@@ -114,7 +129,28 @@ typedef struct {
  * eps1: HS_GC_PROJ's first tolerance (Appendix B, eps_1 <= eps_2 = eps): U_1
  *   keeps the left singular vectors of [X_s, A_sw X_w] with
  *   sigma_i > max(eps1, 1e-12) * sigma_1.  Finite and >= 0; ignored by the
- *   other variants. */
+ *   other variants.
+ * scale: 0, or 1 to factor the symmetrically scaled D^-1/2 A D^-1/2 (D =
+ *   diag A) instead of A and apply A_H^-1 = D^-1/2 A'_H^-1 D^-1/2.  The paper
+ *   does not mention scaling; it keeps every row of A_sw on one scale, which
+ *   GC-constant needs to stay definite at high coefficient contrast.  With
+ *   scaling, GC-constant preserves the constant vector of the scaled system
+ *   and HS_GC_USER / HS_GC_PROJ vectors phi are mapped to D^1/2 phi, so they
+ *   stay preserved for A.  hs_pcg and hs_gmres still solve A x = b.  A
+ *   diagonal entry <= 0 is HS_ERR_NOT_SPD.
+ * timeout_cycles: bound, in SM clock cycles, of each wait inside the
+ *   factorization's kernels (the tensor-core GEMM of HS_PREC_TF32 /
+ *   HS_PREC_BF16 waits on its mbarriers for the tensor core); 0 means the
+ *   default, 2e9 cycles (about one second).  A wait that runs out makes the
+ *   call fail with HS_ERR_TIMEOUT; the device stays usable (the kernel waits
+ *   for its own tensor-core work with the default bound before it frees its
+ *   tensor memory and returns).  >= 0.
+ * order_mode: the elimination order of a level's super nodes, "a given
+ *   ordering" in Sec. 3.2.  HS_ORDER_WAVES (0, the default): canonical waves
+ *   (see the planner below), each wave one batch of independent
+ *   eliminations.  HS_ORDER_SEQUENTIAL (1): one super node at a time in
+ *   ascending index, the paper's sequential reading; the same method, one
+ *   launch group per super node (slow; for comparison). */
 typedef struct {
   double eps;
   int32_t variant;
@@ -124,6 +160,9 @@ typedef struct {
   int32_t n_eps_level;
   int32_t n_phi;
   double eps1;
+  int32_t scale;
+  int64_t timeout_cycles;
+  int32_t order_mode;
 } hs_opts;
 
 /* Sizes and counters of a factorization (all host values). */
@@ -137,7 +176,9 @@ typedef struct {
   int32_t max_super;         /* largest super-node size m                         */
   int64_t device_bytes;      /* device memory held by the handle                  */
   int64_t factor_bytes;      /* bytes one hs_apply reads from the factor records  */
-  double factor_flops;       /* algorithmic flops of the factorization            */
+  double factor_flops;       /* flops the factorization's GEMM and Cholesky
+                                kernels execute (2MNK per product, m^3/3 per
+                                Cholesky); see alg_flops for the algorithmic count */
   double eig_flops;          /* nominal eigen-solve flops, reported apart: per
                                 truncated node 4/3 m^3 + 2 m^2 k                  */
   double factor_ms;          /* device time of the last factorization             */
@@ -157,6 +198,16 @@ typedef struct {
                                 path: 10 prepare, 11 tridiagonal steps, 12 Q^T Z,
                                 13 eigenvectors of T, 14 Q Y; 15 unused;
                                 otherwise zeros                                 */
+  double alg_flops;          /* algorithmic flops of the factorization, counted
+                                per super node from its sizes (m, rank k,
+                                well-separated width w, neighbour width d_N):
+                                Gram 2m^2 w, R^T 2mkw, Cholesky m^3/3, Y 2m^2 k,
+                                S 2mk^2 + k^3/3, G 2m^2 d_N, H 2mk d_N, Schur
+                                2(m+k) d_N^2, M_ss and P_ss 2m^2 k; root m^3/3.
+                                factor_flops counts what the kernels execute.  */
+  double tc_flops;           /* flops executed by the tensor-core GEMM          */
+  double tc_ms;              /* device time of its launches (CUDA event pairs)  */
+  int64_t tc_launches;       /* its launches in the last factorization          */
 } hs_info;
 
 typedef struct hs_factor_s *hs_factor;
@@ -219,19 +270,22 @@ int hs_factor_refactor_batch(int32_t count, hs_factor *f, const double *const *v
 int hs_apply(hs_factor f, const double *r, double *z, int32_t nrhs, int64_t ld, void *stream);
 
 /* hs_apply_static: the same z = A_H^{-1} r as hs_apply, for callers that must
- * not allocate device memory while they solve -- for instance code that
- * records its work inside a CUDA stream capture, or a service whose device
- * memory is fixed at start-up.  It calls no cudaMalloc, cudaFree or other
- * allocating routine: the apply workspace is one 16 MiB static device array
- * inside this library, which every GPU that loads the library holds until the
- * process exits.  The paper has no counterpart; this is a property of this
- * library's interface only.
+ * not allocate device memory while they solve -- for instance a service whose
+ * device memory is fixed at start-up, or code that runs where a cudaMalloc
+ * could block behind other work or is not permitted.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine: the apply workspace is one 16 MiB
+ * static device array inside this library, which every GPU that loads the
+ * library holds until the process exits.  The paper has no counterpart; this
+ * is a property of this library's interface only.
  *   - Needs (ws_unknowns x nrhs + 2 x scratch_unknowns x nrhs) elements of the
  *     factor precision; larger requests fail with HS_ERR_CAPACITY and a
  *     message giving the bytes needed.  r, z, nrhs, ld as for hs_apply.
- *   - The first call on a device looks up the array's device address (with
- *     that device current) and caches it; make that first call before any
- *     stream capture.
+ *   - The device the factorization was created on must be current
+ *     (HS_ERR_INVALID otherwise).
+ *   - Each call outside a stream capture looks up the array's device address
+ *     (with that device current) and keeps it for calls made while a stream
+ *     capture is in progress, which cannot look it up; so the first call on a
+ *     device must come before any stream capture.
  *   - All calls on a device share the array and leave the last call's
  *     contents in it (the parts that must start at zero are cleared by each
  *     call).  Calls that overlap on the GPU -- on different streams or
@@ -284,6 +338,33 @@ int hs_factor_destroy(hs_factor f);
  * 0 turns it off (the default).  A measurement aid; the paper has no
  * counterpart.  Returns HS_OK. */
 int hs_profile_phases(int32_t on);
+
+/* hs_gemm_tc: one C = alpha op(A) op(B) + beta C through the tensor-core GEMM
+ * that the mixed factorizations use for their contractions (tcgen05, operands
+ * rounded to TF32 or BF16, FP32 accumulation), exported so that the kernel can
+ * be checked and measured on its own.  The paper has no counterpart.
+ *   prec: HS_PREC_TF32 or HS_PREC_BF16.  A, B, C: DEVICE, FP32, row-major;
+ *   op(A) is M x K (A[i lda + k], or A[k lda + i] when ta), op(B) is K x N
+ *   (B[k ldb + j], or B[j ldb + k] when tb), C is M x N with leading
+ *   dimension ldc.  C must not overlap A or B.  M, N >= 1, K >= 0.
+ *   bn: tile width, 64 or 128 (0: the library's choice).
+ * The call synchronises `stream`.  HS_ERR_TIMEOUT if a bounded wait inside
+ * the kernel ran out (C is then not fully written). */
+int hs_gemm_tc(int32_t prec, int32_t M, int32_t N, int32_t K, float alpha, const float *A, int64_t lda,
+               int32_t ta, const float *B, int64_t ldb, int32_t tb, float beta, float *C, int64_t ldc,
+               int32_t bn, void *stream);
+
+/* hs_gemm_tune_report: the table of the GEMM autotuner for operand
+ * precision `prec` (HS_PREC_TF32 or HS_PREC_BF16) on the current device,
+ * building it first if needed (that synchronises the device).  For each class
+ * of task shapes c (max(M, N) bucket 0..4 = up to 32, 64, 128, 256, more; K
+ * bucket 0..3 = up to 32, 128, 512, more; c = 4 * mn + k): ms[3c .. 3c+2] =
+ * measured times of the CUDA-core kernel and of the tensor-core kernel with
+ * 64- and 128-wide tiles on a synthetic batch of that class, route[c] = the
+ * choice (0 CUDA cores, 64 or 128).  HOST arrays of 3 cap floats and cap ints.
+ * Returns the number of classes (20), or a negative hs_status on error.  The
+ * paper has no counterpart. */
+int hs_gemm_tune_report(int32_t prec, float *ms, int32_t *route, int32_t cap);
 
 /* hs_last_error: message of the last failing call on this thread. */
 const char *hs_last_error(void);

@@ -31,6 +31,11 @@ HS_MAX_PHI = 4
 
 HS_PREC_F64 = 0
 HS_PREC_F32 = 1
+HS_PREC_TF32 = 2
+HS_PREC_BF16 = 3
+
+HS_ORDER_WAVES = 0
+HS_ORDER_SEQUENTIAL = 1
 
 STATUS_NAMES = {
     0: "HS_OK", 1: "HS_ERR_INVALID", 2: "HS_ERR_NOT_SPD", 3: "HS_ERR_CAPACITY", 4: "HS_ERR_OOM",
@@ -42,7 +47,7 @@ EXPORTS = [
     "hs_factor_create", "hs_factor_refactor", "hs_factor_create_batch", "hs_factor_refactor_batch",
     "hs_launch_count", "hs_profile_phases", "hs_abi_sizes", "hs_apply", "hs_apply_static", "hs_pcg", "hs_gmres", "hs_factor_info", "hs_factor_ranks",
     "hs_factor_destroy", "hs_last_error", "hs_plan_create", "hs_plan_level_waves",
-    "hs_plan_super_lists", "hs_plan_destroy",
+    "hs_plan_super_lists", "hs_plan_destroy", "hs_gemm_tc", "hs_gemm_tune_report",
 ]
 
 
@@ -64,7 +69,8 @@ class HsClustering(C.Structure):
 class HsOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("variant", C.c_int32), ("factor_prec", C.c_int32),
                 ("phi", C.c_void_p), ("eps_level", C.c_void_p), ("n_eps_level", C.c_int32),
-                ("n_phi", C.c_int32), ("eps1", C.c_double)]
+                ("n_phi", C.c_int32), ("eps1", C.c_double), ("scale", C.c_int32),
+                ("timeout_cycles", C.c_int64), ("order_mode", C.c_int32)]
 
 
 def _phi_block(phi):
@@ -82,7 +88,9 @@ class HsInfo(C.Structure):
                 ("max_super", C.c_int32), ("device_bytes", C.c_int64), ("factor_bytes", C.c_int64),
                 ("factor_flops", C.c_double), ("eig_flops", C.c_double), ("factor_ms", C.c_double),
                 ("trunc_big_ms", C.c_double), ("trunc_big_flops", C.c_double), ("trunc_big_launches", C.c_int32),
-                ("host_ms", C.c_double), ("wait_ms", C.c_double), ("phase_ms", C.c_double * 16)]
+                ("host_ms", C.c_double), ("wait_ms", C.c_double), ("phase_ms", C.c_double * 16),
+                ("alg_flops", C.c_double), ("tc_flops", C.c_double), ("tc_ms", C.c_double),
+                ("tc_launches", C.c_int64)]
 
     PHASES = ("merge", "gather", "chol_Ass", "gram", "trunc_small", "trunc_large", "cholqr_large",
               "extension", "schur", "root", "grid_prepare", "grid_tridiag_steps", "grid_qtz",
@@ -126,6 +134,9 @@ def lib():
         L.hs_plan_level_waves.argtypes = [vp, i32, vp, i32, C.POINTER(i32)]
         L.hs_plan_super_lists.argtypes = [vp, i32, i32, vp, vp, i32, C.POINTER(i32), C.POINTER(i32)]
         L.hs_plan_destroy.argtypes = [vp]
+        flt = C.c_float
+        L.hs_gemm_tc.argtypes = [i32, i32, i32, i32, flt, vp, i64, i32, vp, i64, i32, flt, vp, i64, i32, vp]
+        L.hs_gemm_tune_report.argtypes = [i32, vp, vp, i32]
         for name in EXPORTS:
             if name not in ("hs_last_error", "hs_launch_count"):
                 getattr(L, name).restype = C.c_int
@@ -215,7 +226,8 @@ class Factor:
     """
 
     def __init__(self, rowptr, col, val, perm, leaf_ptr, eps, variant=HS_GC_CONSTANT,
-                 prec=HS_PREC_F64, phi=None, stream=None, eps_level=None, eps1=0.0, nbr_dist=1):
+                 prec=HS_PREC_F64, phi=None, stream=None, eps_level=None, eps1=0.0, nbr_dist=1, scale=False,
+                 timeout_cycles=0, order_mode=HS_ORDER_WAVES):
         import torch
 
         assert rowptr.is_cuda and col.is_cuda and val.is_cuda
@@ -229,7 +241,7 @@ class Factor:
         self._epsl = None if eps_level is None else np.ascontiguousarray(eps_level, dtype=np.float64)
         o = HsOpts(float(eps), int(variant), int(prec), None if self._phi is None else _ptr(self._phi),
                    None if self._epsl is None else _ptr(self._epsl), 0 if self._epsl is None else len(self._epsl),
-                   nphi, float(eps1))
+                   nphi, float(eps1), int(bool(scale)), int(timeout_cycles), int(order_mode))
         h = C.c_void_p()
         self._h = None
         check(lib().hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), _stream_ptr(stream), C.byref(h)))
@@ -310,7 +322,7 @@ class Factor:
 
 
 def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=None, stream=None,
-                 eps_level=None, eps1=0.0, nbr_dist=1):
+                 eps_level=None, eps1=0.0, nbr_dist=1, scale=False):
     """hs_factor_create_batch over `problems`: a list of (rowptr, col, val,
     perm, leaf_ptr) with rowptr/col int32 and val float64 CUDA tensors and
     perm/leaf_ptr host arrays.  Returns (factors, status): one Factor per
@@ -341,7 +353,7 @@ def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=N
     epsl = None if eps_level is None else np.ascontiguousarray(eps_level, dtype=np.float64)
     keep.append(epsl)
     o = HsOpts(float(eps), int(variant), int(prec), None, None if epsl is None else _ptr(epsl),
-               0 if epsl is None else len(epsl), nphi, float(eps1))
+               0 if epsl is None else len(epsl), nphi, float(eps1), int(bool(scale)), 0, HS_ORDER_WAVES)
     out = (C.c_void_p * k)()
     status = np.zeros(k, dtype=np.int32)
     code = lib().hs_factor_create_batch(k, A, cl, C.byref(o), phi_arr, _stream_ptr(stream), out, _ptr(status))
@@ -373,6 +385,41 @@ def refactor_batch(factors, vals, stream=None):
     if code not in (HS_OK, HS_ERR_NOT_SPD):
         check(code)
     return status
+
+
+def gemm_tc(prec, A, B, C, alpha=1.0, beta=0.0, ta=False, tb=False, bn=0, stream=None):
+    """C = alpha op(A) op(B) + beta C through the tensor-core GEMM (hs_gemm_tc).
+    A, B, C: 2-D float32 CUDA tensors, row-major with unit column stride
+    (their row strides are the leading dimensions); op(X) = X.T when the
+    flag is set.  C is updated in place."""
+    for X in (A, B, C):
+        if X.dim() != 2 or X.stride(1) != 1 or str(X.dtype) != "torch.float32":
+            raise ValueError("A, B, C must be 2-D float32 tensors with unit column stride")
+    M, N = C.shape
+    K = A.shape[0] if ta else A.shape[1]
+
+    def ld(X):
+        return max(X.stride(0), X.shape[1], 1)
+
+    check(lib().hs_gemm_tc(int(prec), M, N, K, float(alpha), A.data_ptr(), ld(A), int(bool(ta)),
+                           B.data_ptr(), ld(B), int(bool(tb)), float(beta), C.data_ptr(), ld(C),
+                           int(bn), _stream_ptr(stream)))
+    return C
+
+
+def gemm_tune_report(prec) -> list:
+    """The GEMM autotuner's table for operand precision `prec` on the current
+    device: one dict per shape class (hs_gemm_tune_report)."""
+    cap = 32
+    ms = np.zeros(3 * cap, dtype=np.float32)
+    route = np.zeros(cap, dtype=np.int32)
+    n = int(lib().hs_gemm_tune_report(int(prec), _ptr(ms), _ptr(route), cap))
+    if n < 0:
+        check(-n)
+    mn = ("<=32", "<=64", "<=128", "<=256", ">256")
+    kk = ("<=32", "<=128", "<=512", ">512")
+    return [{"max_mn": mn[c // 4], "k": kk[c % 4], "ms_simt": float(ms[3 * c]), "ms_tc64": float(ms[3 * c + 1]),
+             "ms_tc128": float(ms[3 * c + 2]), "route": int(route[c])} for c in range(min(n, cap))]
 
 
 def profile_phases(on: bool) -> None:

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libhs.so")
-SOURCES = ["kernels_dense.cu", "kernels_eig.cu", "factor.cu", "solve.cu", "plan.cpp", "api.cpp"]
+SOURCES = ["kernels_dense.cu", "kernels_eig.cu", "kernels_tc.cu", "kernels_cluster.cu", "factor.cu", "solve.cu", "plan.cpp", "api.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

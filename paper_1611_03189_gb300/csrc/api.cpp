@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "handle.h"
 
@@ -58,6 +59,17 @@ void require_device() {
     fail(HS_ERR_CUDA, std::string("no CUDA device: ") + (e == cudaSuccess ? "count is 0" : cudaGetErrorString(e)));
 }
 
+// The factor's buffers live on the device that was current when it was
+// created; every later call on the handle must run with that device current.
+void require_factor_device(const FactorHandle &h) {
+  require_device();
+  int dev = -1;
+  HS_CUDA(cudaGetDevice(&dev));
+  if (dev != h.device)
+    fail(HS_ERR_INVALID, "the current device is " + std::to_string(dev) + " but the factorization lives on device " +
+                             std::to_string(h.device));
+}
+
 template <typename X>
 X *upload_vec(const std::vector<X> &v, cudaStream_t st) {
   X *d = nullptr;
@@ -73,6 +85,14 @@ void numeric_pre(FactorHandle &h, const double *val, cudaStream_t st) {
   h.stream = st;
   h.drop_graphs();   // the schedule and the record pointers change
   launch_gather_values(val, h.d_src, h.nnz, h.d_val, st);
+  if (h.scale) {
+    HS_CUDA(cudaMemsetAsync(h.d_flag, 0, sizeof(int), st));
+    launch_diag_scale(h.d_rowptr, h.d_col, h.d_val, h.plan.n, h.d_dscale, h.d_val_f, h.d_flag, st);
+    int bad = 0;
+    HS_CUDA(cudaMemcpyAsync(&bad, h.d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HS_CUDA(cudaStreamSynchronize(st));
+    if (bad) fail(HS_ERR_NOT_SPD, "diagonal scaling: a diagonal entry is missing or not positive");
+  }
   cudaFree(h.d_nodes);
   cudaFree(h.d_nbrs);
   cudaFree(h.d_targets);
@@ -170,6 +190,7 @@ void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, con
   h.eps = o->eps;
   h.nphi = (o->variant == HS_GC_USER || o->variant == HS_GC_PROJ) ? std::max(o->n_phi, 1) : 1;
   h.eps1 = o->variant == HS_GC_PROJ ? o->eps1 : 0.0;
+  h.timeout_cycles = o->timeout_cycles;
   h.eps_level.clear();
   // pattern to the host for the planner
   std::vector<int32_t> rp(A->n + 1), ci(A->nnz);
@@ -177,7 +198,8 @@ void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, con
   HS_CUDA(cudaMemcpyAsync(ci.data(), A->col, sizeof(int32_t) * A->nnz, cudaMemcpyDeviceToHost, st));
   HS_CUDA(cudaStreamSynchronize(st));
   if (rp[A->n] != A->nnz) fail(HS_ERR_INVALID, "rowptr[n] != nnz");
-  build_plan(A->n, rp.data(), ci.data(), cl->perm, cl->leaf_ptr, cl->nleaf, h.plan, nbr_rule(cl->nbr_dist));
+  build_plan(A->n, rp.data(), ci.data(), cl->perm, cl->leaf_ptr, cl->nleaf, h.plan, nbr_rule(cl->nbr_dist),
+             o->order_mode);
   if (o->eps_level) {
     const int need = std::max(h.plan.L - 1, 0);
     if (o->n_eps_level < need)
@@ -192,6 +214,12 @@ void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, con
   h.d_src = upload_vec(h.plan.psrc, st);
   h.nnz = A->nnz;
   HS_CUDA(cudaMalloc(&h.d_val, sizeof(double) * A->nnz));
+  h.scale = o->scale != 0;
+  if (h.scale) {
+    HS_CUDA(cudaMalloc(&h.d_val_f, sizeof(double) * A->nnz));
+    HS_CUDA(cudaMalloc(&h.d_dscale, sizeof(double) * A->n));
+    HS_CUDA(cudaMalloc(&h.d_flag, sizeof(int)));
+  }
 }
 
 void check_opts(const hs_opts *o) {
@@ -204,7 +232,13 @@ void check_opts(const hs_opts *o) {
     fail(HS_ERR_INVALID, user ? "n_phi must be 0 .. HS_MAX_PHI" : "n_phi > 1 needs HS_GC_USER or HS_GC_PROJ");
   if (o->variant == HS_GC_PROJ && (!(o->eps1 >= 0.0) || !std::isfinite(o->eps1)))
     fail(HS_ERR_INVALID, "eps1 must be finite and >= 0");
-  if (o->factor_prec != HS_PREC_F64 && o->factor_prec != HS_PREC_F32) fail(HS_ERR_INVALID, "unknown factor_prec");
+  if (o->scale != 0 && o->scale != 1) fail(HS_ERR_INVALID, "scale must be 0 or 1");
+  if (o->timeout_cycles < 0) fail(HS_ERR_INVALID, "timeout_cycles must be >= 0");
+  if (o->order_mode != HS_ORDER_WAVES && o->order_mode != HS_ORDER_SEQUENTIAL)
+    fail(HS_ERR_INVALID, "order_mode must be HS_ORDER_WAVES or HS_ORDER_SEQUENTIAL");
+  if (o->factor_prec != HS_PREC_F64 && o->factor_prec != HS_PREC_F32 && o->factor_prec != HS_PREC_TF32 &&
+      o->factor_prec != HS_PREC_BF16)
+    fail(HS_ERR_INVALID, "unknown factor_prec");
   if (o->eps_level) {
     if (o->n_eps_level < 0) fail(HS_ERR_INVALID, "n_eps_level < 0");
     for (int j = 0; j < o->n_eps_level; ++j) {
@@ -297,7 +331,7 @@ int hs_factor_create_batch(int32_t count, const hs_csr *A, const hs_clustering *
 int hs_factor_refactor(hs_factor f, const double *val, void *stream) {
   return hs::guarded([&]() -> int {
     if (!f || !val) fail(HS_ERR_INVALID, "null argument");
-    hs::require_device();
+    hs::require_factor_device(f->h);
     f->h.valid = false;
     hs::numeric_factor(f->h, val, nullptr, (cudaStream_t)stream);
     f->h.valid = true;
@@ -319,7 +353,7 @@ int hs_factor_refactor_batch(int32_t count, hs_factor *f, const double *const *v
       vals.push_back(val[p]);
       phis.push_back(nullptr);
     }
-    hs::require_device();
+    for (auto *h : hs_) hs::require_factor_device(*h);
     for (auto *h : hs_) h->valid = false;
     std::vector<int> stat;
     std::vector<std::string> msgs;
@@ -333,6 +367,69 @@ int hs_factor_refactor_batch(int32_t count, hs_factor *f, const double *const *v
     if (first >= 0) fail(stat[first], msgs[first]);
     return HS_OK;
   });
+}
+
+int hs_gemm_tc(int32_t prec, int32_t M, int32_t N, int32_t K, float alpha, const float *A, int64_t lda,
+               int32_t ta, const float *B, int64_t ldb, int32_t tb, float beta, float *C, int64_t ldc,
+               int32_t bn, void *stream) {
+  return hs::guarded([&]() -> int {
+    if (prec != HS_PREC_TF32 && prec != HS_PREC_BF16) fail(HS_ERR_INVALID, "prec must be HS_PREC_TF32 or HS_PREC_BF16");
+    if (M < 1 || N < 1 || K < 0) fail(HS_ERR_INVALID, "need M, N >= 1 and K >= 0");
+    if (!A || !B || !C) fail(HS_ERR_INVALID, "null argument");
+    if (bn != 0 && bn != 64 && bn != 128) fail(HS_ERR_INVALID, "bn must be 0, 64 or 128");
+    const int64_t need_a = ta ? M : K, need_b = tb ? K : N;
+    if (lda < std::max<int64_t>(need_a, 1) || ldb < std::max<int64_t>(need_b, 1) || ldc < N)
+      fail(HS_ERR_INVALID, "leading dimension too small");
+    if (lda > INT32_MAX || ldb > INT32_MAX || ldc > INT32_MAX) fail(HS_ERR_INVALID, "leading dimension too large");
+    hs::require_device();
+    cudaStream_t st = (cudaStream_t)stream;
+    const int w = bn ? bn : (N <= 64 ? 64 : 128);
+    hs::GemmTask<float> t;
+    t.A = A;
+    t.B = B;
+    t.C = C;
+    t.M = M;
+    t.N = N;
+    t.K = K;
+    t.lda = (int)lda;
+    t.ldb = (int)ldb;
+    t.ldc = (int)ldc;
+    t.ta = ta ? 1 : 0;
+    t.tb = tb ? 1 : 0;
+    t.alpha = alpha;
+    t.beta = beta;
+    const int tiles = ((M + hs::TC_TILE_M - 1) / hs::TC_TILE_M) * ((N + w - 1) / w);
+    char *d = nullptr;
+    HS_CUDA(cudaMalloc(&d, 256 + sizeof(t)));
+    struct Free {
+      char *p;
+      ~Free() { cudaFree(p); }
+    } fr{d};
+    int *d_err = (int *)d, *d_ts = (int *)(d + 16);
+    hs::GemmTask<float> *d_t = (hs::GemmTask<float> *)(d + 256);
+    HS_CUDA(cudaMemsetAsync(d, 0, 256, st));
+    HS_CUDA(cudaMemcpyAsync(d_t, &t, sizeof(t), cudaMemcpyHostToDevice, st));
+    hs::launch_gemm_tc(prec == HS_PREC_TF32 ? hs::HS_TC_TF32 : hs::HS_TC_BF16, w, d_t, d_ts, 1, tiles, d_err, st);
+    int herr = 0;
+    HS_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HS_CUDA(cudaStreamSynchronize(st));
+    if (herr) fail(HS_ERR_TIMEOUT, "hs_gemm_tc: a bounded wait of the tensor-core GEMM ran out");
+    return HS_OK;
+  });
+}
+
+int hs_gemm_tune_report(int32_t prec, float *ms, int32_t *route, int32_t cap) {
+  int n = 0;
+  const int rc = hs::guarded([&]() -> int {
+    if (prec != HS_PREC_TF32 && prec != HS_PREC_BF16) fail(HS_ERR_INVALID, "prec must be HS_PREC_TF32 or HS_PREC_BF16");
+    if (cap < 0 || (cap > 0 && (!ms || !route))) fail(HS_ERR_INVALID, "null argument");
+    hs::require_device();
+    std::vector<int> r(std::max(cap, 0));
+    n = hs::gemm_tune_report(prec == HS_PREC_TF32 ? hs::HS_TC_TF32 : hs::HS_TC_BF16, ms, r.data(), cap);
+    for (int i = 0; i < cap && i < n; ++i) route[i] = r[i];
+    return HS_OK;
+  });
+  return rc == HS_OK ? n : -rc;
 }
 
 int64_t hs_launch_count(void) { return hs::g_launches.load(); }
@@ -354,7 +451,7 @@ int hs_apply(hs_factor f, const double *r, double *z, int32_t nrhs, int64_t ld, 
     if (!f || !r || !z) fail(HS_ERR_INVALID, "null argument");
     if (nrhs < 1 || nrhs > 64) fail(HS_ERR_INVALID, "nrhs must be in [1, 64]");
     if (ld < f->h.plan.n) fail(HS_ERR_INVALID, "ld < n");
-    hs::require_device();
+    hs::require_factor_device(f->h);
     cudaStream_t st = (cudaStream_t)stream;
     // r and z may alias: r is gathered into the workspace before z is written
     if (!f->h.valid) fail(HS_ERR_INVALID, "the handle holds no valid factorization");
@@ -368,6 +465,7 @@ int hs_apply_static(hs_factor f, const double *r, double *z, int32_t nrhs, int64
     if (!f || !r || !z) fail(HS_ERR_INVALID, "null argument");
     if (nrhs < 1 || nrhs > 64) fail(HS_ERR_INVALID, "nrhs must be in [1, 64]");
     if (ld < f->h.plan.n) fail(HS_ERR_INVALID, "ld < n");
+    hs::require_factor_device(f->h);
     if (!f->h.valid) fail(HS_ERR_INVALID, "the handle holds no valid factorization");
     hs::apply_static(f->h, r, z, nrhs, ld, (cudaStream_t)stream);
     return HS_OK;
@@ -381,7 +479,7 @@ int hs_pcg(hs_factor f, const double *b, double *x, int32_t nrhs, int64_t ld, do
     if (nrhs < 1 || nrhs > 32) fail(HS_ERR_INVALID, "nrhs must be in [1, 32]");
     if (ld < f->h.plan.n) fail(HS_ERR_INVALID, "ld < n");
     if (!(rtol > 0.0) || maxit < 1) fail(HS_ERR_INVALID, "rtol must be > 0 and maxit >= 1");
-    hs::require_device();
+    hs::require_factor_device(f->h);
     if (!f->h.valid) fail(HS_ERR_INVALID, "the handle holds no valid factorization");
     return hs::pcg_solve(f->h, b, x, nrhs, ld, rtol, maxit, iters, relres, (cudaStream_t)stream);
   });
@@ -394,7 +492,7 @@ int hs_gmres(hs_factor f, const double *b, double *x, double rtol, int32_t maxit
     if (!(rtol > 0.0) || maxit < 1 || restart < 0) fail(HS_ERR_INVALID, "rtol must be > 0, maxit >= 1, restart >= 0");
     if ((restart > 0 ? std::min(restart, maxit) : maxit) > 1000)
       fail(HS_ERR_INVALID, "the Krylov basis is limited to 1000 vectors (restart, or maxit without restart)");
-    hs::require_device();
+    hs::require_factor_device(f->h);
     if (!f->h.valid) fail(HS_ERR_INVALID, "the handle holds no valid factorization");
     int it = 0;
     const int r = hs::gmres_solve(f->h, b, x, rtol, maxit, restart, &it, relres, (cudaStream_t)stream);

@@ -28,6 +28,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <type_traits>
 #include <unordered_map>
 
 #include "handle.h"
@@ -134,12 +135,19 @@ struct Uploader {
   }
 };
 
+// Receives an event before and after each tensor-core launch of a GEMM batch
+// (with the flops of the tasks launched), for the kernel's device time.
+struct TcTimer {
+  virtual void before(cudaStream_t st) = 0;
+  virtual void after(cudaStream_t st, double flops) = 0;
+  virtual ~TcTimer() = default;
+};
+
 template <typename T>
 struct GemmBatch {
   std::vector<GemmTask<T>> tasks;
-  std::vector<int> tile_start;
-  int tiles = 0;
   double flops = 0.0;
+  int tc = HS_TC_NONE;   // float batches: run on the tensor cores in this precision
   void add(const T *A, int lda, int ta, const T *B, int ldb, int tb, T *C, int ldc, int M, int N,
            int K, T alpha, T beta) {
     if (M <= 0 || N <= 0) return;
@@ -159,20 +167,53 @@ struct GemmBatch {
     t.alpha = alpha;
     t.beta = beta;
     tasks.push_back(t);
-    tile_start.push_back(tiles);
-    tiles += ((M + GEMM_TM - 1) / GEMM_TM) * ((N + GEMM_TN - 1) / GEMM_TN);
     flops += 2.0 * M * N * (double)std::max(K, 0);
   }
-  void launch(DevArena &scr, Staging &sg, cudaStream_t st) {
+  // d_err: error word of the tensor-core kernel (bounded waits).  With `tc`
+  // set, each task goes to the variant the autotuner picked for its shape
+  // (CUDA-core kernel, or tensor-core kernel with 64- or 128-wide tiles): up
+  // to three launches, whose tasks are independent of each other.
+  void launch(DevArena &scr, Staging &sg, cudaStream_t st, int *d_err = nullptr, TcTimer *timer = nullptr,
+              long long wait_cycles = 0) {
     if (tasks.empty()) return;
-    Uploader u;
-    const size_t ot = u.add(tasks);
-    const size_t os = u.add(tile_start);
-    char *d = u.upload(scr, sg, st);
-    launch_gemm<T>((const GemmTask<T> *)(d + ot), (const int *)(d + os), (int)tasks.size(), tiles, st);
+    const bool on_tc = std::is_same<T, float>::value && tc != HS_TC_NONE;
+    std::vector<GemmTask<T>> part[3];
+    if (on_tc) {
+      for (const GemmTask<T> &t : tasks) {
+        const int r = gemm_route(tc, t.M, t.N, t.K);
+        part[r == 0 ? 0 : r == 64 ? 1 : 2].push_back(t);
+      }
+    } else {
+      part[0].swap(tasks);
+    }
     tasks.clear();
-    tile_start.clear();
-    tiles = 0;
+    const int tms[3] = {GEMM_TM, TC_TILE_M, TC_TILE_M}, tns[3] = {GEMM_TN, 64, 128};
+    for (int v = 0; v < 3; ++v) {
+      if (part[v].empty()) continue;
+      std::vector<int> tile_start;
+      int tiles = 0;
+      for (const GemmTask<T> &t : part[v]) {
+        tile_start.push_back(tiles);
+        tiles += ((t.M + tms[v] - 1) / tms[v]) * ((t.N + tns[v] - 1) / tns[v]);
+      }
+      Uploader u;
+      const size_t ot = u.add(part[v]);
+      const size_t os = u.add(tile_start);
+      char *d = u.upload(scr, sg, st);
+      if (v == 0) {
+        launch_gemm<T>((const GemmTask<T> *)(d + ot), (const int *)(d + os), (int)part[v].size(), tiles, st);
+        continue;
+      }
+      if constexpr (std::is_same<T, float>::value) {
+        if (!d_err) fail(HS_ERR_INVALID, "internal: tensor-core GEMM launched without an error word");
+        double f = 0.0;
+        for (const GemmTask<T> &t : part[v]) f += 2.0 * t.M * t.N * (double)std::max(t.K, 0);
+        if (timer) timer->before(st);
+        launch_gemm_tc(tc, tns[v], (const GemmTask<float> *)(d + ot), (const int *)(d + os), (int)part[v].size(),
+                       tiles, d_err, st, wait_cycles);
+        if (timer) timer->after(st, f);
+      }
+    }
   }
 };
 
@@ -295,6 +336,16 @@ int eig_small_max() {
 std::atomic<int> g_phase_prof{0};
 bool phase_profiling() { return g_phase_prof.load() != 0; }
 
+// The cluster tridiagonalisation of the multi-CTA path (HS_TRI_CLUSTER=0 in
+// the environment turns it off: every node then takes the step kernels).
+inline bool tri_cluster_enabled() {
+  static const bool v = [] {
+    const char *e = std::getenv("HS_TRI_CLUSTER");
+    return !(e && e[0] == '0');
+  }();
+  return v;
+}
+
 inline int grid_tridiag_min() {
   static const int v = [] {
     const char *e = std::getenv("HS_GRID_TRIDIAG_MIN");
@@ -319,7 +370,7 @@ struct PendingStatus {
 // task descriptors, the pinned staging buffers, the status words to check and
 // the host buffer of the per-wave rank read.  One Exec drives one problem, or
 // many independent problems whose steps are batched into the same launches.
-struct Exec {
+struct Exec : TcTimer {
   cudaStream_t st = nullptr;
   DevArena scr{16ull << 20};
   Staging sg;
@@ -334,6 +385,19 @@ struct Exec {
   std::vector<std::string> prob_msg;
   // host time spent waiting for the device (sync_check), in ms
   double wait_ms = 0.0;
+  // tensor-core precision of the elimination's contractions (HS_TC_NONE for
+  // the FP64 and FP32 factors) and the error word of that kernel's bounded
+  // waits, read at every sync_check after a tensor-core launch
+  int tc = HS_TC_NONE;
+  int *d_err = nullptr;
+  bool tc_pending = false;
+  long long wait_cycles = 0;   // bound of the kernels' waits (hs_opts.timeout_cycles; 0 = default)
+  // device time of the tensor-core launches: an event pair around each,
+  // read and summed at the next sync_check (the pairs are then reused)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> tc_ev;
+  size_t tc_ev_used = 0;
+  double tc_ms = 0.0, tc_flops = 0.0;
+  int64_t tc_launches = 0;
   // optional device time per phase (hs_profile_phases): event pairs around
   // each launch group, read after the final synchronisation
   bool prof = false;
@@ -363,6 +427,18 @@ struct Exec {
       if (cudaEventElapsedTime(&t, sp.e0, sp.e1) == cudaSuccess && sp.phase < nphase) ms[sp.phase] += t;
     }
   }
+  // a second stream for work that runs beside the factor stream (joined
+  // back by an event before anything depends on it)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  cudaStream_t side_stream() {
+    if (!side) {
+      HS_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+      HS_CUDA(cudaEventCreateWithFlags(&fork_ev, cudaEventDisableTiming));
+      HS_CUDA(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
+    }
+    return side;
+  }
   explicit Exec(cudaStream_t s) : st(s) {
     HS_CUDA(cudaEventCreate(&ev_big[0]));
     HS_CUDA(cudaEventCreate(&ev_big[1]));
@@ -370,6 +446,17 @@ struct Exec {
   ~Exec() {
     // copies from the pinned staging buffers may still be in flight after an error
     cudaStreamSynchronize(st);
+    if (side) {
+      cudaStreamSynchronize(side);
+      cudaStreamDestroy(side);
+      cudaEventDestroy(fork_ev);
+      cudaEventDestroy(join_ev);
+    }
+    cudaFree(d_err);
+    for (auto &e : tc_ev) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
     for (Span &sp : spans) {
       cudaEventDestroy(sp.e0);
       cudaEventDestroy(sp.e1);
@@ -397,11 +484,54 @@ struct Exec {
     return true;
   }
   bool ok(int prob) const { return prob < 0 || prob >= (int)prob_status.size() || prob_status[prob] == HS_OK; }
+  // a GEMM batch: on the tensor cores in precision `tc` when that is set and
+  // the batch is FP32, else on the CUDA cores
+  template <typename T>
+  void gemm(GemmBatch<T> &g, bool tensor_cores = true) {
+    if (g.tasks.empty()) return;
+    g.tc = (tensor_cores && std::is_same<T, float>::value) ? tc : HS_TC_NONE;
+    if (g.tc != HS_TC_NONE) {
+      if (!d_err) {
+        HS_CUDA(cudaMalloc(&d_err, sizeof(int)));
+        HS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+      }
+      tc_pending = true;
+      g.launch(scr, sg, st, d_err, this, wait_cycles);
+      return;
+    }
+    g.launch(scr, sg, st, d_err);
+  }
+  void before(cudaStream_t s) override {
+    if (tc_ev_used == tc_ev.size()) {
+      std::pair<cudaEvent_t, cudaEvent_t> e{nullptr, nullptr};
+      HS_CUDA(cudaEventCreate(&e.first));
+      HS_CUDA(cudaEventCreate(&e.second));
+      tc_ev.push_back(e);
+    }
+    HS_CUDA(cudaEventRecord(tc_ev[tc_ev_used].first, s));
+  }
+  void after(cudaStream_t s, double flops) override {
+    HS_CUDA(cudaEventRecord(tc_ev[tc_ev_used].second, s));
+    ++tc_ev_used;
+    tc_flops += flops;
+  }
   // waits for the stream, then checks the pending status words
   void sync_check() {
     const auto t0 = std::chrono::steady_clock::now();
     HS_CUDA(cudaStreamSynchronize(st));
     wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (tc_pending) {
+      int e = 0;
+      HS_CUDA(cudaMemcpy(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+      if (e) fail(HS_ERR_TIMEOUT, "a bounded wait of the tensor-core GEMM ran out");
+      tc_pending = false;
+      for (size_t i = 0; i < tc_ev_used; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, tc_ev[i].first, tc_ev[i].second) == cudaSuccess) tc_ms += t;
+      }
+      tc_launches += (int64_t)tc_ev_used;
+      tc_ev_used = 0;
+    }
     for (auto &ps : pending) {
       std::vector<int> hv(ps.what.size());
       HS_CUDA(cudaMemcpy(hv.data(), ps.d, ps.what.size() * sizeof(int), cudaMemcpyDeviceToHost));
@@ -517,8 +647,8 @@ struct Exec {
       const size_t o = u.add(dc);
       char *d = u.upload(scr, sg, st);
       launch_chol_inv<T>((const CholTask<T> *)(d + o), (int)dc.size(), bs, nb, st);
-      pan.launch(scr, sg, st);
-      trl.launch(scr, sg, st);
+      gemm(pan, false);   // the Cholesky of A_ss stays in FP32 on every path
+      gemm(trl, false);
     }
     for (int b = 0; b < maxblk; ++b) {
       GemmBatch<T> g1, g2;
@@ -533,8 +663,8 @@ struct Exec {
         }
         dg.copy(x.t.Linv + (size_t)i0 * m + i0, m, jb, jb, Db, jb, 0);
       }
-      g1.launch(scr, sg, st);
-      g2.launch(scr, sg, st);
+      gemm(g1, false);
+      gemm(g2, false);
       dg.launch(scr, sg, st);
     }
     std::vector<StatusMerge> sm;
@@ -583,7 +713,8 @@ class Run {
   void level_begin(int li, SumBatch<T> &sb);     // merge into the level's super nodes
   void wave_a(int li, int widx, WaveBatches<T> &B);
   void wave_b(const int *hb, size_t nchol, size_t ntrunc, double big_ms, WaveBatches<T> &B);
-  void wave_c(WaveBatches<T> &B);
+  void wave_c(WaveBatches<T> &B);               // the elimination's GEMM tasks
+  void wave_d(WaveBatches<T> &B);               // Schur targets, red-node blocks, apply records
   void level_end(int li);
   void root_a(SumBatch<T> &sb);                  // merge of the last red nodes
   void root_b(CholBatch<T> &cb, GemmBatch<T> &g);
@@ -644,7 +775,7 @@ class Run {
   double flops_ = 0.0;
   // device time (of the launches taken part in) and nominal eigen-solve flops
   // of the large-node truncations
-  double big_ms_ = 0.0, big_flops_ = 0.0, eig_flops_ = 0.0;
+  double big_ms_ = 0.0, big_flops_ = 0.0, eig_flops_ = 0.0, alg_flops_ = 0.0;
   int big_launches_ = 0;
   // root records waiting for root_b
   T *root_linv_ = nullptr, *root_ainv_ = nullptr;
@@ -701,13 +832,21 @@ void Run<T>::leaf_setup() {
         for (int j = 0; j < np; ++j)
           ph[(size_t)p * np + j] = user ? (T)phi_host_[(size_t)j * P_.n + P_.perm[p]] : T(1);
       HS_CUDA(cudaMalloc(&h_.d_phi0, sizeof(T) * ph.size()));
-      HS_CUDA(cudaMemcpyAsync(h_.d_phi0, ph.data(), sizeof(T) * ph.size(), cudaMemcpyHostToDevice, st_));
+      if (h_.scale && user) {
+        // the caller's vectors are kept; each factorization maps them to D^1/2 phi
+        HS_CUDA(cudaMalloc(&h_.d_phi_raw, sizeof(T) * ph.size()));
+        HS_CUDA(cudaMemcpyAsync(h_.d_phi_raw, ph.data(), sizeof(T) * ph.size(), cudaMemcpyHostToDevice, st_));
+      } else {
+        HS_CUDA(cudaMemcpyAsync(h_.d_phi0, ph.data(), sizeof(T) * ph.size(), cudaMemcpyHostToDevice, st_));
+      }
     }
   }
+  if (h_.d_phi_raw)
+    launch_phi_scale<T>((const T *)h_.d_phi_raw, h_.d_dscale, P_.n, h_.nphi, (T *)h_.d_phi0, st_);
   const int64_t total = h_.leaf_total;
   T *base = talloc<T>(*h_.pers, total);
   HS_CUDA(cudaMemsetAsync(base, 0, sizeof(T) * std::max<int64_t>(total, 1), st_));
-  launch_scatter_values<T>(h_.d_val, h_.d_leaf_dest, P_.nnz, base, st_);
+  launch_scatter_values<T>(h_.factor_values(), h_.d_leaf_dest, P_.nnz, base, st_);
   blocks_.clear();
   for (size_t i = 0; i < h_.leaf_blocks.size(); ++i) {
     const auto &ab = h_.leaf_blocks[i];
@@ -1012,7 +1151,25 @@ void Run<T>::wave_c(WaveBatches<T> &B) {
   }
   flops_ += B.c1.flops + B.c2.flops + B.g1.flops + B.g2.flops + B.g3.flops + B.g4.flops + B.g5.flops +
             B.g6.flops + B.g7.flops + B.g8.flops - f0;
+  // algorithmic work of the elimination, counted from the actual sizes: Gram
+  // 2 m^2 w and R^T 2 m k w of the truncation (Sec. 3.2), Cholesky m^3/3,
+  // Y 2 m^2 k, S 2 m k^2 + k^3/3, G_n 2 m^2 d_N, H_n 2 m k d_N, the Schur
+  // update 2 (m + k) d_N^2 over all neighbour pairs, and M_ss, P_ss 2 m^2 k
+  // (w = sum of the well-separated widths, d_N = sum of the neighbour sizes)
+  for (const Sup &x : S) {
+    const double m = x.m, k = x.k, dN = x.dN, w = x.red ? x.dW : 0;
+    alg_flops_ += 2 * m * m * w + 2 * m * k * w + m * m * m / 3 + 2 * m * m * k + 2 * m * k * k + k * k * k / 3 +
+                  2 * m * m * dN + 2 * m * k * dN + 2 * (m + k) * dN * dN + 2 * m * m * k;
+  }
 
+}
+
+// Runs on the host while the GPU executes the wave's GEMMs (wave_c's tasks
+// are launched before this is called).
+template <typename T>
+void Run<T>::wave_d(WaveBatches<T> &B) {
+  DevArena &per = *h_.pers;
+  std::vector<Sup> &S = cur_;
   // register the red nodes' blocks and gather the Schur update by target
   std::unordered_map<uint64_t, std::vector<std::pair<int, int>>> tgt;  // target -> (sup idx, pair)
   std::vector<uint64_t> tgt_order;
@@ -1294,6 +1451,7 @@ void Run<T>::root_b(CholBatch<T> &cb, GemmBatch<T> &g) {
   const BlockRef<T> &b = blocks_.at(bkey(0, 0));
   const double f0 = cb.flops + g.flops;
   cb.add(b.ptr, b.ld, root_linv_, m, tag(4, 0, 0));
+  alg_flops_ += (double)m * m * m / 3;
   g.add(root_linv_, m, 1, root_linv_, m, 0, root_ainv_, m, m, m, m, T(1), T(0));
   flops_ += cb.flops + g.flops - f0;
   h_.root_inv = root_ainv_;
@@ -1307,6 +1465,7 @@ void Run<T>::finish() {
   h_.info.trunc_big_ms = big_ms_;
   h_.info.trunc_big_flops = big_flops_;
   h_.info.trunc_big_launches = big_launches_;
+  h_.info.alg_flops = alg_flops_;
 }
 
 // Truncation of very large nodes across the whole GPU: k_trunc_big up to J
@@ -1341,16 +1500,54 @@ void trunc_grid(Exec &ex, const std::vector<TruncTask<T>> &tasks, const TruncTas
     g.blk0 = blocks;
     blocks += g.nblk;
   }
+  // nodes that fit a thread-block cluster's shared memory are tridiagonalised
+  // there in one launch per cluster size; the others by the step kernels
+  std::vector<GridTri<T>> by_c[4], steps;
+  int cmax[4] = {0, 0, 0, 0}, smax = 0;
+  for (const GridTri<T> &g : gt) {
+    const int c = tri_cluster_enabled() ? tri_cluster_size<T>(g.m) : 0;
+    if (c > 0) {
+      const int q = c == 1 ? 0 : c == 2 ? 1 : c == 4 ? 2 : 3;
+      by_c[q].push_back(g);
+      cmax[q] = std::max(cmax[q], g.m);
+    } else {
+      GridTri<T> h = g;
+      h.blk0 = 0;
+      steps.push_back(h);
+      smax = std::max(smax, g.m);
+    }
+  }
+  int sblocks = 0;
+  for (GridTri<T> &g : steps) {
+    g.blk0 = sblocks;
+    sblocks += g.nblk;
+  }
   Uploader u;
-  const size_t og = u.add(gt);
+  const size_t og = u.add(steps);
+  size_t oc[4];
+  for (int q = 0; q < 4; ++q) oc[q] = u.add(by_c[q]);
   char *dg = u.upload(ex.scr, ex.sg, ex.st);
   const GridTri<T> *d_gt = (const GridTri<T> *)(dg + og);
   ex.begin(11);
-  for (int k = 0; k + 2 <= max_m; ++k) {
-    launch_tri_step<T>(d_gt, n, blocks, k, 0, ex.st);
-    if (k + 3 <= max_m) launch_tri_step<T>(d_gt, n, blocks, k, 1, ex.st);
+  // the cluster launches run on a side stream, beside the step kernels
+  const bool fork = !steps.empty() && (by_c[0].size() + by_c[1].size() + by_c[2].size() + by_c[3].size()) > 0;
+  cudaStream_t cs = fork ? ex.side_stream() : ex.st;
+  if (fork) {
+    HS_CUDA(cudaEventRecord(ex.fork_ev, ex.st));
+    HS_CUDA(cudaStreamWaitEvent(cs, ex.fork_ev, 0));
+  }
+  for (int q = 0; q < 4; ++q)
+    launch_tri_cluster<T>((const GridTri<T> *)(dg + oc[q]), (int)by_c[q].size(), 1 << q, cmax[q], cs);
+  for (int k = 0; k + 2 <= smax; ++k) {
+    launch_tri_step<T>(d_gt, (int)steps.size(), sblocks, k, 0, ex.st);
+    if (k + 3 <= smax) launch_tri_step<T>(d_gt, (int)steps.size(), sblocks, k, 1, ex.st);
+  }
+  if (fork) {
+    HS_CUDA(cudaEventRecord(ex.join_ev, cs));
+    HS_CUDA(cudaStreamWaitEvent(ex.st, ex.join_ev, 0));
   }
   ex.end();
+  (void)blocks;
   const int nb = refl_batch<T>(max_m);
   if (variant != HS_LORASP) {
     // Z = Q^T [U_1, G U_1] has 2 k1 <= 4 np columns, in batches of up to 4
@@ -1468,7 +1665,7 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
         ex.end();
       }
       ex.begin(3);
-      B.gram.launch(ex.scr, ex.sg, ex.st);
+      ex.gemm(B.gram, false);   // the Gram feeds the rank decision
       ex.end();
       const double eps = wp[0]->handle().eps;
       const int variant = wp[0]->handle().variant;
@@ -1515,28 +1712,31 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
         if (r->ok()) r->wave_b(hb, nchol, ntrunc, big_ms, B);
       // U of the large path: CholQR2
       ex.begin(6);
-      B.o1.launch(ex.scr, ex.sg, ex.st);
+      ex.gemm(B.o1);
       ex.chol_checked(B.oc1);
-      B.o2.launch(ex.scr, ex.sg, ex.st);
-      B.o3.launch(ex.scr, ex.sg, ex.st);
+      ex.gemm(B.o2);
+      ex.gemm(B.o3);
       ex.chol_checked(B.oc2);
-      B.o4.launch(ex.scr, ex.sg, ex.st);
+      ex.gemm(B.o4);
       ex.end();
-      // phase B and the Schur update
+      // phase B and the Schur update; the host builds the Schur targets and
+      // the new blocks (wave_d) while the GPU runs the phase-B GEMMs
       for (Run<T> *r : wp)
         if (r->ok()) r->wave_c(B);
       ex.begin(7);
-      B.g1.launch(ex.scr, ex.sg, ex.st);
-      B.g2.launch(ex.scr, ex.sg, ex.st);
+      ex.gemm(B.g1);
+      ex.gemm(B.g2);
       ex.chol_checked(B.c1);
-      B.g3.launch(ex.scr, ex.sg, ex.st);
-      B.g4.launch(ex.scr, ex.sg, ex.st);
+      ex.gemm(B.g3);
+      ex.gemm(B.g4);
       ex.chol_checked(B.c2);
-      B.g5.launch(ex.scr, ex.sg, ex.st);
-      B.g6.launch(ex.scr, ex.sg, ex.st);
-      B.g7.launch(ex.scr, ex.sg, ex.st);
-      B.g8.launch(ex.scr, ex.sg, ex.st);
+      ex.gemm(B.g5);
+      ex.gemm(B.g6);
+      ex.gemm(B.g7);
+      ex.gemm(B.g8);
       ex.end();
+      for (Run<T> *r : wp)
+        if (r->ok()) r->wave_d(B);
       ex.begin(8);
       B.schur.launch(ex.scr, ex.sg, ex.st);
       ex.end();
@@ -1562,7 +1762,7 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
     for (auto &r : runs)
       if (r->ok()) r->root_b(cb, g);
     ex.chol_checked(cb);
-    g.launch(ex.scr, ex.sg, ex.st);
+    ex.gemm(g);
     ex.end();
   }
   ex.sync_check();
@@ -1573,6 +1773,9 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       r->finish();
       r->handle().info.host_ms = total;
       r->handle().info.wait_ms = ex.wait_ms;
+      r->handle().info.tc_flops = ex.tc_flops;
+      r->handle().info.tc_ms = ex.tc_ms;
+      r->handle().info.tc_launches = ex.tc_launches;
       ex.phase_times(r->handle().info.phase_ms, 16);
     }
 }
@@ -1586,6 +1789,10 @@ void factorize_t(const std::vector<FactorHandle *> &hs, const std::vector<const 
                  cudaStream_t st, std::vector<int> *status, std::vector<std::string> *msg) {
   Exec ex(st);
   ex.prof = phase_profiling();
+  const int prec = hs[0]->prec;
+  ex.tc = prec == HS_PREC_TF32 ? HS_TC_TF32 : prec == HS_PREC_BF16 ? HS_TC_BF16 : HS_TC_NONE;
+  gemm_tune(ex.tc);   // the GEMM autotuner's table, built once per device and precision
+  ex.wait_cycles = hs[0]->timeout_cycles;
   if (hs.size() > 1) {
     ex.prob_status.assign(hs.size(), HS_OK);
     ex.prob_msg.assign(hs.size(), std::string());

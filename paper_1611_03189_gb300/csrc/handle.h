@@ -100,6 +100,7 @@ struct FactorHandle {
   std::vector<double> eps_level;       // per level above the leaves (empty: eps everywhere)
   int nphi = 1;                        // preserved vectors per node (GC family)
   double eps1 = 0.0;                   // first tolerance of HS_GC_PROJ (Appendix B)
+  int64_t timeout_cycles = 0;          // bound of the kernels' waits (0: default)
   cudaStream_t stream = nullptr;
   int device = 0;
   bool valid = false;                  // holds a usable factorization
@@ -108,6 +109,13 @@ struct FactorHandle {
   int32_t *d_rowptr = nullptr, *d_col = nullptr;
   double *d_val = nullptr;
   int32_t *d_perm = nullptr;
+  // symmetric diagonal scaling (hs_opts.scale): D^-1/2 per cluster-order
+  // unknown, and the scaled values D^-1/2 A D^-1/2 the factorization reads
+  bool scale = false;
+  double *d_dscale = nullptr;
+  double *d_val_f = nullptr;
+  int *d_flag = nullptr;               // set when a diagonal entry is not positive
+  const double *factor_values() const { return scale ? d_val_f : d_val; }
 
   std::unique_ptr<DevArena> pers;      // factor records and live blocks
   std::unique_ptr<DevArena> scratch;   // per-wave scratch of the factorization
@@ -136,6 +144,7 @@ struct FactorHandle {
   std::vector<int64_t> leaf_block_off;
   int64_t leaf_total = 0;
   void *d_phi0 = nullptr;              // leaf preserved vectors (GC): n x nphi row-major, factor precision
+  void *d_phi_raw = nullptr;           // the caller's vectors before the scaling D^1/2 phi (scaling on)
   int64_t nnz = 0;
 
   // solve buffers (grown on demand)

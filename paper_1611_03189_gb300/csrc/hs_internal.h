@@ -303,6 +303,14 @@ void launch_trunc_big_mode(const TruncTask<T> *d_tasks, int ntasks, int *d_k, do
 // and p = tau A v)
 template <typename T>
 void launch_tri_step(const GridTri<T> *d_tasks, int ntasks, int total_blocks, int k, int phase, cudaStream_t st);
+// the whole tridiagonalisation of each node by one thread-block cluster
+// (kernels_cluster.cu): the cluster size (1, 2, 4 or 8 CTAs) that holds a node
+// of size m in shared memory, 0 when none does; all tasks of a launch use
+// cluster size C
+template <typename T>
+int tri_cluster_size(int m);
+template <typename T>
+void launch_tri_cluster(const GridTri<T> *d_tasks, int ntasks, int C, int m_max, cudaStream_t st);
 // inverse iteration over total_blocks CTAs of `spc` slots each
 template <typename T>
 void launch_invit(const InvitTask<T> *d_tasks, int ntasks, int total_blocks, int spc, int m_max, cudaStream_t st);
@@ -325,10 +333,39 @@ void launch_scatter_values(const double *val, const int64_t *dest, int64_t nnz, 
                            cudaStream_t st);
 void launch_gather_values(const double *val, const int32_t *src, int64_t nnz, double *out,
                           cudaStream_t st);
+// symmetric diagonal scaling of a CSR matrix (rows rp, columns ci, values val,
+// n rows): ds = D^-1/2, val_scaled = D^-1/2 A D^-1/2; *flag = 1 if a diagonal
+// entry is missing or not positive
+void launch_diag_scale(const int32_t *rp, const int32_t *ci, const double *val, int64_t n, double *ds,
+                       double *val_scaled, int *flag, cudaStream_t st);
+// out = D^1/2 raw for n x np vectors (row-major, row p scaled by 1 / ds[p])
+template <typename T>
+void launch_phi_scale(const T *raw, const double *ds, int64_t n, int np, T *out, cudaStream_t st);
 
 // tile bookkeeping for the batched GEMM / sum kernels
 constexpr int GEMM_TM = 64;
 constexpr int GEMM_TN = 64;
 constexpr int SUM_TILE = 32;
+
+// Tensor-core GEMM (kernels_tc.cu): operand precision of the tcgen05 path.
+// C = alpha op(A) op(B) + beta C on FP32 data with the operands rounded to
+// TF32 or BF16 and FP32 accumulation; tiles of TC_TILE_M x bn (bn = 64 or
+// 128), tile_start counted in those tiles.  *d_err becomes 1 if a bounded
+// wait of the kernel ran out (the tile is then not written).
+enum { HS_TC_NONE = 0, HS_TC_TF32 = 1, HS_TC_BF16 = 2 };
+constexpr int TC_TILE_M = 128;
+// wait_cycles: bound of each mbarrier wait in SM clock cycles (0: the
+// default, about one second)
+void launch_gemm_tc(int kind, int bn, const GemmTask<float> *d_tasks, const int *d_tile_start, int ntasks,
+                    int total_tiles, int *d_err, cudaStream_t st, long long wait_cycles = 0);
+// GEMM autotuner (kernels_tc.cu): the variant for a task of this shape in
+// precision `kind` -- 0 for the CUDA-core kernel, 64 or 128 for the
+// tensor-core kernel of that tile width.  gemm_tune builds the device's table
+// (synchronising the device) if it does not exist yet; gemm_tune_report
+// copies it out: per shape class, the times (ms) of the three variants and
+// the choice.
+void gemm_tune(int kind);
+int gemm_route(int kind, int M, int N, int K);
+int gemm_tune_report(int kind, float *ms, int *route, int cap);
 
 }  // namespace hs

@@ -722,6 +722,62 @@ void launch_gather_values(const double *val, const int32_t *src, int64_t nnz, do
   HS_CUDA(cudaGetLastError());
 }
 
+// D^-1/2 of each row (the reciprocal square root of its diagonal entry); a
+// row whose diagonal entry is missing or not positive sets *flag
+static __global__ void k_diag_scale(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                    const double *__restrict__ va, int64_t n, double *__restrict__ ds,
+                                    int *flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e)
+      if (ci[e] == i) d += va[e];
+    if (d > 0.0) {
+      ds[i] = 1.0 / sqrt(d);
+    } else {
+      ds[i] = 1.0;
+      atomicExch(flag, 1);
+    }
+  }
+}
+
+// out = D^-1/2 A D^-1/2 entry by entry
+static __global__ void k_scale_values(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci,
+                                      const double *__restrict__ va, int64_t n, const double *__restrict__ ds,
+                                      double *__restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double di = ds[i];
+    for (int e = rp[i]; e < rp[i + 1]; ++e) out[e] = va[e] * di * ds[ci[e]];
+  }
+}
+
+void launch_diag_scale(const int32_t *rp, const int32_t *ci, const double *val, int64_t n, double *ds,
+                       double *val_scaled, int *flag, cudaStream_t st) {
+  if (n == 0) return;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_diag_scale<<<grid, 256, 0, st>>>(rp, ci, val, n, ds, flag);
+  k_scale_values<<<grid, 256, 0, st>>>(rp, ci, val, n, ds, val_scaled);
+  count_launch(2);
+  HS_CUDA(cudaGetLastError());
+}
+
+// preserved vectors of the scaled system: out = D^1/2 raw, n x np row-major
+template <typename T>
+static __global__ void k_phi_scale(const T *__restrict__ raw, const double *__restrict__ ds, int64_t n, int np,
+                                   T *__restrict__ out) {
+  const int64_t tot = n * np;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (T)((double)raw[e] / ds[e / np]);
+}
+
+template <typename T>
+void launch_phi_scale(const T *raw, const double *ds, int64_t n, int np, T *out, cudaStream_t st) {
+  if (n == 0) return;
+  const int grid = (int)std::min<int64_t>((n * np + 255) / 256, 152 * 16);
+  k_phi_scale<T><<<grid, 256, 0, st>>>(raw, ds, n, np, out);
+  count_launch();
+  HS_CUDA(cudaGetLastError());
+}
+
 void launch_status_merge(const StatusMerge *d_tasks, int ntasks, cudaStream_t st) {
   if (ntasks == 0) return;
   k_status_merge<<<(ntasks + 127) / 128, 128, 0, st>>>(d_tasks, ntasks);
@@ -737,6 +793,7 @@ void launch_status_merge(const StatusMerge *d_tasks, int ntasks, cudaStream_t st
   template int chol_smem_cap<T>();                                                            \
   template void launch_trunc<T>(const TruncTask<T> *, int, int *, double, int, int,           \
                                 cudaStream_t);                                                \
+  template void launch_phi_scale<T>(const T *, const double *, int64_t, int, T *, cudaStream_t); \
   template void launch_scatter_values<T>(const double *, const int64_t *, int64_t, T *,       \
                                          cudaStream_t);
 HS_INST(double)

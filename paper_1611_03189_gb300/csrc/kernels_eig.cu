@@ -135,7 +135,40 @@ __device__ void tridiag(T *A, int m, Big<T> &b) {
       b.tau[k] = tau_t;
     }
     __syncthreads();
-    if (tau != 0.0) {
+    if (tau != 0.0 && in_smem) {
+      // trailing block in shared memory: by its symmetry p_i = tau sum_j
+      // A22_ji v_j and the rank-2 update are column walks, thread i on column
+      // i, consecutive threads on consecutive words (no per-row reductions)
+      T *A22 = W + (int64_t)(k + 1 - off) * ld + (k + 1 - off);
+      T pvt = T(0);
+      for (int i = tid; i < n1; i += nt) {
+        const T *col = A22 + i;
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        int j = 0;
+        for (; j + 3 < n1; j += 4) {
+          a0 = fma(col[(int64_t)j * ld], b.v[j], a0);
+          a1 = fma(col[(int64_t)(j + 1) * ld], b.v[j + 1], a1);
+          a2 = fma(col[(int64_t)(j + 2) * ld], b.v[j + 2], a2);
+          a3 = fma(col[(int64_t)(j + 3) * ld], b.v[j + 3], a3);
+        }
+        for (; j < n1; ++j) a0 = fma(col[(int64_t)j * ld], b.v[j], a0);
+        const T pi = tau_t * ((a0 + a1) + (a2 + a3));
+        b.wt[i] = pi;
+        pvt = fma(pi, b.v[i], pvt);
+      }
+      const T K = T(0.5) * tau_t * bsum_t<T>(pvt, b.redt);
+      for (int i = tid; i < n1; i += nt) b.wt[i] = fma(-K, b.v[i], b.wt[i]);  // w
+      __syncthreads();
+      for (int i = tid; i < n1; i += nt) {
+        T *col = A22 + i;
+        const T vi = b.v[i], wi = b.wt[i];
+        for (int j = 0; j < n1; ++j) {
+          T &a = col[(int64_t)j * ld];
+          a = fma(-b.v[j], wi, fma(-b.wt[j], vi, a));
+        }
+      }
+      __syncthreads();
+    } else if (tau != 0.0) {
       T *A22 = W + (int64_t)(k + 1 - off) * ld + (k + 1 - off);
       // p = tau * A22 v, one warp per row, four independent partial sums
       for (int i = warp; i < n1; i += nw) {

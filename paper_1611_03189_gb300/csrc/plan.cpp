@@ -18,7 +18,8 @@ void check(bool ok, const std::string &msg) {
 }  // namespace
 
 void build_plan(int64_t n, const int32_t *rowptr, const int32_t *col, const int32_t *perm,
-                const int32_t *leaf_ptr, int32_t nleaf, Plan &P, int nbr_dist) {
+                const int32_t *leaf_ptr, int32_t nleaf, Plan &P, int nbr_dist, int order_mode) {
+  check(order_mode == HS_ORDER_WAVES || order_mode == HS_ORDER_SEQUENTIAL, "order_mode must be 0 or 1");
   check(n > 0, "n must be positive");
   check(nbr_dist >= 0 && nbr_dist <= 2, "nbr_dist must be 0, 1 or 2");
   check(n < (int64_t)1 << 31, "n must fit in int32");
@@ -181,6 +182,7 @@ void build_plan(int64_t n, const int32_t *rowptr, const int32_t *col, const int3
         if (ok) {
           wave.push_back(s);
           inwave[s] = 1;
+          if (order_mode == HS_ORDER_SEQUENTIAL) break;   // one super node per step, ascending
         }
       }
       for (int s : wave) {

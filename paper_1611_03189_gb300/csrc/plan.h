@@ -19,6 +19,8 @@
 
 #include <stdint.h>
 
+#include "../../include/hs.h"
+
 #include <vector>
 
 namespace hs {
@@ -52,8 +54,11 @@ struct Plan {
 
 // nbr_dist: 0 or 1, neighbours are joined by an edge of the original graph
 // (Sec. 3.1); 2, also the nodes of a level that share a neighbour.
+// order_mode: HS_ORDER_WAVES (canonical waves) or HS_ORDER_SEQUENTIAL (one
+// super node per step, in ascending index).
 // Throws hs::fail(HS_ERR_INVALID, ...) on bad input.
 void build_plan(int64_t n, const int32_t *rowptr, const int32_t *col, const int32_t *perm,
-                const int32_t *leaf_ptr, int32_t nleaf, Plan &out, int nbr_dist = 1);
+                const int32_t *leaf_ptr, int32_t nleaf, Plan &out, int nbr_dist = 1,
+                int order_mode = HS_ORDER_WAVES);
 
 }  // namespace hs

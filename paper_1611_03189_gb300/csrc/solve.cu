@@ -259,35 +259,41 @@ __global__ void __launch_bounds__(AT) k_root(const T *__restrict__ Ainv, int m, 
 }
 
 // user layout (column-major, ld, FP64) <-> workspace layout (unknown-major, cluster order, T)
+// ds (optional): D^-1/2 per cluster-order unknown of a scaled factorization
+// (A_H^-1 = D^-1/2 A'_H^-1 D^-1/2), applied on the way in and on the way out
 template <typename T>
 __global__ void k_gather_in(const double *__restrict__ r, int64_t ld, const int32_t *__restrict__ perm,
-                            int64_t n, int nrhs, int nrhs_p, T *__restrict__ out) {
+                            int64_t n, int nrhs, int nrhs_p, T *__restrict__ out, const double *__restrict__ ds) {
   const int64_t total = n * nrhs_p;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = e / nrhs_p;
     const int j = (int)(e - p * nrhs_p);
-    out[e] = j < nrhs ? (T)r[(int64_t)perm[p] + j * ld] : T(0);
+    const double v = j < nrhs ? r[(int64_t)perm[p] + j * ld] : 0.0;
+    out[e] = (T)(ds ? v * ds[p] : v);
   }
 }
 
 template <typename T>
 __global__ void k_scatter_out(const T *__restrict__ in, const int32_t *__restrict__ perm, int64_t n, int nrhs,
-                              int nrhs_p, double *__restrict__ z, int64_t ld) {
+                              int nrhs_p, double *__restrict__ z, int64_t ld, const double *__restrict__ ds) {
   const int64_t total = n * nrhs;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = e / nrhs;
     const int j = (int)(e - p * nrhs);
-    z[(int64_t)perm[p] + j * ld] = (double)in[p * nrhs_p + j];
+    const double v = (double)in[p * nrhs_p + j];
+    z[(int64_t)perm[p] + j * ld] = ds ? v * ds[p] : v;
   }
 }
 
-// element-wise precision change between the FP64 PCG vectors and the workspace
+// element-wise precision change between the FP64 PCG vectors (n x np,
+// unknown-major) and the workspace, times ds[unknown] when scaling
 template <typename A, typename B>
-__global__ void k_convert(const A *__restrict__ a, B *__restrict__ b, int64_t n) {
+__global__ void k_convert(const A *__restrict__ a, B *__restrict__ b, int64_t n, int np,
+                          const double *__restrict__ ds) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    b[e] = (B)a[e];
+    b[e] = ds ? (B)((double)a[e] * ds[e / np]) : (B)a[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -680,13 +686,17 @@ void apply_solve(FactorHandle &h, const double *r, double *z, int nrhs, int64_t 
   ensure_buffers(h, std::max(nrhs, h.nrhs_cap));
   const int64_t n = h.plan.n;
   if (h.prec == HS_PREC_F64) {
-    k_gather_in<double><<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, (double *)h.d_ws);
+    k_gather_in<double><<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, (double *)h.d_ws,
+                                                            h.d_dscale);
     apply_ws(h, nrhs, st);
-    k_scatter_out<double><<<grid_for(n * nrhs), 256, 0, st>>>((const double *)h.d_ws, h.d_perm, n, nrhs, nrhs, z, ld);
+    k_scatter_out<double><<<grid_for(n * nrhs), 256, 0, st>>>((const double *)h.d_ws, h.d_perm, n, nrhs, nrhs, z, ld,
+                                                              h.d_dscale);
   } else {
-    k_gather_in<float><<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, (float *)h.d_ws);
+    k_gather_in<float><<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, (float *)h.d_ws,
+                                                           h.d_dscale);
     apply_ws(h, nrhs, st);
-    k_scatter_out<float><<<grid_for(n * nrhs), 256, 0, st>>>((const float *)h.d_ws, h.d_perm, n, nrhs, nrhs, z, ld);
+    k_scatter_out<float><<<grid_for(n * nrhs), 256, 0, st>>>((const float *)h.d_ws, h.d_perm, n, nrhs, nrhs, z, ld,
+                                                             h.d_dscale);
   }
   count_launch(2);
   HS_CUDA(cudaGetLastError());
@@ -698,20 +708,26 @@ namespace {
 // in the factor precision
 void apply_pcg(FactorHandle &h, const double *R, double *Z, int np, cudaStream_t st, bool direct) {
   const int64_t tot = h.plan.n * np;
-  if (h.prec == HS_PREC_F64) {
+  if (h.prec == HS_PREC_F64 && !h.scale) {
     HS_CUDA(cudaMemcpyAsync(h.d_ws, R, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+  } else if (h.prec == HS_PREC_F64) {
+    k_convert<double, double><<<grid_for(tot), 256, 0, st>>>(R, (double *)h.d_ws, tot, np, h.d_dscale);
+    count_launch();
   } else {
-    k_convert<double, float><<<grid_for(tot), 256, 0, st>>>(R, (float *)h.d_ws, tot);
+    k_convert<double, float><<<grid_for(tot), 256, 0, st>>>(R, (float *)h.d_ws, tot, np, h.d_dscale);
     count_launch();
   }
   if (direct)
     apply_ws_direct(h, np, st);
   else
     apply_ws(h, np, st);
-  if (h.prec == HS_PREC_F64) {
+  if (h.prec == HS_PREC_F64 && !h.scale) {
     HS_CUDA(cudaMemcpyAsync(Z, h.d_ws, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
+  } else if (h.prec == HS_PREC_F64) {
+    k_convert<double, double><<<grid_for(tot), 256, 0, st>>>((const double *)h.d_ws, Z, tot, np, h.d_dscale);
+    count_launch();
   } else {
-    k_convert<float, double><<<grid_for(tot), 256, 0, st>>>((const float *)h.d_ws, Z, tot);
+    k_convert<float, double><<<grid_for(tot), 256, 0, st>>>((const float *)h.d_ws, Z, tot, np, h.d_dscale);
     count_launch();
   }
 }
@@ -730,7 +746,7 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
   PcgFlags fl{h.d_iflags, h.d_iflags + 32, h.d_iflags + 64, h.d_iflags + 65};
   const int g = rgrid_for(n);
   const double rtol2 = rtol * rtol;
-  k_gather_in<double><<<grid_for(tot), 256, 0, st>>>(b, ld, h.d_perm, n, nrhs, np, B);
+  k_gather_in<double><<<grid_for(tot), 256, 0, st>>>(b, ld, h.d_perm, n, nrhs, np, B, nullptr);
   count_launch();
   HS_CUDA(cudaMemcpyAsync(R, B, sizeof(double) * tot, cudaMemcpyDeviceToDevice, st));
   HS_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * tot, st));
@@ -789,7 +805,7 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
     k_dot<NP><<<g, PT, 0, st>>>(Q, Q, n, h.d_part, sc, fl, DOT_PLAIN, rr_d);
   });
   count_launch();
-  k_scatter_out<double><<<grid_for(n * nrhs), 256, 0, st>>>(X, h.d_perm, n, nrhs, np, x, ld);
+  k_scatter_out<double><<<grid_for(n * nrhs), 256, 0, st>>>(X, h.d_perm, n, nrhs, np, x, ld, nullptr);
   count_launch();
   HS_CUDA(cudaGetLastError());
   std::vector<double> hs(6 * 32);
@@ -924,7 +940,7 @@ int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int ma
          *R = B + n;
   double *part = R + n, *hd = part + (size_t)(mr + 1) * nb, *yd = hd + 2 * (size_t)(mr + 1) + 2;
   const int g = grid_for(n);
-  k_gather_in<double><<<g, 256, 0, st>>>(b, n, h.d_perm, n, 1, 1, B);
+  k_gather_in<double><<<g, 256, 0, st>>>(b, n, h.d_perm, n, 1, 1, B, nullptr);
   count_launch();
   HS_CUDA(cudaMemsetAsync(X, 0, sizeof(double) * n, st));
   std::vector<double> hh(2 * (size_t)(mr + 1) + 2);
@@ -1024,7 +1040,7 @@ int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int ma
   count_launch();
   gm_dots(R, n, 1, R, part, hd, st);
   read(1);
-  k_scatter_out<double><<<g, 256, 0, st>>>(X, h.d_perm, n, 1, 1, x, n);
+  k_scatter_out<double><<<g, 256, 0, st>>>(X, h.d_perm, n, 1, 1, x, n, nullptr);
   count_launch();
   HS_CUDA(cudaGetLastError());
   HS_CUDA(cudaStreamSynchronize(st));
@@ -1091,10 +1107,10 @@ void apply_static_t(FactorHandle &h, const double *r, double *z, int nrhs, int64
                               std::to_string(kStaticApplyBytes) + " bytes");
   unsigned char *base = (unsigned char *)static_ws_for_current_device(st);
   T *ws = (T *)base, *tb = (T *)(base + ws_b), *tb2 = (T *)(base + ws_b + t_b);
-  k_gather_in<T><<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, ws);
+  k_gather_in<T><<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, ws, h.d_dscale);
   count_launch();
   apply_chunks<T>(h, ws, tb, tb2, nrhs, st);
-  k_scatter_out<T><<<grid_for(n * nrhs), 256, 0, st>>>(ws, h.d_perm, n, nrhs, nrhs, z, ld);
+  k_scatter_out<T><<<grid_for(n * nrhs), 256, 0, st>>>(ws, h.d_perm, n, nrhs, nrhs, z, ld, h.d_dscale);
   count_launch();
   HS_CUDA(cudaGetLastError());
 }
@@ -1115,6 +1131,10 @@ FactorHandle::~FactorHandle() {
   cudaFree(d_src);
   cudaFree(d_leaf_dest);
   cudaFree(d_phi0);
+  cudaFree(d_phi_raw);
+  cudaFree(d_dscale);
+  cudaFree(d_val_f);
+  cudaFree(d_flag);
   cudaFree(d_rowptr);
   cudaFree(d_col);
   cudaFree(d_val);
