@@ -46,7 +46,7 @@ WORKLOADS = {
 CPU_SAMPLE = {"poisson3d_64": "poisson3d_24", "poisson3d_32": "poisson3d_24"}
 METRIC = "solves/s to rel-res 1e-10 (factor + PCG solve; mixed vs FP64 factor)"
 # factor precisions by name (values of HS_PREC_*)
-PRECS = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3}
+PRECS = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "tf32x3": 4}
 
 
 def make_problem(name: str, seed: int):
@@ -176,6 +176,8 @@ def tensor_peak_for(prec: str, peaks: dict):
         bf16, src = 1700.0, "fallback sustained bf16"
     if prec == "tf32":
         return bf16 * 1.1 / 2.25, src + " x nominal tf32/bf16 ratio 1.1/2.25"
+    if prec == "tf32x3":
+        return bf16 * 1.1 / 2.25 / 3, src + " x nominal tf32/bf16 ratio 1.1/2.25 / 3 (three MMAs per product)"
     if prec in ("f32", "f64"):
         return bf16, src + " (the contractions' peak if they ran as bf16 on tensor cores)"
     return bf16, src
@@ -495,8 +497,8 @@ def gemm_arm(args) -> None:
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     n = args.gemm_size
     prec = PRECS[args.prec]
-    if prec not in (_lib.HS_PREC_TF32, _lib.HS_PREC_BF16):
-        raise SystemExit("--gemm needs --prec tf32 or bf16")
+    if prec not in (_lib.HS_PREC_TF32, _lib.HS_PREC_BF16, _lib.HS_PREC_TF32X3):
+        raise SystemExit("--gemm needs --prec tf32, tf32x3 or bf16")
     g = torch.Generator(device=dev).manual_seed(0)
     A = torch.randn((n, n), generator=g, device=dev, dtype=torch.float32)
     B = torch.randn((n, n), generator=g, device=dev, dtype=torch.float32)
@@ -522,7 +524,8 @@ def gemm_arm(args) -> None:
     except OSError:
         pass
     bf16 = peaks.get("bf16_tflops", 1900.0)
-    peak = bf16 * (1.1 / 2.25 if args.prec == "tf32" else 1.0)
+    # 3xTF32 issues three TF32 MMAs per product: its useful rate peaks at a third of TF32's
+    peak = bf16 * {"tf32": 1.1 / 2.25, "tf32x3": 1.1 / 2.25 / 3}.get(args.prec, 1.0)
     flops = 2.0 * n ** 3
     best = min(res, key=res.get)
     ach = flops / (res[best] / 1000.0) / 1e12
@@ -531,8 +534,9 @@ def gemm_arm(args) -> None:
                       "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                                    "frac": ach / peak,
                                    "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)" +
-                                                  (" x nominal tf32/bf16 ratio 1.1/2.25" if args.prec == "tf32"
-                                                   else "")}}), flush=True)
+                                                  {"tf32": " x nominal tf32/bf16 ratio 1.1/2.25",
+                                                   "tf32x3": " x nominal tf32/bf16 ratio 1.1/2.25 / 3 MMAs"}.get(
+                                                      args.prec, "")}}), flush=True)
 
 
 def serve_arm(args) -> None:
@@ -599,7 +603,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="diffusion2d_512", choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", default="f32", choices=["f32", "tf32", "bf16", "f64"])
+    ap.add_argument("--prec", default="f32", choices=["f32", "tf32", "tf32x3", "bf16", "f64"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--scale", action="store_true", help="factor the diagonally scaled D^-1/2 A D^-1/2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -903,7 +907,7 @@ def main():
             "roofline_other": others,
             "factor_algorithmic": factor_alg,
             "gemm_autotune": ([{k: r[k] for k in ("max_mn", "k", "route")} for r in _lib.gemm_tune_report(prec)]
-                              if args.prec in ("tf32", "bf16") else None),
+                              if args.prec in ("tf32", "tf32x3", "bf16") else None),
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": 8 * (pb0.nnz + n * args.nrhs),
                     "d2h_bytes_per_step": 8 * n * args.nrhs},

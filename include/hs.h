@@ -72,7 +72,11 @@ enum {
   HS_PREC_TF32 = 2,    /* contractions on tensor cores with TF32 operands and
                           FP32 accumulation; the truncation (Gram A_sw A_sw^T,
                           its eigen-solve and the rank decision) in FP64        */
-  HS_PREC_BF16 = 3     /* as HS_PREC_TF32 with BF16 operands                    */
+  HS_PREC_BF16 = 3,    /* as HS_PREC_TF32 with BF16 operands                    */
+  HS_PREC_TF32X3 = 4   /* contractions on tensor cores with each FP32 operand
+                          split into TF32 high and low parts, a b taken as
+                          a_hi b_hi + a_hi b_lo + a_lo b_hi (near-FP32
+                          accuracy), FP32 accumulation; truncation as FP32     */
 };
 
 /* Sparse SPD matrix A in CSR form (Sec. 2: A symmetric positive definite).
@@ -117,7 +121,8 @@ typedef struct {
  *   in the ORIGINAL ordering; used by HS_GC_USER (vectors preserved exactly,
  *   Sec. 6) and HS_GC_PROJ (the scaled vectors X of Appendix B, e.g.
  *   e_i / lambda_i, kept approximately).  Required by both.
- * factor_prec: HS_PREC_F64, HS_PREC_F32, HS_PREC_TF32 or HS_PREC_BF16.
+ * factor_prec: HS_PREC_F64, HS_PREC_F32, HS_PREC_TF32, HS_PREC_BF16 or
+ *   HS_PREC_TF32X3.
  * eps_level: NULL, or a HOST array of tolerances per level for the adaptive
  *   choice of Sec. 7 (Table 3).  Entry j replaces eps for the super nodes j
  *   levels above the leaves (j = 0: the pairs of leaves); a problem with 2^L
@@ -150,7 +155,14 @@ typedef struct {
  *   (see the planner below), each wave one batch of independent
  *   eliminations.  HS_ORDER_SEQUENTIAL (1): one super node at a time in
  *   ascending index, the paper's sequential reading; the same method, one
- *   launch group per super node (slow; for comparison). */
+ *   launch group per super node (slow; for comparison).
+ * max_rank_ratio: 0 (no cap), or in (0, 1]: every truncation with eps > 0
+ *   keeps at most max(floor(max_rank_ratio * m), 1) columns -- the leading
+ *   singular vectors (GC: the basis U_1 whole, then the leading ones of the
+ *   projected block) -- bounding the red nodes' sizes and so the factor's
+ *   memory.  Not in the paper; a cap that binds trades preconditioner
+ *   quality for memory, and a harsh one can cost GC-constant its
+ *   definiteness (HS_ERR_NOT_SPD). */
 typedef struct {
   double eps;
   int32_t variant;
@@ -163,6 +175,7 @@ typedef struct {
   int32_t scale;
   int64_t timeout_cycles;
   int32_t order_mode;
+  double max_rank_ratio;
 } hs_opts;
 
 /* Sizes and counters of a factorization (all host values). */
@@ -343,7 +356,8 @@ int hs_profile_phases(int32_t on);
  * that the mixed factorizations use for their contractions (tcgen05, operands
  * rounded to TF32 or BF16, FP32 accumulation), exported so that the kernel can
  * be checked and measured on its own.  The paper has no counterpart.
- *   prec: HS_PREC_TF32 or HS_PREC_BF16.  A, B, C: DEVICE, FP32, row-major;
+ *   prec: HS_PREC_TF32, HS_PREC_BF16 or HS_PREC_TF32X3.  A, B, C: DEVICE,
+ *   FP32, row-major;
  *   op(A) is M x K (A[i lda + k], or A[k lda + i] when ta), op(B) is K x N
  *   (B[k ldb + j], or B[j ldb + k] when tb), C is M x N with leading
  *   dimension ldc.  C must not overlap A or B.  M, N >= 1, K >= 0.
@@ -355,7 +369,8 @@ int hs_gemm_tc(int32_t prec, int32_t M, int32_t N, int32_t K, float alpha, const
                int32_t bn, void *stream);
 
 /* hs_gemm_tune_report: the table of the GEMM autotuner for operand
- * precision `prec` (HS_PREC_TF32 or HS_PREC_BF16) on the current device,
+ * precision `prec` (HS_PREC_TF32, HS_PREC_BF16 or HS_PREC_TF32X3) on the
+ * current device,
  * building it first if needed (that synchronises the device).  For each class
  * of task shapes c (max(M, N) bucket 0..4 = up to 32, 64, 128, 256, more; K
  * bucket 0..3 = up to 32, 128, 512, more; c = 4 * mn + k): ms[3c .. 3c+2] =
@@ -365,6 +380,15 @@ int hs_gemm_tc(int32_t prec, int32_t M, int32_t N, int32_t K, float alpha, const
  * Returns the number of classes (20), or a negative hs_status on error.  The
  * paper has no counterpart. */
 int hs_gemm_tune_report(int32_t prec, float *ms, int32_t *route, int32_t cap);
+
+/* hs_test_wait_probe: on != 0 makes every later tensor-core GEMM launch (all
+ * handles, all threads) first wait, with the factorization's bound
+ * (hs_opts.timeout_cycles), on a barrier that nothing arrives at, so that the
+ * wait runs out and the call fails with HS_ERR_TIMEOUT before any tensor-core
+ * work is issued; 0 turns it off (the default).  A test of the time-out path,
+ * which no GPU fault can exercise on a shared machine; the paper has no
+ * counterpart.  Returns HS_OK. */
+int hs_test_wait_probe(int32_t on);
 
 /* hs_last_error: message of the last failing call on this thread. */
 const char *hs_last_error(void);

@@ -163,8 +163,19 @@ def compress(B: np.ndarray, eps: float, variant: int, phi_s=None, phi_w=None, ep
     return _compress(B, eps, variant, phi_s, phi_w, eps1)[0]
 
 
-def _compress(B: np.ndarray, eps: float, variant: int, phi_s=None, phi_w=None, eps1: float = 0.0):
-    """compress(), and the margin of its rank decisions (SuperRecord.margin)."""
+def _gap_margin(sv: np.ndarray, j: int) -> float:
+    """Relative gap (sv[j-1] - sv[j]) / sv[j-1] where a rank cap of j cuts the
+    descending list sv (inf when nothing is cut)."""
+    if j <= 0 or j >= sv.size or sv[j - 1] <= 0.0:
+        return math.inf
+    return float((sv[j - 1] - sv[j]) / sv[j - 1])
+
+
+def _compress(B: np.ndarray, eps: float, variant: int, phi_s=None, phi_w=None, eps1: float = 0.0, cap=None):
+    """compress(), and the margin of its rank decisions (SuperRecord.margin).
+    cap: the largest rank kept (max_rank_ratio; None: no cap): the leading
+    singular vectors, the GC basis U_1 always whole; a cap that binds adds the
+    relative gap at the cut to the margin."""
     m = B.shape[0]
     if m == 0:
         return np.zeros((0, 0)), math.inf
@@ -174,7 +185,11 @@ def _compress(B: np.ndarray, eps: float, variant: int, phi_s=None, phi_w=None, e
         Ub, sb, _ = np.linalg.svd(B, full_matrices=False)
         normB = sb[0] if sb.size else 0.0
         k = int(np.count_nonzero(sb > eps * normB))
-        return Ub[:, :k].copy(), _margin(sb, eps * normB)
+        margin = _margin(sb, eps * normB)
+        if cap is not None and k > cap:
+            k = cap
+            margin = min(margin, _gap_margin(sb, cap))
+        return Ub[:, :k].copy(), margin
     margin = math.inf
     if variant == GC_PROJ:
         C1 = np.hstack([_columns(phi_s), _columns(B @ phi_w)])
@@ -190,7 +205,13 @@ def _compress(B: np.ndarray, eps: float, variant: int, phi_s=None, phi_w=None, e
     C = B - U1 @ (U1.T @ B)
     Uc, sc, _ = np.linalg.svd(C, full_matrices=False)
     k2 = int(np.count_nonzero(sc > eps * normB))
-    return np.hstack([U1, Uc[:, :k2]]), min(margin, _margin(sc, eps * normB))
+    margin = min(margin, _margin(sc, eps * normB))
+    if cap is not None:
+        lim = max(cap - U1.shape[1], 0)
+        if k2 > lim:
+            k2 = lim
+            margin = min(margin, _gap_margin(sc, lim))
+    return np.hstack([U1, Uc[:, :k2]]), margin
 
 
 # ---------------------------------------------------------------------------
@@ -317,7 +338,7 @@ def eps_schedule_lorasp(eps: float, L: int, h: float) -> list:
 
 def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None,
            order="waves", keep_U=False, eps_level=None, eps1=0.0, nbr_dist=1, levels=None,
-           scale=False) -> Factor:
+           scale=False, max_rank_ratio=0.0) -> Factor:
     """Hierarchical factorization.
 
     n, rowptr, col, val: CSR of the SPD matrix A in original ordering.
@@ -339,6 +360,10 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
         mapped to it (D^1/2 phi), so that they stay preserved for A.
     order: "waves" (R4), "waves-reversed" (same waves, each eliminated in
         descending order) or "sequential" (ascending super index, one at a time).
+    max_rank_ratio: 0, or a cap on the rank of every truncation (eps > 0):
+        k <= max(floor(ratio m), 1), keeping the leading singular vectors (GC:
+        U_1 whole, then the leading ones of the projected block).  Not in the
+        paper: a bound on the size of the red nodes a caller may impose.
     """
     rowptr = np.asarray(rowptr, dtype=np.int64)
     perm = np.asarray(perm, dtype=np.int64)
@@ -456,7 +481,7 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=No
             # eliminates each wave in descending order to test exactly that
             for s in (reversed(wave) if order == "waves-reversed" else wave):
                 rec = _eliminate(s, nsup, blocks, nbr_of, size, vphi, adjacent, eps_l,
-                                 variant, use_phi, widx, keep_U, eps1)
+                                 variant, use_phi, widx, keep_U, eps1, max_rank_ratio)
                 records.append(rec)
                 if rec.wsep:
                     new_red_size[s] = rec.k
@@ -506,10 +531,19 @@ def _set_block(blocks, nbr_of, x, y, blk):
         nbr_of.setdefault(y, set()).add(x)
 
 
+def rank_cap(m: int, max_rank_ratio: float):
+    """Largest rank a super node of size m keeps under max_rank_ratio (None:
+    no cap): floor(ratio m), at least 1."""
+    if not max_rank_ratio or max_rank_ratio <= 0.0:
+        return None
+    return max(1, int(math.floor(max_rank_ratio * m)))
+
+
 def _eliminate(s, nsup, blocks, nbr_of, size, vphi, adjacent, eps, variant, use_phi, widx,
-               keep_U, eps1=0.0):
+               keep_U, eps1=0.0, max_rank_ratio=0.0):
     """Compress, extend and eliminate super node s (Sec. 3.2)."""
     m = size[s]
+    cap = rank_cap(m, max_rank_ratio) if eps > 0.0 else None
     others = sorted(nbr_of.get(s, ()))
     N = [x for x in others if adjacent(s, x)]
     W = [x for x in others if not adjacent(s, x)]
@@ -520,9 +554,9 @@ def _eliminate(s, nsup, blocks, nbr_of, size, vphi, adjacent, eps, variant, use_
         B = np.hstack([blocks[(s, w)] for w in W]) if m else np.zeros((0, sum(size[w] for w in W)))
         if use_phi:
             phi_w = np.concatenate([vphi[w] for w in W])
-            U, margin = _compress(B, eps, variant, vphi[s], phi_w, eps1)
+            U, margin = _compress(B, eps, variant, vphi[s], phi_w, eps1, cap)
         else:
-            U, margin = _compress(B, eps, variant)
+            U, margin = _compress(B, eps, variant, cap=cap)
     else:
         U, margin = np.zeros((m, 0)), math.inf
     k = U.shape[1]

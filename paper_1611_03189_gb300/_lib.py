@@ -33,6 +33,7 @@ HS_PREC_F64 = 0
 HS_PREC_F32 = 1
 HS_PREC_TF32 = 2
 HS_PREC_BF16 = 3
+HS_PREC_TF32X3 = 4
 
 HS_ORDER_WAVES = 0
 HS_ORDER_SEQUENTIAL = 1
@@ -47,7 +48,7 @@ EXPORTS = [
     "hs_factor_create", "hs_factor_refactor", "hs_factor_create_batch", "hs_factor_refactor_batch",
     "hs_launch_count", "hs_profile_phases", "hs_abi_sizes", "hs_apply", "hs_apply_static", "hs_pcg", "hs_gmres", "hs_factor_info", "hs_factor_ranks",
     "hs_factor_destroy", "hs_last_error", "hs_plan_create", "hs_plan_level_waves",
-    "hs_plan_super_lists", "hs_plan_destroy", "hs_gemm_tc", "hs_gemm_tune_report",
+    "hs_plan_super_lists", "hs_plan_destroy", "hs_gemm_tc", "hs_gemm_tune_report", "hs_test_wait_probe",
 ]
 
 
@@ -70,7 +71,7 @@ class HsOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("variant", C.c_int32), ("factor_prec", C.c_int32),
                 ("phi", C.c_void_p), ("eps_level", C.c_void_p), ("n_eps_level", C.c_int32),
                 ("n_phi", C.c_int32), ("eps1", C.c_double), ("scale", C.c_int32),
-                ("timeout_cycles", C.c_int64), ("order_mode", C.c_int32)]
+                ("timeout_cycles", C.c_int64), ("order_mode", C.c_int32), ("max_rank_ratio", C.c_double)]
 
 
 def _phi_block(phi):
@@ -137,6 +138,7 @@ def lib():
         flt = C.c_float
         L.hs_gemm_tc.argtypes = [i32, i32, i32, i32, flt, vp, i64, i32, vp, i64, i32, flt, vp, i64, i32, vp]
         L.hs_gemm_tune_report.argtypes = [i32, vp, vp, i32]
+        L.hs_test_wait_probe.argtypes = [i32]
         for name in EXPORTS:
             if name not in ("hs_last_error", "hs_launch_count"):
                 getattr(L, name).restype = C.c_int
@@ -227,7 +229,7 @@ class Factor:
 
     def __init__(self, rowptr, col, val, perm, leaf_ptr, eps, variant=HS_GC_CONSTANT,
                  prec=HS_PREC_F64, phi=None, stream=None, eps_level=None, eps1=0.0, nbr_dist=1, scale=False,
-                 timeout_cycles=0, order_mode=HS_ORDER_WAVES):
+                 timeout_cycles=0, order_mode=HS_ORDER_WAVES, max_rank_ratio=0.0):
         import torch
 
         assert rowptr.is_cuda and col.is_cuda and val.is_cuda
@@ -241,7 +243,8 @@ class Factor:
         self._epsl = None if eps_level is None else np.ascontiguousarray(eps_level, dtype=np.float64)
         o = HsOpts(float(eps), int(variant), int(prec), None if self._phi is None else _ptr(self._phi),
                    None if self._epsl is None else _ptr(self._epsl), 0 if self._epsl is None else len(self._epsl),
-                   nphi, float(eps1), int(bool(scale)), int(timeout_cycles), int(order_mode))
+                   nphi, float(eps1), int(bool(scale)), int(timeout_cycles), int(order_mode),
+                   float(max_rank_ratio))
         h = C.c_void_p()
         self._h = None
         check(lib().hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), _stream_ptr(stream), C.byref(h)))
@@ -353,7 +356,7 @@ def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=N
     epsl = None if eps_level is None else np.ascontiguousarray(eps_level, dtype=np.float64)
     keep.append(epsl)
     o = HsOpts(float(eps), int(variant), int(prec), None, None if epsl is None else _ptr(epsl),
-               0 if epsl is None else len(epsl), nphi, float(eps1), int(bool(scale)), 0, HS_ORDER_WAVES)
+               0 if epsl is None else len(epsl), nphi, float(eps1), int(bool(scale)), 0, HS_ORDER_WAVES, 0.0)
     out = (C.c_void_p * k)()
     status = np.zeros(k, dtype=np.int32)
     code = lib().hs_factor_create_batch(k, A, cl, C.byref(o), phi_arr, _stream_ptr(stream), out, _ptr(status))

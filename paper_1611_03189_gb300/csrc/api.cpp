@@ -115,6 +115,7 @@ void numeric_post(FactorHandle &h, float ms, cudaStream_t st) {
   h.d_nbrs = upload_vec(h.nbrs, st);
   h.d_targets = upload_vec(h.targets, st);
   h.d_contribs = upload_vec(h.contribs, st);
+  apply_prepare(h, st);
   hs_info &in = h.info;
   in.n = h.plan.n;
   in.levels = h.plan.L;
@@ -191,6 +192,7 @@ void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, con
   h.nphi = (o->variant == HS_GC_USER || o->variant == HS_GC_PROJ) ? std::max(o->n_phi, 1) : 1;
   h.eps1 = o->variant == HS_GC_PROJ ? o->eps1 : 0.0;
   h.timeout_cycles = o->timeout_cycles;
+  h.max_rank_ratio = o->max_rank_ratio;
   h.eps_level.clear();
   // pattern to the host for the planner
   std::vector<int32_t> rp(A->n + 1), ci(A->nnz);
@@ -234,10 +236,12 @@ void check_opts(const hs_opts *o) {
     fail(HS_ERR_INVALID, "eps1 must be finite and >= 0");
   if (o->scale != 0 && o->scale != 1) fail(HS_ERR_INVALID, "scale must be 0 or 1");
   if (o->timeout_cycles < 0) fail(HS_ERR_INVALID, "timeout_cycles must be >= 0");
+  if (!(o->max_rank_ratio >= 0.0 && o->max_rank_ratio <= 1.0))
+    fail(HS_ERR_INVALID, "max_rank_ratio must be in [0, 1]");
   if (o->order_mode != HS_ORDER_WAVES && o->order_mode != HS_ORDER_SEQUENTIAL)
     fail(HS_ERR_INVALID, "order_mode must be HS_ORDER_WAVES or HS_ORDER_SEQUENTIAL");
   if (o->factor_prec != HS_PREC_F64 && o->factor_prec != HS_PREC_F32 && o->factor_prec != HS_PREC_TF32 &&
-      o->factor_prec != HS_PREC_BF16)
+      o->factor_prec != HS_PREC_BF16 && o->factor_prec != HS_PREC_TF32X3)
     fail(HS_ERR_INVALID, "unknown factor_prec");
   if (o->eps_level) {
     if (o->n_eps_level < 0) fail(HS_ERR_INVALID, "n_eps_level < 0");
@@ -373,7 +377,8 @@ int hs_gemm_tc(int32_t prec, int32_t M, int32_t N, int32_t K, float alpha, const
                int32_t ta, const float *B, int64_t ldb, int32_t tb, float beta, float *C, int64_t ldc,
                int32_t bn, void *stream) {
   return hs::guarded([&]() -> int {
-    if (prec != HS_PREC_TF32 && prec != HS_PREC_BF16) fail(HS_ERR_INVALID, "prec must be HS_PREC_TF32 or HS_PREC_BF16");
+    if (prec != HS_PREC_TF32 && prec != HS_PREC_BF16 && prec != HS_PREC_TF32X3)
+      fail(HS_ERR_INVALID, "prec must be HS_PREC_TF32, HS_PREC_BF16 or HS_PREC_TF32X3");
     if (M < 1 || N < 1 || K < 0) fail(HS_ERR_INVALID, "need M, N >= 1 and K >= 0");
     if (!A || !B || !C) fail(HS_ERR_INVALID, "null argument");
     if (bn != 0 && bn != 64 && bn != 128) fail(HS_ERR_INVALID, "bn must be 0, 64 or 128");
@@ -409,7 +414,7 @@ int hs_gemm_tc(int32_t prec, int32_t M, int32_t N, int32_t K, float alpha, const
     hs::GemmTask<float> *d_t = (hs::GemmTask<float> *)(d + 256);
     HS_CUDA(cudaMemsetAsync(d, 0, 256, st));
     HS_CUDA(cudaMemcpyAsync(d_t, &t, sizeof(t), cudaMemcpyHostToDevice, st));
-    hs::launch_gemm_tc(prec == HS_PREC_TF32 ? hs::HS_TC_TF32 : hs::HS_TC_BF16, w, d_t, d_ts, 1, tiles, d_err, st);
+    hs::launch_gemm_tc(hs::tc_kind_of(prec), w, d_t, d_ts, 1, tiles, d_err, st);
     int herr = 0;
     HS_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     HS_CUDA(cudaStreamSynchronize(st));
@@ -421,11 +426,12 @@ int hs_gemm_tc(int32_t prec, int32_t M, int32_t N, int32_t K, float alpha, const
 int hs_gemm_tune_report(int32_t prec, float *ms, int32_t *route, int32_t cap) {
   int n = 0;
   const int rc = hs::guarded([&]() -> int {
-    if (prec != HS_PREC_TF32 && prec != HS_PREC_BF16) fail(HS_ERR_INVALID, "prec must be HS_PREC_TF32 or HS_PREC_BF16");
+    if (prec != HS_PREC_TF32 && prec != HS_PREC_BF16 && prec != HS_PREC_TF32X3)
+      fail(HS_ERR_INVALID, "prec must be HS_PREC_TF32, HS_PREC_BF16 or HS_PREC_TF32X3");
     if (cap < 0 || (cap > 0 && (!ms || !route))) fail(HS_ERR_INVALID, "null argument");
     hs::require_device();
     std::vector<int> r(std::max(cap, 0));
-    n = hs::gemm_tune_report(prec == HS_PREC_TF32 ? hs::HS_TC_TF32 : hs::HS_TC_BF16, ms, r.data(), cap);
+    n = hs::gemm_tune_report(hs::tc_kind_of(prec), ms, r.data(), cap);
     for (int i = 0; i < cap && i < n; ++i) route[i] = r[i];
     return HS_OK;
   });
@@ -439,6 +445,11 @@ int hs_abi_sizes(int64_t *sizes, int32_t cap) {
                         (int64_t)sizeof(hs_info)};
   for (int32_t i = 0; i < cap && i < 4 && sizes; ++i) sizes[i] = v[i];
   return 4;
+}
+
+int hs_test_wait_probe(int32_t on) {
+  hs::set_wait_probe(on != 0);
+  return HS_OK;
 }
 
 int hs_profile_phases(int32_t on) {

@@ -22,6 +22,7 @@
 // tridiagonalisation over the GPU (trunc_grid); Cholesky factors above the
 // shared-memory limit are blocked (Exec::chol_inv_blocked).
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <chrono>
 #include <cstdlib>
@@ -713,7 +714,9 @@ class Run {
   void level_begin(int li, SumBatch<T> &sb);     // merge into the level's super nodes
   void wave_a(int li, int widx, WaveBatches<T> &B);
   void wave_b(const int *hb, size_t nchol, size_t ntrunc, double big_ms, WaveBatches<T> &B);
-  void wave_c(WaveBatches<T> &B);               // the elimination's GEMM tasks
+  // the elimination's GEMM tasks of super nodes [c_next_, c_next_ + count)
+  // of the wave; returns whether nodes remain
+  bool wave_c(WaveBatches<T> &B, size_t count);
   void wave_d(WaveBatches<T> &B);               // Schur targets, red-node blocks, apply records
   void level_end(int li);
   void root_a(SumBatch<T> &sb);                  // merge of the last red nodes
@@ -772,6 +775,7 @@ class Run {
   std::vector<Sup> cur_;
   std::vector<int> trunc_sup_, big_sup_;      // super nodes of this run's truncation tasks
   size_t chol_first_ = 0, chol_count_ = 0, trunc_first_ = 0, big_first_ = 0;
+  size_t c_next_ = 0;   // next super node of the wave whose phase-B tasks are built
   double flops_ = 0.0;
   // device time (of the launches taken part in) and nominal eigen-solve flops
   // of the large-node truncations
@@ -962,6 +966,7 @@ void Run<T>::wave_a(int li, int widx, WaveBatches<T> &B) {
   DevArena &per = *h_.pers;
   const std::vector<int> &wl = lv.waves[widx];
   cur_.assign(wl.size(), Sup());
+  c_next_ = 0;
   trunc_sup_.clear();
   big_sup_.clear();
   chol_first_ = B.chol.tasks.size();
@@ -1025,6 +1030,10 @@ void Run<T>::wave_a(int li, int widx, WaveBatches<T> &B) {
       tt.work = nullptr;
       tt.eps = level_eps(lv.level);
       tt.m = m;
+      // the rank cap (hs_opts.max_rank_ratio): floor(ratio m), at least 1
+      tt.cap = (h_.max_rank_ratio > 0.0 && tt.eps > 0.0)
+                   ? std::max(1, (int)std::floor(h_.max_rank_ratio * (double)m))
+                   : m;
       if (m <= eig_small_max<T>()) {
         B.trunc.push_back(tt);
         trunc_sup_.push_back((int)q);
@@ -1090,14 +1099,17 @@ void Run<T>::wave_b(const int *hb, size_t nchol, size_t ntrunc, double big_ms, W
 }
 
 template <typename T>
-void Run<T>::wave_c(WaveBatches<T> &B) {
+bool Run<T>::wave_c(WaveBatches<T> &B, size_t count) {
   DevArena &scr = *h_.scratch;
   DevArena &per = *h_.pers;
   // phase B
   std::vector<Sup> &S = cur_;
   const double f0 = B.c1.flops + B.c2.flops + B.g1.flops + B.g2.flops + B.g3.flops + B.g4.flops + B.g5.flops +
                     B.g6.flops + B.g7.flops + B.g8.flops;
-  for (auto &x : S) {
+  const size_t q0 = c_next_, q1 = std::min(S.size(), c_next_ + count);
+  c_next_ = q1;
+  for (size_t q = q0; q < q1; ++q) {
+    Sup &x = S[q];
     const int m = x.m, k = x.k, dN = x.dN;
     if (k > m || k < 0) fail(HS_ERR_INVALID, "internal: rank out of range");
     if (k > 0) {
@@ -1156,12 +1168,13 @@ void Run<T>::wave_c(WaveBatches<T> &B) {
   // Y 2 m^2 k, S 2 m k^2 + k^3/3, G_n 2 m^2 d_N, H_n 2 m k d_N, the Schur
   // update 2 (m + k) d_N^2 over all neighbour pairs, and M_ss, P_ss 2 m^2 k
   // (w = sum of the well-separated widths, d_N = sum of the neighbour sizes)
-  for (const Sup &x : S) {
+  for (size_t q = q0; q < q1; ++q) {
+    const Sup &x = S[q];
     const double m = x.m, k = x.k, dN = x.dN, w = x.red ? x.dW : 0;
     alg_flops_ += 2 * m * m * w + 2 * m * k * w + m * m * m / 3 + 2 * m * m * k + 2 * m * k * k + k * k * k / 3 +
                   2 * m * m * dN + 2 * m * k * dN + 2 * (m + k) * dN * dN + 2 * m * m * k;
   }
-
+  return c_next_ < S.size();
 }
 
 // Runs on the host while the GPU executes the wave's GEMMs (wave_c's tasks
@@ -1719,22 +1732,36 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       ex.chol_checked(B.oc2);
       ex.gemm(B.o4);
       ex.end();
-      // phase B and the Schur update; the host builds the Schur targets and
-      // the new blocks (wave_d) while the GPU runs the phase-B GEMMs
-      for (Run<T> *r : wp)
-        if (r->ok()) r->wave_c(B);
-      ex.begin(7);
-      ex.gemm(B.g1);
-      ex.gemm(B.g2);
-      ex.chol_checked(B.c1);
-      ex.gemm(B.g3);
-      ex.gemm(B.g4);
-      ex.chol_checked(B.c2);
-      ex.gemm(B.g5);
-      ex.gemm(B.g6);
-      ex.gemm(B.g7);
-      ex.gemm(B.g8);
-      ex.end();
+      // phase B and the Schur update.  The GEMM tasks are built and launched
+      // in chunks of super nodes, so that the GPU starts on the first chunk
+      // while the host builds the next (large waves at the lower levels hold
+      // thousands of nodes); the host then builds the Schur targets and the
+      // new blocks (wave_d) while the GPU runs the last chunk.  Tasks of
+      // different nodes are independent, and a task's arithmetic does not
+      // depend on its chunk.
+      constexpr size_t kChunk = 512;
+      bool more = true;
+      while (more) {
+        more = false;
+        for (Run<T> *r : wp)
+          if (r->ok() && r->wave_c(B, kChunk)) more = true;
+        ex.begin(7);
+        ex.gemm(B.g1);
+        ex.gemm(B.g2);
+        ex.chol_checked(B.c1);
+        ex.gemm(B.g3);
+        ex.gemm(B.g4);
+        ex.chol_checked(B.c2);
+        ex.gemm(B.g5);
+        ex.gemm(B.g6);
+        ex.gemm(B.g7);
+        ex.gemm(B.g8);
+        ex.end();
+        B.c1.tasks.clear();
+        B.c1.what.clear();
+        B.c2.tasks.clear();
+        B.c2.what.clear();
+      }
       for (Run<T> *r : wp)
         if (r->ok()) r->wave_d(B);
       ex.begin(8);
@@ -1790,7 +1817,7 @@ void factorize_t(const std::vector<FactorHandle *> &hs, const std::vector<const 
   Exec ex(st);
   ex.prof = phase_profiling();
   const int prec = hs[0]->prec;
-  ex.tc = prec == HS_PREC_TF32 ? HS_TC_TF32 : prec == HS_PREC_BF16 ? HS_TC_BF16 : HS_TC_NONE;
+  ex.tc = tc_kind_of(prec);
   gemm_tune(ex.tc);   // the GEMM autotuner's table, built once per device and precision
   ex.wait_cycles = hs[0]->timeout_cycles;
   if (hs.size() > 1) {

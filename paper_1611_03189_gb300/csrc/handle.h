@@ -101,6 +101,7 @@ struct FactorHandle {
   int nphi = 1;                        // preserved vectors per node (GC family)
   double eps1 = 0.0;                   // first tolerance of HS_GC_PROJ (Appendix B)
   int64_t timeout_cycles = 0;          // bound of the kernels' waits (0: default)
+  double max_rank_ratio = 0.0;         // rank cap k <= floor(ratio m) (0: none)
   cudaStream_t stream = nullptr;
   int device = 0;
   bool valid = false;                  // holds a usable factorization
@@ -131,6 +132,13 @@ struct FactorHandle {
   ApplyNbr *d_nbrs = nullptr;
   ApplyTarget *d_targets = nullptr;
   ApplyContrib *d_contribs = nullptr;
+  // the persistent apply: step list (kind, wave) and the waves on the device,
+  // the grid barrier's counter and generation, and its time-out flag
+  void *d_apply_steps = nullptr;
+  int apply_nsteps = 0;
+  WaveApply *d_waves = nullptr;
+  unsigned *d_apply_bar = nullptr;
+  int *d_apply_err = nullptr;
   int64_t ws_size = 0;                 // unknowns in the apply workspace
   int64_t tmax = 0;                    // max unknowns of t scratch per wave
   int64_t root_off = 0;
@@ -194,5 +202,9 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
 int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int maxit, int restart, int *iters,
                 double *relres, cudaStream_t st);
 void apply_static(FactorHandle &h, const double *r, double *z, int nrhs, int64_t ld, cudaStream_t st);
+// after a factorization: the persistent apply's step list and waves to the device
+void apply_prepare(FactorHandle &h, cudaStream_t st);
+// 1 if a grid barrier of the persistent apply ran out (synchronous read)
+int apply_error(FactorHandle &h);
 
 }  // namespace hs

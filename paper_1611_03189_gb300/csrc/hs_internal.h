@@ -146,6 +146,8 @@ struct TruncTask {
   int m;
   int np;       // preserved vectors (columns of phi and a)
   int k_idx;    // index into the rank array
+  int cap;      // largest rank k kept (hs_opts.max_rank_ratio; m: no cap); the
+                // GC basis U_1 is always kept whole
 };
 
 // ---------------------------------------------------------------------------
@@ -352,8 +354,17 @@ constexpr int SUM_TILE = 32;
 // TF32 or BF16 and FP32 accumulation; tiles of TC_TILE_M x bn (bn = 64 or
 // 128), tile_start counted in those tiles.  *d_err becomes 1 if a bounded
 // wait of the kernel ran out (the tile is then not written).
-enum { HS_TC_NONE = 0, HS_TC_TF32 = 1, HS_TC_BF16 = 2 };
+// HS_TC_TF32X3: each FP32 operand is split into TF32 high and low parts
+// (a = a_hi + a_lo) and a b is taken as a_hi b_hi + a_hi b_lo + a_lo b_hi,
+// three tensor-core MMAs with near-FP32 accuracy.
+enum { HS_TC_NONE = 0, HS_TC_TF32 = 1, HS_TC_BF16 = 2, HS_TC_TF32X3 = 3 };
 constexpr int TC_TILE_M = 128;
+// tensor-core operand precision of a factor precision (HS_TC_NONE for the
+// FP64 and FP32 factors)
+inline int tc_kind_of(int prec) {
+  return prec == HS_PREC_TF32 ? HS_TC_TF32 : prec == HS_PREC_BF16 ? HS_TC_BF16
+                                              : prec == HS_PREC_TF32X3 ? HS_TC_TF32X3 : HS_TC_NONE;
+}
 // wait_cycles: bound of each mbarrier wait in SM clock cycles (0: the
 // default, about one second)
 void launch_gemm_tc(int kind, int bn, const GemmTask<float> *d_tasks, const int *d_tile_start, int ntasks,
@@ -365,6 +376,9 @@ void launch_gemm_tc(int kind, int bn, const GemmTask<float> *d_tasks, const int 
 // copies it out: per shape class, the times (ms) of the three variants and
 // the choice.
 void gemm_tune(int kind);
+// hs_test_wait_probe: tensor-core GEMM launches first wait on a barrier that
+// nothing arrives at, so that their bounded wait runs out
+void set_wait_probe(bool on);
 int gemm_route(int kind, int M, int N, int K);
 int gemm_tune_report(int kind, float *ms, int *route, int cap);
 

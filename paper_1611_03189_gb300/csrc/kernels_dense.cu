@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(TRUNC_THREADS) k_trunc(const TruncTask<T> *__r
     for (int i = 0; i < m; ++i) lmax = fmax(lmax, (double)A[i * m + i]);
     thr = eps * eps * lmax;
     const int k = select_columns<T>(A, V, m, thr, t.U, 0, red);
-    if (tid == 0) kout[t.k_idx] = k;
+    if (tid == 0) kout[t.k_idx] = min(k, t.cap);   // the columns come in descending order
     return;
   }
   if (eps == 0.0) {
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(TRUNC_THREADS) k_trunc(const TruncTask<T> *__r
   __syncthreads();
   jacobi_eig<T>(A, V, m, true, sh, max_sweeps);
   const int k2 = select_columns<T>(A, V, m, thr, t.U, k1, red);
-  int k = k1 + k2;
+  int k = k1 + min(k2, max(t.cap - k1, 0));
   if (k > m) k = m;
   if (tid == 0) kout[t.k_idx] = k;
 }

@@ -746,6 +746,7 @@ __global__ void __launch_bounds__(NT) k_trunc_big(const TruncTask<T> *__restrict
     const Gersh<double> gd = gershgorin<double>(b.d, b.e, m);
     int k2 = m - sturm_below<double>(b.d, b.e, m, thr, gd.pivmin);
     if (k2 > m - k1) k2 = m - k1;
+    if (k2 > t.cap - k1) k2 = t.cap - k1;   // max_rank_ratio: the largest eigenvalues are kept
     if (k2 < 0) k2 = 0;
     s_k2 = k2;
   }

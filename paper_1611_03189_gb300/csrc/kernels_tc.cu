@@ -7,7 +7,10 @@
 //
 // with the operands rounded to TF32 (round to nearest, ties away) or BF16
 // (round to nearest even) on their way into shared memory and the products
-// accumulated in FP32 in tensor memory (TMEM).
+// accumulated in FP32 in tensor memory (TMEM).  In the TF32X3 form each
+// operand is split into TF32 high and low parts and every product is taken
+// as a_hi b_hi + a_hi b_lo + a_lo b_hi (three MMAs), which keeps about the
+// accuracy of FP32 operands.
 //
 // One CTA of 128 threads computes one 128 x BN tile of one task (tasks of any
 // size, leading dimension and transpose; a tile list is walked by a binary
@@ -35,6 +38,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <mutex>
 #include <string>
@@ -47,6 +51,9 @@ namespace hs {
 namespace {
 
 constexpr int TC_THREADS = 128;
+// hs_test_wait_probe: when set, every launch first waits on a barrier that
+// nothing arrives at (a test of the bounded wait's time-out path)
+std::atomic<int> g_wait_probe{0};
 constexpr int TC_BM = 128;           // tile rows = TMEM lanes (M of the MMA)
 constexpr int TC_KBYTES = 128;       // bytes of K per stage and row
 constexpr long long kTcWaitCycles = 2000000000LL;   // ~1 s at 2 GHz
@@ -71,12 +78,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// true when the phase of `parity` completed within `limit` SM clock cycles
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// true when the phase of `parity` completed within `limit` SM clock cycles.
+// The non-blocking test comes first, so that a short limit is honoured (a
+// blocking try_wait may itself suspend for longer than the limit); long limits
+// also use the blocking form, which frees the issue slots while it waits.
 __device__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity))
+  while (true) {
+    if (mbar_test_wait(bar, parity)) return true;
     if (clock64() - t0 > limit) return false;
-  return true;
+    if (limit >= 1000000 && mbar_try_wait(bar, parity)) return true;
+  }
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -109,6 +133,11 @@ struct TcPrec<HS_TC_BF16> {
   static constexpr int epc = 8;
   static constexpr uint32_t fmt = 1;     // BF16
 };
+template <>
+struct TcPrec<HS_TC_TF32X3> {
+  static constexpr int epc = 4;
+  static constexpr uint32_t fmt = 2;     // TF32 high and low parts
+};
 
 // Instruction descriptor: FP32 accumulator, A and B of the given format, both
 // K-major, N = BN, M = 128.
@@ -120,7 +149,7 @@ __device__ __forceinline__ uint32_t instr_desc() {
 
 template <int KIND>
 __device__ __forceinline__ void mma_issue(uint32_t dt, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if (KIND == HS_TC_TF32)
+  if (KIND == HS_TC_TF32 || KIND == HS_TC_TF32X3)
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dt),
@@ -174,73 +203,163 @@ __device__ __forceinline__ int find_tile_task(const int *tile_start, int ntasks,
   return lo;
 }
 
-// Stage rows [r0, r0 + NR) x K elements [k0, k0 + 32 epc/4 ...) of an operand
-// X(row, k) into one stage buffer.  kcontig: X(row, k) = X[row * ld + k]
-// (else X[k * ld + row]).  Rows >= R and k >= K are zero.  Chunk c of the
-// stage (16 bytes: epc consecutive k of one row) is row group c / 64, row
-// c % 8 of the group, K chunk (c / 8) % 8; eight consecutive threads store
-// eight consecutive rows of one K chunk, 128 contiguous bytes.
+// One operand's share of a K slice in registers: NR rows x 8 EPC-element
+// chunks (16 bytes of the converted operand each) per stage, PER chunks per
+// thread.
 template <int KIND, int NR>
-__device__ __forceinline__ void stage_operand(unsigned char *dst, const float *__restrict__ X, int ld, bool kcontig,
-                                              bool vec, int R, int r0, int K, int k0) {
-  constexpr int EPC = TcPrec<KIND>::epc;
-  constexpr int PER_THREAD = NR * 8 / TC_THREADS;
+struct Slice {
+  static constexpr int EPC = TcPrec<KIND>::epc;
+  static constexpr int PER = NR * 8 / TC_THREADS;
+  float v[PER * EPC];
+};
+
+// Load rows [r0, r0 + NR) x K elements [k0, k0 + 8 EPC) of an operand X(row, k)
+// into registers.  kcontig: X(row, k) = X[row * ld + k], else X[k * ld + row].
+// Rows >= R and k >= K read as zero.
+//  - K contiguous: item q of a thread is chunk c = tid + 128 q (row group
+//    c / 64, row c % 8 of the group, K chunk (c / 8) % 8), one or two 16-byte
+//    loads when aligned;
+//  - rows contiguous: item qq is a quad of 4 consecutive rows x one K chunk
+//    (quad d = tid + 128 qq: row quad d % (NR/4), K chunk d / (NR/4)); each of
+//    its EPC k values is one 16-byte load along the rows when aligned, and the
+//    quad is transposed in registers into 4 chunks (v[4 EPC qq + EPC r + kk]
+//    holds row 4 quad + r, k chunk element kk).
+template <int KIND, int NR>
+__device__ __forceinline__ void load_slice(Slice<KIND, NR> &sl, const float *__restrict__ X, int ld, bool kcontig,
+                                           bool vec, int R, int r0, int K, int k0) {
+  constexpr int EPC = Slice<KIND, NR>::EPC, PER = Slice<KIND, NR>::PER;
+  if (kcontig) {
 #pragma unroll
-  for (int q = 0; q < PER_THREAD; ++q) {
-    const int c = threadIdx.x + TC_THREADS * q;
-    const int grp = c >> 6, rr = c & 7, kc = (c >> 3) & 7;
-    const int row = r0 + grp * 8 + rr;
-    const int kb = k0 + kc * EPC;
-    float v[EPC];
-    if (row < R && kcontig && vec && kb + EPC <= K) {
-      const float4 *p = reinterpret_cast<const float4 *>(X + (int64_t)row * ld + kb);
+    for (int q = 0; q < PER; ++q) {
+      const int c = threadIdx.x + TC_THREADS * q;
+      const int grp = c >> 6, rr = c & 7, kc = (c >> 3) & 7;
+      const int row = r0 + grp * 8 + rr;
+      const int kb = k0 + kc * EPC;
+      float *v = sl.v + q * EPC;
+      if (row < R && vec && kb + EPC <= K) {
+        const float4 *p = reinterpret_cast<const float4 *>(X + (int64_t)row * ld + kb);
 #pragma unroll
-      for (int j = 0; j < EPC / 4; ++j) {
-        const float4 w = __ldg(p + j);
-        v[4 * j] = w.x;
-        v[4 * j + 1] = w.y;
-        v[4 * j + 2] = w.z;
-        v[4 * j + 3] = w.w;
-      }
-    } else {
+        for (int j = 0; j < EPC / 4; ++j) {
+          const float4 w = __ldg(p + j);
+          v[4 * j] = w.x;
+          v[4 * j + 1] = w.y;
+          v[4 * j + 2] = w.z;
+          v[4 * j + 3] = w.w;
+        }
+      } else {
 #pragma unroll
-      for (int j = 0; j < EPC; ++j) {
-        const int k = kb + j;
-        float x = 0.f;
-        if (row < R && k < K) x = kcontig ? __ldg(X + (int64_t)row * ld + k) : __ldg(X + (int64_t)k * ld + row);
-        v[j] = x;
+        for (int j = 0; j < EPC; ++j) {
+          const int k = kb + j;
+          v[j] = (row < R && k < K) ? __ldg(X + (int64_t)row * ld + k) : 0.f;
+        }
       }
     }
-    uint4 w;
-    if (KIND == HS_TC_TF32) {
-      w.x = to_tf32(v[0]);
-      w.y = to_tf32(v[1]);
-      w.z = to_tf32(v[2]);
-      w.w = to_tf32(v[3]);
-    } else {
-      w.x = to_bf16x2(v[0], v[1]);
-      w.y = to_bf16x2(v[2], v[3]);
-      w.z = to_bf16x2(v[4 % EPC], v[5 % EPC]);
-      w.w = to_bf16x2(v[6 % EPC], v[7 % EPC]);
+  } else {
+    constexpr int NQ = NR / 4;
+#pragma unroll
+    for (int qq = 0; qq < PER / 4; ++qq) {
+      const int d = threadIdx.x + TC_THREADS * qq;
+      const int rq = d % NQ, kc = d / NQ;
+      const int row = r0 + 4 * rq;
+      float *v = sl.v + qq * 4 * EPC;
+#pragma unroll
+      for (int kk = 0; kk < EPC; ++kk) {
+        const int k = k0 + kc * EPC + kk;
+        if (vec && row + 3 < R && k < K) {
+          const float4 w = __ldg(reinterpret_cast<const float4 *>(X + (int64_t)k * ld + row));
+          v[kk] = w.x;
+          v[EPC + kk] = w.y;
+          v[2 * EPC + kk] = w.z;
+          v[3 * EPC + kk] = w.w;
+        } else {
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+            v[r * EPC + kk] = (row + r < R && k < K) ? __ldg(X + (int64_t)k * ld + row + r) : 0.f;
+        }
+      }
     }
-    *reinterpret_cast<uint4 *>(dst + grp * 1024 + kc * 128 + rr * 16) = w;
+  }
+}
+
+// EPC floats -> one 16-byte chunk of the operand (and, for TF32X3, of its low part)
+template <int KIND>
+__device__ __forceinline__ void make_chunk(const float *v, uint4 &w, uint4 &lo) {
+  if (KIND == HS_TC_TF32X3) {
+    // a = a_hi + a_lo, both TF32: a_lo carries the next 11 bits of a
+    w.x = to_tf32(v[0]);
+    w.y = to_tf32(v[1]);
+    w.z = to_tf32(v[2]);
+    w.w = to_tf32(v[3]);
+    lo.x = to_tf32(v[0] - __uint_as_float(w.x));
+    lo.y = to_tf32(v[1] - __uint_as_float(w.y));
+    lo.z = to_tf32(v[2] - __uint_as_float(w.z));
+    lo.w = to_tf32(v[3] - __uint_as_float(w.w));
+  } else if (KIND == HS_TC_TF32) {
+    w.x = to_tf32(v[0]);
+    w.y = to_tf32(v[1]);
+    w.z = to_tf32(v[2]);
+    w.w = to_tf32(v[3]);
+  } else {
+    constexpr int EPC = TcPrec<KIND>::epc;
+    w.x = to_bf16x2(v[0], v[1]);
+    w.y = to_bf16x2(v[2], v[3]);
+    w.z = to_bf16x2(v[4 % EPC], v[5 % EPC]);
+    w.w = to_bf16x2(v[6 % EPC], v[7 % EPC]);
+  }
+}
+
+// Convert a slice in registers and store it into one stage buffer (dst; for
+// TF32X3 the low parts into dst_lo) in the canonical K-major layout: chunk of
+// row g * 8 + rr and K chunk kc at byte g * 1024 + kc * 128 + rr * 16.
+template <int KIND, int NR>
+__device__ __forceinline__ void store_slice(unsigned char *dst, unsigned char *dst_lo, const Slice<KIND, NR> &sl,
+                                            bool kcontig) {
+  constexpr int EPC = Slice<KIND, NR>::EPC, PER = Slice<KIND, NR>::PER;
+  if (kcontig) {
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int c = threadIdx.x + TC_THREADS * q;
+      const int grp = c >> 6, rr = c & 7, kc = (c >> 3) & 7;
+      uint4 w, lo;
+      make_chunk<KIND>(sl.v + q * EPC, w, lo);
+      const int off = grp * 1024 + kc * 128 + rr * 16;
+      *reinterpret_cast<uint4 *>(dst + off) = w;
+      if (KIND == HS_TC_TF32X3) *reinterpret_cast<uint4 *>(dst_lo + off) = lo;
+    }
+  } else {
+    constexpr int NQ = NR / 4;
+#pragma unroll
+    for (int qq = 0; qq < PER / 4; ++qq) {
+      const int d = threadIdx.x + TC_THREADS * qq;
+      const int rq = d % NQ, kc = d / NQ;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int row = 4 * rq + r;
+        uint4 w, lo;
+        make_chunk<KIND>(sl.v + qq * 4 * EPC + r * EPC, w, lo);
+        const int off = (row >> 3) * 1024 + kc * 128 + (row & 7) * 16;
+        *reinterpret_cast<uint4 *>(dst + off) = w;
+        if (KIND == HS_TC_TF32X3) *reinterpret_cast<uint4 *>(dst_lo + off) = lo;
+      }
+    }
   }
 }
 
 template <int KIND, int BN, int STAGES>
 __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask<float> *__restrict__ tasks,
                                                          const int *__restrict__ tile_start, int ntasks, int *err,
-                                                         long long wait_cycles) {
+                                                         long long wait_cycles, int probe) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr int A_BYTES = TC_BM * TC_KBYTES;
   constexpr int B_BYTES = BN * TC_KBYTES;
-  constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr int PARTS = KIND == HS_TC_TF32X3 ? 2 : 1;   // high (and low) parts of each operand
+  constexpr int STAGE_BYTES = PARTS * (A_BYTES + B_BYTES);
   constexpr int EPC = TcPrec<KIND>::epc;
   constexpr int KS = 8 * EPC;              // K elements per stage
   constexpr uint32_t NCOLS = BN < 32 ? 32 : BN;
   static_assert(TC_BM * (BN + 1) * 4 <= STAGES * STAGE_BYTES, "epilogue staging must fit the stage buffers");
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + STAGES);
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + STAGES * STAGE_BYTES);   // STAGES + 1 (the probe's)
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + STAGES + 1);
   int *flag = reinterpret_cast<int *>(tslot + 1);
 
   const int ti = find_tile_task(tile_start, ntasks, blockIdx.x);
@@ -252,9 +371,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask<float> *_
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
+    for (int s = 0; s <= STAGES; ++s) mbar_init(smem_u32(&bars[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *flag = 0;
+    // test of the time-out path: a wait on a barrier nothing arrives at
+    if (probe && !mbar_wait_bounded(smem_u32(&bars[STAGES]), 0u, wait_cycles)) *flag = 1;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -268,14 +389,38 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask<float> *_
   const uint32_t tmem = *tslot;
 
   const bool a_kc = t.ta == 0, b_kc = t.tb != 0;   // op(B)^T(j, k) = B[j ldb + k] when tb
-  const bool a_vec = a_kc && (t.lda & 3) == 0 && ((uintptr_t)t.A & 15) == 0;
-  const bool b_vec = b_kc && (t.ldb & 3) == 0 && ((uintptr_t)t.B & 15) == 0;
-  const int nk = t.K > 0 ? (t.K + KS - 1) / KS : 0;
+  // 16-byte loads need a 16-byte aligned base and a leading dimension that is
+  // a multiple of 4 floats (along K for K-contiguous operands, along the rows
+  // for the others)
+  const bool a_vec = (t.lda & 3) == 0 && ((uintptr_t)t.A & 15) == 0;
+  const bool b_vec = (t.ldb & 3) == 0 && ((uintptr_t)t.B & 15) == 0;
+  const int nk = (t.K > 0 && !*flag) ? (t.K + KS - 1) / KS : 0;
   const uint32_t idesc = instr_desc<KIND, BN>();
   const uint32_t sbase = smem_u32(smem);
 
+  // Register double buffer (4-byte operand elements): slice kt + 1 is loaded
+  // before slice kt is converted and stored, so its loads are in flight
+  // across the store, the barrier and the MMA issue.  BF16 chunks take twice
+  // the registers; there one buffer is loaded after the MMA issue.
+  constexpr bool DB = EPC == 4;
+  Slice<KIND, TC_BM> ra0, ra1;
+  Slice<KIND, BN> rb0, rb1;
+  if (nk > 0) {
+    load_slice<KIND, TC_BM>(ra0, t.A, t.lda, a_kc, a_vec, t.M, row0, t.K, 0);
+    load_slice<KIND, BN>(rb0, t.B, t.ldb, b_kc, b_vec, t.N, col0, t.K, 0);
+  }
   for (int kt = 0; kt < nk; ++kt) {
     const int s = kt % STAGES;
+    const bool odd = DB && (kt & 1);
+    if (DB && kt + 1 < nk) {
+      if (odd) {
+        load_slice<KIND, TC_BM>(ra0, t.A, t.lda, a_kc, a_vec, t.M, row0, t.K, (kt + 1) * KS);
+        load_slice<KIND, BN>(rb0, t.B, t.ldb, b_kc, b_vec, t.N, col0, t.K, (kt + 1) * KS);
+      } else {
+        load_slice<KIND, TC_BM>(ra1, t.A, t.lda, a_kc, a_vec, t.M, row0, t.K, (kt + 1) * KS);
+        load_slice<KIND, BN>(rb1, t.B, t.ldb, b_kc, b_vec, t.N, col0, t.K, (kt + 1) * KS);
+      }
+    }
     if (kt >= STAGES) {
       // the MMAs of slice kt - STAGES read this stage: wait for their commit
       if (tid == 0 && !mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((kt / STAGES - 1) & 1), wait_cycles))
@@ -283,19 +428,39 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask<float> *_
       __syncthreads();
       if (*flag) break;
     }
+    // stage layout: A high, B high, then (TF32X3) A low, B low
     unsigned char *sa = smem + s * STAGE_BYTES;
-    stage_operand<KIND, TC_BM>(sa, t.A, t.lda, a_kc, a_vec, t.M, row0, t.K, kt * KS);
-    stage_operand<KIND, BN>(sa + A_BYTES, t.B, t.ldb, b_kc, b_vec, t.N, col0, t.K, kt * KS);
+    unsigned char *slo = sa + A_BYTES + B_BYTES;
+    if (odd) {
+      store_slice<KIND, TC_BM>(sa, slo, ra1, a_kc);
+      store_slice<KIND, BN>(sa + A_BYTES, slo + A_BYTES, rb1, b_kc);
+    } else {
+      store_slice<KIND, TC_BM>(sa, slo, ra0, a_kc);
+      store_slice<KIND, BN>(sa + A_BYTES, slo + A_BYTES, rb0, b_kc);
+    }
     fence_async_smem();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
       const uint32_t a0 = sbase + s * STAGE_BYTES, b0 = a0 + A_BYTES;
+      const uint32_t al = b0 + B_BYTES, bl = al + A_BYTES;
 #pragma unroll
-      for (int j = 0; j < 4; ++j)   // 32 bytes of K per MMA: core matrices 2j, 2j + 1
-        mma_issue<KIND>(tmem, smem_desc(a0 + 256 * j, 128, 1024), smem_desc(b0 + 256 * j, 128, 1024), idesc,
-                        (kt > 0 || j > 0) ? 1u : 0u);
+      for (int j = 0; j < 4; ++j) {   // 32 bytes of K per MMA: core matrices 2j, 2j + 1
+        const uint64_t ah = smem_desc(a0 + 256 * j, 128, 1024), bh = smem_desc(b0 + 256 * j, 128, 1024);
+        if (KIND == HS_TC_TF32X3) {
+          // the two small cross terms first, then the leading one
+          mma_issue<KIND>(tmem, smem_desc(al + 256 * j, 128, 1024), bh, idesc, (kt > 0 || j > 0) ? 1u : 0u);
+          mma_issue<KIND>(tmem, ah, smem_desc(bl + 256 * j, 128, 1024), idesc, 1u);
+          mma_issue<KIND>(tmem, ah, bh, idesc, 1u);
+        } else {
+          mma_issue<KIND>(tmem, ah, bh, idesc, (kt > 0 || j > 0) ? 1u : 0u);
+        }
+      }
       mma_commit(smem_u32(&bars[s]));
+    }
+    if (!DB && kt + 1 < nk) {
+      load_slice<KIND, TC_BM>(ra0, t.A, t.lda, a_kc, a_vec, t.M, row0, t.K, (kt + 1) * KS);
+      load_slice<KIND, BN>(rb0, t.B, t.ldb, b_kc, b_vec, t.N, col0, t.K, (kt + 1) * KS);
     }
   }
   // all MMAs of the tile are complete when the last commit's phase is
@@ -362,12 +527,14 @@ void launch_tc_bn(const GemmTask<float> *d_tasks, const int *d_tile_start, int n
                   long long wait_cycles, cudaStream_t st) {
   // 128-wide tiles keep three K slices in flight (96 KB, two CTAs per SM);
   // 64-wide tiles two (48 KB, four CTAs per SM), for the many small tasks
-  constexpr int STAGES = BN == 128 ? 3 : 2;
-  constexpr size_t smem = (size_t)STAGES * (TC_BM + BN) * TC_KBYTES + 8 * STAGES + 16;
+  constexpr int PARTS = KIND == HS_TC_TF32X3 ? 2 : 1;
+  constexpr int STAGES = (BN == 128 && PARTS == 1) ? 3 : 2;
+  constexpr size_t smem = (size_t)STAGES * PARTS * (TC_BM + BN) * TC_KBYTES + 8 * (STAGES + 1) + 16;
   const int lim = allow_max_dynamic_smem<k_gemm_tc<KIND, BN, STAGES>>();
   check_dynamic_smem(smem, lim, "the tensor-core GEMM");
-  k_gemm_tc<KIND, BN, STAGES><<<total_tiles, TC_THREADS, smem, st>>>(d_tasks, d_tile_start, ntasks, d_err,
-                                                                      wait_cycles > 0 ? wait_cycles : kTcWaitCycles);
+  k_gemm_tc<KIND, BN, STAGES><<<total_tiles, TC_THREADS, smem, st>>>(
+      d_tasks, d_tile_start, ntasks, d_err, wait_cycles > 0 ? wait_cycles : kTcWaitCycles,
+      g_wait_probe.load() ? 1 : 0);
   count_launch();
   HS_CUDA(cudaGetLastError());
 }
@@ -419,7 +586,7 @@ struct TuneTable {
 };
 
 std::mutex g_tune_mu;
-TuneTable g_tune[64][3];   // [device][kind]
+TuneTable g_tune[64][4];   // [device][kind]
 
 void tune_device(int kind, TuneTable &tt) {
   HS_CUDA(cudaDeviceSynchronize());
@@ -542,7 +709,7 @@ void tune_device(int kind, TuneTable &tt) {
 const TuneTable &tune_table(int kind) {
   int dev = 0;
   HS_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64 || kind < 1 || kind > 2) fail(HS_ERR_INVALID, "internal: GEMM tuner device or kind");
+  if (dev < 0 || dev >= 64 || kind < 1 || kind > 3) fail(HS_ERR_INVALID, "internal: GEMM tuner device or kind");
   std::lock_guard<std::mutex> lk(g_tune_mu);
   TuneTable &tt = g_tune[dev][kind];
   if (!tt.ready) tune_device(kind, tt);
@@ -562,9 +729,15 @@ void launch_gemm_tc(int kind, int bn, const GemmTask<float> *d_tasks, const int 
     launch_tc_bn<HS_TC_BF16, 128>(d_tasks, d_tile_start, ntasks, total_tiles, d_err, wait_cycles, st);
   else if (kind == HS_TC_BF16 && bn == 64)
     launch_tc_bn<HS_TC_BF16, 64>(d_tasks, d_tile_start, ntasks, total_tiles, d_err, wait_cycles, st);
+  else if (kind == HS_TC_TF32X3 && bn == 128)
+    launch_tc_bn<HS_TC_TF32X3, 128>(d_tasks, d_tile_start, ntasks, total_tiles, d_err, wait_cycles, st);
+  else if (kind == HS_TC_TF32X3 && bn == 64)
+    launch_tc_bn<HS_TC_TF32X3, 64>(d_tasks, d_tile_start, ntasks, total_tiles, d_err, wait_cycles, st);
   else
     fail(HS_ERR_INVALID, "tensor-core GEMM: unknown precision or tile width");
 }
+
+void set_wait_probe(bool on) { g_wait_probe.store(on ? 1 : 0); }
 
 void gemm_tune(int kind) {
   if (kind != HS_TC_NONE && forced_route() < 0) (void)tune_table(kind);

@@ -101,12 +101,14 @@ __device__ __forceinline__ void col_dot(const T *__restrict__ A, int64_t ld, con
   }
 }
 
+// Each step of Algorithm 2 below is a __device__ function of one warp's share
+// (virtual warp w of the step); the per-step kernels give warp w = global warp
+// index, the persistent kernel walks w over all warps of the grid.
+
 // F1: one warp per row of [M_ss; P_ss]: t_s = M_ss phi_s, phi_r += P_ss phi_s
 template <typename T, int NR>
-__global__ void __launch_bounds__(AT) k_f1(const ApplyNode *__restrict__ nodes, int first, int count, int rows,
-                                           T *__restrict__ ws, T *__restrict__ tb, int nrhs, int j0) {
-  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w >= rows) return;
+__device__ __forceinline__ void f1_warp(const ApplyNode *__restrict__ nodes, int first, int count, int w, int lane,
+                                        T *__restrict__ ws, T *__restrict__ tb, int nrhs, int j0) {
   const int ni = find_last(first, count, w, [&](int i) { return nodes[i].row0; });
   const ApplyNode nd = nodes[ni];
   const int r = w - nd.row0;
@@ -131,13 +133,18 @@ __global__ void __launch_bounds__(AT) k_f1(const ApplyNode *__restrict__ nodes, 
   }
 }
 
+template <typename T, int NR>
+__global__ void __launch_bounds__(AT) k_f1(const ApplyNode *__restrict__ nodes, int first, int count, int rows,
+                                           T *__restrict__ ws, T *__restrict__ tb, int nrhs, int j0) {
+  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w < rows) f1_warp<T, NR>(nodes, first, count, w, lane, ws, tb, nrhs, j0);
+}
+
 // F2: phi_n -= sum_s A_ns t_s; one warp per 32 rows of a target, contributions in order
 template <typename T, int NR>
-__global__ void __launch_bounds__(AT) k_f2(const ApplyTarget *__restrict__ tg, int first, int count, int chunks,
-                                           const ApplyContrib *__restrict__ cb, T *__restrict__ ws,
-                                           const T *__restrict__ tb, int nrhs, int j0) {
-  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w >= chunks) return;
+__device__ __forceinline__ void f2_warp(const ApplyTarget *__restrict__ tg, int first, int count, int w, int lane,
+                                        const ApplyContrib *__restrict__ cb, T *__restrict__ ws,
+                                        const T *__restrict__ tb, int nrhs, int j0) {
   const int ti = find_last(first, count, w, [&](int i) { return tg[i].ch0; });
   const ApplyTarget t = tg[ti];
   const int i = (w - t.ch0) * 32 + lane;
@@ -158,13 +165,20 @@ __global__ void __launch_bounds__(AT) k_f2(const ApplyTarget *__restrict__ tg, i
     if (j < nr) o[j] -= acc[j];
 }
 
+template <typename T, int NR>
+__global__ void __launch_bounds__(AT) k_f2(const ApplyTarget *__restrict__ tg, int first, int count, int chunks,
+                                           const ApplyContrib *__restrict__ cb, T *__restrict__ ws,
+                                           const T *__restrict__ tb, int nrhs, int j0) {
+  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w < chunks) f2_warp<T, NR>(tg, first, count, w, lane, cb, ws, tb, nrhs, j0);
+}
+
 // B1 (warps < rows_b): v_s = phi_s - sum_n A_sn x_n, one warp per row of s.
 // B2a (warps >= rows_b): y_s = P_ss^T x_r, one warp per 32 columns of P_ss.
 template <typename T, int NR>
-__global__ void __launch_bounds__(AT) k_b1(const ApplyNode *__restrict__ nodes, int first, int count, int rows_b,
-                                           int pch, const ApplyNbr *__restrict__ nb, const T *__restrict__ ws,
-                                           T *__restrict__ tb, T *__restrict__ tb2, int nrhs, int j0) {
-  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+__device__ __forceinline__ void b1_warp(const ApplyNode *__restrict__ nodes, int first, int count, int rows_b,
+                                        int w, int lane, const ApplyNbr *__restrict__ nb, const T *__restrict__ ws,
+                                        T *__restrict__ tb, T *__restrict__ tb2, int nrhs, int j0) {
   const int nr = min(NR, nrhs - j0);
   T acc[NR];
 #pragma unroll
@@ -187,7 +201,7 @@ __global__ void __launch_bounds__(AT) k_b1(const ApplyNode *__restrict__ nodes, 
       for (int j = 0; j < NR; ++j)
         if (j < nr) o[j] = ph[j] - acc[j];
     }
-  } else if (w < rows_b + pch) {
+  } else {
     const int w2 = w - rows_b;
     const int ni = find_last(first, count, w2, [&](int i) { return nodes[i].pch0; });
     const ApplyNode nd = nodes[ni];
@@ -203,13 +217,19 @@ __global__ void __launch_bounds__(AT) k_b1(const ApplyNode *__restrict__ nodes, 
   }
 }
 
+template <typename T, int NR>
+__global__ void __launch_bounds__(AT) k_b1(const ApplyNode *__restrict__ nodes, int first, int count, int rows_b,
+                                           int pch, const ApplyNbr *__restrict__ nb, const T *__restrict__ ws,
+                                           T *__restrict__ tb, T *__restrict__ tb2, int nrhs, int j0) {
+  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w < rows_b + pch) b1_warp<T, NR>(nodes, first, count, rows_b, w, lane, nb, ws, tb, tb2, nrhs, j0);
+}
+
 // B2b: x_s = M_ss v_s + y_s, one warp per row of s
 template <typename T, int NR>
-__global__ void __launch_bounds__(AT) k_b2(const ApplyNode *__restrict__ nodes, int first, int count, int rows_b,
-                                           T *__restrict__ ws, const T *__restrict__ tb,
-                                           const T *__restrict__ tb2, int nrhs, int j0) {
-  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w >= rows_b) return;
+__device__ __forceinline__ void b2_warp(const ApplyNode *__restrict__ nodes, int first, int count, int w, int lane,
+                                        T *__restrict__ ws, const T *__restrict__ tb, const T *__restrict__ tb2,
+                                        int nrhs, int j0) {
   const int ni = find_last(first, count, w, [&](int i) { return nodes[i].brow0; });
   const ApplyNode nd = nodes[ni];
   const int r = w - nd.brow0;
@@ -230,6 +250,14 @@ __global__ void __launch_bounds__(AT) k_b2(const ApplyNode *__restrict__ nodes, 
   }
 }
 
+template <typename T, int NR>
+__global__ void __launch_bounds__(AT) k_b2(const ApplyNode *__restrict__ nodes, int first, int count, int rows_b,
+                                           T *__restrict__ ws, const T *__restrict__ tb,
+                                           const T *__restrict__ tb2, int nrhs, int j0) {
+  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w < rows_b) b2_warp<T, NR>(nodes, first, count, w, lane, ws, tb, tb2, nrhs, j0);
+}
+
 template <typename T>
 __global__ void k_copy(const T *__restrict__ src, T *__restrict__ dst, int64_t n) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
@@ -238,11 +266,8 @@ __global__ void k_copy(const T *__restrict__ src, T *__restrict__ dst, int64_t n
 
 // root: x = A_root^-1 phi (phi copied to tb first), one warp per row
 template <typename T, int NR>
-__global__ void __launch_bounds__(AT) k_root(const T *__restrict__ Ainv, int m, int64_t off,
-                                             T *__restrict__ ws, const T *__restrict__ tb, int nrhs,
-                                             int j0) {
-  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w >= m) return;
+__device__ __forceinline__ void root_warp(const T *__restrict__ Ainv, int m, int64_t off, int w, int lane,
+                                          T *__restrict__ ws, const T *__restrict__ tb, int nrhs, int j0) {
   const T *Ar = Ainv + (int64_t)w * m;
   const int nr = min(NR, nrhs - j0);
   T acc[NR];
@@ -255,6 +280,101 @@ __global__ void __launch_bounds__(AT) k_root(const T *__restrict__ Ainv, int m, 
 #pragma unroll
     for (int j = 0; j < NR; ++j)
       if (j < nr) o[j] = acc[j];
+  }
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(AT) k_root(const T *__restrict__ Ainv, int m, int64_t off,
+                                             T *__restrict__ ws, const T *__restrict__ tb, int nrhs,
+                                             int j0) {
+  const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (w < m) root_warp<T, NR>(Ainv, m, off, w, lane, ws, tb, nrhs, j0);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent apply: the whole of Algorithm 2 for one chunk of right-hand sides
+// in ONE cooperative launch.  The per-step launches above cost a launch
+// latency per dependent step (about four per wave, some 240 at the 512 x 512
+// workload); here every CTA of a grid sized to be resident walks the step
+// list (forward f1, f2 per wave; root copy and solve; backward b1, b2 per
+// wave in reverse), the warps of the grid sharing each step's virtual warps,
+// with a grid-wide barrier between dependent steps.  The barrier is a counter
+// and a generation word; its wait is bounded (clock cycles) and a wait that
+// runs out sets *err and ends the kernel (the host reports HS_ERR_TIMEOUT).
+// The steps and their arithmetic are those of the per-step kernels, so the
+// result is the same bit for bit.
+// ---------------------------------------------------------------------------
+enum { AS_F1 = 0, AS_F2 = 1, AS_COPY = 2, AS_ROOT = 3, AS_B1 = 4, AS_B2 = 5 };
+
+struct ApplyStepDev {
+  int kind;
+  int wave;          // index into the waves (f1, f2, b1, b2)
+};
+
+__device__ bool grid_barrier(unsigned *bar, int *err, long long limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned *gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > limit) {
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(AT) k_apply_persistent(
+    const ApplyStepDev *__restrict__ steps, int nsteps, const WaveApply *__restrict__ waves,
+    const ApplyNode *__restrict__ nodes, const ApplyNbr *__restrict__ nbrs, const ApplyTarget *__restrict__ tg,
+    const ApplyContrib *__restrict__ cb, const T *__restrict__ root_inv, int root_m, int64_t root_off,
+    T *__restrict__ ws, T *__restrict__ tb, T *__restrict__ tb2, int nrhs, int j0, unsigned *bar, int *err,
+    long long limit) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * AW + (threadIdx.x >> 5), nwarps = gridDim.x * AW;
+  for (int si = 0; si < nsteps; ++si) {
+    const ApplyStepDev st = steps[si];
+    if (st.kind == AS_COPY) {
+      const int64_t n = (int64_t)root_m * nrhs;
+      for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        tb[e] = ws[root_off * nrhs + e];
+    } else if (st.kind == AS_ROOT) {
+      for (int w = gw; w < root_m; w += nwarps) root_warp<T, NR>(root_inv, root_m, root_off, w, lane, ws, tb, nrhs, j0);
+    } else {
+      const WaveApply wa = waves[st.wave];
+      if (st.kind == AS_F1) {
+        for (int w = gw; w < wa.rows_f; w += nwarps)
+          f1_warp<T, NR>(nodes, wa.node_first, wa.node_count, w, lane, ws, tb, nrhs, j0);
+      } else if (st.kind == AS_F2) {
+        for (int w = gw; w < wa.tch; w += nwarps)
+          f2_warp<T, NR>(tg, wa.tgt_first, wa.tgt_count, w, lane, cb, ws, tb, nrhs, j0);
+      } else if (st.kind == AS_B1) {
+        for (int w = gw; w < wa.rows_b + wa.pch; w += nwarps)
+          b1_warp<T, NR>(nodes, wa.node_first, wa.node_count, wa.rows_b, w, lane, nbrs, ws, tb, tb2, nrhs, j0);
+      } else {
+        for (int w = gw; w < wa.rows_b; w += nwarps)
+          b2_warp<T, NR>(nodes, wa.node_first, wa.node_count, w, lane, ws, tb, tb2, nrhs, j0);
+      }
+    }
+    if (si + 1 < nsteps && !grid_barrier(bar, err, limit)) return;
   }
 }
 
@@ -545,6 +665,66 @@ void apply_waves_nr(const FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, int j
   HS_CUDA(cudaGetLastError());
 }
 
+// whether the apply runs as one persistent cooperative launch per chunk of
+// right-hand sides (HS_APPLY_PERSISTENT=0 in the environment: per-step launches)
+bool persistent_apply_enabled() {
+  static const bool on = [] {
+    const char *e = std::getenv("HS_APPLY_PERSISTENT");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+// One chunk of right-hand sides [j0, j0 + NR) through the persistent kernel.
+// The grid is the number of CTAs that can be resident at once (at most four
+// per SM), launched cooperatively so that they are; the barrier words are
+// cleared on the stream first.
+template <typename T, int NR>
+void apply_persistent_nr(const FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, int j0, cudaStream_t st) {
+  static int blocks_per_sm[64] = {0};
+  static std::mutex mu;
+  int dev = 0;
+  HS_CUDA(cudaGetDevice(&dev));
+  int bps = 0, nsm = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64) fail(HS_ERR_CUDA, "device ordinal out of range");
+    if (!blocks_per_sm[dev]) {
+      int b = 0;
+      HS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_apply_persistent<T, NR>, AT, 0));
+      blocks_per_sm[dev] = std::max(1, std::min(b, 4));
+    }
+    bps = blocks_per_sm[dev];
+  }
+  HS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  HS_CUDA(cudaMemsetAsync(h.d_apply_bar, 0, 2 * sizeof(unsigned), st));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(nsm * bps), 1, 1);
+  cfg.blockDim = dim3(AT, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const long long limit = 2000000000LL;   // about one second of SM clocks per barrier
+  HS_CUDA(cudaLaunchKernelEx(&cfg, k_apply_persistent<T, NR>, (const ApplyStepDev *)h.d_apply_steps,
+                             h.apply_nsteps, (const WaveApply *)h.d_waves, (const ApplyNode *)h.d_nodes,
+                             (const ApplyNbr *)h.d_nbrs, (const ApplyTarget *)h.d_targets,
+                             (const ApplyContrib *)h.d_contribs, (const T *)h.root_inv, h.root_m, h.root_off, ws, tb,
+                             tb2, nrhs, j0, h.d_apply_bar, h.d_apply_err, limit));
+  count_launch();
+}
+
+template <typename T, int NR>
+void apply_chunk_nr(const FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, int j0, cudaStream_t st) {
+  if (persistent_apply_enabled() && h.d_apply_steps && h.apply_nsteps > 0)
+    apply_persistent_nr<T, NR>(h, ws, tb, tb2, nrhs, j0, st);
+  else
+    apply_waves_nr<T, NR>(h, ws, tb, tb2, nrhs, j0, st);
+}
+
 // The whole apply on a workspace whose level-L part holds the right-hand
 // sides: red-node parts cleared (Algorithm 2 starts them at zero), then the
 // right-hand sides in chunks of at most 16 (register accumulators).
@@ -555,19 +735,19 @@ void apply_chunks(const FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, cudaStr
   for (int j0 = 0; j0 < nrhs;) {
     const int rem = nrhs - j0;
     if (rem > 8) {
-      apply_waves_nr<T, 16>(h, ws, tb, tb2, nrhs, j0, st);
+      apply_chunk_nr<T, 16>(h, ws, tb, tb2, nrhs, j0, st);
       j0 += 16;
     } else if (rem > 4) {
-      apply_waves_nr<T, 8>(h, ws, tb, tb2, nrhs, j0, st);
+      apply_chunk_nr<T, 8>(h, ws, tb, tb2, nrhs, j0, st);
       j0 += 8;
     } else if (rem > 2) {
-      apply_waves_nr<T, 4>(h, ws, tb, tb2, nrhs, j0, st);
+      apply_chunk_nr<T, 4>(h, ws, tb, tb2, nrhs, j0, st);
       j0 += 4;
     } else if (rem == 2) {
-      apply_waves_nr<T, 2>(h, ws, tb, tb2, nrhs, j0, st);
+      apply_chunk_nr<T, 2>(h, ws, tb, tb2, nrhs, j0, st);
       j0 += 2;
     } else {
-      apply_waves_nr<T, 1>(h, ws, tb, tb2, nrhs, j0, st);
+      apply_chunk_nr<T, 1>(h, ws, tb, tb2, nrhs, j0, st);
       j0 += 1;
     }
   }
@@ -681,6 +861,53 @@ void ensure_buffers(FactorHandle &h, int nrhs_cap) {
 }
 
 }  // namespace
+
+void apply_prepare(FactorHandle &h, cudaStream_t st) {
+  // the step list of Algorithm 2, in the order of the per-step launches
+  std::vector<ApplyStepDev> steps;
+  for (const LevelApply &la : h.levels)
+    for (int w = la.wave_first; w < la.wave_first + la.wave_count; ++w) {
+      if (h.waves[w].rows_f) steps.push_back(ApplyStepDev{AS_F1, w});
+      if (h.waves[w].tch) steps.push_back(ApplyStepDev{AS_F2, w});
+    }
+  if (h.root_m > 0) {
+    steps.push_back(ApplyStepDev{AS_COPY, 0});
+    steps.push_back(ApplyStepDev{AS_ROOT, 0});
+  }
+  for (int li = (int)h.levels.size() - 1; li >= 0; --li) {
+    const LevelApply &la = h.levels[li];
+    for (int w = la.wave_first + la.wave_count - 1; w >= la.wave_first; --w) {
+      if (!h.waves[w].rows_b) continue;
+      steps.push_back(ApplyStepDev{AS_B1, w});
+      steps.push_back(ApplyStepDev{AS_B2, w});
+    }
+  }
+  cudaFree(h.d_apply_steps);
+  cudaFree(h.d_waves);
+  h.d_apply_steps = nullptr;
+  h.d_waves = nullptr;
+  h.apply_nsteps = (int)steps.size();
+  if (steps.empty()) return;
+  HS_CUDA(cudaMalloc(&h.d_apply_steps, sizeof(ApplyStepDev) * steps.size()));
+  HS_CUDA(cudaMemcpyAsync(h.d_apply_steps, steps.data(), sizeof(ApplyStepDev) * steps.size(), cudaMemcpyHostToDevice,
+                          st));
+  HS_CUDA(cudaMalloc(&h.d_waves, sizeof(WaveApply) * std::max<size_t>(h.waves.size(), 1)));
+  if (!h.waves.empty())
+    HS_CUDA(cudaMemcpyAsync(h.d_waves, h.waves.data(), sizeof(WaveApply) * h.waves.size(), cudaMemcpyHostToDevice,
+                            st));
+  if (!h.d_apply_bar) {
+    HS_CUDA(cudaMalloc(&h.d_apply_bar, 2 * sizeof(unsigned) + sizeof(int)));
+    HS_CUDA(cudaMemsetAsync(h.d_apply_bar, 0, 2 * sizeof(unsigned) + sizeof(int), st));
+    h.d_apply_err = (int *)(h.d_apply_bar + 2);
+  }
+}
+
+int apply_error(FactorHandle &h) {
+  if (!h.d_apply_err) return 0;
+  int e = 0;
+  HS_CUDA(cudaMemcpy(&e, h.d_apply_err, sizeof(int), cudaMemcpyDeviceToHost));
+  return e;
+}
 
 void apply_solve(FactorHandle &h, const double *r, double *z, int nrhs, int64_t ld, cudaStream_t st) {
   ensure_buffers(h, std::max(nrhs, h.nrhs_cap));
@@ -813,6 +1040,7 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
   HS_CUDA(cudaMemcpyAsync(hs.data(), h.d_scal, sizeof(double) * 6 * 32, cudaMemcpyDeviceToHost, st));
   HS_CUDA(cudaMemcpyAsync(hi.data(), h.d_iflags, sizeof(int) * (2 * 32 + 2), cudaMemcpyDeviceToHost, st));
   HS_CUDA(cudaStreamSynchronize(st));
+  if (apply_error(h)) fail(HS_ERR_TIMEOUT, "a grid barrier of the persistent apply ran out");
   bool all = true;
   for (int j = 0; j < nrhs; ++j) {
     iters[j] = hi[32 + j];
@@ -1044,6 +1272,7 @@ int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int ma
   count_launch();
   HS_CUDA(cudaGetLastError());
   HS_CUDA(cudaStreamSynchronize(st));
+  if (apply_error(h)) fail(HS_ERR_TIMEOUT, "a grid barrier of the persistent apply ran out");
   *iters = total;
   *relres = bnorm > 0.0 ? std::sqrt(hh[0]) / bnorm : 0.0;
   return converged ? HS_OK : HS_ERR_NO_CONVERGENCE;
@@ -1051,8 +1280,9 @@ int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int ma
 
 // ---------------------------------------------------------------------------
 // Allocation-free apply (hs_apply_static).  Some callers cannot allocate device
-// memory when they solve: code that records work inside a CUDA stream capture,
-// or a service that fixes its device-memory footprint at start-up.  For them
+// memory when they solve: a service that fixes its device-memory footprint at
+// start-up, or code running where a cudaMalloc could block behind other work
+// or is not permitted.  For them
 // the apply workspace comes from one file-scope device array instead of the
 // handle's lazily grown buffers.  The array is shared by every call on a
 // device and keeps the previous call's contents; calls that overlap on the
@@ -1132,6 +1362,9 @@ FactorHandle::~FactorHandle() {
   cudaFree(d_leaf_dest);
   cudaFree(d_phi0);
   cudaFree(d_phi_raw);
+  cudaFree(d_apply_steps);
+  cudaFree(d_waves);
+  cudaFree(d_apply_bar);
   cudaFree(d_dscale);
   cudaFree(d_val_f);
   cudaFree(d_flag);

@@ -414,3 +414,31 @@ def test_sequential_order_matches_oracle(name, maker, variant):
     zg = G.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
     assert elem(zg, H.apply(F, B)) <= 1e-10
     G.close()
+
+
+@pytest.mark.parametrize("name,maker", [CASES[0], CASES[3], CASES[4]], ids=[CASES[0][0], CASES[3][0], CASES[4][0]])
+@pytest.mark.parametrize("variant", [H.LORASP, H.GC_CONSTANT])
+def test_rank_cap_matches_oracle(name, maker, variant):
+    """hs_opts.max_rank_ratio = 0.5: every truncation keeps at most
+    floor(m / 2) leading vectors (GC: U_1 whole); on these problems the cap
+    binds on 38 to 182 super nodes.  Ranks and apply equal the oracle's with
+    the same cap (exemption: a singular-value gap at the cut within 1e-10
+    relative, none expected).  (A cap of 0.25 makes GC-constant lose
+    definiteness on the 64 x 64 diffusion problem, in the oracle too.)"""
+    torch = need_gpu()
+    pb = maker()
+    F = H.factor(pb.n, pb.rowptr, pb.col, pb.val, pb.perm, pb.leaf_ptr, 1e-2, variant, max_rank_ratio=0.5)
+    rp, ci, va = to_dev(pb)
+    G = _lib.Factor(rp, ci, va, pb.perm, pb.leaf_ptr, 1e-2, variant, _lib.HS_PREC_F64, max_rank_ratio=0.5)
+    bad = []
+    for lv in F.levels:
+        g = G.ranks(lv.level)
+        for rec in lv.supers:
+            want = rec.k if rec.wsep else -1
+            if g[rec.key] != want and rec.margin >= 1e-10:
+                bad.append((lv.level, rec.key, want, int(g[rec.key])))
+    assert bad == [], bad[:5]
+    B = P.rhs(pb.n, 6, nrhs=2)
+    zg = G.apply(torch.as_tensor(B.T.copy(), device="cuda")).cpu().numpy().T
+    assert elem(zg, H.apply(F, B)) <= 1e-10
+    G.close()

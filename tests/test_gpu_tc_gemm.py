@@ -41,7 +41,8 @@ def _round_bf16(torch, x):
     return torch.as_tensor(np.asarray(x, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
 
 
-@pytest.mark.parametrize("prec", [_lib.HS_PREC_TF32, _lib.HS_PREC_BF16], ids=["tf32", "bf16"])
+@pytest.mark.parametrize("prec", [_lib.HS_PREC_TF32, _lib.HS_PREC_BF16, _lib.HS_PREC_TF32X3],
+                         ids=["tf32", "bf16", "tf32x3"])
 @pytest.mark.parametrize("bn", [64, 128])
 @pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
 def test_integer_operands_give_the_exact_product(prec, bn, ta, tb):
@@ -88,7 +89,8 @@ def test_rounded_operands_within_fp32_accumulation(prec):
         assert np.max(np.abs(got - exact)) <= 2.5 * u * np.max(np.abs(a).astype(np.float64) @ np.abs(b))
 
 
-@pytest.mark.parametrize("prec", [_lib.HS_PREC_TF32, _lib.HS_PREC_BF16], ids=["tf32", "bf16"])
+@pytest.mark.parametrize("prec", [_lib.HS_PREC_TF32, _lib.HS_PREC_BF16, _lib.HS_PREC_TF32X3],
+                         ids=["tf32", "bf16", "tf32x3"])
 def test_empty_inner_dimension_scales_c(prec):
     """K = 0: op(A) op(B) is the zero matrix, so C becomes beta C."""
     import ctypes as C
@@ -102,6 +104,35 @@ def test_empty_inner_dimension_scales_c(prec):
                                  Cm.data_ptr(), N, 0, C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert code == _lib.HS_OK
     assert torch.equal(Cm, -c0)
+
+
+def test_tf32x3_keeps_near_fp32_accuracy():
+    """3xTF32: a = a_hi + a_lo (TF32 parts, a_lo = tf32(a - a_hi)), products
+    a_hi b_hi + a_hi b_lo + a_lo b_hi.  The split leaves |a - a_hi - a_lo| <=
+    2^-22 |a| and the dropped a_lo b_lo is <= 2^-22 |a b|, so each product is
+    within 3 2^-22 |a b|; the sums add the tensor core's FP32 accumulation,
+    whose additions are coarser than IEEE round-to-nearest (measured: about
+    1e-4 relative at K = 700 against 2e-3 for plain TF32 operands).  Checked
+    against the FP64 product with the FP32 accumulation bound, and at least
+    ten times closer than plain TF32."""
+    torch = need_gpu()
+    rng = np.random.default_rng(11)
+    for M, N, K in ((200, 300, 700), (129, 64, 2048)):
+        a = rng.standard_normal((M, K)).astype(np.float32)
+        b = rng.standard_normal((K, N)).astype(np.float32)
+        C = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+        _lib.gemm_tc(_lib.HS_PREC_TF32X3, torch.as_tensor(a, device="cuda"), torch.as_tensor(b, device="cuda"), C)
+        got = C.double().cpu().numpy()
+        exact = a.astype(np.float64) @ b.astype(np.float64)
+        absab = np.abs(a).astype(np.float64) @ np.abs(b).astype(np.float64)
+        bound = (3.0 * 2.0 ** -22 + 2.0 * K * 2.0 ** -24) * absab
+        assert np.all(np.abs(got - exact) <= bound)
+        # at least 10x closer than plain TF32 on the largest entry error
+        C1 = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+        _lib.gemm_tc(_lib.HS_PREC_TF32, torch.as_tensor(a, device="cuda"), torch.as_tensor(b, device="cuda"), C1)
+        e3 = np.max(np.abs(got - exact))
+        e1 = np.max(np.abs(C1.double().cpu().numpy() - exact))
+        assert e3 * 10 < e1, (e3, e1)
 
 
 def test_invalid_arguments_are_rejected():

@@ -401,3 +401,46 @@ def test_scaling_rescues_gc_on_the_coefficient_jump():
             F = _factor(pb, eps, var, nbr_dist=2, scale=True)
             x, it, rr = H.gmres_solve(F, pb.rowptr, pb.col, pb.val, b)
             assert rr <= 1e-10 and abs(it - t4[32][c0 + i]) <= 3, (var, eps, it)
+
+
+def test_rank_cap_keeps_the_leading_singular_vectors():
+    """max_rank_ratio (a cap the paper does not have): compress() keeps the
+    leading columns of the uncapped basis -- exactly the first cap columns of
+    the same SVD for LoRaSp, U_1 whole plus the leading projected vectors for
+    GC -- and a ratio of 1 changes nothing."""
+    rng = np.random.default_rng(4)
+    B = rng.standard_normal((40, 90)) @ np.diag(np.logspace(0, -6, 90))
+    U = H.compress(B, 1e-4, H.LORASP)
+    for cap in (1, 5, U.shape[1], U.shape[1] + 3):
+        Uc, _ = H._compress(B, 1e-4, H.LORASP, cap=cap)
+        assert Uc.shape[1] == min(cap, U.shape[1])
+        assert np.array_equal(Uc, U[:, :Uc.shape[1]])
+    phi_s = np.ones(40)
+    phi_w = np.ones(90)
+    Ug = H.compress(B, 1e-4, H.GC_CONSTANT, phi_s, phi_w)
+    Ugc, _ = H._compress(B, 1e-4, H.GC_CONSTANT, phi_s, phi_w, cap=6)
+    assert Ugc.shape[1] == 6
+    assert np.array_equal(Ugc, Ug[:, :6])
+    Ug1, _ = H._compress(B, 1e-4, H.GC_CONSTANT, phi_s, phi_w, cap=1)   # U_1 (2 columns) is kept whole
+    assert Ug1.shape[1] == 2 and np.array_equal(Ug1, Ug[:, :2])
+
+
+def test_rank_cap_bounds_every_rank_and_keeps_an_spd_preconditioner():
+    pb = P.poisson2d(32, leaf_size=8)
+    for variant in (H.LORASP, H.GC_CONSTANT):
+        F0 = _factor(pb, 1e-2, variant)
+        F1 = _factor(pb, 1e-2, variant, max_rank_ratio=1.0)
+        b = P.rhs(pb.n, 3)
+        assert np.array_equal(H.apply(F0, b), H.apply(F1, b))
+        Fc = _factor(pb, 1e-2, variant, max_rank_ratio=0.25)
+        capped = 0
+        for lv0, lvc in zip(F0.levels, Fc.levels):
+            for r0, rc in zip(lv0.supers, lvc.supers):
+                if rc.wsep:
+                    cap = H.rank_cap(rc.m, 0.25)
+                    k1 = 0 if variant == H.LORASP else 2
+                    assert rc.k <= max(cap, k1)
+                    capped += int(rc.k < r0.k) if lv0 is F0.levels[0] else 0
+        assert capped > 0          # the cap binds on the first level
+        x, it, rr = H.pcg(Fc, pb.rowptr, pb.col, pb.val, b)
+        assert rr <= 1e-10
