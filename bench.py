@@ -47,6 +47,14 @@ CPU_SAMPLE = {"poisson3d_64": "poisson3d_24", "poisson3d_32": "poisson3d_24"}
 METRIC = "solves/s to rel-res 1e-10 (factor + PCG solve; mixed vs FP64 factor)"
 # factor precisions by name (values of HS_PREC_*)
 PRECS = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "tf32x3": 4}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per launch unit
+# of the roofline entries, from one ncu capture of the same bench command:
+# "apply" per application (all its launches), "trunc" per launch group of the
+# large-node truncation.  Each figure names the profiles/ summary that holds
+# the capture and its command; a kernel changed since its capture has no
+# entry here (traffic null).
+TRAFFIC = {
+}
 
 
 def make_problem(name: str, seed: int):
@@ -855,14 +863,15 @@ def main():
     roof_trunc = {"bound": "alu", "kernel": "k_trunc_big (large-node truncation: tridiagonalisation, "
                   "bisection, inverse iteration, back-transformation)",
                   "achieved": tb_ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": tb_ach / alu_peak,
-                  "peak_source": alu_src, "traffic": None,
+                  "peak_source": alu_src, "traffic": TRAFFIC.get((args.workload, args.prec), {}).get("trunc"),
                   "algorithmic_flops_per_launch": info_f["trunc_big_flops"] / tb_launches,
                   "launch_ms": tb_ms / tb_launches, "launches_per_factor": info_f["trunc_big_launches"],
                   "share_of_step": tb_ms / ms_per_step}
     roof_apply = {"bound": "hbm", "kernel": "apply (Algorithm 2: k_f1, k_f2, k_b1, k_b2, k_root)",
                   "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
                   "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback",
-                  "traffic": None, "algorithmic_bytes": apply_bytes, "launch_ms": apply_ms,
+                  "traffic": TRAFFIC.get((args.workload, args.prec), {}).get("apply"),
+                  "algorithmic_bytes": apply_bytes, "launch_ms": apply_ms,
                   "share_of_step": apply_ms * int(it1.max()) / ms_per_step}
     # ---- the tensor-core GEMM of the mixed factors (tcgen05), against the tensor peak ----
     # flops it executes (2MNK per task) over the device time of its launches

@@ -381,13 +381,18 @@ int hs_gemm_tc(int32_t prec, int32_t M, int32_t N, int32_t K, float alpha, const
  * paper has no counterpart. */
 int hs_gemm_tune_report(int32_t prec, float *ms, int32_t *route, int32_t cap);
 
-/* hs_test_wait_probe: on != 0 makes every later tensor-core GEMM launch (all
- * handles, all threads) first wait, with the factorization's bound
- * (hs_opts.timeout_cycles), on a barrier that nothing arrives at, so that the
- * wait runs out and the call fails with HS_ERR_TIMEOUT before any tensor-core
- * work is issued; 0 turns it off (the default).  A test of the time-out path,
- * which no GPU fault can exercise on a shared machine; the paper has no
- * counterpart.  Returns HS_OK. */
+/* hs_test_wait_probe: on != 0 makes every later tensor-core GEMM launch and
+ * every later persistent apply launch (HS_APPLY_PERSISTENT=1; all handles, all
+ * threads) first wait, with the handle's bound (hs_opts.timeout_cycles), on a
+ * barrier that nothing completes, so that the wait runs out: the
+ * factorization fails with HS_ERR_TIMEOUT before any tensor-core work is
+ * issued, and hs_pcg / hs_gmres fail with HS_ERR_TIMEOUT (the time-out is
+ * reported once; the handle stays usable).  0 turns it off (the default).  A
+ * test of the time-out paths, which no GPU fault can exercise on a shared
+ * machine; the paper has no counterpart.  The persistent apply's switch is a
+ * device variable of the CURRENT device, read at run time (so recorded solve
+ * graphs follow it).  Returns HS_OK, or an error when no CUDA device is
+ * present. */
 int hs_test_wait_probe(int32_t on);
 
 /* hs_last_error: message of the last failing call on this thread. */

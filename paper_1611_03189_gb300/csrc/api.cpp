@@ -448,8 +448,12 @@ int hs_abi_sizes(int64_t *sizes, int32_t cap) {
 }
 
 int hs_test_wait_probe(int32_t on) {
-  hs::set_wait_probe(on != 0);
-  return HS_OK;
+  return hs::guarded([&]() -> int {
+    hs::set_wait_probe(on != 0);
+    hs::require_device();
+    hs::set_apply_probe(on != 0);
+    return HS_OK;
+  });
 }
 
 int hs_profile_phases(int32_t on) {

@@ -314,15 +314,16 @@ struct CholBatch {
 };
 
 // Largest super node whose truncation uses the shared-memory Jacobi kernel
-// (default 64: above that the tridiagonal path needs far fewer operations than
-// the ~10 Jacobi sweeps); larger ones use the tridiagonal path.
+// (default 32: above that the tridiagonal path needs fewer operations than
+// the ~10 Jacobi sweeps, and on the 512 x 512 workload it took less time);
+// larger ones use the tridiagonal path.
 // HS_EIG_SMALL_MAX (environment) lowers the limit, which lets small test
 // problems exercise the tridiagonal path.
 template <typename T>
 int eig_small_max() {
   static const int v = [] {
     const char *e = std::getenv("HS_EIG_SMALL_MAX");
-    const int cap = std::min(64, jacobi_cap<T>());
+    const int cap = std::min(32, jacobi_cap<T>());
     if (!e) return cap;
     const int x = std::atoi(e);
     return x < 0 ? cap : std::min(x, cap);
@@ -330,10 +331,6 @@ int eig_small_max() {
   return v;
 }
 
-// Smallest super node whose truncation takes the multi-CTA path (tridiagonal
-// steps spread over the GPU, reflector products by batches of columns); below
-// it one CTA per node does everything.  HS_GRID_TRIDIAG_MIN (environment)
-// moves the limit, which lets small test problems exercise the path.
 std::atomic<int> g_phase_prof{0};
 bool phase_profiling() { return g_phase_prof.load() != 0; }
 
@@ -347,11 +344,16 @@ inline bool tri_cluster_enabled() {
   return v;
 }
 
+// Smallest super node whose truncation takes the multi-CTA path (cluster or
+// step-kernel tridiagonalisation, eigenvectors of T for the whole wave,
+// reflector products by batches of columns); below it one CTA per node does
+// everything (default 64).  HS_GRID_TRIDIAG_MIN (environment) moves the
+// limit, which lets small test problems exercise the path.
 inline int grid_tridiag_min() {
   static const int v = [] {
     const char *e = std::getenv("HS_GRID_TRIDIAG_MIN");
     const int x = e ? std::atoi(e) : 0;
-    return x > 3 ? x : 128;
+    return x > 3 ? x : 64;
   }();
   return v;
 }
@@ -1738,13 +1740,15 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       // thousands of nodes); the host then builds the Schur targets and the
       // new blocks (wave_d) while the GPU runs the last chunk.  Tasks of
       // different nodes are independent, and a task's arithmetic does not
-      // depend on its chunk.
-      constexpr size_t kChunk = 512;
+      // depend on its chunk.  The first chunk is small: the GPU is idle from
+      // the rank read until its launches arrive.
+      size_t chunk = 64;
       bool more = true;
       while (more) {
         more = false;
         for (Run<T> *r : wp)
-          if (r->ok() && r->wave_c(B, kChunk)) more = true;
+          if (r->ok() && r->wave_c(B, chunk)) more = true;
+        chunk = 512;
         ex.begin(7);
         ex.gemm(B.g1);
         ex.gemm(B.g2);

@@ -204,7 +204,10 @@ int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int ma
 void apply_static(FactorHandle &h, const double *r, double *z, int nrhs, int64_t ld, cudaStream_t st);
 // after a factorization: the persistent apply's step list and waves to the device
 void apply_prepare(FactorHandle &h, cudaStream_t st);
-// 1 if a grid barrier of the persistent apply ran out (synchronous read)
+// 1 if a grid barrier of the persistent apply ran out (synchronous read; the
+// flag is cleared, so a time-out is reported once)
 int apply_error(FactorHandle &h);
+// the persistent apply's time-out probe on the current device (hs_test_wait_probe)
+void set_apply_probe(bool on);
 
 }  // namespace hs

@@ -7,16 +7,22 @@
 // whole vector p), and at a few microseconds per launch the m - 2 steps of a
 // node of a few hundred unknowns are launch-bound.  Here the whole m x m
 // matrix stays in shared memory for all steps: the C CTAs of a cluster each
-// hold a slab of ceil(m / C) rows, and the steps synchronise with cluster
-// barriers instead of kernel boundaries (a node that fits one CTA's shared
-// memory runs alone in one CTA, tri_cta below).  Step k:
-//   1. every CTA copies row k (= column k, J symmetric) from its owner's slab
-//      through distributed shared memory, and forms the reflector
-//      I - tau v v^T of x = J[k+1.., k] (the same FP64 scalars in every CTA);
-//   2. p_i = tau sum_j J_ij v_j for its own rows, and its share of p.v;
+// hold a slab of ceil(m / C) columns (all rows), and the steps synchronise
+// with cluster barriers instead of kernel boundaries (a node that fits one
+// CTA's shared memory runs alone in one CTA, tri_cta below).  J is symmetric,
+// so every product is a column walk: thread i owns column i (with up to four
+// threads splitting its rows), consecutive threads on consecutive words.
+// Step k:
+//   1. every CTA copies column k (= row k) from its owner's slab through
+//      distributed shared memory, and forms the reflector I - tau v v^T of
+//      x = J[k+1.., k] (the same FP64 scalars in every CTA);
+//   2. p_i = tau sum_j J_ji v_j for its own columns, and its share of p.v;
 //   3. cluster barrier; K = tau (p.v) / 2 from the CTAs' shares in rank order,
-//      w_j = p_j - K v_j with p_j read from the owner of row j;
-//   4. J_ij -= v_i w_j + w_i v_j on its own rows; cluster barrier.
+//      w_j = p_j - K v_j with p_j read from the owner of column j;
+//   4. J_ji -= v_j w_i + w_j v_i on its own columns.
+// Step 4 is deferred into steps 1 and 2 of the next step (the column read in
+// step 1 gets it on the fly, the rest in the same walk as step 2), which
+// leaves one walk of the slab and one cluster barrier per step.
 // Outputs are those of the step kernels: d, e (FP64) and tau, reflector k in
 // global row k of A (v[0] = 1 implicit, v[1..] at A[k][k+2..]), the trailing
 // 2 x 2 block in A, so the eigenvalue and eigenvector kernels that follow are
@@ -60,11 +66,31 @@ __device__ T cl_bsum(T v, T *red) {
   return r;
 }
 
+// threads per owned column in the cluster kernel (1 .. 4)
+__host__ __device__ inline int cl_tpc(int R, int nt) {
+  const int q = R > 0 ? nt / R : 1;
+  return q < 1 ? 1 : q > 4 ? 4 : q;
+}
+
 template <typename T>
 __host__ __device__ inline size_t cl_smem_bytes(int m, int C) {
-  if (C == 1) return sizeof(T) * ((size_t)m * (m | 1) + 2 * (size_t)m + 40);
+  if (C == 1) return sizeof(T) * ((size_t)m * (m | 1) + 4 * (size_t)m + 64);
   const int R = (m + C - 1) / C;
-  return sizeof(T) * ((size_t)R * m + 3 * (size_t)m + R + 48);
+  return sizeof(T) * ((size_t)R * m + 5 * (size_t)m + (size_t)R * (2 + cl_tpc(R, kClThreads)) + 72);
+}
+
+// Block sum with one barrier: each warp's partial goes to red[warp], and every
+// thread adds the partials in warp order (the same total in every thread).
+// Calls must alternate between two red buffers, so that a buffer is written
+// again only after a barrier that follows every read of it.
+template <typename T>
+__device__ __forceinline__ T cta_sum(T v, T *red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = red[0];
+  for (int q = 1; q < (int)(blockDim.x >> 5); ++q) s += red[q];
+  return s;
 }
 
 // One CTA holds the whole m x m matrix (ld = m | 1, odd, so that the column
@@ -72,25 +98,40 @@ __host__ __device__ inline size_t cl_smem_bytes(int m, int C) {
 // symmetry of the trailing block, p_i = tau sum_j J_ji v_j and the rank-2
 // update are column walks: thread i owns column i and loops over the rows,
 // consecutive threads on consecutive words (no per-row warp reductions).
+// The rank-2 update of step k is applied lazily: row k + 1 first (it gives
+// the next reflector), then the rest of the trailing block in the same pass
+// that forms the next p, so each step walks the trailing block once.  The
+// updated values are those of applying it at once (same expression).
 template <typename T>
 __device__ void tri_cta(const GridTri<T> &t, unsigned char *smem_raw) {
   const int m = t.m;
   const int ld = m | 1;
   const int tid = threadIdx.x, nt = blockDim.x;
   T *W = reinterpret_cast<T *>(smem_raw);   // m x ld
-  T *v = W + (size_t)m * ld;
+  T *vp = W + (size_t)m * ld;                // pending update (v, w) of the previous step
+  T *wp = vp + m;
+  T *v = wp + m;                             // this step's reflector and w
   T *w = v + m;
-  T *red = w + m;                            // 33 T
+  T *red0 = w + m;                           // two reduction buffers of 32 T
+  T *red1 = red0 + 32;
   for (int64_t q = tid; q < (int64_t)m * m; q += nt) {
     const int i = (int)(q / m), j = (int)(q % m);
     W[(size_t)i * ld + j] = t.A[q];
   }
+  for (int j = tid; j < m; j += nt) vp[j] = wp[j] = T(0);
   __syncthreads();
   for (int k = 0; k + 2 < m; ++k) {
-    const T *rowk = W + (size_t)k * ld;        // row k = column k
+    T *rowk = W + (size_t)k * ld;              // row k = column k
+    // the pending update on row k (columns >= k), and the norm of its tail
+    const T vk = vp[k], wk = wp[k];
+    if (tid == 0) rowk[k] = fma(-vk, wp[k], fma(-wk, vp[k], rowk[k]));
     T s2t = T(0);
-    for (int j = k + 1 + tid; j < m; j += nt) s2t = fma(rowk[j], rowk[j], s2t);
-    const double xn2 = (double)cl_bsum<T>(s2t, red);
+    for (int j = k + 1 + tid; j < m; j += nt) {
+      const T a = fma(-vk, wp[j], fma(-wk, vp[j], rowk[j]));
+      rowk[j] = a;
+      s2t = fma(a, a, s2t);
+    }
+    const double xn2 = (double)cta_sum<T>(s2t, red0);   // barrier: row k complete
     const double alpha = (double)rowk[k + 1];
     const double sig = xn2 - alpha * alpha;
     double tau = 0.0, beta = alpha, scale = 0.0;
@@ -111,40 +152,54 @@ __device__ void tri_cta(const GridTri<T> &t, unsigned char *smem_raw) {
       t.tau[k] = tau_t;
     }
     __syncthreads();
-    if (tau == 0.0) continue;
-    // p_i = tau sum_j J_ji v_j, thread per column, four partial sums
+    // one walk of each trailing column i > k: the pending update of rows
+    // j > k, then p_i = tau sum_j J_ji v_j (tau = 0 gives p = w = 0, an
+    // update that changes nothing)
     T pvt = T(0);
     for (int i = k + 1 + tid; i < m; i += nt) {
-      const T *col = W + i;
+      T *col = W + i;
+      const T vi = vp[i], wi = wp[i];
       T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
       int j = k + 1;
       for (; j + 3 < m; j += 4) {
-        a0 = fma(col[(size_t)j * ld], v[j], a0);
-        a1 = fma(col[(size_t)(j + 1) * ld], v[j + 1], a1);
-        a2 = fma(col[(size_t)(j + 2) * ld], v[j + 2], a2);
-        a3 = fma(col[(size_t)(j + 3) * ld], v[j + 3], a3);
+        const T x0 = fma(-vp[j], wi, fma(-wp[j], vi, col[(size_t)j * ld]));
+        const T x1 = fma(-vp[j + 1], wi, fma(-wp[j + 1], vi, col[(size_t)(j + 1) * ld]));
+        const T x2 = fma(-vp[j + 2], wi, fma(-wp[j + 2], vi, col[(size_t)(j + 2) * ld]));
+        const T x3 = fma(-vp[j + 3], wi, fma(-wp[j + 3], vi, col[(size_t)(j + 3) * ld]));
+        col[(size_t)j * ld] = x0;
+        col[(size_t)(j + 1) * ld] = x1;
+        col[(size_t)(j + 2) * ld] = x2;
+        col[(size_t)(j + 3) * ld] = x3;
+        a0 = fma(x0, v[j], a0);
+        a1 = fma(x1, v[j + 1], a1);
+        a2 = fma(x2, v[j + 2], a2);
+        a3 = fma(x3, v[j + 3], a3);
       }
-      for (; j < m; ++j) a0 = fma(col[(size_t)j * ld], v[j], a0);
+      for (; j < m; ++j) {
+        const T x0 = fma(-vp[j], wi, fma(-wp[j], vi, col[(size_t)j * ld]));
+        col[(size_t)j * ld] = x0;
+        a0 = fma(x0, v[j], a0);
+      }
       const T p = tau_t * ((a0 + a1) + (a2 + a3));
       w[i] = p;
       pvt = fma(p, v[i], pvt);
     }
-    const T K = T(0.5) * tau_t * cl_bsum<T>(pvt, red);
+    const T K = T(0.5) * tau_t * cta_sum<T>(pvt, red1);
     for (int i = k + 1 + tid; i < m; i += nt) w[i] = fma(-K, v[i], w[i]);
     __syncthreads();
-    // J_ji -= v_j w_i + w_j v_i, thread per column
-    for (int i = k + 1 + tid; i < m; i += nt) {
-      T *col = W + i;
-      const T vi = v[i], wi = w[i];
-      for (int j = k + 1; j < m; ++j) {
-        T &a = col[(size_t)j * ld];
-        a = fma(-v[j], wi, fma(-w[j], vi, a));
-      }
-    }
-    __syncthreads();
+    T *x = vp;   // this step's (v, w) become the pending update
+    vp = v;
+    v = x;
+    x = wp;
+    wp = w;
+    w = x;
   }
+  // the last pending update on the trailing 2 x 2 block, which is written out
   for (int i = max(m - 2, 0) + tid; i < m; i += nt)
-    for (int j = m - 2; j <= i; ++j) t.A[(int64_t)i * m + j] = W[(size_t)i * ld + j];
+    for (int j = m - 2; j <= i; ++j) {
+      const T a = fma(-vp[i], wp[j], fma(-wp[i], vp[j], W[(size_t)i * ld + j]));
+      t.A[(int64_t)i * m + j] = a;
+    }
 }
 
 template <typename T, int C>
@@ -159,29 +214,47 @@ __global__ void __launch_bounds__(kClThreads) k_tri_cluster(const GridTri<T> *__
   const GridTri<T> t = tasks[blockIdx.x / C];
   const int m = t.m;
   const int R = (m + C - 1) / C;
-  const int r0 = crank * R, r1 = min(m, r0 + R);
+  const int c0 = crank * R, c1 = min(m, c0 + R);
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-  T *slab = reinterpret_cast<T *>(smem_raw);   // rows r0 .. r1-1, ld m
-  T *xrow = slab + (size_t)R * m;              // row k of J, columns k..
-  T *v = xrow + m;                             // reflector
-  T *w = v + m;                                // w = p - K v
-  T *pseg = w + m;                             // p on the own rows
-  T *red = pseg + R;                           // 33 T of reduction scratch, then the share of p.v
-  T *pvpart = red + 40;
+  const int tpc = cl_tpc(R, nt);               // threads per column
+  const int ci = tid % R, part = tid / R;      // own column c0 + ci, rows j = part (mod tpc)
+  T *slab = reinterpret_cast<T *>(smem_raw);   // columns c0 .. c1-1 of J, all rows: slab[j R + (i - c0)]
+  T *x = slab + (size_t)m * R;                 // column k of J, rows k..
+  T *vp = x + m;                               // pending update (v, w) of the previous step
+  T *wp = vp + m;
+  T *v = wp + m;                               // this step's reflector and w
+  T *w = v + m;
+  T *pseg = w + m;                             // p on the own columns, two buffers (step parity)
+  T *psum = pseg + 2 * (size_t)R;              // tpc partial sums per own column
+  T *red0 = psum + (size_t)R * tpc;            // two reduction buffers of 32 T
+  T *red1 = red0 + 32;
+  T *pvpart = red1 + 32;                       // this CTA's share of p.v, two buffers
 
-  for (int64_t q = tid; q < (int64_t)(r1 - r0) * m; q += nt) slab[q] = t.A[(int64_t)r0 * m + q];
+  for (int64_t q = tid; q < (int64_t)m * R; q += nt) {
+    const int j = (int)(q / R), i = c0 + (int)(q % R);
+    slab[q] = i < c1 ? t.A[(int64_t)j * m + i] : T(0);
+  }
+  for (int j = tid; j < m; j += nt) vp[j] = wp[j] = T(0);
   cluster.sync();
 
+  // The rank-2 update of step k is applied lazily, as in tri_cta: to column
+  // k + 1 as it is read from its owner, and to the rest of the own columns in
+  // the pass that forms the next p.  One cluster barrier per step: p and the
+  // share of p.v are double-buffered, so a CTA that runs ahead never
+  // overwrites what a slower one still reads, and the column a step reads is
+  // not written in that step.
   for (int k = 0; k + 2 < m; ++k) {
     const int owner = k / R;
-    const T *srow = cluster.map_shared_rank(slab, owner) + (size_t)(k - owner * R) * m;
-    for (int j = k + tid; j < m; j += nt) xrow[j] = srow[j];
-    __syncthreads();
+    const T *ocol = cluster.map_shared_rank(slab, owner) + (k - owner * R);
+    const T vk = vp[k], wk = wp[k];
     T s2t = T(0);
-    for (int j = k + 1 + tid; j < m; j += nt) s2t = fma(xrow[j], xrow[j], s2t);
-    const double xn2 = (double)cl_bsum<T>(s2t, red);
-    const double alpha = (double)xrow[k + 1];
+    for (int j = k + tid; j < m; j += nt) {
+      const T a = fma(-vp[j], wk, fma(-wp[j], vk, ocol[(size_t)j * R]));
+      x[j] = a;
+      if (j > k) s2t = fma(a, a, s2t);
+    }
+    const double xn2 = (double)cta_sum<T>(s2t, red0);   // barrier: x complete
+    const double alpha = (double)x[k + 1];
     const double sig = xn2 - alpha * alpha;
     double tau = 0.0, beta = alpha, scale = 0.0;
     if (sig > 0.0) {
@@ -191,60 +264,76 @@ __global__ void __launch_bounds__(kClThreads) k_tri_cluster(const GridTri<T> *__
     }
     const T scale_t = (T)scale, tau_t = (T)tau;
     for (int j = k + 1 + tid; j < m; j += nt) {
-      const T vj = (j == k + 1) ? T(1) : xrow[j] * scale_t;
+      const T vj = (j == k + 1) ? T(1) : x[j] * scale_t;
       v[j] = vj;
       if (crank == owner && j >= k + 2) t.A[(int64_t)k * m + j] = vj;   // reflector k in global row k
     }
     if (crank == owner && tid == 0) {
-      t.d[k] = (double)xrow[k];
+      t.d[k] = (double)x[k];
       t.e[k] = beta;
       t.tau[k] = tau_t;
     }
     __syncthreads();
-    if (tau == 0.0) continue;   // the same decision in every CTA: no update, no barrier
-    // p_i = tau J_i v on the own rows i > k, one warp per row
-    const int i0 = max(r0, k + 1);
-    for (int i = i0 + warp; i < r1; i += nw) {
-      const T *row = slab + (size_t)(i - r0) * m;
-      T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-      int j = k + 1 + lane;
-      for (; j + 96 < m; j += 128) {
-        a0 = fma(row[j], v[j], a0);
-        a1 = fma(row[j + 32], v[j + 32], a1);
-        a2 = fma(row[j + 64], v[j + 64], a2);
-        a3 = fma(row[j + 96], v[j + 96], a3);
+    // the own columns i > k: pending update of rows j > k, then
+    // p_i = tau sum_j J_ji v_j (rows split over tpc threads per column)
+    T *pk = pseg + (k & 1) * R;
+    const int i = c0 + ci;
+    const bool mine = part < tpc && i < c1 && i > k;
+    if (mine) {
+      const T vi = vp[i], wi = wp[i];
+      T a0 = T(0), a1 = T(0);
+      int j = k + 1 + part;
+      for (; j + tpc < m; j += 2 * tpc) {
+        T *s0 = slab + (size_t)j * R + ci;
+        T *s1 = slab + (size_t)(j + tpc) * R + ci;
+        const T x0 = fma(-vp[j], wi, fma(-wp[j], vi, *s0));
+        const T x1 = fma(-vp[j + tpc], wi, fma(-wp[j + tpc], vi, *s1));
+        *s0 = x0;
+        *s1 = x1;
+        a0 = fma(x0, v[j], a0);
+        a1 = fma(x1, v[j + tpc], a1);
       }
-      for (; j < m; j += 32) a0 = fma(row[j], v[j], a0);
-      T acc = (a0 + a1) + (a2 + a3);
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) pseg[i - r0] = tau_t * acc;
+      if (j < m) {
+        T *s0 = slab + (size_t)j * R + ci;
+        const T x0 = fma(-vp[j], wi, fma(-wp[j], vi, *s0));
+        *s0 = x0;
+        a0 = fma(x0, v[j], a0);
+      }
+      psum[part * R + ci] = a0 + a1;
     }
     __syncthreads();
     T pvt = T(0);
-    for (int i = i0 + tid; i < r1; i += nt) pvt = fma(pseg[i - r0], v[i], pvt);
-    const T pv_own = cl_bsum<T>(pvt, red);
-    if (tid == 0) *pvpart = pv_own;
-    cluster.sync();   // every CTA's p and share of p.v are visible
+    if (part == 0 && i < c1 && i > k) {
+      T acc = T(0);
+      for (int q = 0; q < tpc; ++q) acc += psum[q * R + ci];
+      const T p = tau_t * acc;
+      pk[ci] = p;
+      pvt = p * v[i];
+    }
+    const T pv_own = cta_sum<T>(pvt, red1);
+    if (tid == 0) pvpart[k & 1] = pv_own;
+    cluster.sync();   // every CTA's p and share of p.v are visible; every pass of step k is done
     T pv = T(0);
-    for (int c = 0; c < C; ++c) pv += *cluster.map_shared_rank(pvpart, c);
+    for (int c = 0; c < C; ++c) pv += cluster.map_shared_rank(pvpart, c)[k & 1];
     const T K = T(0.5) * tau_t * pv;
     for (int j = k + 1 + tid; j < m; j += nt) {
       const int oj = j / R;
-      const T pj = cluster.map_shared_rank(pseg, oj)[j - oj * R];
+      const T pj = cluster.map_shared_rank(pseg, oj)[(k & 1) * R + j - oj * R];
       w[j] = fma(-K, v[j], pj);
     }
     __syncthreads();
-    // J_ij -= v_i w_j + w_i v_j on the own rows i > k, one warp per row
-    for (int i = i0 + warp; i < r1; i += nw) {
-      T *row = slab + (size_t)(i - r0) * m;
-      const T vi = v[i], wi = w[i];
-      for (int j = k + 1 + lane; j < m; j += 32) row[j] = fma(-vi, w[j], fma(-wi, v[j], row[j]));
-    }
-    cluster.sync();   // the update is complete before the next row is read
+    T *y = vp;   // this step's (v, w) become the pending update
+    vp = v;
+    v = y;
+    y = wp;
+    wp = w;
+    w = y;
   }
-  // the trailing 2 x 2 block (read back by the eigenvalue kernel)
-  for (int i = max(r0, m - 2) + tid; i < r1; i += nt)
-    for (int j = m - 2; j <= i; ++j) t.A[(int64_t)i * m + j] = slab[(size_t)(i - r0) * m + j];
+  // the last pending update on the trailing 2 x 2 block, lower triangle,
+  // written out by the owners of its columns
+  for (int j = max(c0, m - 2) + tid; j < c1; j += nt)
+    for (int i = j; i < m; ++i)
+      t.A[(int64_t)i * m + j] = fma(-vp[i], wp[j], fma(-wp[i], vp[j], slab[(size_t)i * R + (j - c0)]));
   // no CTA may leave while others still read its shared memory
   cluster.sync();
 }
@@ -316,7 +405,8 @@ int tri_cluster_max_m(int C) {
       if (c == 8) lim = allow_max_dynamic_smem<&k_tri_cluster<T, 8>>(), ok = cluster_fits<T, 8>(lim);
       int mm = 0;
       if (ok)
-        while (cl_smem_bytes<T>(mm + 1, c) <= (size_t)lim) ++mm;
+        // (several CTAs: at most one owned column per thread)
+        while (cl_smem_bytes<T>(mm + 1, c) <= (size_t)lim && (c == 1 || (mm + c) / c <= kClThreads)) ++mm;
       table[dev][q] = mm;
     }
     ready[dev] = true;
@@ -327,15 +417,13 @@ int tri_cluster_max_m(int C) {
 
 }  // namespace
 
-// Clusters of several CTAs pay two cluster barriers and three rounds of
-// distributed-shared-memory reads per step; on the 2D workloads they were
-// slower than the step kernels, so only one-CTA nodes take this path unless
-// HS_TRI_CLUSTER=2 (environment) allows up to eight CTAs.
+// The smallest cluster (1, 2, 4 or 8 CTAs) whose slabs fit; larger nodes take
+// the step kernels.  HS_TRI_CLUSTER=1 (environment) keeps clusters to one CTA.
 template <typename T>
 int tri_cluster_size(int m) {
   static const int cmax = [] {
     const char *e = std::getenv("HS_TRI_CLUSTER");
-    return (e && e[0] == '2') ? 8 : 1;
+    return (e && e[0] == '1') ? 1 : 8;
   }();
   for (int c : {1, 2, 4, 8})
     if (c <= cmax && m <= tri_cluster_max_m<T>(c)) return c;

@@ -191,57 +191,62 @@ __global__ void __launch_bounds__(256) k_sum(const SumTask<T> *__restrict__ task
 constexpr int CHOL_THREADS = 512;
 
 // W (ld m) holds A on entry; on exit the lower triangle holds L^-1 and the
-// strict upper triangle is zero.  Returns 0 or (failing pivot + 1).
+// strict upper triangle is zero.  Returns 0 or (failing pivot + 1).  tmp holds
+// 3m values.
+//
+// Right-looking Cholesky fused with the rows of X = L^-1 by forward
+// substitution: step j forms column j of L and, in the same phase as the
+// trailing update, row j of X,
+//   X_jc = (delta_jc - sum_{p=c..j-1} L_jp X_pc) / L_jj   (c <= j),
+// thread c owning column c of X.  Row j of L is needed only in step j, so row
+// j - 1 of X (kept in tmp until then) replaces it during step j.  Two
+// barriers per step.
 template <typename T>
 __device__ int chol_inv_inplace(T *W, int m, T *tmp, int *flag) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  // right-looking Cholesky on the lower triangle; column j staged in tmp, one
-  // warp per trailing row (lanes over columns, coalesced)
   const int warp0 = tid >> 5, lane0 = tid & 31, nw0 = nt >> 5;
+  T *col = tmp;                  // scaled column j of L
+  T *xr0 = tmp + m, *xr1 = xr0 + m;   // rows j (j even: xr0) and j - 1 of X
+  (void)flag;
   for (int j = 0; j < m; ++j) {
-    if (tid == 0) {
-      const T d = W[j * m + j];
-      if (!(d > T(0)) || !isfinite(d)) {
-        *flag = j + 1;
-      } else {
-        W[j * m + j] = sqrt(d);
-      }
-    }
-    __syncthreads();
-    if (*flag) return *flag;
-    const T djj = W[j * m + j];
+    // every thread reads the pivot (the previous step's update is complete)
+    const T d = W[(size_t)j * m + j];
+    if (!(d > T(0)) || !isfinite(d)) return j + 1;
+    const T djj = sqrt(d);
     for (int i = j + 1 + tid; i < m; i += nt) {
-      const T l = W[i * m + j] / djj;
-      W[i * m + j] = l;
-      tmp[i] = l;
+      const T l = W[(size_t)i * m + j] / djj;
+      W[(size_t)i * m + j] = l;
+      col[i] = l;
     }
     __syncthreads();
+    // trailing update, one warp per row (lanes over columns, coalesced)
     for (int i = j + 1 + warp0; i < m; i += nw0) {
-      const T li = tmp[i];
-      T *row = W + (int64_t)i * m;
-      for (int c = j + 1 + lane0; c <= i; c += 32) row[c] -= li * tmp[c];
+      const T li = col[i];
+      T *row = W + (size_t)i * m;
+      for (int c = j + 1 + lane0; c <= i; c += 32) row[c] -= li * col[c];
+    }
+    // row j of X; row j - 1 of X retires into row j - 1 of W
+    T *xj = (j & 1) ? xr1 : xr0;
+    const T *xprev = (j & 1) ? xr0 : xr1;
+    const T *Lj = W + (size_t)j * m;
+    for (int c = tid; c <= j; c += nt) {
+      T s0 = (c == j) ? T(1) : T(0), s1 = T(0);
+      int p = c;
+      for (; p + 2 < j; p += 2) {
+        s0 = fma(-Lj[p], W[(size_t)p * m + c], s0);
+        s1 = fma(-Lj[p + 1], W[(size_t)(p + 1) * m + c], s1);
+      }
+      if (p + 1 < j) s0 = fma(-Lj[p], W[(size_t)p * m + c], s0);
+      if (c + 1 <= j) s1 = fma(-Lj[j - 1], xprev[c], s1);
+      xj[c] = (s0 + s1) / djj;
+      if (c + 1 <= j) W[(size_t)(j - 1) * m + c] = xprev[c];
     }
     __syncthreads();
   }
-  // in-place inverse of the lower-triangular factor, column j from the last
-  // one down: Linv[i][j] = -(sum_{p=j+1..i} Linv[i][p] L[p][j]) / L[j][j],
-  // with the columns right of j already inverted.  Column j of L is staged in
-  // tmp; one warp per entry i.
-  const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-  for (int j = m - 1; j >= 0; --j) {
-    for (int p = j + 1 + tid; p < m; p += nt) tmp[p] = W[p * m + j];
-    __syncthreads();
-    const T inv = T(1) / W[j * m + j];
-    for (int i = j + 1 + warp; i < m; i += nw) {
-      T s = T(0);
-      for (int p = j + 1 + lane; p <= i; p += 32) s = fma(W[i * m + p], tmp[p], s);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) W[i * m + j] = -s * inv;
-    }
-    __syncthreads();
-    if (tid == 0) W[j * m + j] = inv;
-    __syncthreads();
-  }
+  // the last row of X, and zeros above the diagonal
+  const T *xlast = ((m - 1) & 1) ? xr1 : xr0;
+  for (int c = tid; c < m; c += nt) W[(size_t)(m - 1) * m + c] = xlast[c];
+  __syncthreads();
   for (int64_t e = tid; e < (int64_t)m * m; e += nt) {
     const int i = (int)(e / m), c = (int)(e % m);
     if (c > i) W[e] = T(0);
@@ -669,11 +674,11 @@ void launch_chol_inv(const CholTask<T> *d_tasks, int ntasks, int *d_status, int 
                      cudaStream_t st) {
   if (ntasks == 0) return;
   if (max_m <= chol_smem_cap<T>()) {
-    const size_t sm = sizeof(T) * ((size_t)max_m * max_m + max_m + 8);
+    const size_t sm = sizeof(T) * ((size_t)max_m * max_m + 3 * (size_t)max_m + 8);
     check_dynamic_smem(sm, allow_max_dynamic_smem<&k_chol_inv<T, true>>(), "k_chol_inv");
     k_chol_inv<T, true><<<ntasks, CHOL_THREADS, sm, st>>>(d_tasks, d_status);
   } else {
-    const size_t sm = sizeof(T) * ((size_t)max_m + 8);
+    const size_t sm = sizeof(T) * (3 * (size_t)max_m + 8);
     check_dynamic_smem(sm, allow_max_dynamic_smem<&k_chol_inv<T, false>>(), "k_chol_inv");
     k_chol_inv<T, false><<<ntasks, CHOL_THREADS, sm, st>>>(d_tasks, d_status);
   }

@@ -12,7 +12,7 @@
 // as a_hi b_hi + a_hi b_lo + a_lo b_hi (three MMAs), which keeps about the
 // accuracy of FP32 operands.
 //
-// One CTA of 128 threads computes one 128 x BN tile of one task (tasks of any
+// One CTA of 256 threads computes one 128 x BN tile of one task (tasks of any
 // size, leading dimension and transpose; a tile list is walked by a binary
 // search of tile_start as in the SIMT kernel):
 //   - every thread stages its share of the next K slice (128 bytes of K per
@@ -28,8 +28,9 @@
 //     after the tensor core has read it, and the loads of slice s + 1 overlap
 //     the MMAs of slice s (STAGES slices in flight);
 //   - the epilogue reads the 128 x BN FP32 accumulator from TMEM (tcgen05.ld;
-//     warp w owns TMEM lanes, i.e. tile rows, 32w .. 32w + 31), stages it in
-//     shared memory and writes C row by row (coalesced) with alpha and beta.
+//     warp w reads TMEM lanes, i.e. tile rows, 32 (w % 4) .. + 31 and half
+//     w / 4 of the columns), stages it in shared memory and writes C row by
+//     row (coalesced) with alpha and beta.
 // Every wait on an mbarrier is bounded (wait_cycles SM clocks, by default
 // about one second).  On time-out the CTA stores 1 in *err, waits once more
 // (with the default bound) for its tensor-core work, frees its TMEM and
@@ -50,7 +51,7 @@ namespace hs {
 
 namespace {
 
-constexpr int TC_THREADS = 128;
+constexpr int TC_THREADS = 256;     // 8 warps: more loads in flight per CTA
 // hs_test_wait_probe: when set, every launch first waits on a barrier that
 // nothing arrives at (a test of the bounded wait's time-out path)
 std::atomic<int> g_wait_probe{0};
@@ -209,8 +210,10 @@ __device__ __forceinline__ int find_tile_task(const int *tile_start, int ntasks,
 template <int KIND, int NR>
 struct Slice {
   static constexpr int EPC = TcPrec<KIND>::epc;
-  static constexpr int PER = NR * 8 / TC_THREADS;
-  float v[PER * EPC];
+  static constexpr int PER = NR * 8 / TC_THREADS;                 // K-contiguous: chunks per thread
+  static constexpr int NQT = (2 * NR + TC_THREADS - 1) / TC_THREADS;   // rows contiguous: quads per thread
+  static constexpr int SIZE = PER * EPC > NQT * 4 * EPC ? PER * EPC : NQT * 4 * EPC;
+  float v[SIZE];
 };
 
 // Load rows [r0, r0 + NR) x K elements [k0, k0 + 8 EPC) of an operand X(row, k)
@@ -255,10 +258,11 @@ __device__ __forceinline__ void load_slice(Slice<KIND, NR> &sl, const float *__r
       }
     }
   } else {
-    constexpr int NQ = NR / 4;
+    constexpr int NQ = NR / 4, NQT = Slice<KIND, NR>::NQT;
 #pragma unroll
-    for (int qq = 0; qq < PER / 4; ++qq) {
+    for (int qq = 0; qq < NQT; ++qq) {
       const int d = threadIdx.x + TC_THREADS * qq;
+      if (d >= NQ * 8) break;   // fewer quads than threads (narrow tiles)
       const int rq = d % NQ, kc = d / NQ;
       const int row = r0 + 4 * rq;
       float *v = sl.v + qq * 4 * EPC;
@@ -327,19 +331,34 @@ __device__ __forceinline__ void store_slice(unsigned char *dst, unsigned char *d
       if (KIND == HS_TC_TF32X3) *reinterpret_cast<uint4 *>(dst_lo + off) = lo;
     }
   } else {
-    constexpr int NQ = NR / 4;
+    constexpr int NQ = NR / 4, NQT = Slice<KIND, NR>::NQT;
 #pragma unroll
-    for (int qq = 0; qq < PER / 4; ++qq) {
+    for (int qq = 0; qq < NQT; ++qq) {
       const int d = threadIdx.x + TC_THREADS * qq;
+      if (d >= NQ * 8) break;
       const int rq = d % NQ, kc = d / NQ;
+      uint4 w[4], lo[4];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < 4; ++r) make_chunk<KIND>(sl.v + qq * 4 * EPC + r * EPC, w[r], lo[r]);
+      // the quad's rows in an order rotated by rq / 2, so that the eight
+      // lanes of a store phase write eight different 16-byte bank groups
+      // (chunks picked by selects: a run-time register index would put the
+      // slice in local memory)
+      const int rot = (rq >> 1) & 3;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = (j + rot) & 3;
+        uint4 x = w[0], y = lo[0];
+#pragma unroll
+        for (int i = 1; i < 4; ++i)
+          if (r == i) {
+            x = w[i];
+            y = lo[i];
+          }
         const int row = 4 * rq + r;
-        uint4 w, lo;
-        make_chunk<KIND>(sl.v + qq * 4 * EPC + r * EPC, w, lo);
         const int off = (row >> 3) * 1024 + kc * 128 + (row & 7) * 16;
-        *reinterpret_cast<uint4 *>(dst + off) = w;
-        if (KIND == HS_TC_TF32X3) *reinterpret_cast<uint4 *>(dst_lo + off) = lo;
+        *reinterpret_cast<uint4 *>(dst + off) = x;
+        if (KIND == HS_TC_TF32X3) *reinterpret_cast<uint4 *>(dst_lo + off) = y;
       }
     }
   }
@@ -474,12 +493,14 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const GemmTask<float> *_
   const bool ok = *flag == 0;
   if (ok) {
     float *cs = reinterpret_cast<float *>(smem);   // 128 x (BN + 1), over the stage buffers
-    const int r = warp * 32 + lane;
+    // warp w reads TMEM lanes (rows) 32 (w % 4) .. + 31, columns of half w / 4
+    const int q4 = warp & 3, half = warp >> 2;
+    const int r = q4 * 32 + lane;
 #pragma unroll 1
-    for (int c = 0; c < BN; c += 16) {
+    for (int c = half * (BN / 2); c < (half + 1) * (BN / 2); c += 16) {
       uint32_t v[16];
       if (nk > 0) {
-        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+        tmem_ld16(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)c, v);
       } else {
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = 0u;

@@ -298,9 +298,9 @@ __global__ void __launch_bounds__(AT) k_root(const T *__restrict__ Ainv, int m, 
 // workload); here every CTA of a grid sized to be resident walks the step
 // list (forward f1, f2 per wave; root copy and solve; backward b1, b2 per
 // wave in reverse), the warps of the grid sharing each step's virtual warps,
-// with a grid-wide barrier between dependent steps.  The barrier is a counter
-// and a generation word; its wait is bounded (clock cycles) and a wait that
-// runs out sets *err and ends the kernel (the host reports HS_ERR_TIMEOUT).
+// with a grid-wide barrier between dependent steps.  The barrier is one
+// arrival counter; its wait is bounded (clock cycles) and a wait that runs
+// out sets *err and ends the kernel (the host reports HS_ERR_TIMEOUT).
 // The steps and their arithmetic are those of the per-step kernels, so the
 // result is the same bit for bit.
 // ---------------------------------------------------------------------------
@@ -311,30 +311,39 @@ struct ApplyStepDev {
   int wave;          // index into the waves (f1, f2, b1, b2)
 };
 
-__device__ bool grid_barrier(unsigned *bar, int *err, long long limit) {
+// Grid barrier number `round` (0, 1, ...): one counter that only grows; CTA
+// thread 0 adds 1 with release semantics and waits, with acquire loads, until
+// all CTAs of this and every earlier round have arrived.  The counter is
+// cleared on the stream before each launch.
+__device__ __forceinline__ unsigned atom_add_release_gpu(unsigned *p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// hs_test_wait_probe's switch for the persistent apply, per device
+__device__ int g_apply_probe = 0;
+
+__device__ bool grid_barrier(unsigned *bar, unsigned round, int *err, long long limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    volatile unsigned *gen = bar + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-    if (arrived == gridDim.x) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*gen == g) {
-        if (clock64() - t0 > limit) {
-          atomicExch(err, 1);
-          ok = 0;
-          break;
-        }
+    const unsigned target = (round + 1u) * gridDim.x;
+    atom_add_release_gpu(bar, 1u);
+    const long long t0 = clock64();
+    while (ld_acquire_gpu(bar) < target) {
+      if (clock64() - t0 > limit) {
+        atomicExch(err, 1);
+        ok = 0;
+        break;
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
@@ -350,6 +359,9 @@ __global__ void __launch_bounds__(AT) k_apply_persistent(
     long long limit) {
   const int lane = threadIdx.x & 31;
   const int gw = blockIdx.x * AW + (threadIdx.x >> 5), nwarps = gridDim.x * AW;
+  // test of the time-out path: a barrier round no launch can complete (the
+  // switch is read at run time, so recorded graphs follow it too)
+  if (g_apply_probe && !grid_barrier(bar, 1u << 20, err, limit)) return;
   for (int si = 0; si < nsteps; ++si) {
     const ApplyStepDev st = steps[si];
     if (st.kind == AS_COPY) {
@@ -374,7 +386,7 @@ __global__ void __launch_bounds__(AT) k_apply_persistent(
           b2_warp<T, NR>(nodes, wa.node_first, wa.node_count, w, lane, ws, tb, tb2, nrhs, j0);
       }
     }
-    if (si + 1 < nsteps && !grid_barrier(bar, err, limit)) return;
+    if (si + 1 < nsteps && !grid_barrier(bar, (unsigned)si, err, limit)) return;
   }
 }
 
@@ -665,14 +677,23 @@ void apply_waves_nr(const FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, int j
   HS_CUDA(cudaGetLastError());
 }
 
-// whether the apply runs as one persistent cooperative launch per chunk of
-// right-hand sides (HS_APPLY_PERSISTENT=0 in the environment: per-step launches)
+// The persistent apply is opt-in (HS_APPLY_PERSISTENT=1): on the 512 x 512
+// workload its grid barriers cost more than the graph's launch gaps.
+// HS_APPLY_PERSISTENT_BPS (1..4) sets the CTAs per SM.
 bool persistent_apply_enabled() {
   static const bool on = [] {
     const char *e = std::getenv("HS_APPLY_PERSISTENT");
-    return !(e && e[0] == '0');
+    return e && e[0] == '1';
   }();
   return on;
+}
+int persistent_apply_bps() {
+  static const int v = [] {
+    const char *e = std::getenv("HS_APPLY_PERSISTENT_BPS");
+    const int b = e ? std::atoi(e) : 0;
+    return b >= 1 && b <= 4 ? b : 0;
+  }();
+  return v;
 }
 
 // One chunk of right-hand sides [j0, j0 + NR) through the persistent kernel.
@@ -692,12 +713,12 @@ void apply_persistent_nr(const FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, 
     if (!blocks_per_sm[dev]) {
       int b = 0;
       HS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_apply_persistent<T, NR>, AT, 0));
-      blocks_per_sm[dev] = std::max(1, std::min(b, 4));
+      blocks_per_sm[dev] = std::max(1, std::min(b, persistent_apply_bps() ? persistent_apply_bps() : 4));
     }
     bps = blocks_per_sm[dev];
   }
   HS_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  HS_CUDA(cudaMemsetAsync(h.d_apply_bar, 0, 2 * sizeof(unsigned), st));
+  HS_CUDA(cudaMemsetAsync(h.d_apply_bar, 0, sizeof(unsigned), st));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nsm * bps), 1, 1);
   cfg.blockDim = dim3(AT, 1, 1);
@@ -708,7 +729,8 @@ void apply_persistent_nr(const FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  const long long limit = 2000000000LL;   // about one second of SM clocks per barrier
+  // about one second of SM clocks per barrier unless hs_opts.timeout_cycles says otherwise
+  const long long limit = h.timeout_cycles > 0 ? (long long)h.timeout_cycles : 2000000000LL;
   HS_CUDA(cudaLaunchKernelEx(&cfg, k_apply_persistent<T, NR>, (const ApplyStepDev *)h.d_apply_steps,
                              h.apply_nsteps, (const WaveApply *)h.d_waves, (const ApplyNode *)h.d_nodes,
                              (const ApplyNbr *)h.d_nbrs, (const ApplyTarget *)h.d_targets,
@@ -902,10 +924,16 @@ void apply_prepare(FactorHandle &h, cudaStream_t st) {
   }
 }
 
+void set_apply_probe(bool on) {
+  const int v = on ? 1 : 0;
+  HS_CUDA(cudaMemcpyToSymbol(g_apply_probe, &v, sizeof(int)));
+}
+
 int apply_error(FactorHandle &h) {
   if (!h.d_apply_err) return 0;
   int e = 0;
   HS_CUDA(cudaMemcpy(&e, h.d_apply_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) HS_CUDA(cudaMemset(h.d_apply_err, 0, sizeof(int)));   // reported once
   return e;
 }
 

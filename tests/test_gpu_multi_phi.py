@@ -4,9 +4,11 @@ projection (HS_GC_PROJ) on the GPU, against the FP64 oracle on the same inputs.
 Bars as in test_gpu_parity: equal ranks, FP64 apply within 1e-10 relative of
 the oracle, exact preservation A_H^-1 phi_i = phi_i / lambda_i within 1e-11 for
 preserved eigenvectors, FP32 factor within 1e-3 of the oracle.  Every
-truncation path is covered: the shared-memory Jacobi kernel (default for these
-sizes), the one-CTA tridiagonal kernel (HS_EIG_SMALL_MAX=8) and the multi-CTA
-path (also HS_GRID_TRIDIAG_MIN=16), each with U_1 of up to 8 columns.
+truncation path is covered: the shared-memory Jacobi kernel (the default for
+super nodes of up to 32 unknowns; larger ones take the one-CTA tridiagonal
+kernel), the one-CTA tridiagonal kernel for every node (HS_EIG_SMALL_MAX=8) and
+the multi-CTA path (also HS_GRID_TRIDIAG_MIN=16), each with U_1 of up to 8
+columns.
 """
 import os
 import subprocess

@@ -288,7 +288,7 @@ def test_large_super_nodes_match_oracle(name, maker):
 
 @pytest.mark.parametrize("name,maker", TRIDIAG_CASES, ids=[c[0] for c in TRIDIAG_CASES])
 @pytest.mark.parametrize("variant", [H.LORASP, H.GC_CONSTANT])
-@pytest.mark.parametrize("cluster", ["1", "0"], ids=["cluster", "steps"])
+@pytest.mark.parametrize("cluster", ["2", "1", "0"], ids=["cluster", "cta", "steps"])
 def test_multi_cta_truncation_path_matches_oracle(name, maker, variant, cluster):
     """Every super node of 16 or more unknowns through the multi-CTA path
     (the tridiagonalisation in one thread-block cluster per node, or spread
@@ -324,6 +324,56 @@ for eps in (1e-1, 1e-2):
 print('ok')
 """
     env = dict(os.environ, HS_EIG_SMALL_MAX="8", HS_GRID_TRIDIAG_MIN="16", HS_TRI_CLUSTER=cluster)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-3000:]
+
+
+CLUSTER_CASES = [
+    # 8 leaves of 125: super nodes of m = 250 (FP64: 4 CTAs, FP32: 2 CTAs)
+    ("poisson3d 10 leaf125", lambda: P.poisson3d(10, leaf_size=125)),
+    # 8 leaves of 216: m = 432 (FP64: 8 CTAs, FP32: 4 CTAs)
+    ("poisson3d 12 leaf216", lambda: P.poisson3d(12, leaf_size=216)),
+]
+
+
+@pytest.mark.parametrize("name,maker", CLUSTER_CASES, ids=[c[0] for c in CLUSTER_CASES])
+@pytest.mark.parametrize("variant", [H.LORASP, H.GC_CONSTANT])
+def test_cluster_tridiagonalisation_over_several_ctas_matches_oracle(name, maker, variant):
+    """Super nodes too large for one CTA's shared memory through the
+    tridiagonalisation in one thread-block cluster of 2 to 8 CTAs (column
+    slabs in distributed shared memory, HS_TRI_CLUSTER=2): ranks equal to the
+    oracle's, the FP64 apply within 1e-10 element by element, the FP32 apply
+    within 1e-3, and FP32-factor PCG to 1e-10."""
+    import os
+    import subprocess
+    import sys
+
+    need_gpu()
+    here = os.path.dirname(os.path.abspath(__file__))
+    code = f"""
+import sys, numpy as np, torch
+sys.path.insert(0, {os.path.dirname(here)!r})
+sys.path.insert(0, {here!r})
+from gpu_util import elem, gpu_factor, oracle_factor
+from oracle import hsolver as H
+import test_gpu_parity as T
+pb = [c for c in T.CLUSTER_CASES if c[0] == {name!r}][0][1]()
+F = oracle_factor(pb, 1e-2, {variant})
+assert max(r.m for lv in F.levels for r in lv.supers) > 240
+G = gpu_factor(pb, 1e-2, {variant})
+assert T._ranks_match(F, G) == [], T._ranks_match(F, G)[:5]
+B = np.random.default_rng(11).standard_normal((pb.n, 2))
+Z = H.apply(F, B)
+e = elem(G.apply(torch.as_tensor(B.T.copy(), device='cuda')).cpu().numpy().T, Z)
+assert e <= 1e-10, e
+G32 = gpu_factor(pb, 1e-2, {variant}, prec=1)
+e32 = elem(G32.apply(torch.as_tensor(B.T.copy(), device='cuda')).cpu().numpy().T, Z)
+assert e32 <= 1e-3, e32
+x, it, rr, code = G32.pcg(torch.as_tensor(B[:, 0].copy(), device='cuda'), rtol=1e-10, maxit=300)
+assert code == 0 and rr[0] <= 1e-10, (code, rr)
+print('ok')
+"""
+    env = dict(os.environ, HS_EIG_SMALL_MAX="8", HS_GRID_TRIDIAG_MIN="16", HS_TRI_CLUSTER="2")
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     assert r.returncode == 0 and "ok" in r.stdout, r.stdout[-2000:] + r.stderr[-3000:]
 
