@@ -54,6 +54,10 @@ PRECS = {"f64": 0, "f32": 1, "tf32": 2, "bf16": 3, "tf32x3": 4}
 # the capture and its command; a kernel changed since its capture has no
 # entry here (traffic null).
 TRAFFIC = {
+    # profiles/traffic_diffusion2d_512_f32.md: one application = 181 launches
+    # (454.3 MB read, 0.01 MB written); the large-node truncation of one
+    # factorization = 193.5 MB over its 46 launch groups
+    ("diffusion2d_512", "f32"): {"apply": 454.26e6, "trunc": 193.48e6 / 46},
 }
 
 
@@ -570,7 +574,7 @@ def serve_arm(args) -> None:
     for name, prec in (("mixed_f32", _lib.HS_PREC_F32), ("f64", _lib.HS_PREC_F64)):
         if name == "f64" and args.no_f64_arm:
             continue
-        srv = S.Server(budget, slots=args.serve_slots, max_rhs=16, prec=prec)
+        srv = S.Server(budget, slots=args.serve_slots, max_rhs=16, prec=prec, scale=args.scale)
         srv.run(warm, realtime=False)
         clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
         clocks.start()
@@ -594,6 +598,7 @@ def serve_arm(args) -> None:
         "config": {"workload": "serving_diffusion3d", "sides": [lo, hi], "s": 2.0, "leaf": 64, "eps": 1e-2,
                    "p_factor": 0.2, "nrhs": [1, 16], "rate_per_s": args.serve_rate,
                    "budget_gb": args.serve_budget_gb, "slots": args.serve_slots, "max_batch_rhs": 16,
+                   "diagonal_scaling": bool(args.scale),
                    "requests": args.serve_requests, "generation_s": t_gen},
         "p50_ms": m["p50_ms"], "p99_ms": m["p99_ms"],
         "serving": out,

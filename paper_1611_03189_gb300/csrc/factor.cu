@@ -25,13 +25,14 @@
 #include <cmath>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
 #include <type_traits>
-#include <unordered_map>
 
+#include "flat_map.h"
 #include "handle.h"
 
 namespace hs {
@@ -755,7 +756,7 @@ class Run {
   bool use_phi_ = false;
   const double *phi_host_ = nullptr;
 
-  std::unordered_map<uint64_t, BlockRef<T>> blocks_;
+  FlatMap<BlockRef<T>> blocks_;
   std::vector<int> size_;      // by key of the current level
   std::vector<T *> phi_;       // by key
   int nsup_ = 0;
@@ -801,7 +802,7 @@ void Run<T>::leaf_setup() {
     std::vector<int> leaf_of(P_.n);
     for (int i = 0; i < nleaf; ++i)
       for (int p = lp[i]; p < lp[i + 1]; ++p) leaf_of[p] = i;
-    std::unordered_map<uint64_t, int64_t> off;
+    FlatMap<int64_t> off;
     h_.leaf_blocks.clear();
     h_.leaf_block_off.clear();
     int64_t total = 0;
@@ -854,6 +855,7 @@ void Run<T>::leaf_setup() {
   HS_CUDA(cudaMemsetAsync(base, 0, sizeof(T) * std::max<int64_t>(total, 1), st_));
   launch_scatter_values<T>(h_.factor_values(), h_.d_leaf_dest, P_.nnz, base, st_);
   blocks_.clear();
+  blocks_.reserve(h_.leaf_blocks.size());
   for (size_t i = 0; i < h_.leaf_blocks.size(); ++i) {
     const auto &ab = h_.leaf_blocks[i];
     BlockRef<T> br;
@@ -892,26 +894,31 @@ void Run<T>::merge(int nred, int key_base, SumBatch<T> &sb) {
     ssize[j] = any ? m : -1;
   }
   // super-block list
-  std::unordered_map<uint64_t, int64_t> off;
+  FlatMap<int64_t> off;
+  off.reserve(blocks_.size());
   std::vector<std::pair<int, int>> order;
+  std::vector<int64_t> order_off;
   int64_t total = 0;
   for (auto &kv : blocks_) {
     const int a = (int)(kv.first >> 32) - key_base, b = (int)(kv.first & 0xffffffffu) - key_base;
     if (a < 0 || b < 0 || a >= nred || b >= nred) fail(HS_ERR_INVALID, "internal: stray block at merge");
     const int I = a / 2, J = b / 2;
-    const uint64_t key = bkey(I, J);
-    if (!off.count(key)) {
-      off[key] = total;
+    auto ins = off.try_emplace(bkey(I, J));
+    if (ins.second) {
+      *ins.first = total;
       order.emplace_back(std::min(I, J), std::max(I, J));
+      order_off.push_back(total);
       total += ((int64_t)ssize[I] * ssize[J] + 3) & ~(int64_t)3;
     }
   }
   T *base = talloc<T>(*h_.pers, total);
   HS_CUDA(cudaMemsetAsync(base, 0, sizeof(T) * std::max<int64_t>(total, 1), st_));
-  std::unordered_map<uint64_t, BlockRef<T>> nb;
-  for (auto &IJ : order) {
+  FlatMap<BlockRef<T>> nb;
+  nb.reserve(order.size());
+  for (size_t q = 0; q < order.size(); ++q) {
+    const auto &IJ = order[q];
     BlockRef<T> br;
-    br.ptr = base + off[bkey(IJ.first, IJ.second)];
+    br.ptr = base + order_off[q];
     br.ld = ssize[IJ.second];
     br.rowkey = IJ.first;
     nb[bkey(IJ.first, IJ.second)] = br;
@@ -921,7 +928,9 @@ void Run<T>::merge(int nred, int key_base, SumBatch<T> &sb) {
     const int b = std::max((int)(kv.first >> 32), (int)(kv.first & 0xffffffffu)) - key_base;
     const BlockRef<T> &rb = kv.second;
     const int I = a / 2, J = b / 2;
-    const BlockRef<T> &sbk = nb[bkey(I, J)];
+    auto sit = nb.find(bkey(I, J));
+    if (sit == nb.end()) fail(HS_ERR_INVALID, "internal: missing super block at merge");
+    const BlockRef<T> sbk = sit->second;
     // rows a, cols b
     const int ta = (rb.rowkey - key_base == a) ? 0 : 1;
     sb.copy(sbk.ptr + (int64_t)coff[a] * sbk.ld + coff[b], sbk.ld, rsize[a], rsize[b], rb.ptr, rb.ld, ta);
@@ -1185,22 +1194,33 @@ template <typename T>
 void Run<T>::wave_d(WaveBatches<T> &B) {
   DevArena &per = *h_.pers;
   std::vector<Sup> &S = cur_;
-  // register the red nodes' blocks and gather the Schur update by target
-  std::unordered_map<uint64_t, std::vector<std::pair<int, int>>> tgt;  // target -> (sup idx, pair)
+  // register the red nodes' blocks and gather the Schur update by target:
+  // targets in order of first appearance, each target's contributions in
+  // ascending super-node order (a stable counting sort of the contributions)
+  FlatMap<int> tgt_idx;
   std::vector<uint64_t> tgt_order;
+  std::vector<int> c_tgt, c_sup;
   for (size_t q = 0; q < S.size(); ++q) {
     const Sup &x = S[q];
     const PlanSuper &ps = lv_->sup[x.s];
     for (size_t i = 0; i < ps.N.size(); ++i)
       for (size_t j = i; j < ps.N.size(); ++j) {
         const uint64_t key = bkey(ps.N[i], ps.N[j]);
-        auto it = tgt.find(key);
-        if (it == tgt.end()) {
+        auto ins = tgt_idx.try_emplace(key);
+        if (ins.second) {
+          *ins.first = (int)tgt_order.size();
           tgt_order.push_back(key);
-          it = tgt.emplace(key, std::vector<std::pair<int, int>>()).first;
         }
-        it->second.emplace_back((int)q, (int)(i * ps.N.size() + j));
+        c_tgt.push_back(*ins.first);
+        c_sup.push_back((int)q);
       }
+  }
+  std::vector<int> c_start(tgt_order.size() + 1, 0), c_list(c_tgt.size());
+  for (int t : c_tgt) ++c_start[t + 1];
+  for (size_t t = 0; t < tgt_order.size(); ++t) c_start[t + 1] += c_start[t];
+  {
+    std::vector<int> cur(c_start.begin(), c_start.end() - 1);
+    for (size_t c = 0; c < c_tgt.size(); ++c) c_list[cur[c_tgt[c]]++] = c_sup[c];
   }
   // new fill blocks (zero) in one allocation
   {
@@ -1225,13 +1245,16 @@ void Run<T>::wave_d(WaveBatches<T> &B) {
       }
     }
   }
-  for (uint64_t key : tgt_order) {
-    const BlockRef<T> &dst = blocks_[key];
+  for (size_t ti = 0; ti < tgt_order.size(); ++ti) {
+    const uint64_t key = tgt_order[ti];
+    auto dit = blocks_.find(key);
+    if (dit == blocks_.end()) fail(HS_ERR_INVALID, "internal: missing Schur target");
+    const BlockRef<T> dst = dit->second;
     const int a = (int)(key >> 32), b = (int)(key & 0xffffffffu);
     const int rk = dst.rowkey, ck = (rk == a) ? b : a;
     B.schur.begin(dst.ptr, dst.ld, size_[rk], size_[ck], T(-1), T(1));
-    for (auto &c : tgt[key]) {
-      const Sup &x = S[c.first];
+    for (int c = c_start[ti]; c < c_start[ti + 1]; ++c) {
+      const Sup &x = S[c_list[c]];
       const PlanSuper &ps = lv_->sup[x.s];
       // offsets of the row key and column key inside s's neighbour list
       int orow = -1, ocol = -1;
@@ -1321,8 +1344,10 @@ void Run<T>::end_level(const PlanLevel &lv, int li) {
   size_t rp = 0;
   for (int w = wfirst; w < (int)h_.waves.size(); ++w) {
     WaveApply &wa = h_.waves[w];
-    std::unordered_map<int, std::vector<std::pair<int, int>>> by_target;  // key -> (node, col)
-    std::vector<int> torder;
+    // contributions (node, column) by target key, in node order; the targets
+    // in ascending key order
+    FlatMap<int> tix;
+    std::vector<int> torder, c_t, c_node, c_col;
     int64_t t = 0;
     wa.max_m = 0;
     wa.rows_f = wa.rows_b = wa.pch = wa.tch = 0;
@@ -1350,27 +1375,45 @@ void Run<T>::end_level(const PlanLevel &lv, int li) {
         nb.col = col;
         col += size_[n];
         h_.nbrs.push_back(nb);
-        if (!by_target.count(n)) torder.push_back(n);
-        by_target[n].emplace_back(rc.node, nb.col);
+        auto ins = tix.try_emplace((uint64_t)n);
+        if (ins.second) {
+          *ins.first = (int)torder.size();
+          torder.push_back(n);
+        }
+        c_t.push_back(*ins.first);
+        c_node.push_back(rc.node);
+        c_col.push_back(nb.col);
       }
+    }
+    // group the contributions by target (stable counting sort)
+    std::vector<int> c_start(torder.size() + 1, 0), c_list(c_t.size());
+    for (int x : c_t) ++c_start[x + 1];
+    for (size_t x = 0; x < torder.size(); ++x) c_start[x + 1] += c_start[x];
+    {
+      std::vector<int> cur(c_start.begin(), c_start.end() - 1);
+      for (size_t c = 0; c < c_t.size(); ++c) c_list[cur[c_t[c]]++] = (int)c;
     }
     wa.tsize = t;
     h_.tmax = std::max(h_.tmax, t);
-    std::sort(torder.begin(), torder.end());
+    std::vector<int> tsorted(torder.size());
+    for (size_t x = 0; x < torder.size(); ++x) tsorted[x] = (int)x;
+    std::sort(tsorted.begin(), tsorted.end(), [&](int p, int q) { return torder[p] < torder[q]; });
     wa.tgt_first = (int)h_.targets.size();
     wa.tgt_count = (int)torder.size();
-    for (int n : torder) {
+    for (int ti : tsorted) {
+      const int n = torder[ti];
       ApplyTarget tg;
       tg.x = xoff(n);
       tg.size = size_[n];
       tg.ch0 = wa.tch;
       wa.tch += (tg.size + 31) / 32;
       tg.first = (int)h_.contribs.size();
-      tg.count = (int)by_target[n].size();
-      for (auto &c : by_target[n]) {
-        const ApplyNode &an = h_.nodes[c.first];
+      tg.count = c_start[ti + 1] - c_start[ti];
+      for (int cc = c_start[ti]; cc < c_start[ti + 1]; ++cc) {
+        const int c = c_list[cc];
+        const ApplyNode &an = h_.nodes[c_node[c]];
         ApplyContrib ac;
-        ac.A = (const char *)an.AsN + sizeof(T) * (size_t)c.second;
+        ac.A = (const char *)an.AsN + sizeof(T) * (size_t)c_col[c];
         ac.ld = an.dN;
         ac.m = an.m;
         ac.toff = an.toff;
@@ -1386,7 +1429,8 @@ void Run<T>::end_level(const PlanLevel &lv, int li) {
   la.wave_count = (int)lv.waves.size();
   h_.levels.push_back(la);
   // parent level: red node nsup+i becomes red i
-  std::unordered_map<uint64_t, BlockRef<T>> nb;
+  FlatMap<BlockRef<T>> nb;
+  nb.reserve(blocks_.size());
   for (auto &kv : blocks_) {
     const int a = (int)(kv.first >> 32), b = (int)(kv.first & 0xffffffffu);
     if (a < nsup || b < nsup) fail(HS_ERR_INVALID, "internal: super node block left at level end");
@@ -1463,7 +1507,9 @@ template <typename T>
 void Run<T>::root_b(CholBatch<T> &cb, GemmBatch<T> &g) {
   if (!root_ainv_) return;
   const int m = h_.root_m;
-  const BlockRef<T> &b = blocks_.at(bkey(0, 0));
+  auto bit = blocks_.find(bkey(0, 0));
+  if (bit == blocks_.end()) fail(HS_ERR_INVALID, "internal: missing root block");
+  const BlockRef<T> b = bit->second;
   const double f0 = cb.flops + g.flops;
   cb.add(b.ptr, b.ld, root_linv_, m, tag(4, 0, 0));
   alg_flops_ += (double)m * m * m / 3;
@@ -1621,12 +1667,42 @@ void trunc_grid(Exec &ex, const std::vector<TruncTask<T>> &tasks, const TruncTas
   ex.end();
 }
 
+// Host time per part of the factorization loop, printed to stderr after each
+// factorization when HS_HOST_PROFILE=1 (environment): the time since the
+// previous tick goes to the named part.
+struct HostClock {
+  static constexpr int kParts = 12;
+  bool on = false;
+  double ms[kParts] = {};
+  std::chrono::steady_clock::time_point t;
+  HostClock() {
+    const char *e = std::getenv("HS_HOST_PROFILE");
+    on = e && e[0] == '1';
+    t = std::chrono::steady_clock::now();
+  }
+  void tick(int part) {
+    if (!on) return;
+    const auto n = std::chrono::steady_clock::now();
+    ms[part] += std::chrono::duration<double, std::milli>(n - t).count();
+    t = n;
+  }
+  void report() const {
+    if (!on) return;
+    static const char *names[kParts] = {"level_begin", "wave_a",  "launch_a", "sync_wait", "wave_b",    "launch_qr",
+                                        "wave_c",      "launch_c", "wave_d",   "launch_schur", "level_end", "root"};
+    std::fprintf(stderr, "hs host ms:");
+    for (int i = 0; i < kParts; ++i) std::fprintf(stderr, " %s=%.2f", names[i], ms[i]);
+    std::fprintf(stderr, "\n");
+  }
+};
+
 // Runs the factorizations of `runs` in lock step: at every step (level counted
 // from the leaves, wave index) the work of all problems that have that step
 // goes into one launch per kernel kind, with one read of the new ranks.
 template <typename T>
 void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
   const auto t_start = std::chrono::steady_clock::now();
+  HostClock hc;
   for (auto &r : runs) {
     r->handle().scratch->reset();
     r->begin();
@@ -1650,6 +1726,7 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       ex.begin(0);
       sb.launch(ex.scr, ex.sg, ex.st);
       ex.end();
+      hc.tick(0);
     }
     int nw = 0;
     for (Run<T> *r : part) nw = std::max(nw, r->waves(li));
@@ -1666,6 +1743,7 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       WaveBatches<T> B;
       // phase A
       for (Run<T> *r : wp) r->wave_a(li, w, B);
+      hc.tick(1);
       const size_t nchol = B.chol.tasks.size(), ntrunc = B.trunc.size(), nbig = B.trunc_big.size();
       for (size_t i = 0; i < ntrunc; ++i) B.trunc[i].k_idx = (int)i;
       for (size_t i = 0; i < nbig; ++i) B.trunc_big[i].k_idx = (int)(ntrunc + i);
@@ -1720,11 +1798,14 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       const size_t nread = nchol + ntrunc + nbig;
       int *hb = ex.host_ints(nread + 1);
       if (nread) HS_CUDA(cudaMemcpyAsync(hb, d_stat, sizeof(int) * nread, cudaMemcpyDeviceToHost, ex.st));
+      hc.tick(2);
       ex.sync_check();
+      hc.tick(3);
       float big_ms = 0.f;
       if (nbig) HS_CUDA(cudaEventElapsedTime(&big_ms, ex.ev_big[0], ex.ev_big[1]));
       for (Run<T> *r : wp)
         if (r->ok()) r->wave_b(hb, nchol, ntrunc, big_ms, B);
+      hc.tick(4);
       // U of the large path: CholQR2
       ex.begin(6);
       ex.gemm(B.o1);
@@ -1734,6 +1815,7 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       ex.chol_checked(B.oc2);
       ex.gemm(B.o4);
       ex.end();
+      hc.tick(5);
       // phase B and the Schur update.  The GEMM tasks are built and launched
       // in chunks of super nodes, so that the GPU starts on the first chunk
       // while the host builds the next (large waves at the lower levels hold
@@ -1749,6 +1831,7 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
         for (Run<T> *r : wp)
           if (r->ok() && r->wave_c(B, chunk)) more = true;
         chunk = 512;
+        hc.tick(6);
         ex.begin(7);
         ex.gemm(B.g1);
         ex.gemm(B.g2);
@@ -1765,15 +1848,19 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
         B.c1.what.clear();
         B.c2.tasks.clear();
         B.c2.what.clear();
+        hc.tick(7);
       }
       for (Run<T> *r : wp)
         if (r->ok()) r->wave_d(B);
+      hc.tick(8);
       ex.begin(8);
       B.schur.launch(ex.scr, ex.sg, ex.st);
       ex.end();
+      hc.tick(9);
     }
     for (Run<T> *r : part)
       if (r->ok()) r->level_end(li);
+    hc.tick(10);
   }
   // the roots (one flip: the last wave step synchronised after the other
   // buffer's copies)
@@ -1797,6 +1884,8 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
     ex.end();
   }
   ex.sync_check();
+  hc.tick(11);
+  hc.report();
   const double total =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   for (auto &r : runs)

@@ -103,7 +103,7 @@ class CudaBackend:
     """Runs the work of a slot through the C ABI on the slot's CUDA stream."""
 
     def __init__(self, device: int = 0, eps: float = 1e-2, variant: int = _lib.HS_GC_CONSTANT,
-                 prec: int = _lib.HS_PREC_F32, rtol: float = 1e-10, maxit: int = 1000):
+                 prec: int = _lib.HS_PREC_F32, rtol: float = 1e-10, maxit: int = 1000, scale: bool = False):
         import torch
 
         if not torch.cuda.is_available():
@@ -112,9 +112,11 @@ class CudaBackend:
         self.device = torch.device("cuda", device)
         self.eps, self.variant, self.prec = eps, variant, prec
         self.rtol, self.maxit = rtol, maxit
+        self.scale = scale   # factor D^-1/2 A D^-1/2 (hs_opts.scale)
 
     def clone(self):
-        return CudaBackend(self.device.index or 0, self.eps, self.variant, self.prec, self.rtol, self.maxit)
+        return CudaBackend(self.device.index or 0, self.eps, self.variant, self.prec, self.rtol, self.maxit,
+                           self.scale)
 
     def slot(self):
         """Per-worker state: a CUDA stream of its own."""
@@ -129,7 +131,8 @@ class CudaBackend:
             rp = torch.as_tensor(pb.rowptr, dtype=torch.int32).pin_memory().to(d, non_blocking=True)
             ci = torch.as_tensor(pb.col, dtype=torch.int32).pin_memory().to(d, non_blocking=True)
             va = torch.as_tensor(pb.val, dtype=torch.float64).pin_memory().to(d, non_blocking=True)
-            f = _lib.Factor(rp, ci, va, pb.perm, pb.leaf_ptr, self.eps, self.variant, self.prec, stream=stream)
+            f = _lib.Factor(rp, ci, va, pb.perm, pb.leaf_ptr, self.eps, self.variant, self.prec, stream=stream,
+                            scale=self.scale)
             stream.synchronize()
         # factor arenas + permuted CSR and maps
         return f, int(f.info()["device_bytes"]) + 16 * (pb.n + 1 + 2 * len(pb.col))
