@@ -76,6 +76,10 @@ struct WaveApply {
   int rows_b;        // sum of m: backward rows
   int pch;           // sum of 32-column chunks of P_ss
   int tch;           // sum of 32-row chunks of the targets
+  // offsets into FactorHandle::d_hints of the per-CTA search starts of the
+  // per-step kernels (-1: none): f1 by row0, f2 by ch0, b1/b2 by brow0, b1's
+  // P_ss^T part by pch0
+  int hf1 = -1, hf2 = -1, hb = -1, hp = -1;
 };
 struct LevelApply {
   int level;
@@ -139,6 +143,10 @@ struct FactorHandle {
   WaveApply *d_waves = nullptr;
   unsigned *d_apply_bar = nullptr;
   int *d_apply_err = nullptr;
+  // per-CTA first node (or target) of each per-step apply kernel, for a
+  // CTA's first warp; each warp scans forward from it (WaveApply::hf1 ...)
+  int *d_hints = nullptr;
+  size_t hints_cap = 0;
   int64_t ws_size = 0;                 // unknowns in the apply workspace
   int64_t tmax = 0;                    // max unknowns of t scratch per wave
   int64_t root_off = 0;

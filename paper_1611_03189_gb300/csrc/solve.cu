@@ -47,6 +47,18 @@ __device__ __forceinline__ int find_last(int first, int count, int w, F key) {
   return lo;
 }
 
+// The same index, from a start known not to be past it (hint >= 0: the
+// answer for the CTA's first warp): a forward scan over the few node
+// boundaries inside the CTA's rows instead of a search of the whole wave.
+template <typename F>
+__device__ __forceinline__ int find_from(int first, int count, int w, int hint, F key) {
+  if (hint < 0) return find_last(first, count, w, key);
+  int i = hint;
+  const int last = first + count - 1;
+  while (i < last && key(i + 1) <= w) ++i;
+  return i;
+}
+
 template <typename T, int NR>
 __device__ __forceinline__ void warp_reduce(T (&acc)[NR]) {
 #pragma unroll
@@ -108,8 +120,8 @@ __device__ __forceinline__ void col_dot(const T *__restrict__ A, int64_t ld, con
 // F1: one warp per row of [M_ss; P_ss]: t_s = M_ss phi_s, phi_r += P_ss phi_s
 template <typename T, int NR>
 __device__ __forceinline__ void f1_warp(const ApplyNode *__restrict__ nodes, int first, int count, int w, int lane,
-                                        T *__restrict__ ws, T *__restrict__ tb, int nrhs, int j0) {
-  const int ni = find_last(first, count, w, [&](int i) { return nodes[i].row0; });
+                                        T *__restrict__ ws, T *__restrict__ tb, int nrhs, int j0, int hint = -1) {
+  const int ni = find_from(first, count, w, hint, [&](int i) { return nodes[i].row0; });
   const ApplyNode nd = nodes[ni];
   const int r = w - nd.row0;
   const T *Ar = r < nd.m ? (const T *)nd.M + (int64_t)r * nd.m : (const T *)nd.P + (int64_t)(r - nd.m) * nd.m;
@@ -135,17 +147,18 @@ __device__ __forceinline__ void f1_warp(const ApplyNode *__restrict__ nodes, int
 
 template <typename T, int NR>
 __global__ void __launch_bounds__(AT) k_f1(const ApplyNode *__restrict__ nodes, int first, int count, int rows,
-                                           T *__restrict__ ws, T *__restrict__ tb, int nrhs, int j0) {
+                                           T *__restrict__ ws, T *__restrict__ tb, int nrhs, int j0,
+                                           const int *__restrict__ hint) {
   const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w < rows) f1_warp<T, NR>(nodes, first, count, w, lane, ws, tb, nrhs, j0);
+  if (w < rows) f1_warp<T, NR>(nodes, first, count, w, lane, ws, tb, nrhs, j0, hint ? hint[blockIdx.x] : -1);
 }
 
 // F2: phi_n -= sum_s A_ns t_s; one warp per 32 rows of a target, contributions in order
 template <typename T, int NR>
 __device__ __forceinline__ void f2_warp(const ApplyTarget *__restrict__ tg, int first, int count, int w, int lane,
                                         const ApplyContrib *__restrict__ cb, T *__restrict__ ws,
-                                        const T *__restrict__ tb, int nrhs, int j0) {
-  const int ti = find_last(first, count, w, [&](int i) { return tg[i].ch0; });
+                                        const T *__restrict__ tb, int nrhs, int j0, int hint = -1) {
+  const int ti = find_from(first, count, w, hint, [&](int i) { return tg[i].ch0; });
   const ApplyTarget t = tg[ti];
   const int i = (w - t.ch0) * 32 + lane;
   if (i >= t.size) return;
@@ -168,9 +181,9 @@ __device__ __forceinline__ void f2_warp(const ApplyTarget *__restrict__ tg, int 
 template <typename T, int NR>
 __global__ void __launch_bounds__(AT) k_f2(const ApplyTarget *__restrict__ tg, int first, int count, int chunks,
                                            const ApplyContrib *__restrict__ cb, T *__restrict__ ws,
-                                           const T *__restrict__ tb, int nrhs, int j0) {
+                                           const T *__restrict__ tb, int nrhs, int j0, const int *__restrict__ hint) {
   const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w < chunks) f2_warp<T, NR>(tg, first, count, w, lane, cb, ws, tb, nrhs, j0);
+  if (w < chunks) f2_warp<T, NR>(tg, first, count, w, lane, cb, ws, tb, nrhs, j0, hint ? hint[blockIdx.x] : -1);
 }
 
 // B1 (warps < rows_b): v_s = phi_s - sum_n A_sn x_n, one warp per row of s.
@@ -178,13 +191,14 @@ __global__ void __launch_bounds__(AT) k_f2(const ApplyTarget *__restrict__ tg, i
 template <typename T, int NR>
 __device__ __forceinline__ void b1_warp(const ApplyNode *__restrict__ nodes, int first, int count, int rows_b,
                                         int w, int lane, const ApplyNbr *__restrict__ nb, const T *__restrict__ ws,
-                                        T *__restrict__ tb, T *__restrict__ tb2, int nrhs, int j0) {
+                                        T *__restrict__ tb, T *__restrict__ tb2, int nrhs, int j0, int hint_b = -1,
+                                        int hint_p = -1) {
   const int nr = min(NR, nrhs - j0);
   T acc[NR];
 #pragma unroll
   for (int j = 0; j < NR; ++j) acc[j] = T(0);
   if (w < rows_b) {
-    const int ni = find_last(first, count, w, [&](int i) { return nodes[i].brow0; });
+    const int ni = find_from(first, count, w, hint_b, [&](int i) { return nodes[i].brow0; });
     const ApplyNode nd = nodes[ni];
     const int r = w - nd.brow0;
     for (int b = 0; b < nd.nb_count; ++b) {
@@ -203,7 +217,7 @@ __device__ __forceinline__ void b1_warp(const ApplyNode *__restrict__ nodes, int
     }
   } else {
     const int w2 = w - rows_b;
-    const int ni = find_last(first, count, w2, [&](int i) { return nodes[i].pch0; });
+    const int ni = find_from(first, count, w2, hint_p, [&](int i) { return nodes[i].pch0; });
     const ApplyNode nd = nodes[ni];
     const int i = (w2 - nd.pch0) * 32 + lane;
     if (i >= nd.m || nd.k == 0) return;
@@ -220,17 +234,20 @@ __device__ __forceinline__ void b1_warp(const ApplyNode *__restrict__ nodes, int
 template <typename T, int NR>
 __global__ void __launch_bounds__(AT) k_b1(const ApplyNode *__restrict__ nodes, int first, int count, int rows_b,
                                            int pch, const ApplyNbr *__restrict__ nb, const T *__restrict__ ws,
-                                           T *__restrict__ tb, T *__restrict__ tb2, int nrhs, int j0) {
+                                           T *__restrict__ tb, T *__restrict__ tb2, int nrhs, int j0,
+                                           const int *__restrict__ hint_b, const int *__restrict__ hint_p) {
   const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w < rows_b + pch) b1_warp<T, NR>(nodes, first, count, rows_b, w, lane, nb, ws, tb, tb2, nrhs, j0);
+  if (w < rows_b + pch)
+    b1_warp<T, NR>(nodes, first, count, rows_b, w, lane, nb, ws, tb, tb2, nrhs, j0,
+                   hint_b ? hint_b[blockIdx.x] : -1, hint_p ? hint_p[blockIdx.x] : -1);
 }
 
 // B2b: x_s = M_ss v_s + y_s, one warp per row of s
 template <typename T, int NR>
 __device__ __forceinline__ void b2_warp(const ApplyNode *__restrict__ nodes, int first, int count, int w, int lane,
                                         T *__restrict__ ws, const T *__restrict__ tb, const T *__restrict__ tb2,
-                                        int nrhs, int j0) {
-  const int ni = find_last(first, count, w, [&](int i) { return nodes[i].brow0; });
+                                        int nrhs, int j0, int hint = -1) {
+  const int ni = find_from(first, count, w, hint, [&](int i) { return nodes[i].brow0; });
   const ApplyNode nd = nodes[ni];
   const int r = w - nd.brow0;
   const T *Mr = (const T *)nd.M + (int64_t)r * nd.m;
@@ -253,9 +270,9 @@ __device__ __forceinline__ void b2_warp(const ApplyNode *__restrict__ nodes, int
 template <typename T, int NR>
 __global__ void __launch_bounds__(AT) k_b2(const ApplyNode *__restrict__ nodes, int first, int count, int rows_b,
                                            T *__restrict__ ws, const T *__restrict__ tb,
-                                           const T *__restrict__ tb2, int nrhs, int j0) {
+                                           const T *__restrict__ tb2, int nrhs, int j0, const int *__restrict__ hint) {
   const int w = blockIdx.x * AW + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (w < rows_b) b2_warp<T, NR>(nodes, first, count, w, lane, ws, tb, tb2, nrhs, j0);
+  if (w < rows_b) b2_warp<T, NR>(nodes, first, count, w, lane, ws, tb, tb2, nrhs, j0, hint ? hint[blockIdx.x] : -1);
 }
 
 template <typename T>
@@ -637,6 +654,9 @@ int grid_for(int64_t total) {
 // grid of the PCG reduction kernels: a function of n only (see above)
 int rgrid_for(int64_t n) { return grid_for(n); }
 
+// a wave's per-CTA search starts (nullptr: the kernels search the whole wave)
+inline const int *hint_at(const FactorHandle &h, int off) { return (h.d_hints && off >= 0) ? h.d_hints + off : nullptr; }
+
 // One pass of Algorithm 2 over right-hand sides [j0, j0 + NR) of the
 // workspace ws (layout [unknown][nrhs]); tb and tb2 are the per-wave scratch.
 template <typename T, int NR>
@@ -647,12 +667,12 @@ void apply_waves_nr(const FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, int j
       const WaveApply &wa = h.waves[w];
       if (wa.rows_f) {
         k_f1<T, NR><<<blocks(wa.rows_f), AT, 0, st>>>(h.d_nodes, wa.node_first, wa.node_count, wa.rows_f, ws, tb,
-                                                      nrhs, j0);
+                                                      nrhs, j0, hint_at(h, wa.hf1));
         count_launch();
       }
       if (wa.tch) {
         k_f2<T, NR><<<blocks(wa.tch), AT, 0, st>>>(h.d_targets, wa.tgt_first, wa.tgt_count, wa.tch, h.d_contribs,
-                                                   ws, tb, nrhs, j0);
+                                                   ws, tb, nrhs, j0, hint_at(h, wa.hf2));
         count_launch();
       }
     }
@@ -668,9 +688,10 @@ void apply_waves_nr(const FactorHandle &h, T *ws, T *tb, T *tb2, int nrhs, int j
       const WaveApply &wa = h.waves[w];
       if (!wa.rows_b) continue;
       k_b1<T, NR><<<blocks(wa.rows_b + wa.pch), AT, 0, st>>>(h.d_nodes, wa.node_first, wa.node_count, wa.rows_b,
-                                                             wa.pch, h.d_nbrs, ws, tb, tb2, nrhs, j0);
+                                                             wa.pch, h.d_nbrs, ws, tb, tb2, nrhs, j0,
+                                                             hint_at(h, wa.hb), hint_at(h, wa.hp));
       k_b2<T, NR><<<blocks(wa.rows_b), AT, 0, st>>>(h.d_nodes, wa.node_first, wa.node_count, wa.rows_b, ws, tb,
-                                                    tb2, nrhs, j0);
+                                                    tb2, nrhs, j0, hint_at(h, wa.hb));
       count_launch(2);
     }
   }
@@ -904,6 +925,50 @@ void apply_prepare(FactorHandle &h, cudaStream_t st) {
       steps.push_back(ApplyStepDev{AS_B2, w});
     }
   }
+  // per-CTA search starts of the per-step kernels: for CTA b, the last node
+  // (target) whose first row (chunk) is <= b AW, found by one sweep per key
+  std::vector<int> hints;
+  auto sweep = [&](int nrows, int first, int count, auto key) -> int {
+    if (nrows <= 0 || count <= 0) return -1;
+    const int off = (int)hints.size();
+    const int nb = (nrows + AW - 1) / AW;
+    int i = first;
+    for (int b = 0; b < nb; ++b) {
+      const int w0 = b * AW;
+      while (i + 1 < first + count && key(i + 1) <= w0) ++i;
+      hints.push_back(i);
+    }
+    return off;
+  };
+  for (WaveApply &wa : h.waves) {
+    const ApplyNode *nd = h.nodes.data();
+    const ApplyTarget *tg = h.targets.data();
+    wa.hf1 = sweep(wa.rows_f, wa.node_first, wa.node_count, [&](int i) { return nd[i].row0; });
+    wa.hf2 = sweep(wa.tch, wa.tgt_first, wa.tgt_count, [&](int i) { return tg[i].ch0; });
+    // b1 runs blocks(rows_b + pch) CTAs: by brow0 for its first rows_b warps,
+    // by pch0 for the rest (CTA b's first warp there: max(b AW - rows_b, 0))
+    const int nb1 = (wa.rows_b + wa.pch + AW - 1) / AW;
+    wa.hb = sweep(nb1 * AW, wa.node_first, wa.node_count, [&](int i) { return nd[i].brow0; });
+    if (wa.pch > 0 && wa.node_count > 0) {
+      wa.hp = (int)hints.size();
+      int i = wa.node_first;
+      for (int b = 0; b < nb1; ++b) {
+        const int w2 = std::max(b * AW - wa.rows_b, 0);
+        while (i + 1 < wa.node_first + wa.node_count && nd[i + 1].pch0 <= w2) ++i;
+        hints.push_back(i);
+      }
+    } else {
+      wa.hp = -1;
+    }
+  }
+  if (hints.size() > h.hints_cap) {
+    cudaFree(h.d_hints);
+    h.d_hints = nullptr;
+    HS_CUDA(cudaMalloc(&h.d_hints, sizeof(int) * hints.size()));
+    h.hints_cap = hints.size();
+  }
+  if (!hints.empty())
+    HS_CUDA(cudaMemcpyAsync(h.d_hints, hints.data(), sizeof(int) * hints.size(), cudaMemcpyHostToDevice, st));
   cudaFree(h.d_apply_steps);
   cudaFree(h.d_waves);
   h.d_apply_steps = nullptr;
@@ -1393,6 +1458,7 @@ FactorHandle::~FactorHandle() {
   cudaFree(d_apply_steps);
   cudaFree(d_waves);
   cudaFree(d_apply_bar);
+  cudaFree(d_hints);
   cudaFree(d_dscale);
   cudaFree(d_val_f);
   cudaFree(d_flag);
