@@ -144,12 +144,15 @@ typedef struct {
  *   stay preserved for A.  hs_pcg and hs_gmres still solve A x = b.  A
  *   diagonal entry <= 0 is HS_ERR_NOT_SPD.
  * timeout_cycles: bound, in SM clock cycles, of each wait inside the
- *   factorization's kernels (the tensor-core GEMM of HS_PREC_TF32 /
- *   HS_PREC_BF16 waits on its mbarriers for the tensor core); 0 means the
- *   default, 2e9 cycles (about one second).  A wait that runs out makes the
- *   call fail with HS_ERR_TIMEOUT; the device stays usable (the kernel waits
- *   for its own tensor-core work with the default bound before it frees its
- *   tensor memory and returns).  >= 0.
+ *   handle's kernels: the tensor-core GEMM of HS_PREC_TF32 / HS_PREC_BF16 /
+ *   HS_PREC_TF32X3 (its mbarriers) and the grid barriers of the opt-in
+ *   persistent apply (HS_APPLY_PERSISTENT=1); 0 means the default, 2e9
+ *   cycles (about one second).  A wait that runs out makes the call fail
+ *   with HS_ERR_TIMEOUT (the factorization, or hs_pcg / hs_gmres for the
+ *   apply); the device stays usable (the GEMM waits for its own tensor-core
+ *   work with the default bound before it frees its tensor memory and
+ *   returns).  A bound far below a real wait (a few microseconds) fails
+ *   correct work.  >= 0.
  * order_mode: the elimination order of a level's super nodes, "a given
  *   ordering" in Sec. 3.2.  HS_ORDER_WAVES (0, the default): canonical waves
  *   (see the planner below), each wave one batch of independent
