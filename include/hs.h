@@ -110,6 +110,40 @@ typedef struct {
   int32_t nbr_dist;
 } hs_clustering;
 
+/* Device-memory hook (hs_opts.allocator).  The paper has no counterpart:
+ * this is how a caller that manages device memory itself -- a serving loop
+ * that admits work against a fixed budget, or a framework with its own
+ * caching allocator (PyTorch's) -- makes the handle take every block of
+ * device memory it holds from that allocator, so that the caller's count of
+ * the bytes in use is exact.
+ *   alloc(bytes, device, stream, ctx): returns a DEVICE pointer to `bytes`
+ *     bytes on `device`, 256-byte aligned, that work enqueued on `stream` may
+ *     use at once (stream-ordered, as the PyTorch caching allocator and
+ *     cudaMallocAsync give), or NULL when it cannot; the library then fails
+ *     the call with HS_ERR_OOM after returning what that call allocated.  A
+ *     misaligned pointer is handed back through free and the call fails with
+ *     HS_ERR_INVALID.
+ *   free(ptr, device, stream, ctx): takes back a pointer alloc returned.  The
+ *     library first synchronises the device (as cudaFree does), so no work of
+ *     the library still uses the block.
+ *   ctx: passed through unchanged.
+ * Both are called on the calling thread, inside library calls on the handle
+ * (creation, refactor, the solves, which grow their workspaces on first use
+ * of a larger right-hand-side count, and destroy), never concurrently for one
+ * handle.  The hook covers the device memory a handle owns: its copies of the
+ * CSR, blocks and factor records, the factorization's scratch and task
+ * descriptors, and the solve workspaces.  Pinned host staging buffers, the
+ * per-device autotuner table and hs_gemm_tc's buffers are not handle memory
+ * and use the CUDA runtime.  The struct is copied at creation; the functions
+ * and ctx must stay valid until hs_factor_destroy returns. */
+typedef void *(*hs_alloc_fn)(uint64_t bytes, int32_t device, void *stream, void *ctx);
+typedef void (*hs_free_fn)(void *ptr, int32_t device, void *stream, void *ctx);
+typedef struct {
+  hs_alloc_fn alloc;
+  hs_free_fn free;
+  void *ctx;
+} hs_allocator;
+
 /* Factorization options.
  * eps: truncation tolerance (Sec. 3.2, "compression threshold"); a singular
  *   value is kept when sigma_i > eps * ||A_sw||_2.  eps == 0 disables
@@ -165,7 +199,11 @@ typedef struct {
  *   projected block) -- bounding the red nodes' sizes and so the factor's
  *   memory.  Not in the paper; a cap that binds trades preconditioner
  *   quality for memory, and a harsh one can cost GC-constant its
- *   definiteness (HS_ERR_NOT_SPD). */
+ *   definiteness (HS_ERR_NOT_SPD).
+ * allocator: NULL (the CUDA runtime: cudaMalloc / cudaFree), or a device-
+ *   memory hook (hs_allocator above) with both functions set; the handle
+ *   takes all its device memory from it.  hs_factor_create_batch gives every
+ *   handle of the batch the same hook. */
 typedef struct {
   double eps;
   int32_t variant;
@@ -179,6 +217,7 @@ typedef struct {
   int64_t timeout_cycles;
   int32_t order_mode;
   double max_rank_ratio;
+  const hs_allocator *allocator;
 } hs_opts;
 
 /* Sizes and counters of a factorization (all host values). */
@@ -406,10 +445,10 @@ const char *hs_last_error(void);
 int64_t hs_launch_count(void);
 
 /* hs_abi_sizes: sizeof of the ABI structs as this library was compiled --
- * sizes[0] hs_csr, [1] hs_clustering, [2] hs_opts, [3] hs_info -- so that a
- * binding can check its own struct layouts (no device needed).  Writes
- * min(cap, 4) entries and returns the number of structs (4).  A build check;
- * the paper has no counterpart. */
+ * sizes[0] hs_csr, [1] hs_clustering, [2] hs_opts, [3] hs_info,
+ * [4] hs_allocator -- so that a binding can check its own struct layouts (no
+ * device needed).  Writes min(cap, 5) entries and returns the number of
+ * structs (5).  A build check; the paper has no counterpart. */
 int hs_abi_sizes(int64_t *sizes, int32_t cap);
 
 /* ---------------------------------------------------------------------------

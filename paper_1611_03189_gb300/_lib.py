@@ -71,7 +71,77 @@ class HsOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("variant", C.c_int32), ("factor_prec", C.c_int32),
                 ("phi", C.c_void_p), ("eps_level", C.c_void_p), ("n_eps_level", C.c_int32),
                 ("n_phi", C.c_int32), ("eps1", C.c_double), ("scale", C.c_int32),
-                ("timeout_cycles", C.c_int64), ("order_mode", C.c_int32), ("max_rank_ratio", C.c_double)]
+                ("timeout_cycles", C.c_int64), ("order_mode", C.c_int32), ("max_rank_ratio", C.c_double),
+                ("allocator", C.c_void_p)]
+
+
+# hs_allocator: alloc(bytes, device, stream, ctx) -> device pointer or NULL;
+# free(ptr, device, stream, ctx)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_uint64, C.c_int32, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p)
+
+
+class HsAllocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", C.c_void_p)]
+
+
+class DeviceAllocator:
+    """A device-memory hook (hs_opts.allocator) that takes the handle's
+    memory from PyTorch's caching allocator and counts it: `held` is the bytes
+    the handles using this hook hold right now, `peak` the most they held at
+    once.  With `limit` set, a request that would take `held` past it gets no
+    memory (the library call then fails with HS_ERR_OOM), which is how a
+    serving loop caps what one factorization may take.
+
+    One object may serve several handles; it must outlive them (Factor keeps a
+    reference).  The callbacks run on the thread that called the library.
+    """
+
+    def __init__(self, limit: int | None = None):
+        import threading
+
+        self.limit = limit
+        self.held = 0
+        self.peak = 0
+        self.calls = 0
+        self.blocks: dict[int, int] = {}
+        self._mu = threading.Lock()
+        self._alloc = ALLOC_FN(self._on_alloc)
+        self._free = FREE_FN(self._on_free)
+        self.struct = HsAllocator(self._alloc, self._free, None)
+
+    def _on_alloc(self, nbytes, device, stream, ctx):
+        try:
+            import torch
+
+            nbytes = int(nbytes)
+            with self._mu:
+                if self.limit is not None and self.held + nbytes > self.limit:
+                    return None
+            p = int(torch.cuda.caching_allocator_alloc(nbytes, device=int(device), stream=int(stream or 0)))
+            with self._mu:
+                self.blocks[p] = nbytes
+                self.held += nbytes
+                self.peak = max(self.peak, self.held)
+                self.calls += 1
+            return p
+        except Exception:
+            return None   # the library reports HS_ERR_OOM
+
+    def _on_free(self, ptr, device, stream, ctx):
+        try:
+            import torch
+
+            p = int(ptr)
+            with self._mu:
+                nbytes = self.blocks.pop(p)
+                self.held -= nbytes
+            torch.cuda.caching_allocator_delete(p)
+        except Exception:
+            pass
+
+    def ptr(self) -> int:
+        return C.addressof(self.struct)
 
 
 def _phi_block(phi):
@@ -229,7 +299,7 @@ class Factor:
 
     def __init__(self, rowptr, col, val, perm, leaf_ptr, eps, variant=HS_GC_CONSTANT,
                  prec=HS_PREC_F64, phi=None, stream=None, eps_level=None, eps1=0.0, nbr_dist=1, scale=False,
-                 timeout_cycles=0, order_mode=HS_ORDER_WAVES, max_rank_ratio=0.0):
+                 timeout_cycles=0, order_mode=HS_ORDER_WAVES, max_rank_ratio=0.0, allocator=None):
         import torch
 
         assert rowptr.is_cuda and col.is_cuda and val.is_cuda
@@ -244,9 +314,10 @@ class Factor:
         o = HsOpts(float(eps), int(variant), int(prec), None if self._phi is None else _ptr(self._phi),
                    None if self._epsl is None else _ptr(self._epsl), 0 if self._epsl is None else len(self._epsl),
                    nphi, float(eps1), int(bool(scale)), int(timeout_cycles), int(order_mode),
-                   float(max_rank_ratio))
+                   float(max_rank_ratio), None if allocator is None else allocator.ptr())
         h = C.c_void_p()
         self._h = None
+        self._alloc = allocator   # the hook must outlive the handle
         check(lib().hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), _stream_ptr(stream), C.byref(h)))
         self._h = h
 
@@ -316,6 +387,7 @@ class Factor:
         if self._h:
             lib().hs_factor_destroy(self._h)
             self._h = None
+        self._alloc = None
 
     def __del__(self):
         try:
@@ -325,7 +397,7 @@ class Factor:
 
 
 def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=None, stream=None,
-                 eps_level=None, eps1=0.0, nbr_dist=1, scale=False):
+                 eps_level=None, eps1=0.0, nbr_dist=1, scale=False, allocator=None):
     """hs_factor_create_batch over `problems`: a list of (rowptr, col, val,
     perm, leaf_ptr) with rowptr/col int32 and val float64 CUDA tensors and
     perm/leaf_ptr host arrays.  Returns (factors, status): one Factor per
@@ -356,7 +428,8 @@ def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=N
     epsl = None if eps_level is None else np.ascontiguousarray(eps_level, dtype=np.float64)
     keep.append(epsl)
     o = HsOpts(float(eps), int(variant), int(prec), None, None if epsl is None else _ptr(epsl),
-               0 if epsl is None else len(epsl), nphi, float(eps1), int(bool(scale)), 0, HS_ORDER_WAVES, 0.0)
+               0 if epsl is None else len(epsl), nphi, float(eps1), int(bool(scale)), 0, HS_ORDER_WAVES, 0.0,
+               None if allocator is None else allocator.ptr())
     out = (C.c_void_p * k)()
     status = np.zeros(k, dtype=np.int32)
     code = lib().hs_factor_create_batch(k, A, cl, C.byref(o), phi_arr, _stream_ptr(stream), out, _ptr(status))
@@ -372,6 +445,7 @@ def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=N
         f._perm = keep[2 * p]
         f._lp = keep[2 * p + 1]
         f._phi = None
+        f._alloc = allocator
         f._h = C.c_void_p(out[p])
         fs.append(f)
     return fs, status

@@ -71,9 +71,9 @@ void require_factor_device(const FactorHandle &h) {
 }
 
 template <typename X>
-X *upload_vec(const std::vector<X> &v, cudaStream_t st) {
+X *upload_vec(const FactorHandle &h, const std::vector<X> &v, cudaStream_t st) {
   X *d = nullptr;
-  HS_CUDA(cudaMalloc(&d, sizeof(X) * std::max<size_t>(v.size(), 1)));
+  h.alloc.get(&d, sizeof(X) * std::max<size_t>(v.size(), 1), st);
   if (!v.empty()) HS_CUDA(cudaMemcpyAsync(d, v.data(), sizeof(X) * v.size(), cudaMemcpyHostToDevice, st));
   return d;
 }
@@ -93,10 +93,10 @@ void numeric_pre(FactorHandle &h, const double *val, cudaStream_t st) {
     HS_CUDA(cudaStreamSynchronize(st));
     if (bad) fail(HS_ERR_NOT_SPD, "diagonal scaling: a diagonal entry is missing or not positive");
   }
-  cudaFree(h.d_nodes);
-  cudaFree(h.d_nbrs);
-  cudaFree(h.d_targets);
-  cudaFree(h.d_contribs);
+  h.alloc.put(h.d_nodes, st);
+  h.alloc.put(h.d_nbrs, st);
+  h.alloc.put(h.d_targets, st);
+  h.alloc.put(h.d_contribs, st);
   h.d_nodes = nullptr;
   h.d_nbrs = nullptr;
   h.d_targets = nullptr;
@@ -111,10 +111,10 @@ void numeric_failed(FactorHandle &h) {
 }
 
 void numeric_post(FactorHandle &h, float ms, cudaStream_t st) {
-  h.d_nodes = upload_vec(h.nodes, st);
-  h.d_nbrs = upload_vec(h.nbrs, st);
-  h.d_targets = upload_vec(h.targets, st);
-  h.d_contribs = upload_vec(h.contribs, st);
+  h.d_nodes = upload_vec(h, h.nodes, st);
+  h.d_nbrs = upload_vec(h, h.nbrs, st);
+  h.d_targets = upload_vec(h, h.targets, st);
+  h.d_contribs = upload_vec(h, h.contribs, st);
   apply_prepare(h, st);
   hs_info &in = h.info;
   in.n = h.plan.n;
@@ -186,6 +186,12 @@ void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, con
   if (!cl->perm || !cl->leaf_ptr) fail(HS_ERR_INVALID, "bad clustering");
   HS_CUDA(cudaGetDevice(&h.device));
   h.stream = st;
+  if (o->allocator) {
+    h.alloc.fa = o->allocator->alloc;
+    h.alloc.ff = o->allocator->free;
+    h.alloc.ctx = o->allocator->ctx;
+  }
+  h.alloc.device = h.device;
   h.prec = o->factor_prec;
   h.variant = o->variant;
   h.eps = o->eps;
@@ -210,17 +216,17 @@ void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, con
     h.eps_level.assign(o->eps_level, o->eps_level + need);
   }
   // permuted CSR on the device; values gathered there
-  h.d_rowptr = upload_vec(h.plan.prow, st);
-  h.d_col = upload_vec(h.plan.pcol, st);
-  h.d_perm = upload_vec(h.plan.perm, st);
-  h.d_src = upload_vec(h.plan.psrc, st);
+  h.d_rowptr = upload_vec(h, h.plan.prow, st);
+  h.d_col = upload_vec(h, h.plan.pcol, st);
+  h.d_perm = upload_vec(h, h.plan.perm, st);
+  h.d_src = upload_vec(h, h.plan.psrc, st);
   h.nnz = A->nnz;
-  HS_CUDA(cudaMalloc(&h.d_val, sizeof(double) * A->nnz));
+  h.alloc.get(&h.d_val, sizeof(double) * A->nnz, st);
   h.scale = o->scale != 0;
   if (h.scale) {
-    HS_CUDA(cudaMalloc(&h.d_val_f, sizeof(double) * A->nnz));
-    HS_CUDA(cudaMalloc(&h.d_dscale, sizeof(double) * A->n));
-    HS_CUDA(cudaMalloc(&h.d_flag, sizeof(int)));
+    h.alloc.get(&h.d_val_f, sizeof(double) * A->nnz, st);
+    h.alloc.get(&h.d_dscale, sizeof(double) * A->n, st);
+    h.alloc.get(&h.d_flag, sizeof(int), st);
   }
 }
 
@@ -238,6 +244,8 @@ void check_opts(const hs_opts *o) {
   if (o->timeout_cycles < 0) fail(HS_ERR_INVALID, "timeout_cycles must be >= 0");
   if (!(o->max_rank_ratio >= 0.0 && o->max_rank_ratio <= 1.0))
     fail(HS_ERR_INVALID, "max_rank_ratio must be in [0, 1]");
+  if (o->allocator && (!o->allocator->alloc || !o->allocator->free))
+    fail(HS_ERR_INVALID, "an allocator hook needs both alloc and free");
   if (o->order_mode != HS_ORDER_WAVES && o->order_mode != HS_ORDER_SEQUENTIAL)
     fail(HS_ERR_INVALID, "order_mode must be HS_ORDER_WAVES or HS_ORDER_SEQUENTIAL");
   if (o->factor_prec != HS_PREC_F64 && o->factor_prec != HS_PREC_F32 && o->factor_prec != HS_PREC_TF32 &&
@@ -441,10 +449,10 @@ int hs_gemm_tune_report(int32_t prec, float *ms, int32_t *route, int32_t cap) {
 int64_t hs_launch_count(void) { return hs::g_launches.load(); }
 
 int hs_abi_sizes(int64_t *sizes, int32_t cap) {
-  const int64_t v[4] = {(int64_t)sizeof(hs_csr), (int64_t)sizeof(hs_clustering), (int64_t)sizeof(hs_opts),
-                        (int64_t)sizeof(hs_info)};
-  for (int32_t i = 0; i < cap && i < 4 && sizes; ++i) sizes[i] = v[i];
-  return 4;
+  const int64_t v[5] = {(int64_t)sizeof(hs_csr), (int64_t)sizeof(hs_clustering), (int64_t)sizeof(hs_opts),
+                        (int64_t)sizeof(hs_info), (int64_t)sizeof(hs_allocator)};
+  for (int32_t i = 0; i < cap && i < 5 && sizes; ++i) sizes[i] = v[i];
+  return 5;
 }
 
 int hs_test_wait_probe(int32_t on) {

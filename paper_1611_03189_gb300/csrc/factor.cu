@@ -40,8 +40,33 @@ namespace hs {
 // ---------------------------------------------------------------------------
 // DevArena
 // ---------------------------------------------------------------------------
+void *DevAlloc::get(size_t bytes, cudaStream_t st) const {
+  if (!fa) {
+    void *p = nullptr;
+    HS_CUDA(cudaMalloc(&p, bytes));
+    return p;
+  }
+  void *p = fa((uint64_t)bytes, device, (void *)st, ctx);
+  if (!p) fail(HS_ERR_OOM, "the allocator hook returned no memory for " + std::to_string(bytes) + " bytes");
+  if ((uintptr_t)p & 255) {
+    put(p, st);
+    fail(HS_ERR_INVALID, "the allocator hook returned a pointer that is not 256-byte aligned");
+  }
+  return p;
+}
+
+void DevAlloc::put(void *p, cudaStream_t st) const noexcept {
+  if (!p) return;
+  if (!ff) {
+    cudaFree(p);
+    return;
+  }
+  cudaDeviceSynchronize();
+  ff(p, device, (void *)st, ctx);
+}
+
 DevArena::~DevArena() {
-  for (auto &c : chunks_) cudaFree(c.first);
+  for (auto &c : chunks_) al_.put(c.first, st_);
 }
 
 void *DevArena::alloc(size_t bytes) {
@@ -53,8 +78,7 @@ void *DevArena::alloc(size_t bytes) {
   }
   if (cur_ < 0 || cur_ >= (int)chunks_.size()) {
     const size_t sz = std::max(min_chunk_, bytes);
-    char *p = nullptr;
-    HS_CUDA(cudaMalloc(&p, sz));
+    char *p = (char *)al_.get(sz, st_);
     chunks_.push_back({p, sz});
     cur_ = (int)chunks_.size() - 1;
     off_ = 0;
@@ -447,6 +471,14 @@ struct Exec : TcTimer {
     HS_CUDA(cudaEventCreate(&ev_big[0]));
     HS_CUDA(cudaEventCreate(&ev_big[1]));
   }
+  // the device memory of this factorization's descriptors and status words
+  // comes from the (first) handle's source; set before the first allocation
+  DevAlloc al;
+  void use_alloc(const DevAlloc &a) {
+    al = a;
+    scr.set_alloc(a, st);
+    stat.set_alloc(a, st);
+  }
   ~Exec() {
     // copies from the pinned staging buffers may still be in flight after an error
     cudaStreamSynchronize(st);
@@ -456,7 +488,7 @@ struct Exec : TcTimer {
       cudaEventDestroy(fork_ev);
       cudaEventDestroy(join_ev);
     }
-    cudaFree(d_err);
+    al.put(d_err, st);
     for (auto &e : tc_ev) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
@@ -496,7 +528,7 @@ struct Exec : TcTimer {
     g.tc = (tensor_cores && std::is_same<T, float>::value) ? tc : HS_TC_NONE;
     if (g.tc != HS_TC_NONE) {
       if (!d_err) {
-        HS_CUDA(cudaMalloc(&d_err, sizeof(int)));
+        al.get(&d_err, 256, st);
         HS_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
       }
       tc_pending = true;
@@ -826,7 +858,7 @@ void Run<T>::leaf_setup() {
         if (a > b) continue;
         dest[e] = off[bkey(a, b)] + (int64_t)(p - lp[a]) * size_[b] + (c - lp[b]);
       }
-    HS_CUDA(cudaMalloc(&h_.d_leaf_dest, sizeof(int64_t) * std::max<int64_t>(P_.nnz, 1)));
+    h_.alloc.get(&h_.d_leaf_dest, sizeof(int64_t) * std::max<int64_t>(P_.nnz, 1), st_);
     HS_CUDA(cudaMemcpyAsync(h_.d_leaf_dest, dest.data(), sizeof(int64_t) * P_.nnz, cudaMemcpyHostToDevice, st_));
     h_.leaf_total = total;
     if (use_phi_) {
@@ -838,10 +870,10 @@ void Run<T>::leaf_setup() {
       for (int64_t p = 0; p < P_.n; ++p)
         for (int j = 0; j < np; ++j)
           ph[(size_t)p * np + j] = user ? (T)phi_host_[(size_t)j * P_.n + P_.perm[p]] : T(1);
-      HS_CUDA(cudaMalloc(&h_.d_phi0, sizeof(T) * ph.size()));
+      h_.alloc.get(&h_.d_phi0, sizeof(T) * ph.size(), st_);
       if (h_.scale && user) {
         // the caller's vectors are kept; each factorization maps them to D^1/2 phi
-        HS_CUDA(cudaMalloc(&h_.d_phi_raw, sizeof(T) * ph.size()));
+        h_.alloc.get(&h_.d_phi_raw, sizeof(T) * ph.size(), st_);
         HS_CUDA(cudaMemcpyAsync(h_.d_phi_raw, ph.data(), sizeof(T) * ph.size(), cudaMemcpyHostToDevice, st_));
       } else {
         HS_CUDA(cudaMemcpyAsync(h_.d_phi0, ph.data(), sizeof(T) * ph.size(), cudaMemcpyHostToDevice, st_));
@@ -1908,6 +1940,7 @@ template <typename T>
 void factorize_t(const std::vector<FactorHandle *> &hs, const std::vector<const double *> &phis,
                  cudaStream_t st, std::vector<int> *status, std::vector<std::string> *msg) {
   Exec ex(st);
+  ex.use_alloc(hs[0]->alloc);
   ex.prof = phase_profiling();
   const int prec = hs[0]->prec;
   ex.tc = tc_kind_of(prec);
@@ -1920,8 +1953,10 @@ void factorize_t(const std::vector<FactorHandle *> &hs, const std::vector<const 
   std::vector<std::unique_ptr<Run<T>>> runs;
   for (size_t p = 0; p < hs.size(); ++p) {
     FactorHandle &h = *hs[p];
-    if (!h.pers) h.pers.reset(new DevArena(256ull << 20));
-    if (!h.scratch) h.scratch.reset(new DevArena(64ull << 20));
+    if (!h.pers) h.pers.reset(new DevArena(256ull << 20, h.alloc));
+    if (!h.scratch) h.scratch.reset(new DevArena(64ull << 20, h.alloc));
+    h.pers->set_alloc(h.alloc, st);
+    h.scratch->set_alloc(h.alloc, st);
     h.pers->reset();     // a refactorization reuses the previous factor's memory
     h.scratch->reset();
     h.info = hs_info{};

@@ -14,18 +14,45 @@
 
 namespace hs {
 
-// Chunked bump allocator over cudaMalloc'ed chunks (256-byte aligned).
+// Where a handle's device memory comes from: the CUDA runtime, or the
+// caller's hook (hs_opts.allocator).  get() fails with HS_ERR_OOM when the
+// hook has no memory and HS_ERR_INVALID when it returns a pointer that is
+// not 256-byte aligned; put() synchronises the device before it hands a
+// block back to the hook, as cudaFree does before it releases one.
+struct DevAlloc {
+  hs_alloc_fn fa = nullptr;
+  hs_free_fn ff = nullptr;
+  void *ctx = nullptr;
+  int device = 0;
+  bool hooked() const { return fa != nullptr; }
+  void *get(size_t bytes, cudaStream_t st) const;
+  void put(void *p, cudaStream_t st) const noexcept;
+  template <typename X>
+  void get(X **p, size_t bytes, cudaStream_t st) const {
+    *p = (X *)get(bytes, st);
+  }
+};
+
+// Chunked bump allocator over device chunks (256-byte aligned) taken from a
+// DevAlloc.
 class DevArena {
  public:
   explicit DevArena(size_t min_chunk) : min_chunk_(min_chunk) {}
+  DevArena(size_t min_chunk, const DevAlloc &al) : min_chunk_(min_chunk), al_(al) {}
   ~DevArena();
   void *alloc(size_t bytes);
   void reset();  // keeps the chunks for reuse
   size_t used() const { return used_; }
   size_t reserved() const { return reserved_; }
+  void set_alloc(const DevAlloc &al, cudaStream_t st) {
+    al_ = al;
+    st_ = st;
+  }
 
  private:
   std::vector<std::pair<char *, size_t>> chunks_;
+  DevAlloc al_;
+  cudaStream_t st_ = nullptr;
   size_t min_chunk_;
   int cur_ = -1;
   size_t off_ = 0;
@@ -109,6 +136,7 @@ struct FactorHandle {
   cudaStream_t stream = nullptr;
   int device = 0;
   bool valid = false;                  // holds a usable factorization
+  DevAlloc alloc;                      // source of every device block the handle holds
 
   // permuted CSR (cluster order), FP64, for the SpMV of PCG
   int32_t *d_rowptr = nullptr, *d_col = nullptr;

@@ -873,31 +873,32 @@ void apply_ws(FactorHandle &h, int nrhs, cudaStream_t st) {
   run_graph(graph_for(h, nrhs, [&](cudaStream_t cs) { apply_ws_direct(h, nrhs, cs); }), st);
 }
 
-void ensure_buffers(FactorHandle &h, int nrhs_cap) {
+void ensure_buffers(FactorHandle &h, int nrhs_cap, cudaStream_t st) {
   const int64_t tneed0 = std::max<int64_t>(std::max<int64_t>(h.tmax, h.root_m), 1);
   if (h.nrhs_cap >= nrhs_cap && h.d_ws && h.ws_cap >= h.ws_size && h.t_cap >= tneed0) return;
   nrhs_cap = std::max(nrhs_cap, h.nrhs_cap);
   h.drop_graphs();   // they hold the old buffers
-  cudaFree(h.d_ws);
-  cudaFree(h.d_t);
-  cudaFree(h.d_pcg);
-  cudaFree(h.d_part);
-  cudaFree(h.d_scal);
-  cudaFree(h.d_iflags);
+  h.alloc.put(h.d_ws, st);
+  h.alloc.put(h.d_t, st);
+  h.alloc.put(h.d_pcg, st);
+  h.alloc.put(h.d_part, st);
+  h.alloc.put(h.d_scal, st);
+  h.alloc.put(h.d_iflags, st);
   h.d_ws = h.d_t = h.d_pcg = h.d_part = h.d_scal = nullptr;
   h.d_iflags = nullptr;
+  h.nrhs_cap = 0;   // until every buffer below exists (an allocation may fail)
   const int64_t n = h.plan.n;
   const size_t es = h.prec == HS_PREC_F64 ? sizeof(double) : sizeof(float);
-  HS_CUDA(cudaMalloc(&h.d_ws, es * std::max<int64_t>(h.ws_size, 1) * nrhs_cap));
+  h.alloc.get(&h.d_ws, es * std::max<int64_t>(h.ws_size, 1) * nrhs_cap, st);
   const int64_t tneed = tneed0;
-  HS_CUDA(cudaMalloc(&h.d_t, es * 2 * tneed * nrhs_cap));
+  h.alloc.get(&h.d_t, es * 2 * tneed * nrhs_cap, st);
   h.ws_cap = std::max<int64_t>(h.ws_size, 1);
   h.t_cap = tneed;
-  HS_CUDA(cudaMalloc(&h.d_pcg, sizeof(double) * 7 * n * nrhs_cap));
+  h.alloc.get(&h.d_pcg, sizeof(double) * 7 * n * nrhs_cap, st);
   h.part_blocks = 152 * 8;
-  HS_CUDA(cudaMalloc(&h.d_part, sizeof(double) * h.part_blocks * 32));
-  HS_CUDA(cudaMalloc(&h.d_scal, sizeof(double) * 6 * 32));
-  HS_CUDA(cudaMalloc(&h.d_iflags, sizeof(int) * (2 * 32 + 2)));
+  h.alloc.get(&h.d_part, sizeof(double) * h.part_blocks * 32, st);
+  h.alloc.get(&h.d_scal, sizeof(double) * 6 * 32, st);
+  h.alloc.get(&h.d_iflags, sizeof(int) * (2 * 32 + 2), st);
   HS_CUDA(cudaMemset(h.d_iflags, 0, sizeof(int) * (2 * 32 + 2)));
   if (!h.h_done) HS_CUDA(cudaMallocHost(&h.h_done, sizeof(int)));
   h.nrhs_cap = nrhs_cap;
@@ -962,28 +963,28 @@ void apply_prepare(FactorHandle &h, cudaStream_t st) {
     }
   }
   if (hints.size() > h.hints_cap) {
-    cudaFree(h.d_hints);
+    h.alloc.put(h.d_hints, st);
     h.d_hints = nullptr;
-    HS_CUDA(cudaMalloc(&h.d_hints, sizeof(int) * hints.size()));
+    h.alloc.get(&h.d_hints, sizeof(int) * hints.size(), st);
     h.hints_cap = hints.size();
   }
   if (!hints.empty())
     HS_CUDA(cudaMemcpyAsync(h.d_hints, hints.data(), sizeof(int) * hints.size(), cudaMemcpyHostToDevice, st));
-  cudaFree(h.d_apply_steps);
-  cudaFree(h.d_waves);
+  h.alloc.put(h.d_apply_steps, st);
+  h.alloc.put(h.d_waves, st);
   h.d_apply_steps = nullptr;
   h.d_waves = nullptr;
   h.apply_nsteps = (int)steps.size();
   if (steps.empty()) return;
-  HS_CUDA(cudaMalloc(&h.d_apply_steps, sizeof(ApplyStepDev) * steps.size()));
+  h.alloc.get(&h.d_apply_steps, sizeof(ApplyStepDev) * steps.size(), st);
   HS_CUDA(cudaMemcpyAsync(h.d_apply_steps, steps.data(), sizeof(ApplyStepDev) * steps.size(), cudaMemcpyHostToDevice,
                           st));
-  HS_CUDA(cudaMalloc(&h.d_waves, sizeof(WaveApply) * std::max<size_t>(h.waves.size(), 1)));
+  h.alloc.get(&h.d_waves, sizeof(WaveApply) * std::max<size_t>(h.waves.size(), 1), st);
   if (!h.waves.empty())
     HS_CUDA(cudaMemcpyAsync(h.d_waves, h.waves.data(), sizeof(WaveApply) * h.waves.size(), cudaMemcpyHostToDevice,
                             st));
   if (!h.d_apply_bar) {
-    HS_CUDA(cudaMalloc(&h.d_apply_bar, 2 * sizeof(unsigned) + sizeof(int)));
+    h.alloc.get(&h.d_apply_bar, 2 * sizeof(unsigned) + sizeof(int), st);
     HS_CUDA(cudaMemsetAsync(h.d_apply_bar, 0, 2 * sizeof(unsigned) + sizeof(int), st));
     h.d_apply_err = (int *)(h.d_apply_bar + 2);
   }
@@ -1003,7 +1004,7 @@ int apply_error(FactorHandle &h) {
 }
 
 void apply_solve(FactorHandle &h, const double *r, double *z, int nrhs, int64_t ld, cudaStream_t st) {
-  ensure_buffers(h, std::max(nrhs, h.nrhs_cap));
+  ensure_buffers(h, std::max(nrhs, h.nrhs_cap), st);
   const int64_t n = h.plan.n;
   if (h.prec == HS_PREC_F64) {
     k_gather_in<double><<<grid_for(n * nrhs), 256, 0, st>>>(r, ld, h.d_perm, n, nrhs, nrhs, (double *)h.d_ws,
@@ -1058,7 +1059,7 @@ int pcg_solve(FactorHandle &h, const double *b, double *x, int nrhs, int64_t ld,
               int maxit, int *iters, double *relres, cudaStream_t st) {
   int np = 1;
   while (np < nrhs) np <<= 1;
-  ensure_buffers(h, std::max(np, h.nrhs_cap));
+  ensure_buffers(h, std::max(np, h.nrhs_cap), st);
   const int64_t n = h.plan.n;
   const int64_t tot = n * np;
   double *X = h.d_pcg, *R = X + tot, *P0 = R + tot, *P1 = P0 + tot, *Q = P1 + tot, *B = Q + tot, *Z = B + tot;
@@ -1243,7 +1244,7 @@ void gm_dots(const double *V, int64_t n, int nv, const double *w, double *part, 
 
 int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int maxit, int restart, int *iters,
                 double *relres, cudaStream_t st) {
-  ensure_buffers(h, std::max(1, h.nrhs_cap));
+  ensure_buffers(h, std::max(1, h.nrhs_cap), st);
   const int64_t n = h.plan.n;
   const int mr = std::max(1, (restart > 0 && restart < maxit) ? restart : maxit);
   // V (mr + 1 vectors), Z (mr), w, u, X, B, R; part (mr + 1) x blocks; h1, h2,
@@ -1251,10 +1252,10 @@ int gmres_solve(FactorHandle &h, const double *b, double *x, double rtol, int ma
   const int nb = gm_blocks(n);
   const size_t need = (size_t)(2 * mr + 6) * n + (size_t)(mr + 1) * nb + 2 * (size_t)(mr + 1) + 2 + (size_t)(mr + 1);
   if (h.gm_cap < need) {
-    cudaFree(h.d_gm);
+    h.alloc.put(h.d_gm, st);
     h.d_gm = nullptr;
     h.gm_cap = 0;
-    HS_CUDA(cudaMalloc(&h.d_gm, sizeof(double) * need));
+    h.alloc.get(&h.d_gm, sizeof(double) * need, st);
     h.gm_cap = need;
   }
   double *V = h.d_gm, *Zm = V + (size_t)(mr + 1) * n, *W = Zm + (size_t)mr * n, *U = W + n, *X = U + n, *B = X + n,
@@ -1451,32 +1452,32 @@ FactorHandle::~FactorHandle() {
   drop_graphs();
   if (cap_stream) cudaStreamDestroy(cap_stream);
   if (h_done) cudaFreeHost(h_done);
-  cudaFree(d_src);
-  cudaFree(d_leaf_dest);
-  cudaFree(d_phi0);
-  cudaFree(d_phi_raw);
-  cudaFree(d_apply_steps);
-  cudaFree(d_waves);
-  cudaFree(d_apply_bar);
-  cudaFree(d_hints);
-  cudaFree(d_dscale);
-  cudaFree(d_val_f);
-  cudaFree(d_flag);
-  cudaFree(d_rowptr);
-  cudaFree(d_col);
-  cudaFree(d_val);
-  cudaFree(d_perm);
-  cudaFree(d_nodes);
-  cudaFree(d_nbrs);
-  cudaFree(d_targets);
-  cudaFree(d_contribs);
-  cudaFree(d_ws);
-  cudaFree(d_t);
-  cudaFree(d_pcg);
-  cudaFree(d_gm);
-  cudaFree(d_part);
-  cudaFree(d_scal);
-  cudaFree(d_iflags);
+  alloc.put(d_src, stream);
+  alloc.put(d_leaf_dest, stream);
+  alloc.put(d_phi0, stream);
+  alloc.put(d_phi_raw, stream);
+  alloc.put(d_apply_steps, stream);
+  alloc.put(d_waves, stream);
+  alloc.put(d_apply_bar, stream);
+  alloc.put(d_hints, stream);
+  alloc.put(d_dscale, stream);
+  alloc.put(d_val_f, stream);
+  alloc.put(d_flag, stream);
+  alloc.put(d_rowptr, stream);
+  alloc.put(d_col, stream);
+  alloc.put(d_val, stream);
+  alloc.put(d_perm, stream);
+  alloc.put(d_nodes, stream);
+  alloc.put(d_nbrs, stream);
+  alloc.put(d_targets, stream);
+  alloc.put(d_contribs, stream);
+  alloc.put(d_ws, stream);
+  alloc.put(d_t, stream);
+  alloc.put(d_pcg, stream);
+  alloc.put(d_gm, stream);
+  alloc.put(d_part, stream);
+  alloc.put(d_scal, stream);
+  alloc.put(d_iflags, stream);
 }
 
 }  // namespace hs

@@ -20,7 +20,12 @@ Scheduling
     device bytes fit in the budget. If they do not, idle resident
     factorizations are evicted, least recently used first. The estimate per
     unknown is calibrated by the factorizations done so far; an admitted
-    factor is then charged its measured bytes.
+    factor is then charged its measured bytes. ``CudaBackend`` measures them
+    exactly: every handle takes its device memory through a counting
+    allocator hook (``_lib.DeviceAllocator``, hs_opts.allocator) backed by
+    PyTorch's caching allocator, so a factor is charged the bytes it holds,
+    plus a reservation for its solve workspaces; when the workspaces outgrow
+    that reservation, the charge follows the bytes held.
   * Right-hand-side batching: solve requests waiting for the same resident
     factorization are merged in arrival order into one ``hs_pcg`` call of at
     most ``max_rhs`` columns.
@@ -103,7 +108,8 @@ class CudaBackend:
     """Runs the work of a slot through the C ABI on the slot's CUDA stream."""
 
     def __init__(self, device: int = 0, eps: float = 1e-2, variant: int = _lib.HS_GC_CONSTANT,
-                 prec: int = _lib.HS_PREC_F32, rtol: float = 1e-10, maxit: int = 1000, scale: bool = False):
+                 prec: int = _lib.HS_PREC_F32, rtol: float = 1e-10, maxit: int = 1000, scale: bool = False,
+                 exact_memory: bool = True):
         import torch
 
         if not torch.cuda.is_available():
@@ -113,10 +119,12 @@ class CudaBackend:
         self.eps, self.variant, self.prec = eps, variant, prec
         self.rtol, self.maxit = rtol, maxit
         self.scale = scale   # factor D^-1/2 A D^-1/2 (hs_opts.scale)
+        # each handle's device memory through its own counting allocator hook
+        self.exact_memory = exact_memory
 
     def clone(self):
         return CudaBackend(self.device.index or 0, self.eps, self.variant, self.prec, self.rtol, self.maxit,
-                           self.scale)
+                           self.scale, self.exact_memory)
 
     def slot(self):
         """Per-worker state: a CUDA stream of its own."""
@@ -131,11 +139,19 @@ class CudaBackend:
             rp = torch.as_tensor(pb.rowptr, dtype=torch.int32).pin_memory().to(d, non_blocking=True)
             ci = torch.as_tensor(pb.col, dtype=torch.int32).pin_memory().to(d, non_blocking=True)
             va = torch.as_tensor(pb.val, dtype=torch.float64).pin_memory().to(d, non_blocking=True)
+            hook = _lib.DeviceAllocator() if self.exact_memory else None
             f = _lib.Factor(rp, ci, va, pb.perm, pb.leaf_ptr, self.eps, self.variant, self.prec, stream=stream,
-                            scale=self.scale)
+                            scale=self.scale, allocator=hook)
             stream.synchronize()
+        if hook is not None:
+            return f, hook.held   # every device byte the handle holds
         # factor arenas + permuted CSR and maps
         return f, int(f.info()["device_bytes"]) + 16 * (pb.n + 1 + 2 * len(pb.col))
+
+    def held(self, f):
+        """Device bytes handle f holds now (None when not counted)."""
+        hook = getattr(f, "_alloc", None)
+        return None if hook is None else hook.held
 
     def solve(self, stream, f, B: np.ndarray):
         """PCG on the rows of B (nrhs, n); returns (X, iters, relres, status)."""
@@ -166,6 +182,7 @@ class Server:
         self.bytes_per_unknown = 24_000.0          # first guess, replaced by measurements
         self._measured = []                        # (n, bytes)
         self.peak_used = 0                         # largest charged total seen
+        self.overgrown = 0                         # solves whose workspaces outgrew the reservation
 
     # ---- memory model -------------------------------------------------------
     def _solve_bytes(self, n: int) -> int:
@@ -221,6 +238,7 @@ class Server:
                     results[q.rid].start = start
                 did_factor = kind == "factor" or not rs.ready
                 err = None
+                grow = [0]   # solve workspaces beyond the charge of the factor
                 try:
                     if did_factor:
                         if rs.factor is not None:
@@ -233,6 +251,10 @@ class Server:
                     if kind == "solve":
                         B = np.concatenate([q.rhs for q in reqlist], axis=0)
                         X, it, rr, code = be.solve(stream, rs.factor, B)
+                        held = getattr(be, "held", None)
+                        now_held = held(rs.factor) if held is not None else None
+                        if now_held is not None and now_held > rs.bytes:
+                            grow[0] = now_held - rs.bytes   # charged below, under the lock
                         c = 0
                         for q in reqlist:
                             r = results[q.rid]
@@ -262,6 +284,10 @@ class Server:
                             self._calibrate(rs.n, rs.bytes)
                         else:
                             rs.bytes = 0
+                    if grow[0] > 0 and rs.ready:
+                        rs.bytes += grow[0]
+                        charge(grow[0])
+                        self.overgrown += 1
                     rs.busy = False
                     rs.last_use = fin
                     state["done"] += len(reqlist)

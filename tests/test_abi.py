@@ -40,9 +40,10 @@ def test_binding_structs_match_the_compiled_abi(lib):
     shift every later field)."""
     import ctypes as C
 
-    sizes = np.zeros(4, dtype=np.int64)
-    assert lib.hs_abi_sizes(sizes.ctypes.data, 4) == 4
-    mine = [C.sizeof(_lib.HsCsr), C.sizeof(_lib.HsClustering), C.sizeof(_lib.HsOpts), C.sizeof(_lib.HsInfo)]
+    sizes = np.zeros(5, dtype=np.int64)
+    assert lib.hs_abi_sizes(sizes.ctypes.data, 5) == 5
+    mine = [C.sizeof(_lib.HsCsr), C.sizeof(_lib.HsClustering), C.sizeof(_lib.HsOpts), C.sizeof(_lib.HsInfo),
+            C.sizeof(_lib.HsAllocator)]
     assert sizes.tolist() == mine
 
 
@@ -140,3 +141,21 @@ def test_options_are_validated_before_any_device_work(lib):
                                  (_lib.HS_GC_PROJ, None, 1, 0.1)):
         o = _lib.HsOpts(0.1, var, 0, ptr, None, 0, nphi, eps1)
         assert lib.hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), None, C.byref(h)) == _lib.HS_ERR_INVALID
+
+
+def test_allocator_hook_is_validated_before_any_device_work(lib):
+    """hs_opts.allocator needs both functions; a half-set hook is refused
+    before the device is touched (no GPU needed)."""
+    import ctypes as C
+
+    A = _lib.HsCsr(4, 4, 1, 1, 1)
+    cl = _lib.HsClustering(1, 1, 1)
+    h = C.c_void_p()
+    hook = _lib.DeviceAllocator()
+    half = _lib.HsAllocator(hook.struct.alloc, _lib.FREE_FN(), None)
+    o = _lib.HsOpts(0.1, _lib.HS_GC_CONSTANT, 0, None)
+    o.allocator = C.addressof(half)
+    assert lib.hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), None, C.byref(h)) == _lib.HS_ERR_INVALID
+    assert "both alloc and free" in lib.hs_last_error().decode()
+    # the binding's hook: every field set, and its counters start at zero
+    assert hook.struct.alloc and hook.struct.free and hook.held == 0 and hook.peak == 0
