@@ -68,15 +68,19 @@ enum {
   HS_PREC_F64 = 0,     /* every factor step in FP64                              */
   HS_PREC_F32 = 1,     /* blocks, Gram, eigen-solves and factor records in FP32
                           (CUDA cores); the rank is decided on the FP32
-                          eigenvalues of the Gram matrix                        */
+                          eigenvalues of the Gram matrix (an FP64 Sturm count
+                          and threshold comparison on the FP32 tridiagonal),
+                          or entirely in FP64 with hs_opts.rank_f64          */
   HS_PREC_TF32 = 2,    /* contractions on tensor cores with TF32 operands and
-                          FP32 accumulation; the truncation (Gram A_sw A_sw^T,
-                          its eigen-solve and the rank decision) in FP64        */
+                          FP32 accumulation; blocks, records and the
+                          truncation as HS_PREC_F32 (hs_opts.rank_f64 moves
+                          the truncation to FP64)                           */
   HS_PREC_BF16 = 3,    /* as HS_PREC_TF32 with BF16 operands                    */
   HS_PREC_TF32X3 = 4   /* contractions on tensor cores with each FP32 operand
                           split into TF32 high and low parts, a b taken as
                           a_hi b_hi + a_hi b_lo + a_lo b_hi (near-FP32
-                          accuracy), FP32 accumulation; truncation as FP32     */
+                          accuracy), FP32 accumulation; truncation as
+                          HS_PREC_F32                                          */
 };
 
 /* Sparse SPD matrix A in CSR form (Sec. 2: A symmetric positive definite).
@@ -203,7 +207,16 @@ typedef struct {
  * allocator: NULL (the CUDA runtime: cudaMalloc / cudaFree), or a device-
  *   memory hook (hs_allocator above) with both functions set; the handle
  *   takes all its device memory from it.  hs_factor_create_batch gives every
- *   handle of the batch the same hook. */
+ *   handle of the batch the same hook.
+ * rank_f64: 0, or 1 to keep the truncation of the FP32 / TF32 / BF16 /
+ *   3xTF32 factors in FP64: the Gram matrix A_sw A_sw^T (and A_sw phi_w) is
+ *   formed in FP64 from FP64 copies of the FP32 blocks, eigen-decomposed in
+ *   FP64, the rank decided in FP64 (Sec. 3.2 threshold; Sec. 6 for GC), and
+ *   the basis U rounded to FP32 for the elimination, which stays in the
+ *   factor precision.  The rank then answers for the FP32 blocks themselves
+ *   rather than for an FP32 eigen-solve of their Gram matrix.  It costs the
+ *   FP64 eigen-solves (GB300's FP64 rate is a small fraction of its FP32
+ *   rate).  Ignored by HS_PREC_F64, which decides in FP64 anyway. */
 typedef struct {
   double eps;
   int32_t variant;
@@ -218,6 +231,7 @@ typedef struct {
   int32_t order_mode;
   double max_rank_ratio;
   const hs_allocator *allocator;
+  int32_t rank_f64;
 } hs_opts;
 
 /* Sizes and counters of a factorization (all host values). */

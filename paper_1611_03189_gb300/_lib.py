@@ -72,7 +72,7 @@ class HsOpts(C.Structure):
                 ("phi", C.c_void_p), ("eps_level", C.c_void_p), ("n_eps_level", C.c_int32),
                 ("n_phi", C.c_int32), ("eps1", C.c_double), ("scale", C.c_int32),
                 ("timeout_cycles", C.c_int64), ("order_mode", C.c_int32), ("max_rank_ratio", C.c_double),
-                ("allocator", C.c_void_p)]
+                ("allocator", C.c_void_p), ("rank_f64", C.c_int32)]
 
 
 # hs_allocator: alloc(bytes, device, stream, ctx) -> device pointer or NULL;
@@ -299,7 +299,8 @@ class Factor:
 
     def __init__(self, rowptr, col, val, perm, leaf_ptr, eps, variant=HS_GC_CONSTANT,
                  prec=HS_PREC_F64, phi=None, stream=None, eps_level=None, eps1=0.0, nbr_dist=1, scale=False,
-                 timeout_cycles=0, order_mode=HS_ORDER_WAVES, max_rank_ratio=0.0, allocator=None):
+                 timeout_cycles=0, order_mode=HS_ORDER_WAVES, max_rank_ratio=0.0, allocator=None,
+                 rank_f64=False):
         import torch
 
         assert rowptr.is_cuda and col.is_cuda and val.is_cuda
@@ -314,7 +315,7 @@ class Factor:
         o = HsOpts(float(eps), int(variant), int(prec), None if self._phi is None else _ptr(self._phi),
                    None if self._epsl is None else _ptr(self._epsl), 0 if self._epsl is None else len(self._epsl),
                    nphi, float(eps1), int(bool(scale)), int(timeout_cycles), int(order_mode),
-                   float(max_rank_ratio), None if allocator is None else allocator.ptr())
+                   float(max_rank_ratio), None if allocator is None else allocator.ptr(), int(bool(rank_f64)))
         h = C.c_void_p()
         self._h = None
         self._alloc = allocator   # the hook must outlive the handle
@@ -397,7 +398,7 @@ class Factor:
 
 
 def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=None, stream=None,
-                 eps_level=None, eps1=0.0, nbr_dist=1, scale=False, allocator=None):
+                 eps_level=None, eps1=0.0, nbr_dist=1, scale=False, allocator=None, rank_f64=False):
     """hs_factor_create_batch over `problems`: a list of (rowptr, col, val,
     perm, leaf_ptr) with rowptr/col int32 and val float64 CUDA tensors and
     perm/leaf_ptr host arrays.  Returns (factors, status): one Factor per
@@ -429,7 +430,7 @@ def factor_batch(problems, eps, variant=HS_GC_CONSTANT, prec=HS_PREC_F64, phis=N
     keep.append(epsl)
     o = HsOpts(float(eps), int(variant), int(prec), None, None if epsl is None else _ptr(epsl),
                0 if epsl is None else len(epsl), nphi, float(eps1), int(bool(scale)), 0, HS_ORDER_WAVES, 0.0,
-               None if allocator is None else allocator.ptr())
+               None if allocator is None else allocator.ptr(), int(bool(rank_f64)))
     out = (C.c_void_p * k)()
     status = np.zeros(k, dtype=np.int32)
     code = lib().hs_factor_create_batch(k, A, cl, C.byref(o), phi_arr, _stream_ptr(stream), out, _ptr(status))

@@ -199,6 +199,7 @@ void setup_handle(FactorHandle &h, const hs_csr *A, const hs_clustering *cl, con
   h.eps1 = o->variant == HS_GC_PROJ ? o->eps1 : 0.0;
   h.timeout_cycles = o->timeout_cycles;
   h.max_rank_ratio = o->max_rank_ratio;
+  h.rank_f64 = o->rank_f64 != 0 && o->factor_prec != HS_PREC_F64;
   h.eps_level.clear();
   // pattern to the host for the planner
   std::vector<int32_t> rp(A->n + 1), ci(A->nnz);
@@ -244,6 +245,7 @@ void check_opts(const hs_opts *o) {
   if (o->timeout_cycles < 0) fail(HS_ERR_INVALID, "timeout_cycles must be >= 0");
   if (!(o->max_rank_ratio >= 0.0 && o->max_rank_ratio <= 1.0))
     fail(HS_ERR_INVALID, "max_rank_ratio must be in [0, 1]");
+  if (o->rank_f64 != 0 && o->rank_f64 != 1) fail(HS_ERR_INVALID, "rank_f64 must be 0 or 1");
   if (o->allocator && (!o->allocator->alloc || !o->allocator->free))
     fail(HS_ERR_INVALID, "an allocator hook needs both alloc and free");
   if (o->order_mode != HS_ORDER_WAVES && o->order_mode != HS_ORDER_SEQUENTIAL)

@@ -721,6 +721,14 @@ struct WaveBatches {
   CholBatch<T> chol;
   std::vector<TruncTask<T>> trunc, trunc_big;
   int max_trunc_m = 0, max_big_m = 0;
+  // the FP64 truncation of the mixed factors (hs_opts.rank_f64): FP64 copies
+  // of A_sW, phi_W and phi_s, their Gram, FP64 truncation tasks (ranks in the
+  // slots after the T tasks', from k_off64 on), the basis narrowed to T
+  std::vector<ConvTask> widen, narrow;
+  GemmBatch<double> gram64;
+  std::vector<TruncTask<double>> trunc64, trunc_big64;
+  int max_trunc64_m = 0, max_big64_m = 0;
+  size_t k_off64 = 0;
   // large-path re-orthonormalisation of U (CholQR2)
   GemmBatch<T> o1, o2, o3, o4;
   CholBatch<T> oc1, oc2;
@@ -774,6 +782,8 @@ class Run {
   void merge(int nred, int key_base, SumBatch<T> &sb);
   void end_level(const PlanLevel &lv, int li);
   Tag tag(int kind, int level, int s) const { return Tag{kind, level, s, prob_}; }
+  // the truncation (Gram, eigen-solve, rank) in FP64 on an FP32 factor
+  bool rank64() const { return std::is_same<T, float>::value && h_.rank_f64; }
   // tolerance of the super nodes of a level (adaptive list indexed from the leaves)
   double level_eps(int level) const {
     const int j = P_.L - level;
@@ -809,7 +819,9 @@ class Run {
   const PlanLevel *lv_ = nullptr;
   std::vector<Sup> cur_;
   std::vector<int> trunc_sup_, big_sup_;      // super nodes of this run's truncation tasks
+  std::vector<int> trunc64_sup_, big64_sup_;  // the same for the FP64 truncation tasks
   size_t chol_first_ = 0, chol_count_ = 0, trunc_first_ = 0, big_first_ = 0;
+  size_t trunc64_first_ = 0, big64_first_ = 0;
   size_t c_next_ = 0;   // next super node of the wave whose phase-B tasks are built
   double flops_ = 0.0;
   // device time (of the launches taken part in) and nominal eigen-solve flops
@@ -1012,10 +1024,14 @@ void Run<T>::wave_a(int li, int widx, WaveBatches<T> &B) {
   c_next_ = 0;
   trunc_sup_.clear();
   big_sup_.clear();
+  trunc64_sup_.clear();
+  big64_sup_.clear();
   chol_first_ = B.chol.tasks.size();
   trunc_first_ = B.trunc.size();
   big_first_ = B.trunc_big.size();
-  const double f0 = B.chol.flops + B.gram.flops;
+  trunc64_first_ = B.trunc64.size();
+  big64_first_ = B.trunc_big64.size();
+  const double f0 = B.chol.flops + B.gram.flops + B.gram64.flops;
   for (size_t q = 0; q < wl.size(); ++q) {
     Sup &x = cur_[q];
     const int s = wl[q];
@@ -1046,7 +1062,7 @@ void Run<T>::wave_a(int li, int widx, WaveBatches<T> &B) {
     if (x.red) {
       x.AsW = talloc<T>(scr, (size_t)m * x.dW);
       for (size_t j = 0; j < ps.W.size(); ++j) oriented(s, ps.W[j], x.AsW + x.Woff[j], x.dW, size_[ps.W[j]]);
-      x.G = talloc<T>(scr, (size_t)m * m);
+      x.G = rank64() ? nullptr : talloc<T>(scr, (size_t)m * m);
       x.U = talloc<T>(scr, (size_t)m * m);
       if (use_phi_) {
         const int np = h_.nphi;
@@ -1060,7 +1076,49 @@ void Run<T>::wave_a(int li, int widx, WaveBatches<T> &B) {
     auto dit = blocks_.find(bkey(s, s));
     if (dit == blocks_.end()) fail(HS_ERR_INVALID, "internal: missing diagonal block");
     B.chol.add(dit->second.ptr, dit->second.ld, x.Linv, m, tag(0, lv.level, s));
-    if (x.red && m > 0) {
+    if (x.red && m > 0 && rank64()) {
+      // FP64 copies of the FP32 operands; Gram, eigen-solve and rank in FP64
+      const int np = use_phi_ ? h_.nphi : 0;
+      double *AsW64 = talloc<double>(scr, (size_t)m * x.dW);
+      B.widen.push_back(ConvTask{x.AsW, AsW64, (int64_t)m * x.dW, 1});
+      TruncTask<double> tt;
+      tt.G = talloc<double>(scr, (size_t)m * m);
+      tt.a = nullptr;
+      tt.phi = nullptr;
+      if (use_phi_) {
+        double *phiW64 = talloc<double>(scr, (size_t)x.dW * np);
+        B.widen.push_back(ConvTask{x.phiW, phiW64, (int64_t)x.dW * np, 1});
+        double *phi64 = talloc<double>(scr, (size_t)m * np);
+        B.widen.push_back(ConvTask{phi_[s], phi64, (int64_t)m * np, 1});
+        double *a64 = talloc<double>(scr, (size_t)m * np);
+        B.gram64.add(AsW64, x.dW, 0, phiW64, np, 0, a64, np, m, np, x.dW, 1.0, 0.0);
+        tt.a = a64;
+        tt.phi = phi64;
+      }
+      B.gram64.add(AsW64, x.dW, 0, AsW64, x.dW, 1, const_cast<double *>(tt.G), m, m, m, x.dW, 1.0, 0.0);
+      tt.np = np;
+      tt.eps1 = h_.eps1;
+      double *U64 = talloc<double>(scr, (size_t)m * m);
+      tt.U = U64;
+      tt.work = nullptr;
+      tt.eps = level_eps(lv.level);
+      tt.m = m;
+      tt.k_idx = 0;
+      tt.cap = (h_.max_rank_ratio > 0.0 && tt.eps > 0.0)
+                   ? std::max(1, (int)std::floor(h_.max_rank_ratio * (double)m))
+                   : m;
+      if (m <= eig_small_max<double>()) {
+        B.trunc64.push_back(tt);
+        trunc64_sup_.push_back((int)q);
+        B.max_trunc64_m = std::max(B.max_trunc64_m, m);
+      } else {
+        tt.work = talloc<double>(scr, trunc_big_work_elems<double>(m));
+        big64_sup_.push_back((int)q);
+        B.max_big64_m = std::max(B.max_big64_m, m);
+        B.trunc_big64.push_back(tt);
+      }
+      B.narrow.push_back(ConvTask{U64, x.U, (int64_t)m * m, 0});
+    } else if (x.red && m > 0) {
       B.gram.add(x.AsW, x.dW, 0, x.AsW, x.dW, 1, x.G, m, m, m, x.dW, T(1), T(0));
       if (use_phi_) B.gram.add(x.AsW, x.dW, 0, x.phiW, h_.nphi, 0, x.a, h_.nphi, m, h_.nphi, x.dW, T(1), T(0));
       TruncTask<T> tt;
@@ -1089,7 +1147,7 @@ void Run<T>::wave_a(int li, int widx, WaveBatches<T> &B) {
       }
     }
   }
-  flops_ += B.chol.flops + B.gram.flops - f0;
+  flops_ += B.chol.flops + B.gram.flops + B.gram64.flops - f0;
   chol_count_ = B.chol.tasks.size() - chol_first_;
 }
 
@@ -1104,6 +1162,11 @@ void Run<T>::wave_b(const int *hb, size_t nchol, size_t ntrunc, double big_ms, W
   if (bad) return;   // this problem leaves the lock step
   for (size_t i = 0; i < trunc_sup_.size(); ++i) S[trunc_sup_[i]].k = hb[nchol + trunc_first_ + i];
   for (size_t i = 0; i < big_sup_.size(); ++i) S[big_sup_[i]].k = hb[nchol + ntrunc + big_first_ + i];
+  for (size_t i = 0; i < trunc64_sup_.size(); ++i) S[trunc64_sup_[i]].k = hb[nchol + B.k_off64 + trunc64_first_ + i];
+  for (size_t i = 0; i < big64_sup_.size(); ++i)
+    S[big64_sup_[i]].k = hb[nchol + B.k_off64 + B.trunc64.size() + big64_first_ + i];
+  for (size_t i = 0; i < trunc64_sup_.size(); ++i) trunc_sup_.push_back(trunc64_sup_[i]);
+  for (size_t i = 0; i < big64_sup_.size(); ++i) big_sup_.push_back(big64_sup_[i]);
   // nominal eigen-solve work of a node: Householder tridiagonalisation
   // (4/3 m^3) and back-transformation of the k kept vectors (2 m^2 k)
   auto eig_work = [](double m, double k) { return 4.0 / 3.0 * m * m * m + 2.0 * m * m * k; };
@@ -1731,6 +1794,33 @@ struct HostClock {
 // Runs the factorizations of `runs` in lock step: at every step (level counted
 // from the leaves, wave index) the work of all problems that have that step
 // goes into one launch per kernel kind, with one read of the new ranks.
+// The large-node truncation tasks of a wave split by class (256 or 1024
+// threads per node, or the multi-CTA path), uploaded, then launched.
+template <typename U>
+struct BigClasses {
+  std::vector<TruncTask<U>> cls[3];
+  int cmax[3] = {0, 0, 0};
+  size_t o[3] = {0, 0, 0};
+  char *d = nullptr;
+  void prepare(Exec &ex, const std::vector<TruncTask<U>> &tasks) {
+    for (const TruncTask<U> &t : tasks) {
+      const int c = (t.eps > 0.0 && t.m >= grid_tridiag_min()) ? 2 : t.m <= kTruncBigMidMax ? 0 : 1;
+      cls[c].push_back(t);
+      cmax[c] = std::max(cmax[c], t.m);
+    }
+    Uploader u;
+    o[0] = u.add(cls[0]);
+    o[1] = u.add(cls[1]);
+    o[2] = u.add(cls[2]);
+    d = u.upload(ex.scr, ex.sg, ex.st);
+  }
+  void launch(Exec &ex, int *d_k, double eps, int variant) {
+    launch_trunc_big<U>((const TruncTask<U> *)(d + o[0]), (int)cls[0].size(), d_k, eps, variant, cmax[0], ex.st);
+    launch_trunc_big<U>((const TruncTask<U> *)(d + o[1]), (int)cls[1].size(), d_k, eps, variant, cmax[1], ex.st);
+    if (!cls[2].empty()) trunc_grid<U>(ex, cls[2], (const TruncTask<U> *)(d + o[2]), d_k, eps, variant, cmax[2]);
+  }
+};
+
 template <typename T>
 void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
   const auto t_start = std::chrono::steady_clock::now();
@@ -1777,12 +1867,16 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       for (Run<T> *r : wp) r->wave_a(li, w, B);
       hc.tick(1);
       const size_t nchol = B.chol.tasks.size(), ntrunc = B.trunc.size(), nbig = B.trunc_big.size();
+      const size_t nt64 = B.trunc64.size(), nb64 = B.trunc_big64.size();
       for (size_t i = 0; i < ntrunc; ++i) B.trunc[i].k_idx = (int)i;
       for (size_t i = 0; i < nbig; ++i) B.trunc_big[i].k_idx = (int)(ntrunc + i);
+      B.k_off64 = ntrunc + nbig;
+      for (size_t i = 0; i < nt64; ++i) B.trunc64[i].k_idx = (int)(B.k_off64 + i);
+      for (size_t i = 0; i < nb64; ++i) B.trunc_big64[i].k_idx = (int)(B.k_off64 + nt64 + i);
       ex.begin(1);
       B.gather.launch(ex.scr, ex.sg, ex.st);
       ex.end();
-      int *d_stat = (int *)ex.scr.alloc(sizeof(int) * (nchol + ntrunc + nbig + 1));
+      int *d_stat = (int *)ex.scr.alloc(sizeof(int) * (nchol + ntrunc + nbig + nt64 + nb64 + 1));
       int *d_k = d_stat + nchol;
       if (nchol) {
         ex.begin(2);
@@ -1791,6 +1885,14 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
       }
       ex.begin(3);
       ex.gemm(B.gram, false);   // the Gram feeds the rank decision
+      if (!B.widen.empty()) {
+        // FP64 truncation of an FP32 factor: FP64 copies, then their Gram
+        Uploader u;
+        const size_t o = u.add(B.widen);
+        char *d = u.upload(ex.scr, ex.sg, ex.st);
+        launch_convert_list((const ConvTask *)(d + o), (int)B.widen.size(), ex.st);
+        ex.gemm(B.gram64, false);
+      }
       ex.end();
       const double eps = wp[0]->handle().eps;
       const int variant = wp[0]->handle().variant;
@@ -1802,39 +1904,45 @@ void execute(Exec &ex, std::vector<std::unique_ptr<Run<T>>> &runs) {
         launch_trunc<T>((const TruncTask<T> *)(d + o), (int)ntrunc, d_k, eps, variant, B.max_trunc_m, ex.st);
         ex.end();
       }
-      if (nbig) {
+      if (nt64) {
+        Uploader u;
+        const size_t o = u.add(B.trunc64);
+        char *d = u.upload(ex.scr, ex.sg, ex.st);
+        ex.begin(4);
+        launch_trunc<double>((const TruncTask<double> *)(d + o), (int)nt64, d_k, eps, variant, B.max_trunc64_m,
+                             ex.st);
+        ex.end();
+      }
+      if (nbig || nb64) {
         // one launch per class (k_idx keeps each rank's slot): 256 or 1024
         // threads per node, or the multi-CTA path for very large nodes
-        std::vector<TruncTask<T>> cls[3];
-        int cmax[3] = {0, 0, 0};
-        for (const TruncTask<T> &t : B.trunc_big) {
-          const int c = (t.eps > 0.0 && t.m >= grid_tridiag_min()) ? 2 : t.m <= kTruncBigMidMax ? 0 : 1;
-          cls[c].push_back(t);
-          cmax[c] = std::max(cmax[c], t.m);
-        }
-        Uploader u;
-        const size_t o0 = u.add(cls[0]);
-        const size_t o1 = u.add(cls[1]);
-        const size_t o2 = u.add(cls[2]);
-        char *d = u.upload(ex.scr, ex.sg, ex.st);
+        BigClasses<T> bc;
+        BigClasses<double> bc64;
+        if (nbig) bc.prepare(ex, B.trunc_big);
+        if (nb64) bc64.prepare(ex, B.trunc_big64);
         ex.begin(5);
         HS_CUDA(cudaEventRecord(ex.ev_big[0], ex.st));
-        launch_trunc_big<T>((const TruncTask<T> *)(d + o0), (int)cls[0].size(), d_k, eps, variant, cmax[0], ex.st);
-        launch_trunc_big<T>((const TruncTask<T> *)(d + o1), (int)cls[1].size(), d_k, eps, variant, cmax[1], ex.st);
-        if (!cls[2].empty())
-          trunc_grid<T>(ex, cls[2], (const TruncTask<T> *)(d + o2), d_k, eps, variant, cmax[2]);
+        if (nbig) bc.launch(ex, d_k, eps, variant);
+        if (nb64) bc64.launch(ex, d_k, eps, variant);
         HS_CUDA(cudaEventRecord(ex.ev_big[1], ex.st));
         ex.end();
       }
+      if (!B.narrow.empty()) {
+        // the FP64 bases back to the factor precision
+        Uploader u;
+        const size_t o = u.add(B.narrow);
+        char *d = u.upload(ex.scr, ex.sg, ex.st);
+        launch_convert_list((const ConvTask *)(d + o), (int)B.narrow.size(), ex.st);
+      }
       // one read of the statuses and ranks
-      const size_t nread = nchol + ntrunc + nbig;
+      const size_t nread = nchol + ntrunc + nbig + nt64 + nb64;
       int *hb = ex.host_ints(nread + 1);
       if (nread) HS_CUDA(cudaMemcpyAsync(hb, d_stat, sizeof(int) * nread, cudaMemcpyDeviceToHost, ex.st));
       hc.tick(2);
       ex.sync_check();
       hc.tick(3);
       float big_ms = 0.f;
-      if (nbig) HS_CUDA(cudaEventElapsedTime(&big_ms, ex.ev_big[0], ex.ev_big[1]));
+      if (nbig || nb64) HS_CUDA(cudaEventElapsedTime(&big_ms, ex.ev_big[0], ex.ev_big[1]));
       for (Run<T> *r : wp)
         if (r->ok()) r->wave_b(hb, nchol, ntrunc, big_ms, B);
       hc.tick(4);

@@ -133,6 +133,7 @@ struct FactorHandle {
   double eps1 = 0.0;                   // first tolerance of HS_GC_PROJ (Appendix B)
   int64_t timeout_cycles = 0;          // bound of the kernels' waits (0: default)
   double max_rank_ratio = 0.0;         // rank cap k <= floor(ratio m) (0: none)
+  bool rank_f64 = false;               // FP32 factors: truncation (Gram, eigen-solve, rank) in FP64
   cudaStream_t stream = nullptr;
   int device = 0;
   bool valid = false;                  // holds a usable factorization

@@ -171,6 +171,17 @@ struct StatusMerge {
   int *out;
 };
 void launch_status_merge(const StatusMerge *d_tasks, int ntasks, cudaStream_t st);
+// element-wise FP32 -> FP64 (widen = 1) or FP64 -> FP32 copies of a task list
+// (one CTA per task): the FP64 truncation of the mixed factors
+// (hs_opts.rank_f64) reads FP64 copies of the FP32 blocks and writes its
+// basis back in FP32
+struct ConvTask {
+  const void *src;
+  void *dst;
+  int64_t n;
+  int widen;
+};
+void launch_convert_list(const ConvTask *d_tasks, int ntasks, cudaStream_t st);
 template <typename T>
 void launch_chol_inv(const CholTask<T> *d_tasks, int ntasks, int *d_status, int max_m,
                      cudaStream_t st);

@@ -783,6 +783,27 @@ void launch_phi_scale(const T *raw, const double *ds, int64_t n, int np, T *out,
   HS_CUDA(cudaGetLastError());
 }
 
+// one CTA per task, a grid-stride loop over its elements
+static __global__ void k_convert_list(const ConvTask *__restrict__ t, int n) {
+  const ConvTask c = t[blockIdx.x];
+  if (c.widen) {
+    const float *s = (const float *)c.src;
+    double *d = (double *)c.dst;
+    for (int64_t e = threadIdx.x; e < c.n; e += blockDim.x) d[e] = (double)s[e];
+  } else {
+    const double *s = (const double *)c.src;
+    float *d = (float *)c.dst;
+    for (int64_t e = threadIdx.x; e < c.n; e += blockDim.x) d[e] = (float)s[e];
+  }
+}
+
+void launch_convert_list(const ConvTask *d_tasks, int ntasks, cudaStream_t st) {
+  if (ntasks == 0) return;
+  k_convert_list<<<ntasks, 256, 0, st>>>(d_tasks, ntasks);
+  count_launch();
+  HS_CUDA(cudaGetLastError());
+}
+
 void launch_status_merge(const StatusMerge *d_tasks, int ntasks, cudaStream_t st) {
   if (ntasks == 0) return;
   k_status_merge<<<(ntasks + 127) / 128, 128, 0, st>>>(d_tasks, ntasks);

@@ -159,3 +159,15 @@ def test_allocator_hook_is_validated_before_any_device_work(lib):
     assert "both alloc and free" in lib.hs_last_error().decode()
     # the binding's hook: every field set, and its counters start at zero
     assert hook.struct.alloc and hook.struct.free and hook.held == 0 and hook.peak == 0
+
+
+def test_rank_f64_option_is_validated_before_any_device_work(lib):
+    import ctypes as C
+
+    A = _lib.HsCsr(4, 4, 1, 1, 1)
+    cl = _lib.HsClustering(1, 1, 1)
+    h = C.c_void_p()
+    o = _lib.HsOpts(0.1, _lib.HS_GC_CONSTANT, _lib.HS_PREC_F32, None)
+    o.rank_f64 = 2
+    assert lib.hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), None, C.byref(h)) == _lib.HS_ERR_INVALID
+    assert "rank_f64" in lib.hs_last_error().decode()
