@@ -619,6 +619,8 @@ def main():
     ap.add_argument("--prec", default="f32", choices=["f32", "tf32", "tf32x3", "bf16", "f64"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--scale", action="store_true", help="factor the diagonally scaled D^-1/2 A D^-1/2")
+    ap.add_argument("--rank-f64", action="store_true",
+                    help="mixed factors: truncation (Gram, eigen-solve, rank decision) in FP64 (hs_opts.rank_f64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-f64-arm", action="store_true", help="skip the FP64-factor comparison")
     ap.add_argument("--profile", action="store_true", help="print a phase breakdown to stderr")
@@ -695,7 +697,8 @@ def main():
           for k in range(nsteps)]
     stream = torch.cuda.current_stream()
     t_plan = time.perf_counter()
-    G = _lib.Factor(rp, ci, vals[0], pb0.perm, pb0.leaf_ptr, eps, _lib.HS_GC_CONSTANT, prec, scale=args.scale)
+    G = _lib.Factor(rp, ci, vals[0], pb0.perm, pb0.leaf_ptr, eps, _lib.HS_GC_CONSTANT, prec, scale=args.scale,
+                    rank_f64=args.rank_f64)
     t_plan = time.perf_counter() - t_plan
 
     iters_seen = []
@@ -915,6 +918,8 @@ def main():
                        "leaf": WORKLOADS[args.workload][4], "variant": "GC-constant",
                        "factor_prec": args.prec, "pcg": "fp64", "rtol": 1e-10, "nrhs": args.nrhs,
                        "diagonal_scaling": bool(args.scale),
+                       "rank_decision": ("fp64" if args.prec == "f64" or args.rank_f64
+                                         else "fp32 eigen-solve, fp64 comparison"),
                        "l2": "inputs larger than L2 (factor records > 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "roofline": dominant,

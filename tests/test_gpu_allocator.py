@@ -69,14 +69,11 @@ def test_hook_without_memory_fails_with_oom_and_leaks_nothing():
     assert "allocator hook" in str(ei.value)
     torch.cuda.synchronize()
     assert small.held == 0 and not small.blocks
-    # enough for the factorization but not for the PCG workspace: the solve
+    # no room left for the PCG workspace after the factorization: the solve
     # fails, and succeeds once the hook has memory again
-    probe = _lib.DeviceAllocator()
-    Gp = _factor(pb, _lib.HS_PREC_F32, probe)
-    need = probe.held
-    Gp.close()
-    hook = _lib.DeviceAllocator(limit=need)
+    hook = _lib.DeviceAllocator()
     G = _factor(pb, _lib.HS_PREC_F32, hook)
+    hook.limit = hook.held
     b = torch.as_tensor(P.rhs(pb.n, 9), device="cuda")
     with pytest.raises(_lib.HsError) as ei:
         G.pcg(b, rtol=1e-10, maxit=500)
