@@ -128,8 +128,14 @@ typedef struct {
  *     misaligned pointer is handed back through free and the call fails with
  *     HS_ERR_INVALID.
  *   free(ptr, device, stream, ctx): takes back a pointer alloc returned.  The
- *     library first synchronises the device (as cudaFree does), so no work of
- *     the library still uses the block.
+ *     library first synchronises `stream`, the stream of the call that gives
+ *     the block back (hs_factor_destroy: the stream of the last
+ *     factorization; a solve that grows its workspaces: its own), so no work
+ *     the library enqueued there still uses the block.  It does not
+ *     synchronise the whole device (that would break CUDA graph captures
+ *     under way in other threads), so work of the handle that the caller
+ *     enqueued on other streams must have completed by then: the same rule
+ *     as for any stream-ordered allocator.
  *   ctx: passed through unchanged.
  * Both are called on the calling thread, inside library calls on the handle
  * (creation, refactor, the solves, which grow their workspaces on first use

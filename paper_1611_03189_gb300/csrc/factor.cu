@@ -61,7 +61,10 @@ void DevAlloc::put(void *p, cudaStream_t st) const noexcept {
     cudaFree(p);
     return;
   }
-  cudaDeviceSynchronize();
+  // the library's work that used the block is on `st` (a handle's calls are
+  // ordered); a device-wide synchronisation here would also invalidate
+  // graph captures other threads have under way on this device
+  cudaStreamSynchronize(st);
   ff(p, device, (void *)st, ctx);
 }
 

@@ -17,8 +17,8 @@ namespace hs {
 // Where a handle's device memory comes from: the CUDA runtime, or the
 // caller's hook (hs_opts.allocator).  get() fails with HS_ERR_OOM when the
 // hook has no memory and HS_ERR_INVALID when it returns a pointer that is
-// not 256-byte aligned; put() synchronises the device before it hands a
-// block back to the hook, as cudaFree does before it releases one.
+// not 256-byte aligned; put() waits for the work enqueued on the freeing
+// call's stream before it hands a block back to the hook.
 struct DevAlloc {
   hs_alloc_fn fa = nullptr;
   hs_free_fn ff = nullptr;
