@@ -761,12 +761,15 @@ def stationary(F: Factor, rowptr, col, val, x_star, tol=1e-6, maxit=2000):
     return maxit
 
 
-def gmres_solve(F: Factor, rowptr, col, val, b, rtol=1e-10, maxit=300, restart=0):
+def gmres_solve(F: Factor, rowptr, col, val, b, rtol=1e-10, maxit=300, restart=0, precond=None):
     """Right-preconditioned GMRES (Sec. 7, Tables 2-5), x_0 = 0: Arnoldi on
     A A_H^-1 with modified Gram-Schmidt, the Hessenberg least-squares problem
     solved directly at every step, stop when its residual is below rtol ||b||;
     restart every `restart` steps (0: never), x += A_H^-1 V y at the end of a
-    cycle.  Returns (x, Arnoldi steps, true relative residual)."""
+    cycle.  Returns (x, Arnoldi steps, true relative residual).  precond:
+    the map v -> A_H^-1 v (default: apply(F, v))."""
+    if precond is None:
+        precond = lambda v: apply(F, v)  # noqa: E731
     b = np.asarray(b, dtype=np.float64)
     nb = float(np.linalg.norm(b))
     x = np.zeros_like(b)
@@ -786,7 +789,7 @@ def gmres_solve(F: Factor, rowptr, col, val, b, rtol=1e-10, maxit=300, restart=0
         for j in range(m):
             if total >= maxit:
                 break
-            w = csr_matvec(rowptr, col, val, apply(F, V[j]))
+            w = csr_matvec(rowptr, col, val, precond(V[j]))
             for i in range(j + 1):
                 Hm[i, j] = float(V[i] @ w)
                 w = w - Hm[i, j] * V[i]
@@ -801,7 +804,7 @@ def gmres_solve(F: Factor, rowptr, col, val, b, rtol=1e-10, maxit=300, restart=0
                 break
             V.append(w / Hm[j + 1, j])
         if y.size:
-            x = x + apply(F, np.column_stack(V[:y.size]) @ y)
+            x = x + precond(np.column_stack(V[:y.size]) @ y)
     rel = float(np.linalg.norm(b - csr_matvec(rowptr, col, val, x))) / nb
     return x, total, rel
 

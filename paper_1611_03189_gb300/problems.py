@@ -226,6 +226,33 @@ def make_problem(shape, coef: np.ndarray, leaf_size: int = 16, levels: int | Non
     return Problem(n, rowptr, col, val, perm, leaf_ptr, shape, name)
 
 
+def convdiff2d(nx: int, beta: float, theta: float = 0.6, leaf_size: int = 16, levels=None) -> Problem:
+    """Nonsymmetric input (an M-matrix with the five-point pattern): the 2D
+    Poisson stencil plus first-order upwind convection -div grad u + w . grad u,
+    w = (cos theta, sin theta) with cell strength beta (the convection term of
+    a row is beta times the upwind difference).  The pattern is structurally
+    symmetric; the values are not."""
+    ny = nx
+    shape = (nx, ny)
+    n = nx * ny
+    rowptr, col, val = stencil_matrix(shape, coef_constant(shape))
+    val = val.copy()
+    wx, wy = beta * math.cos(theta), beta * math.sin(theta)
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    for ax, w, stride, size in ((0, wx, 1, nx), (1, wy, nx, ny)):
+        coord = (rows // stride) % size
+        # upwind: w > 0 differences with the lower neighbour, w < 0 with the upper
+        up = -stride if w > 0 else stride
+        aw = abs(w)
+        is_diag = col == rows
+        val[is_diag] += aw
+        is_up = (col == rows + up) & (((coord > 0) if w > 0 else (coord < size - 1)))
+        val[is_up] -= aw
+    L = levels_for(n, leaf_size) if levels is None else levels
+    perm, leaf_ptr = bisect_clusters(shape, L)
+    return Problem(n, rowptr, col, val, perm, leaf_ptr, shape, f"convdiff2d_{nx}_b{beta}")
+
+
 def poisson2d(nx: int, ny: int | None = None, leaf_size: int = 16, levels=None) -> Problem:
     ny = nx if ny is None else ny
     return make_problem((nx, ny), coef_constant((nx, ny)), leaf_size, levels,

@@ -183,6 +183,7 @@ class Server:
         self._measured = []                        # (n, bytes)
         self.peak_used = 0                         # largest charged total seen
         self.overgrown = 0                         # solves whose workspaces outgrew the reservation
+        self.final_used = 0                        # charged total when the last request finished
 
     # ---- memory model -------------------------------------------------------
     def _solve_bytes(self, n: int) -> int:
@@ -397,6 +398,7 @@ class Server:
             cv.notify_all()
         for t in threads:
             t.join()
+        self.final_used = used[0]   # charged bytes of the residents left at the end
         for rs in residents.values():
             if rs.factor is not None:
                 be.release(rs.factor)

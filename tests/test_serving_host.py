@@ -178,3 +178,48 @@ def test_failed_request_reports_error_and_loop_continues():
     good = [r for r in res if r.matrix != 1]
     assert bad and all(r.status != 0 and "on purpose" in r.error for r in bad)
     assert all(r.status == 0 for r in good)
+
+
+class CountingBackend(FakeBackend):
+    """As FakeBackend, with held(f): the bytes a handle holds as an allocator
+    hook counts them -- its factor bytes, then its solve workspaces, which
+    appear with its first solve and here grow past the server's reservation."""
+
+    def __init__(self, extra):
+        super().__init__()
+        self.extra = extra
+        self.held_bytes = {}
+
+    def clone(self):
+        return CountingBackend(self.extra)
+
+    def factor(self, stream, pb):
+        f, nbytes = super().factor(stream, pb)
+        self.held_bytes[id(f)] = nbytes
+        return f, nbytes
+
+    def solve(self, stream, f, B):
+        out = super().solve(stream, f, B)
+        self.held_bytes[id(f)] = self.bpu * f.n + self.extra * f.n
+        return out
+
+    def held(self, f):
+        return self.held_bytes.get(id(f))
+
+
+@pytest.mark.parametrize("extra,grows", [(10, False), (10_000, True)])
+def test_charge_follows_the_bytes_a_handle_holds(extra, grows):
+    """A resident's charge is its counted factor bytes plus the solve
+    reservation; when the counted bytes after a solve exceed that, the charge
+    moves up to them (and stays within the budget accounting)."""
+    reqs = [Request(0, "factor", 0, 0.0, problem=_pb(1000, 0)),
+            Request(1, "solve", 0, 0.001, rhs=np.ones((2, 1000)))]
+    be = CountingBackend(extra)
+    srv = Server(budget_bytes=1 << 40, slots=1, backend=be)
+    res = srv.run(reqs, realtime=False)
+    assert all(r.status == 0 for r in res)
+    reserved = 1000 * 1000 + srv._solve_bytes(1000)
+    held = 1000 * 1000 + extra * 1000
+    assert srv.overgrown == (1 if grows else 0)
+    assert srv.final_used == (held if grows else reserved)
+    assert srv.peak_used >= srv.final_used
