@@ -21,8 +21,7 @@ What it follows (arXiv 1611.03189, Yang, Pouransari, Darve):
   * Sec. 7: preconditioned Krylov iteration stopped at relative residual
     1e-10; the stationary iteration x_{k+1} = x_k + A_H^-1 (b - A x_k).
 
-Readings where the paper is silent or ambiguous (each is also listed in the
-design notes):
+Readings where the paper is silent or ambiguous:
   R1 well separated = no edge of the ORIGINAL graph between the two leaf sets.
   R2 truncation: keep sigma_i > eps * ||A_sw||_2 (strict); GC applies the same
      threshold to the singular values of (I - U_1 U_1^T) A_sw.  eps = 0 means no
