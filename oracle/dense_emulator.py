@@ -13,6 +13,13 @@ nonzero pattern of the dense matrix, adjacency from the original matrix,
 compression is recomputed from the dense well-separated block, and no M_ss or
 P_ss is ever formed.  Only the truncation rule (Sec. 3.2 / Sec. 6, readings
 R2-R5 of the oracle) is the same by definition.
+
+With lu=True the matrix may be nonsymmetric (reading R16 of the LU variant,
+oracle/hsolver_lu.py): the basis U compresses [A_sw, A_ws^T] jointly, the
+extended matrix keeps A_ws U in the rest rows of the red column and U^T A_sw
+in the red row's rest columns, and the pivot's lower and upper couplings are
+kept apart (no transposes), so the same literal construction checks the LU
+variant.
 """
 from __future__ import annotations
 
@@ -73,8 +80,10 @@ def _truncate(B, eps, variant, phi_s, phi_w, eps1=0.0):
 class DenseEmulator:
     """Dense extended-system factorization; `solve(b)` returns A_H^-1 b."""
 
-    def __init__(self, A_dense, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None, eps1=0.0, nbr_dist=1):
+    def __init__(self, A_dense, perm, leaf_ptr, eps, variant=GC_CONSTANT, phi=None, eps1=0.0, nbr_dist=1,
+                 lu=False):
         n = A_dense.shape[0]
+        self.lu = lu
         perm = np.asarray(perm)
         self.perm = perm
         Ap = A_dense[np.ix_(perm, perm)]
@@ -147,7 +156,11 @@ class DenseEmulator:
         m = len(Is)
         total = K.shape[0]
         rest = [i for i in range(total) if i not in set(Is)]
-        if W:
+        if W and self.lu:
+            # one basis for both sides: [A_sw, A_ws^T]; GC candidates A_sw phi_w
+            B = np.hstack([K[np.ix_(Is, Iw)], K[np.ix_(Iw, Is)].T])
+            U = _truncate(B, eps, variant, vphi[Is], np.concatenate([vphi[Iw], np.zeros(len(Iw))]), self.eps1)
+        elif W:
             B = K[np.ix_(Is, Iw)]
             U = _truncate(B, eps, variant, vphi[Is], vphi[Iw], self.eps1)
         else:
@@ -166,23 +179,34 @@ class DenseEmulator:
         wpos = [rest.index(i) for i in Iw]
         Ksr[:, wpos] = 0.0                     # A_sw moved onto the black/red nodes
         E[sl_s, sl_o] = Ksr
-        E[sl_o, sl_s] = Ksr.T
+        if self.lu:
+            Krs = K[np.ix_(rest, Is)].copy()
+            Krs[wpos, :] = 0.0                 # A_ws moved onto the red node
+            E[sl_o, sl_s] = Krs
+        else:
+            E[sl_o, sl_s] = Ksr.T
         E[sl_s, sl_b] = U
         E[sl_b, sl_s] = U.T
         E[sl_b, sl_r] = -np.eye(k)
         E[sl_r, sl_b] = -np.eye(k)
-        R = (U.T @ K[np.ix_(Is, Iw)]).T         # A_ws U
+        R = (U.T @ K[np.ix_(Is, Iw)]).T         # (U^T A_sw)^T
         Rfull = np.zeros((nr, k))
         Rfull[wpos, :] = R
-        E[sl_o, sl_r] = Rfull
+        if self.lu:
+            Rcol = np.zeros((nr, k))
+            Rcol[wpos, :] = K[np.ix_(Iw, Is)] @ U   # A_ws U
+            E[sl_o, sl_r] = Rcol
+        else:
+            E[sl_o, sl_r] = Rfull
         E[sl_r, sl_o] = Rfull.T
         piv = list(range(0, m + k))
         keep = list(range(m + k, m + 2 * k + nr))
         P = E[np.ix_(piv, piv)]
         C = E[np.ix_(keep, piv)]
-        Knew = E[np.ix_(keep, keep)] - C @ np.linalg.solve(P, C.T)
+        Cu = E[np.ix_(piv, keep)]
+        Knew = E[np.ix_(keep, keep)] - C @ np.linalg.solve(P, Cu)
         # bookkeeping: map old rest indices -> new positions 0..nr-1, red at the end
-        self.steps.append((Is, rest, P, C, m, k))
+        self.steps.append((Is, rest, P, C, Cu, m, k))
         pos = {old: i for i, old in enumerate(rest)}
         del groups[s]
         for g in list(groups):
@@ -202,16 +226,16 @@ class DenseEmulator:
         b = np.asarray(b, dtype=np.float64)
         cur = b[self.perm]
         saved = []
-        for (Is, rest, P, C, m, k) in self.steps:
+        for (Is, rest, P, C, Cu, m, k) in self.steps:
             top = np.concatenate([cur[Is], np.zeros(k)])
             lower = np.concatenate([cur[rest], np.zeros(k)])
             lower = lower - C @ np.linalg.solve(P, top)
             saved.append(top)
             cur = lower if k else lower[: len(rest)]
         x = np.linalg.solve(self.K_root, cur) if cur.size else cur
-        for (Is, rest, P, C, m, k), top in zip(reversed(self.steps), reversed(saved)):
+        for (Is, rest, P, C, Cu, m, k), top in zip(reversed(self.steps), reversed(saved)):
             psi = x
-            xtop = np.linalg.solve(P, top - C.T @ psi)
+            xtop = np.linalg.solve(P, top - Cu @ psi)
             full = np.empty(len(rest) + m)
             full[rest] = psi[: len(rest)]
             full[Is] = xtop[:m]

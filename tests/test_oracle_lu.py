@@ -1,6 +1,10 @@
 """Pins of the nonsymmetric (LU) variant of the oracle (reading R16), none of
 which re-types its formulas:
 
+* the literal dense extended system (oracle/dense_emulator.py with lu=True:
+  the well-separated blocks moved onto a black/red pair, the pivot
+  eliminated by an explicit dense Schur complement, no M_ss, P_ss or Q_ss
+  formed) gives the same A_H^-1 at eps > 0, to rounding;
 * eps = 0 keeps complete bases, so the factorization is exact: the apply
   equals a dense solve of the nonsymmetric A (Sec. 3.2: the extension is an
   equivalent system) -- this fixes the elimination algebra (M_ss, P_ss, Q_ss,
@@ -22,6 +26,7 @@ import scipy.sparse as sp
 
 from oracle import hsolver as H
 from oracle import hsolver_lu as HL
+from oracle.dense_emulator import DenseEmulator
 from paper_1611_03189_gb300 import problems as P
 
 
@@ -119,3 +124,17 @@ def test_singular_pivot_is_reported():
     val[rows == int(pb.perm[0])] = 0.0
     with pytest.raises(HL.Singular):
         HL.factor(pb.n, pb.rowptr, pb.col, val, pb.perm, pb.leaf_ptr, 0.1, HL.LORASP)
+
+
+@pytest.mark.parametrize("nbr_dist", [1, 2])
+@pytest.mark.parametrize("eps", [0.1, 0.3])
+@pytest.mark.parametrize("variant", [HL.LORASP, HL.GC_CONSTANT])
+@pytest.mark.parametrize("nx", [8, 12])
+def test_matches_the_literal_extended_system(nx, variant, eps, nbr_dist):
+    pb = P.convdiff2d(nx, 2.0, leaf_size=4)
+    F = _factor(pb, eps, variant, nbr_dist=nbr_dist)
+    E = DenseEmulator(_dense(pb), pb.perm, pb.leaf_ptr, eps, variant, nbr_dist=nbr_dist, lu=True)
+    B = P.rhs(pb.n, 8, nrhs=2)
+    Z = HL.apply(F, B)
+    Ze = np.column_stack([E.solve(B[:, j]) for j in range(2)])
+    assert np.max(np.abs(Z - Ze)) <= 1e-12 * np.max(np.abs(Ze))
