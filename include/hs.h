@@ -134,8 +134,9 @@ typedef struct {
  *     the library enqueued there still uses the block.  It does not
  *     synchronise the whole device (that would break CUDA graph captures
  *     under way in other threads), so work of the handle that the caller
- *     enqueued on other streams must have completed by then: the same rule
- *     as for any stream-ordered allocator.
+ *     enqueued on other streams must have completed by then, and the stream
+ *     of the last factorization must still exist when hs_factor_destroy
+ *     runs: the same rules as for any stream-ordered allocator.
  *   ctx: passed through unchanged.
  * Both are called on the calling thread, inside library calls on the handle
  * (creation, refactor, the solves, which grow their workspaces on first use

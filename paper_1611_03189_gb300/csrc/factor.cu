@@ -64,7 +64,7 @@ void DevAlloc::put(void *p, cudaStream_t st) const noexcept {
   // the library's work that used the block is on `st` (a handle's calls are
   // ordered); a device-wide synchronisation here would also invalidate
   // graph captures other threads have under way on this device
-  cudaStreamSynchronize(st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) cudaGetLastError();   // not left for a later check
   ff(p, device, (void *)st, ctx);
 }
 
