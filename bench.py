@@ -551,6 +551,40 @@ def gemm_arm(args) -> None:
                                                       args.prec, "")}}), flush=True)
 
 
+# The short serving stream of the step benchmark's line: the serving recipe
+# (3D diffusion requests, s = 2, leaves of 64, 20 % factor requests, 1-16
+# right-hand sides, Poisson arrivals), at grid sides 16-32 and 60 requests so
+# that it stays within seconds; `--serve` runs the full recipe (sides 32-96).
+SERVE_LEG = {"requests": 60, "rate": 40.0, "sides": (16, 32), "budget_gb": 16, "slots": 4}
+
+
+def serve_leg(prec: int) -> dict:
+    """Served latency (p50/p99 over all requests, arrival to result) and solve
+    requests/s of the continuous-batching loop on the short stream, with the
+    step benchmark's factor precision and diagonal scaling (every 3D matrix of
+    the recipe then factors)."""
+    from paper_1611_03189_gb300 import serving as S
+
+    c = SERVE_LEG
+    warm = S.poisson_stream(8, 1000.0, seed=12, sides=(c["sides"][0], c["sides"][0]), s=2.0, leaf=64)
+    reqs = S.poisson_stream(c["requests"], c["rate"], seed=11, sides=c["sides"], s=2.0, leaf=64)
+    srv = S.Server(int(c["budget_gb"]) << 30, slots=c["slots"], max_rhs=16, prec=prec, scale=True)
+    srv.run(warm, realtime=False)
+    w0 = time.perf_counter()
+    res = srv.run(reqs, realtime=True)
+    wall = time.perf_counter() - w0
+    summ = S.summarize(res, wall)
+    rr = [float(np.max(r.relres)) for r in res if r.kind == "solve" and r.relres is not None]
+    return {"p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"], "solve_p50_ms": summ["solve_p50_ms"],
+            "solve_p99_ms": summ["solve_p99_ms"], "solve_requests_per_s": summ["solves_per_s"],
+            "rhs_per_s": summ["rhs_per_s"], "requests": summ["requests"], "failed": summ["failed"],
+            "mean_batch": summ["mean_batch"], "max_relres": max(rr) if rr else None, "wall_s": wall,
+            "peak_charged_gb": srv.peak_used / 2**30,
+            "config": {"workload": "serving_diffusion3d_short", "sides": list(c["sides"]), "s": 2.0, "leaf": 64,
+                       "eps": 1e-2, "p_factor": 0.2, "nrhs": [1, 16], "rate_per_s": c["rate"],
+                       "slots": c["slots"], "budget_gb": c["budget_gb"], "diagonal_scaling": True}}
+
+
 def serve_arm(args) -> None:
     """Served latency (p50/p99) and throughput of the continuous-batching loop,
     mixed (FP32) factor against the plain FP64 factor on the same stream."""
@@ -622,6 +656,8 @@ def main():
     ap.add_argument("--rank-f64", action="store_true",
                     help="mixed factors: truncation (Gram, eigen-solve, rank decision) in FP64 (hs_opts.rank_f64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve-leg", action="store_true",
+                    help="skip the short serving stream (served p50/p99) of the step benchmark's line")
     ap.add_argument("--no-f64-arm", action="store_true", help="skip the FP64-factor comparison")
     ap.add_argument("--profile", action="store_true", help="print a phase breakdown to stderr")
     ap.add_argument("--batched", action="store_true", help="run the batched many-problem benchmark")
@@ -847,6 +883,14 @@ def main():
                           "apply_ms": apply_ms, "iters": int(it1.max()), "info": info,
                           "apply_GBps": achieved, "wall_timed_s": wall}), file=sys.stderr, flush=True)
 
+    # ---- served latency on a short stream of the serving recipe ----
+    served = None
+    if world == 1 and not args.no_serve_leg:
+        try:
+            served = serve_leg(prec)
+        except Exception as ex:  # the serving figures must not hide the step's number
+            served = {"error": str(ex)[:300]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -931,6 +975,7 @@ def main():
             "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": 8 * (pb0.nnz + n * args.nrhs),
                     "d2h_bytes_per_step": 8 * n * args.nrhs},
             "fp64_factor": f64,
+            "served": served,
             "gpu_launches": launches,
             "launches_before_timed": l0,
             "clocks": clk,
