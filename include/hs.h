@@ -124,9 +124,11 @@ typedef struct {
  *     bytes on `device`, 256-byte aligned, that work enqueued on `stream` may
  *     use at once (stream-ordered, as the PyTorch caching allocator and
  *     cudaMallocAsync give), or NULL when it cannot; the library then fails
- *     the call with HS_ERR_OOM after returning what that call allocated.  A
- *     misaligned pointer is handed back through free and the call fails with
- *     HS_ERR_INVALID.
+ *     the call with HS_ERR_OOM.  A failed hs_factor_create (or batch create)
+ *     returns every block it took; a handle whose refactor or solve ran out
+ *     keeps what it holds until a later call succeeds or hs_factor_destroy.
+ *     A misaligned pointer is handed back through free and the call fails
+ *     with HS_ERR_INVALID.
  *   free(ptr, device, stream, ctx): takes back a pointer alloc returned.  The
  *     library first synchronises `stream`, the stream of the call that gives
  *     the block back (hs_factor_destroy: the stream of the last
