@@ -105,6 +105,7 @@ class DeviceAllocator:
         self.peak = 0
         self.calls = 0
         self.blocks: dict[int, int] = {}
+        self.errors: list[str] = []   # exceptions the callbacks caught (they cannot raise into C)
         self._mu = threading.Lock()
         self._alloc = ALLOC_FN(self._on_alloc)
         self._free = FREE_FN(self._on_free)
@@ -125,7 +126,8 @@ class DeviceAllocator:
                 self.peak = max(self.peak, self.held)
                 self.calls += 1
             return p
-        except Exception:
+        except Exception as ex:
+            self.errors.append(f"alloc({int(nbytes)}): {ex!r}")
             return None   # the library reports HS_ERR_OOM
 
     def _on_free(self, ptr, device, stream, ctx):
@@ -137,8 +139,8 @@ class DeviceAllocator:
                 nbytes = self.blocks.pop(p)
                 self.held -= nbytes
             torch.cuda.caching_allocator_delete(p)
-        except Exception:
-            pass
+        except Exception as ex:
+            self.errors.append(f"free({int(ptr or 0):#x}): {ex!r}")
 
     def ptr(self) -> int:
         return C.addressof(self.struct)
