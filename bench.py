@@ -555,7 +555,7 @@ def gemm_arm(args) -> None:
 # (3D diffusion requests, s = 2, leaves of 64, 20 % factor requests, 1-16
 # right-hand sides, Poisson arrivals), at grid sides 16-32 and 60 requests so
 # that it stays within seconds; `--serve` runs the full recipe (sides 32-96).
-SERVE_LEG = {"requests": 60, "rate": 40.0, "sides": (16, 32), "budget_gb": 16, "slots": 4}
+SERVE_LEG = {"requests": 60, "rate": 40.0, "sides": (16, 32), "budget_gb": 16, "slots": 4, "limit_s": 120}
 
 
 def serve_leg(prec: int) -> dict:
@@ -570,9 +570,21 @@ def serve_leg(prec: int) -> dict:
     reqs = S.poisson_stream(c["requests"], c["rate"], seed=11, sides=c["sides"], s=2.0, leaf=64)
     srv = S.Server(int(c["budget_gb"]) << 30, slots=c["slots"], max_rhs=16, prec=prec, scale=True)
     srv.run(warm, realtime=False)
+    # bounded: the stream normally takes seconds; a run still going after
+    # c["limit_s"] is reported as such and left to the daemon worker threads
+    box = {}
+
+    def serve():
+        box["res"] = srv.run(reqs, realtime=True)
+
     w0 = time.perf_counter()
-    res = srv.run(reqs, realtime=True)
+    th = threading.Thread(target=serve, daemon=True)
+    th.start()
+    th.join(c["limit_s"])
     wall = time.perf_counter() - w0
+    if "res" not in box:
+        return {"error": f"the serving stream did not finish within {c['limit_s']} s"}
+    res = box["res"]
     summ = S.summarize(res, wall)
     rr = [float(np.max(r.relres)) for r in res if r.kind == "solve" and r.relres is not None]
     return {"p50_ms": summ["p50_ms"], "p99_ms": summ["p99_ms"], "solve_p50_ms": summ["solve_p50_ms"],
