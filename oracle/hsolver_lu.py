@@ -53,6 +53,7 @@ from oracle import hsolver as H
 
 LORASP = H.LORASP
 GC_CONSTANT = H.GC_CONSTANT
+GC_USER = H.GC_USER
 
 
 class Singular(RuntimeError):
@@ -131,9 +132,12 @@ def _leaf_blocks_full(n, rowptr, col, val, perm, leaf_ptr):
     return blocks, adj
 
 
-def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=LORASP, keep_U=False, nbr_dist=1) -> LuFactor:
+def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=LORASP, keep_U=False, nbr_dist=1,
+           phi=None) -> LuFactor:
     """Hierarchical LU factorization (Algorithm 1 with the R16 elimination).
-    variant: LORASP or GC_CONSTANT (right-hand preservation of the constant).
+    variant: LORASP, GC_CONSTANT (right-hand preservation of the constant) or
+    GC_USER (of the caller's vectors phi: an n-vector, or n x p for several,
+    original ordering).
     keep_U: keep each compressed node's basis U and blocks A_sW, A_Ws in its
     record.  nbr_dist: the neighbour rule, 1 (R1) or 2 (R14, as in
     oracle/hsolver.py); only with 2 do compressed super nodes of the
@@ -144,13 +148,14 @@ def factor(n, rowptr, col, val, perm, leaf_ptr, eps, variant=LORASP, keep_U=Fals
     L = int(round(math.log2(nleaf)))
     if 2 ** L != nleaf:
         raise ValueError("number of leaves must be a power of two")
-    if variant not in (LORASP, GC_CONSTANT):
-        raise ValueError("variant must be LORASP or GC_CONSTANT")
+    if variant not in (LORASP, GC_CONSTANT, GC_USER):
+        raise ValueError("variant must be LORASP, GC_CONSTANT or GC_USER")
     blocks, leaf_adj = _leaf_blocks_full(n, rowptr, col, val, perm, leaf_ptr)
-    use_phi = variant == GC_CONSTANT
+    use_phi = variant in (GC_CONSTANT, GC_USER)
+    phi_perm = np.asarray(phi, dtype=np.float64)[perm] if variant == GC_USER else np.ones(n)
     red_size = {i: int(leaf_ptr[i + 1] - leaf_ptr[i]) for i in range(nleaf)}
     red_leaves = {i: (i,) for i in range(nleaf)}
-    red_phi = {i: np.ones(red_size[i]) for i in range(nleaf)}
+    red_phi = {i: phi_perm[leaf_ptr[i]:leaf_ptr[i + 1]].copy() for i in range(nleaf)}
     levels = []
     for lev in range(L, 1, -1):
         nsup = 2 ** (lev - 1)
@@ -265,7 +270,8 @@ def _eliminate(s, nsup, blocks, nbr_of, size, vphi, adjacent, eps, variant, use_
         B = np.hstack([blocks[(s, w)] for w in W] + [blocks[(w, s)].T for w in W]) if m else np.zeros((0, 2 * wtot))
         if use_phi:
             # B @ [phi_W; 0] = A_sW phi_W: the GC candidates of Sec. 6
-            phi_w = np.concatenate([np.concatenate([vphi[w] for w in W]), np.zeros(wtot)])
+            pw = np.concatenate([vphi[w] for w in W])
+            phi_w = np.concatenate([pw, np.zeros((wtot,) + pw.shape[1:])])
             U, margin = H._compress(B, eps, variant, vphi[s], phi_w)
         else:
             U, margin = H._compress(B, eps, variant)

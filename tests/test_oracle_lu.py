@@ -138,3 +138,22 @@ def test_matches_the_literal_extended_system(nx, variant, eps, nbr_dist):
     Z = HL.apply(F, B)
     Ze = np.column_stack([E.solve(B[:, j]) for j in range(2)])
     assert np.max(np.abs(Z - Ze)) <= 1e-12 * np.max(np.abs(Ze))
+
+
+@pytest.mark.parametrize("nbr_dist", [1, 2])
+@pytest.mark.parametrize("eps", [0.1, 0.3])
+def test_gc_user_keeps_the_callers_vectors_on_the_right(eps, nbr_dist):
+    """Sec. 6 with caller-supplied vectors (one, then two): A_H^-1 (A phi) =
+    phi on the nonsymmetric input; the literal extended system agrees."""
+    pb = P.convdiff2d(16, 2.0, leaf_size=4)
+    A = _dense(pb)
+    p1 = P.laplacian_eigvec_2d(16, 16, 1, 2)
+    Phi = np.column_stack([p1, P.laplacian_eigvec_2d(16, 16, 2, 1)])
+    for phi in (p1, Phi):
+        F = _factor(pb, eps, HL.GC_USER, nbr_dist=nbr_dist, phi=phi)
+        assert np.max(np.abs(HL.apply(F, A @ phi) - phi)) <= 1e-12 * np.max(np.abs(phi))
+    E = DenseEmulator(A, pb.perm, pb.leaf_ptr, eps, HL.GC_USER, phi=p1, nbr_dist=nbr_dist, lu=True)
+    F = _factor(pb, eps, HL.GC_USER, nbr_dist=nbr_dist, phi=p1)
+    b = P.rhs(pb.n, 4)
+    zb = E.solve(b)
+    assert np.max(np.abs(HL.apply(F, b) - zb)) <= 1e-12 * np.max(np.abs(zb))
