@@ -171,3 +171,25 @@ def test_rank_f64_option_is_validated_before_any_device_work(lib):
     o.rank_f64 = 2
     assert lib.hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), None, C.byref(h)) == _lib.HS_ERR_INVALID
     assert "rank_f64" in lib.hs_last_error().decode()
+
+
+def test_hook_is_not_called_without_a_device(lib):
+    """With no CUDA device the create fails before any allocation: the hook
+    sees no call and holds nothing."""
+    import ctypes as C
+
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    pb = P.poisson2d(8, leaf_size=4)
+    rp, ci, pe, lp = (np.ascontiguousarray(x, np.int32) for x in (pb.rowptr, pb.col, pb.perm, pb.leaf_ptr))
+    val = np.ascontiguousarray(pb.val)
+    A = _lib.HsCsr(pb.n, pb.nnz, rp.ctypes.data, ci.ctypes.data, val.ctypes.data)
+    cl = _lib.HsClustering(pe.ctypes.data, lp.ctypes.data, len(lp) - 1)
+    hook = _lib.DeviceAllocator()
+    o = _lib.HsOpts(0.1, _lib.HS_GC_CONSTANT, _lib.HS_PREC_F32, None)
+    o.allocator = hook.ptr()
+    h = C.c_void_p()
+    assert lib.hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), None, C.byref(h)) == _lib.HS_ERR_CUDA
+    assert not h.value and hook.calls == 0 and hook.held == 0 and not hook.errors

@@ -3,6 +3,7 @@ import math
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 from paper_1611_03189_gb300 import problems as P
 
@@ -122,3 +123,25 @@ def test_levels_for():
     assert P.levels_for(262144, 16) == 14
     assert P.levels_for(64 ** 3, 64) == 12
     assert math.isclose(2 ** P.levels_for(128 ** 3, 64), 128 ** 3 / 64)
+
+
+@pytest.mark.parametrize("beta,theta", [(0.5, 0.6), (4.0, 0.6), (2.0, 2.5)])
+def test_upwind_convection_diffusion_is_a_nonsymmetric_m_matrix(beta, theta):
+    """convdiff2d: the five-point pattern (structurally symmetric), values of
+    -Laplace + first-order upwind w . grad with w = beta (cos t, sin t):
+    diagonal 4 + |w_x| + |w_y|, the upwind neighbour of each axis -1 - |w_a|,
+    the downwind one -1; rows weakly diagonally dominant, so an M-matrix."""
+    nx = 7
+    pb = P.convdiff2d(nx, beta, theta=theta, leaf_size=4)
+    A = sp.csr_matrix((pb.val, pb.col, pb.rowptr), shape=(pb.n, pb.n)).toarray()
+    pat = A != 0
+    assert (pat == pat.T).all() and np.abs(A - A.T).max() > 0.5 * beta * min(abs(math.cos(theta)), 1)
+    wx, wy = beta * math.cos(theta), beta * math.sin(theta)
+    i = 3 + nx * 3                                   # an interior point
+    assert A[i, i] == pytest.approx(4 + abs(wx) + abs(wy))
+    for w, stride in ((wx, 1), (wy, nx)):
+        up, down = (i - stride, i + stride) if w > 0 else (i + stride, i - stride)
+        assert A[i, up] == pytest.approx(-1 - abs(w))
+        assert A[i, down] == pytest.approx(-1.0)
+    off = np.abs(A).sum(axis=1) - np.abs(np.diag(A))
+    assert (np.diag(A) >= off - 1e-12).all() and (A - np.diag(np.diag(A)) <= 0).all()
