@@ -13,7 +13,8 @@ whole FP64 oracle factorization of the same matrix (about 25 s on one core).
   too and its solution agrees with the FP64 one; the FP64 preconditioner is
   symmetric and positive and keeps the constant vector (Sec. 6).
 
-Collected last, so that a failure here skips no other test.
+Collected after the other parity tests (only the allocation-free apply's
+file comes later), so that a failure here skips none of them.
 """
 import numpy as np
 import pytest
