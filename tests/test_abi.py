@@ -193,3 +193,18 @@ def test_hook_is_not_called_without_a_device(lib):
     h = C.c_void_p()
     assert lib.hs_factor_create(C.byref(A), C.byref(cl), C.byref(o), None, C.byref(h)) == _lib.HS_ERR_CUDA
     assert not h.value and hook.calls == 0 and hook.held == 0 and not hook.errors
+
+
+def test_device_allocator_bookkeeping_without_a_device():
+    """The binding's hook: a request past its limit gets NULL and is not an
+    error; a request the backing allocator cannot serve gets NULL and is kept
+    in `errors`; freeing an unknown pointer is recorded, not raised into C."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    hook = _lib.DeviceAllocator(limit=100)
+    assert hook._on_alloc(200, 0, None, None) is None and not hook.errors and hook.held == 0
+    assert hook._on_alloc(50, 0, None, None) is None and len(hook.errors) == 1   # no CUDA here
+    hook._on_free(0x1234, 0, None, None)
+    assert len(hook.errors) == 2 and hook.held == 0 and hook.calls == 0
